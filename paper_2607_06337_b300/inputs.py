@@ -1,0 +1,554 @@
+"""Seeded synthetic tree forests: the input recipe consumed by both the CUDA step and the oracle.
+
+This module holds none of the step's arithmetic (no kinematics, dynamics, factorisation or
+event logic). It samples tree topologies and rest geometry and writes out the per-body and
+per-apple descriptor values that the step takes as inputs:
+
+* topology: a random-frontier growth (each expansion gives a node U{2,3} children, up to a
+  depth limit and an exact body budget), children placed at a U(20 deg, 60 deg) branch angle
+  and at azimuths phi + i * 137.5 deg, the golden-angle divergence of the L-system (Sec. III,
+  Eq. 1);
+* diameters by the pipe rule with exponent 2 (Sec. III, Eq. 2 with beta = 2):
+  d_b = d_trunk * sqrt(leaves(b) / leaves(root)), which gives d_p^2 = sum d_c^2 exactly;
+* solid-cylinder links of wood density rho (Sec. IV): m = rho pi d^2 l / 4,
+  I_xx = I_yy = m (3 r^2 + l^2) / 12, I_zz = m r^2 / 2, centre of mass at l / 2;
+* joint rest transforms (Sec. IV, Eq. 3): T = (0, 0, l_parent) * q_rel;
+* Euler-Bernoulli stiffness k = E I / l with I = pi r^4 / 4 (Sec. IV-A, Eq. 4);
+* damping kd = 2 zeta sqrt(k J), the inversion of the paper's zeta_eff = c_d sqrt(k) / (2 sqrt(J))
+  (Sec. IV-A), J the subtree's moment of inertia about the joint axes at rest;
+* rupture moment M_max = sigma_r pi r^3 / 4 (Sec. IV-B, Eq. 5);
+* apples on leaf spurs (Sec. IV-C): tether hang point 3 cm below the spur tip, k_s, c_s,
+  detach force, initial position at the rest sag m g / k_s below the hang point;
+* the external pull schedule on apples.
+
+Every value is derived in float64 from a ``numpy.random.Generator(PCG64(seed))`` with
+seed = 1_000_003 * config + world, so both sides receive bit-identical inputs.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+GRAVITY = 9.81
+GOLDEN_ANGLE = math.radians(137.5)
+
+
+# ----------------------------------------------------------------------------------------
+# Model flags (the readings of the paper that are switchable).
+# ----------------------------------------------------------------------------------------
+@dataclass
+class Flags:
+    dt: float = 2e-3
+    alpha_implicit_spring: int = 1   # 1: H += dt^2 K' (implicit position actuator), 0: explicit
+    tether_implicit: int = 1         # 1: tether reaction linearised at the end of the step
+    n_break: int = 5                 # N_b: steps over the rupture moment before a break
+    n_pull: int = 3                  # N_p: steps of pull > f_det before detach
+    n_tension: int = 10              # N_t: steps of tension > gamma f_det before detach
+    gamma_tension: float = 1.2       # tension threshold factor (and reaction clamp factor)
+    clamp_factor: float = 1.2        # reaction clamp F_clamp = clamp_factor * f_det
+    fp64_twig_diam: float = 0.0      # joints thinner than this use float64 pivots (0: none)
+
+
+@dataclass
+class Forest:
+    """Packed-CSR batch of worlds; per-world arrays are indexed world-locally."""
+
+    n_worlds: int
+    body_off: np.ndarray      # int32 [W+1]
+    apple_off: np.ndarray     # int32 [W+1]
+    tip_off: np.ndarray       # int32 [W+1]
+    # per body
+    parent: np.ndarray        # int32 world-local parent, -1 for the root
+    ndof: np.ndarray          # int32 0, 1 or 2 (Cardan x then y')
+    jpos: np.ndarray          # (nb,3) joint origin in the parent frame
+    qrel: np.ndarray          # (nb,4) rest rotation relative to the parent (w,x,y,z)
+    length: np.ndarray        # (nb,)
+    diam: np.ndarray          # (nb,)
+    mass: np.ndarray          # (nb,)
+    com: np.ndarray           # (nb,3) centre of mass in the body frame
+    inertia: np.ndarray       # (nb,3) principal inertia about the com, body axes
+    k: np.ndarray             # (nb,) joint stiffness [N m / rad]
+    kd: np.ndarray            # (nb,) joint damping [N m s / rad]
+    armature: np.ndarray      # (nb,)
+    m_max: np.ndarray         # (nb,) rupture moment [N m]
+    # per apple
+    apple_body: np.ndarray    # int32 world-local body
+    hang_local: np.ndarray    # (na,3) hang point in the body frame
+    attach_local: np.ndarray  # (na,3) stem attach point in the body frame
+    apple_mass: np.ndarray
+    k_s: np.ndarray
+    c_s: np.ndarray
+    f_detach: np.ndarray
+    # per tip (loss / record points)
+    tip_body: np.ndarray      # int32 world-local
+    tip_local: np.ndarray     # (nt,3)
+    # per world
+    gravity: np.ndarray       # (W,3)
+    # initial state
+    q0: np.ndarray = None     # (nv,)
+    qd0: np.ndarray = None
+    apple_x0: np.ndarray = None   # (na,3)
+    apple_v0: np.ndarray = None
+    # external pull schedule: force applied from pull_start (inclusive) to pull_end (exclusive)
+    pull_force: np.ndarray = None  # (na,3)
+    pull_start: np.ndarray = None  # int32 (na,), large = never
+    pull_end: np.ndarray = None    # int32 (na,)
+    # rest geometry in world coordinates (for pins and diagnostics)
+    rest_x: np.ndarray = None      # (nb,3) joint origins
+    rest_R: np.ndarray = None      # (nb,3,3)
+    meta: dict = field(default_factory=dict)
+
+    # --------------------------------------------------------------------------------
+    @property
+    def n_bodies(self) -> int:
+        return int(self.body_off[-1])
+
+    @property
+    def n_apples(self) -> int:
+        return int(self.apple_off[-1])
+
+    @property
+    def n_tips(self) -> int:
+        return int(self.tip_off[-1])
+
+    @property
+    def dof_off(self) -> np.ndarray:
+        per_world = np.add.reduceat(self.ndof.astype(np.int64), self.body_off[:-1]) \
+            if self.n_bodies else np.zeros(self.n_worlds, np.int64)
+        per_world = np.where(np.diff(self.body_off) > 0, per_world, 0)
+        return np.concatenate([[0], np.cumsum(per_world)]).astype(np.int32)
+
+    @property
+    def n_dofs(self) -> int:
+        return int(self.ndof.sum())
+
+    def world_sizes(self):
+        return (np.diff(self.body_off), np.diff(self.dof_off), np.diff(self.apple_off))
+
+    def subset(self, worlds) -> "Forest":
+        """A new forest holding only the listed worlds (in the given order)."""
+        worlds = [int(w) for w in worlds]
+        bo, ao, to, do = self.body_off, self.apple_off, self.tip_off, self.dof_off
+        bsel = np.concatenate([np.arange(bo[w], bo[w + 1]) for w in worlds]).astype(np.int64)
+        asel = np.concatenate([np.arange(ao[w], ao[w + 1]) for w in worlds] + [np.zeros(0, np.int64)]).astype(np.int64)
+        tsel = np.concatenate([np.arange(to[w], to[w + 1]) for w in worlds] + [np.zeros(0, np.int64)]).astype(np.int64)
+        dsel = np.concatenate([np.arange(do[w], do[w + 1]) for w in worlds] + [np.zeros(0, np.int64)]).astype(np.int64)
+
+        def off(o):
+            return np.concatenate([[0], np.cumsum([o[w + 1] - o[w] for w in worlds])]).astype(np.int32)
+
+        def opt(a, sel):
+            return None if a is None else a[sel].copy()
+
+        return Forest(
+            n_worlds=len(worlds), body_off=off(bo), apple_off=off(ao), tip_off=off(to),
+            parent=self.parent[bsel].copy(), ndof=self.ndof[bsel].copy(), jpos=self.jpos[bsel].copy(),
+            qrel=self.qrel[bsel].copy(), length=self.length[bsel].copy(), diam=self.diam[bsel].copy(),
+            mass=self.mass[bsel].copy(), com=self.com[bsel].copy(), inertia=self.inertia[bsel].copy(),
+            k=self.k[bsel].copy(), kd=self.kd[bsel].copy(), armature=self.armature[bsel].copy(),
+            m_max=self.m_max[bsel].copy(), apple_body=self.apple_body[asel].copy(),
+            hang_local=self.hang_local[asel].copy(), attach_local=self.attach_local[asel].copy(),
+            apple_mass=self.apple_mass[asel].copy(), k_s=self.k_s[asel].copy(), c_s=self.c_s[asel].copy(),
+            f_detach=self.f_detach[asel].copy(), tip_body=self.tip_body[tsel].copy(),
+            tip_local=self.tip_local[tsel].copy(), gravity=self.gravity[worlds].copy(),
+            q0=opt(self.q0, dsel), qd0=opt(self.qd0, dsel), apple_x0=opt(self.apple_x0, asel),
+            apple_v0=opt(self.apple_v0, asel), pull_force=opt(self.pull_force, asel),
+            pull_start=opt(self.pull_start, asel), pull_end=opt(self.pull_end, asel),
+            rest_x=opt(self.rest_x, bsel), rest_R=opt(self.rest_R, bsel),
+            meta=dict(self.meta, subset=worlds),
+        )
+
+    def forces_at(self, step: int) -> np.ndarray:
+        """External pull on every apple during simulation step ``step`` (na,3)."""
+        on = (step >= self.pull_start) & (step < self.pull_end)
+        return np.where(on[:, None], self.pull_force, 0.0)
+
+
+# ----------------------------------------------------------------------------------------
+# Quaternion / rotation helpers (input geometry only).
+# ----------------------------------------------------------------------------------------
+def quat_mul(a, b):
+    aw, ax, ay, az = a[..., 0], a[..., 1], a[..., 2], a[..., 3]
+    bw, bx, by, bz = b[..., 0], b[..., 1], b[..., 2], b[..., 3]
+    return np.stack([
+        aw * bw - ax * bx - ay * by - az * bz,
+        aw * bx + ax * bw + ay * bz - az * by,
+        aw * by - ax * bz + ay * bw + az * bx,
+        aw * bz + ax * by - ay * bx + az * bw,
+    ], axis=-1)
+
+
+def quat_to_mat(q):
+    q = q / np.linalg.norm(q, axis=-1, keepdims=True)
+    w, x, y, z = q[..., 0], q[..., 1], q[..., 2], q[..., 3]
+    R = np.empty(q.shape[:-1] + (3, 3))
+    R[..., 0, 0] = 1 - 2 * (y * y + z * z)
+    R[..., 0, 1] = 2 * (x * y - w * z)
+    R[..., 0, 2] = 2 * (x * z + w * y)
+    R[..., 1, 0] = 2 * (x * y + w * z)
+    R[..., 1, 1] = 1 - 2 * (x * x + z * z)
+    R[..., 1, 2] = 2 * (y * z - w * x)
+    R[..., 2, 0] = 2 * (x * z - w * y)
+    R[..., 2, 1] = 2 * (y * z + w * x)
+    R[..., 2, 2] = 1 - 2 * (x * x + y * y)
+    return R
+
+
+def quat_axis_angle(axis, angle):
+    axis = np.asarray(axis, dtype=np.float64)
+    angle = np.asarray(angle, dtype=np.float64)
+    h = 0.5 * angle
+    s = np.sin(h)
+    out = np.zeros(np.broadcast(angle, axis[..., 0]).shape + (4,))
+    out[..., 0] = np.cos(h)
+    out[..., 1:] = axis * s[..., None]
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# Topology growth.
+# ----------------------------------------------------------------------------------------
+def _grow_topology(rng: np.random.Generator, n_b: int, depth_max: int):
+    """Random-frontier growth, returned in breadth-first order.
+
+    Repeatedly a uniformly random unexpanded node of depth < depth_max receives U{2,3}
+    children (truncated at the body budget). If the frontier empties before n_b bodies exist,
+    a random node of depth < depth_max with fewer than 3 children receives one more child.
+    """
+    parent = [-1]
+    depth = [0]
+    nchild = [0]
+    frontier = [0] if depth_max > 0 else []
+    while len(parent) < n_b:
+        if frontier:
+            i = int(rng.integers(len(frontier)))
+            node = frontier[i]
+            frontier[i] = frontier[-1]
+            frontier.pop()
+            c = min(int(rng.integers(2, 4)), n_b - len(parent))
+        else:
+            cands = [j for j in range(len(parent)) if depth[j] < depth_max and 0 < nchild[j] < 3]
+            if not cands:
+                break
+            node = cands[int(rng.integers(len(cands)))]
+            c = 1
+        for _ in range(c):
+            parent.append(node)
+            depth.append(depth[node] + 1)
+            nchild.append(0)
+            nchild[node] += 1
+            if depth[-1] < depth_max:
+                frontier.append(len(parent) - 1)
+    n = len(parent)
+    children = [[] for _ in range(n)]
+    for j in range(1, n):
+        children[parent[j]].append(j)
+    order = [0]
+    head = 0
+    while head < len(order):
+        order.extend(children[order[head]])
+        head += 1
+    new = np.empty(n, np.int64)
+    new[np.asarray(order)] = np.arange(n)
+    par = np.full(n, -1, np.int64)
+    cidx = np.zeros(n, np.int64)
+    for old in range(n):
+        if parent[old] >= 0:
+            par[new[old]] = new[parent[old]]
+    for old_p in range(n):
+        for i, old_c in enumerate(children[old_p]):
+            cidx[new[old_c]] = i
+    dep = np.asarray(depth)[np.asarray(order)]
+    return par, cidx, dep
+
+
+# ----------------------------------------------------------------------------------------
+# Config recipes (the five workloads).
+# ----------------------------------------------------------------------------------------
+@dataclass
+class WorldRecipe:
+    n_bodies: int
+    depth: int
+    n_apples: int
+    pulls: str = "none"           # "none" | "random25" | "fixed5"
+
+
+CONFIG_STEPS = {0: 1000, 1: 1000, 2: 1000, 3: 200, 4: 500}
+
+
+def world_recipe(config: int, w: int, n_worlds: int, rng: np.random.Generator) -> WorldRecipe:
+    if config == 0:
+        return WorldRecipe(64, 5, 8)
+    if config == 1:
+        return WorldRecipe(int(rng.integers(100, 601)), int(rng.integers(6, 9)),
+                           int(rng.integers(20, 121)), "random25")
+    if config == 2:
+        return WorldRecipe(300, 8, 60)
+    if config == 3:
+        return WorldRecipe(200, 8, 30, "fixed5")
+    if config == 4:
+        frac = (w + 0.5) / n_worlds
+        n_a = int(rng.integers(10, 201))
+        if frac < 0.5:
+            return WorldRecipe(50, 6, n_a)
+        if frac < 0.9:
+            return WorldRecipe(400, 8, n_a)
+        return WorldRecipe(2000, 10, n_a)
+    raise ValueError(f"unknown config {config}")
+
+
+CONFIG_WORLDS = {0: 16, 1: 4096, 2: 16384, 3: 1024, 4: 8192}
+
+
+def world_seed(config: int, w: int, sweep: int = 0) -> int:
+    return 1_000_003 * config + w + 10_000_019 * sweep
+
+
+def make_forest(config: int, n_worlds: int | None = None, worlds=None, sweep: int = 0,
+                recipe_override: WorldRecipe | None = None) -> Forest:
+    """Generate the synthetic workload of a config (optionally a subset of its worlds).
+
+    ``worlds`` picks world indices of the full config (the seeds do not change), so a subset
+    holds exactly the same trees as the full batch. ``sweep`` > 0 draws fresh seeds of the
+    same distribution (the world-count sweep).
+    """
+    full = CONFIG_WORLDS[config] if n_worlds is None else n_worlds
+    worlds = list(range(full)) if worlds is None else [int(w) for w in worlds]
+    per = []
+    for w in worlds:
+        rng = np.random.Generator(np.random.PCG64(world_seed(config, w, sweep)))
+        rec = recipe_override or world_recipe(config, w, full, rng)
+        per.append(_make_world(rng, rec))
+    forest = _pack(per)
+    forest.meta.update(config=config, n_worlds_full=full, worlds=worlds, sweep=sweep)
+    return forest
+
+
+def _make_world(rng: np.random.Generator, rec: WorldRecipe) -> dict:
+    par, cidx, dep = _grow_topology(rng, rec.n_bodies, rec.depth)
+    n = len(par)
+    E = rng.uniform(6e9, 10e9)
+    sigma_r = rng.uniform(50e6, 90e6)
+    rho = 700.0
+    zeta = 0.05
+    length = rng.uniform(0.1, 0.3, n)
+    phi = rng.uniform(0.0, 2 * math.pi, n)
+    angle = np.radians(rng.uniform(20.0, 60.0, n))
+    # apples on leaf spurs
+    is_leaf = np.ones(n, bool)
+    is_leaf[par[par >= 0]] = False
+    leaves = np.nonzero(is_leaf)[0]
+    n_a = rec.n_apples
+    if n_a <= len(leaves):
+        abody = rng.choice(leaves, n_a, replace=False)
+    else:
+        abody = rng.choice(leaves, n_a, replace=True)
+    amass = rng.uniform(0.15, 0.25, n_a)
+    fdet = rng.uniform(10.0, 30.0, n_a)
+    pull_force = np.zeros((n_a, 3))
+    pull_start = np.full(n_a, 1 << 30, np.int64)
+    pull_end = np.full(n_a, 1 << 30, np.int64)
+    if rec.pulls == "random25" and n_a > 0:
+        n_pull = int(round(0.25 * n_a))
+        sel = rng.choice(n_a, n_pull, replace=False)
+        mag = rng.uniform(0.0, 60.0, n_pull)
+        d = rng.standard_normal((n_pull, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        pull_force[sel] = d * mag[:, None]
+        pull_start[sel] = rng.integers(0, 501, n_pull)
+    elif rec.pulls == "fixed5" and n_a > 0:
+        pull_force[0] = 5.0 * np.array([1.0, 0.0, -1.0]) / math.sqrt(2.0)
+        pull_start[0] = 0
+    return dict(par=par, cidx=cidx, dep=dep, E=E, sigma_r=sigma_r, rho=rho, zeta=zeta,
+                length=length, phi=phi, angle=angle, abody=abody, amass=amass, fdet=fdet,
+                pull_force=pull_force, pull_start=pull_start, pull_end=pull_end, leaves=leaves)
+
+
+def _pack(per: list) -> Forest:
+    W = len(per)
+    nbs = np.array([len(p["par"]) for p in per], np.int64)
+    nas = np.array([len(p["abody"]) for p in per], np.int64)
+    nts = np.array([len(p["leaves"]) for p in per], np.int64)
+    body_off = np.concatenate([[0], np.cumsum(nbs)]).astype(np.int32)
+    apple_off = np.concatenate([[0], np.cumsum(nas)]).astype(np.int32)
+    tip_off = np.concatenate([[0], np.cumsum(nts)]).astype(np.int32)
+    NB = int(body_off[-1])
+    cat = lambda key: np.concatenate([p[key] for p in per]) if per else np.zeros(0)
+    par = cat("par").astype(np.int64)
+    cidx = cat("cidx").astype(np.int64)
+    dep = cat("dep").astype(np.int64)
+    length = cat("length")
+    phi = cat("phi")
+    angle = cat("angle")
+    wid = np.repeat(np.arange(W), nbs)
+    base = body_off[:-1].astype(np.int64)[wid]
+    gpar = np.where(par >= 0, par + base, -1)
+    E = np.array([p["E"] for p in per])[wid]
+    sig = np.array([p["sigma_r"] for p in per])[wid]
+    rho = np.array([p["rho"] for p in per])[wid]
+    zeta = np.array([p["zeta"] for p in per])[wid]
+
+    # rest rotation relative to the parent: about the parent z by the azimuth, then tilt about x
+    azim = np.zeros(NB)
+    nonroot = gpar >= 0
+    azim[nonroot] = phi[gpar[nonroot]] + cidx[nonroot] * GOLDEN_ANGLE
+    qz = quat_axis_angle(np.array([0.0, 0.0, 1.0]), azim)
+    qx = quat_axis_angle(np.array([1.0, 0.0, 0.0]), angle)
+    qrel = quat_mul(qz, qx)
+    qrel[~nonroot] = np.array([1.0, 0.0, 0.0, 0.0])
+    jpos = np.zeros((NB, 3))
+    jpos[nonroot, 2] = length[gpar[nonroot]]
+
+    # rest world frames, level by level
+    Qw = np.zeros((NB, 4))
+    Xw = np.zeros((NB, 3))
+    maxd = int(dep.max()) if NB else 0
+    for lvl in range(maxd + 1):
+        idx = np.nonzero(dep == lvl)[0]
+        if lvl == 0:
+            Qw[idx] = qrel[idx]
+            Xw[idx] = jpos[idx]
+        else:
+            p = gpar[idx]
+            Qw[idx] = quat_mul(Qw[p], qrel[idx])
+            Xw[idx] = Xw[p] + np.einsum("nij,nj->ni", quat_to_mat(Qw[p]), jpos[idx])
+    Rw = quat_to_mat(Qw)
+
+    # pipe-model diameters from leaf counts
+    leaves_in = np.zeros(NB)
+    is_leaf = np.ones(NB, bool)
+    is_leaf[gpar[nonroot]] = False
+    leaves_in[is_leaf] = 1.0
+    for lvl in range(maxd, 0, -1):
+        idx = np.nonzero(dep == lvl)[0]
+        np.add.at(leaves_in, gpar[idx], leaves_in[idx])
+    root_of = body_off[:-1].astype(np.int64)[wid]
+    diam = 0.06 * np.sqrt(leaves_in / leaves_in[root_of])
+    r = 0.5 * diam
+    mass = rho * math.pi * diam ** 2 * length / 4.0
+    inertia = np.stack([mass * (3 * r ** 2 + length ** 2) / 12.0,
+                        mass * (3 * r ** 2 + length ** 2) / 12.0,
+                        mass * r ** 2 / 2.0], axis=1)
+    com = np.zeros((NB, 3))
+    com[:, 2] = 0.5 * length
+    ndof = np.where(nonroot, 2, 0).astype(np.int32)
+    k = np.where(nonroot, math.pi * E * r ** 4 / (4.0 * length), 0.0)
+    m_max = sig * math.pi * r ** 3 / 4.0
+
+    # subtree moment of inertia about each joint's rest x and y axes (through the joint)
+    comw = Xw + np.einsum("nij,nj->ni", Rw, com)
+    Ic_w = np.einsum("nij,nj,nkj->nik", Rw, inertia, Rw)
+    J = np.zeros((NB, 2))
+    anc = np.arange(NB)
+    for _ in range(maxd + 1):
+        ok = anc >= 0
+        b = anc[ok]
+        c = np.nonzero(ok)[0]
+        for a in range(2):
+            e = Rw[b, :, a]
+            d = comw[c] - Xw[b]
+            cr = np.cross(d, e)
+            val = np.einsum("ni,nij,nj->n", e, Ic_w[c], e) + mass[c] * np.einsum("ni,ni->n", cr, cr)
+            np.add.at(J[:, a], b, val)
+        anc = np.where(ok, gpar[np.maximum(anc, 0)], -1)
+    Jm = J.mean(axis=1)
+    kd = np.where(nonroot, 2.0 * zeta * np.sqrt(k * Jm), 0.0)
+
+    # apples
+    abody = cat("abody").astype(np.int64) if W else np.zeros(0, np.int64)
+    awid = np.repeat(np.arange(W), nas)
+    gab = abody + body_off[:-1].astype(np.int64)[awid]
+    NA = int(apple_off[-1])
+    attach_local = np.zeros((NA, 3))
+    attach_local[:, 2] = length[gab]
+    attach_w = Xw[gab] + np.einsum("nij,nj->ni", Rw[gab], attach_local)
+    hang_w = attach_w - np.array([0.0, 0.0, 0.03])
+    hang_local = np.einsum("nji,nj->ni", Rw[gab], hang_w - Xw[gab])
+    amass = cat("amass")
+    k_s = np.full(NA, 1000.0)
+    c_s = 2.0 * 0.2 * np.sqrt(k_s * amass)
+    x0 = hang_w - (amass * GRAVITY / k_s)[:, None] * np.array([0.0, 0.0, 1.0])
+
+    # tips: the far end of every leaf segment
+    tbody = cat("leaves").astype(np.int64) if W else np.zeros(0, np.int64)
+    twid = np.repeat(np.arange(W), nts)
+    tip_local = np.zeros((len(tbody), 3))
+    tip_local[:, 2] = length[tbody + body_off[:-1].astype(np.int64)[twid]]
+
+    NV = int(ndof.sum())
+    f = Forest(
+        n_worlds=W, body_off=body_off, apple_off=apple_off, tip_off=tip_off,
+        parent=par.astype(np.int32), ndof=ndof, jpos=jpos, qrel=qrel, length=length, diam=diam,
+        mass=mass, com=com, inertia=inertia, k=k, kd=kd, armature=np.zeros(NB), m_max=m_max,
+        apple_body=abody.astype(np.int32), hang_local=hang_local, attach_local=attach_local,
+        apple_mass=amass, k_s=k_s, c_s=c_s, f_detach=cat("fdet"),
+        tip_body=tbody.astype(np.int32), tip_local=tip_local,
+        gravity=np.tile(np.array([0.0, 0.0, -GRAVITY]), (W, 1)),
+        q0=np.zeros(NV), qd0=np.zeros(NV), apple_x0=x0, apple_v0=np.zeros((NA, 3)),
+        pull_force=cat("pull_force").reshape(-1, 3) if W else np.zeros((0, 3)),
+        pull_start=cat("pull_start").astype(np.int32), pull_end=cat("pull_end").astype(np.int32),
+        rest_x=Xw, rest_R=Rw,
+    )
+    f.meta["E"] = np.array([p["E"] for p in per])
+    f.meta["sigma_r"] = np.array([p["sigma_r"] for p in per])
+    return f
+
+
+def from_bodies(bodies: list, apples: list = (), tips: list = (), gravity=(0.0, 0.0, -GRAVITY)) -> Forest:
+    """A one-world forest from explicit body / apple dicts (for hand-built test trees).
+
+    body keys: parent, ndof, jpos, qrel, mass, com, inertia, k, kd, m_max, length, diam, armature
+    apple keys: body, hang_local, attach_local, mass, k_s, c_s, f_detach, x0, v0
+    """
+    nb = len(bodies)
+    g = lambda key, default=0.0: np.array([b.get(key, default) for b in bodies], dtype=np.float64)
+    apples = list(apples)
+    tips = list(tips)
+    na = len(apples)
+    ga = lambda key, default=0.0: np.array([a.get(key, default) for a in apples], dtype=np.float64).reshape(
+        (na,) + np.shape(default))
+    ndof = np.array([b.get("ndof", 2) for b in bodies], np.int32)
+    NV = int(ndof.sum())
+    f = Forest(
+        n_worlds=1, body_off=np.array([0, nb], np.int32), apple_off=np.array([0, na], np.int32),
+        tip_off=np.array([0, len(tips)], np.int32),
+        parent=np.array([b["parent"] for b in bodies], np.int32), ndof=ndof,
+        jpos=g("jpos", (0.0, 0.0, 0.0)).reshape(nb, 3),
+        qrel=g("qrel", (1.0, 0.0, 0.0, 0.0)).reshape(nb, 4),
+        length=g("length", 0.0), diam=g("diam", 0.0), mass=g("mass"),
+        com=g("com", (0.0, 0.0, 0.0)).reshape(nb, 3), inertia=g("inertia", (0.0, 0.0, 0.0)).reshape(nb, 3),
+        k=g("k"), kd=g("kd"), armature=g("armature"), m_max=g("m_max", 1e30),
+        apple_body=np.array([a["body"] for a in apples], np.int32),
+        hang_local=ga("hang_local", (0.0, 0.0, 0.0)), attach_local=ga("attach_local", (0.0, 0.0, 0.0)),
+        apple_mass=ga("mass"), k_s=ga("k_s"), c_s=ga("c_s"), f_detach=ga("f_detach", 1e30),
+        tip_body=np.array([t[0] for t in tips], np.int32),
+        tip_local=np.array([t[1] for t in tips], np.float64).reshape(len(tips), 3),
+        gravity=np.array([gravity], np.float64),
+        q0=np.zeros(NV), qd0=np.zeros(NV),
+        apple_x0=ga("x0", (0.0, 0.0, 0.0)), apple_v0=ga("v0", (0.0, 0.0, 0.0)),
+        pull_force=np.zeros((na, 3)), pull_start=np.full(na, 1 << 30, np.int32),
+        pull_end=np.full(na, 1 << 30, np.int32),
+    )
+    return f
+
+
+def cylinder(diam: float, length: float, rho: float):
+    """Mass, com and principal inertia of a solid cylinder link along +z."""
+    r = 0.5 * diam
+    m = rho * math.pi * diam ** 2 * length / 4.0
+    return m, (0.0, 0.0, 0.5 * length), (m * (3 * r * r + length * length) / 12.0,
+                                          m * (3 * r * r + length * length) / 12.0, m * r * r / 2.0)
+
+
+def beam_stiffness(E: float, diam: float, length: float) -> float:
+    """Euler-Bernoulli rotational stiffness k = E I / l, I = pi r^4 / 4 (Sec. IV-A, Eq. 4)."""
+    r = 0.5 * diam
+    return math.pi * E * r ** 4 / (4.0 * length)
+
+
+def rupture_moment(sigma_r: float, diam: float) -> float:
+    """Modulus of rupture times section modulus, M_max = sigma_r pi r^3 / 4 (Sec. IV-B, Eq. 5)."""
+    r = 0.5 * diam
+    return sigma_r * math.pi * r ** 3 / 4.0
