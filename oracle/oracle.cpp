@@ -276,8 +276,9 @@ template <class T> inline V3<T> jac_point(const World& W, const Kin<T>& K, int i
   return cross(K.e[i], p - K.x[W.dof_body[i]]);
 }
 
-// Per-step apple forces on the tree (Sec. IV-C). The stem force on the apple is
-// f_s = -k_s (x - x_hang) (Eq. 6); the spur receives f_react = -(f_s - m g z) = -(f_s + m g_vec),
+// Per-step apple forces on the tree (Sec. IV-C). An attached apple's state is its stem
+// elongation u = x - x_hang (so du/dt = v - v_hang); the stem force on it is
+// f_s = -k_s u (Eq. 6); the spur receives f_react = -(f_s - m g z) = -(f_s + m g_vec),
 // clamped in norm (Eq. 7). Reading of the time integration: the tether is stepped by backward
 // Euler in its elongation for the apple and the tree together. The apple's new velocity is
 // v' = a + beta v_hang' with a = (m v + dt (f_ext + m g + f_s)) / D, beta = dt^2 k_s / D,
@@ -308,9 +309,10 @@ void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax,
     V3<T> h = K.x[b] + mvec(K.R[b], dv<T>(W.hang + 3 * a));
     A.hang[a] = h;
     A.vhang[a] = K.vx[b] + cross(K.w[b], h - K.x[b]);
-    V3<T> xa = {ax[3 * a], ax[3 * a + 1], ax[3 * a + 2]};
+    // attached: the state holds the stem elongation u = x - x_hang; detached: the position
+    V3<T> ua = {ax[3 * a], ax[3 * a + 1], ax[3 * a + 2]};
     V3<T> va = {av[3 * a], av[3 * a + 1], av[3 * a + 2]};
-    V3<T> fs = T(-W.ks[a]) * (xa - h);
+    V3<T> fs = T(-W.ks[a]) * ua;
     A.tension[a] = sqrt(dot(fs, fs));
     V3<T> fe = dv<T>(fext + 3 * a);
     A.pull[a] = sqrt(dot(fe, fe));
@@ -318,6 +320,7 @@ void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax,
     T m = T(W.am[a]);
     if (detached[a]) {
       A.fapp[a] = zero;
+      A.tension[a] = T(0);
       A.a[a] = va + T(dt) * (g + (T(1) / m) * fe);
       continue;
     }
@@ -480,6 +483,12 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
   const double dt = fl.dt;
   Kin<T> K;
   kinematics(W, s.q.data(), s.qd.data(), K);
+  for (int a = 0; a < W.na; ++a) {
+    if (s.detached[a] != 2) continue;  // detached last step: elongation -> world position
+    V3<T> h = K.x[W.abody[a]] + mvec(K.R[W.abody[a]], dv<T>(W.hang + 3 * a));
+    s.ax[3 * a] += h.x; s.ax[3 * a + 1] += h.y; s.ax[3 * a + 2] += h.z;
+    s.detached[a] = 1;
+  }
   AppleLoads<T> A;
   apple_loads(W, fl, K, s.ax.data(), s.av.data(), s.detached.data(), fext, A);
   std::vector<T> M, c;
@@ -507,10 +516,12 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
   std::vector<int> newly(W.na, 0);
   for (int a = 0; a < W.na; ++a) {
     V3<T> vh = {T(0), T(0), T(0)};
-    for (int i : W.chain[W.abody[a]]) vh = vh + s.qd[i] * jac_point(W, K, i, A.hang[a]);
+    if (!s.detached[a])
+      for (int i : W.chain[W.abody[a]]) vh = vh + s.qd[i] * jac_point(W, K, i, A.hang[a]);
     V3<T> vn = A.a[a] + A.beta[a] * vh;
     V3<T> xa = {s.ax[3 * a], s.ax[3 * a + 1], s.ax[3 * a + 2]};
-    V3<T> xn = xa + T(dt) * vn;
+    // attached: u' = u + dt (v' - v_hang'); detached: x' = x + dt v'
+    V3<T> xn = s.detached[a] ? xa + T(dt) * vn : xa + T(dt) * (vn - vh);
     s.ax[3 * a] = xn.x; s.ax[3 * a + 1] = xn.y; s.ax[3 * a + 2] = xn.z;
     s.av[3 * a] = vn.x; s.av[3 * a + 1] = vn.y; s.av[3 * a + 2] = vn.z;
     if (s.detached[a]) continue;
@@ -526,8 +537,10 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
     s.tcnt[a] = Tn > thr_t ? s.tcnt[a] + 1 : 0;
     if (s.pcnt[a] >= fl.n_pull || s.tcnt[a] >= fl.n_tension) newly[a] = 1;
   }
+  // a newly detached apple keeps its elongation until the next step's kinematics turn it
+  // into a world position (flag 2)
   for (int a = 0; a < W.na; ++a)
-    if (newly[a]) { s.detached[a] = 1; s.detach_step[a] = step; }
+    if (newly[a]) { s.detached[a] = 2; s.detach_step[a] = step; }
   // rupture test on the updated angles: k |theta| > sigma_r pi r^3 / 4 for N_b steps (Eq. 5)
   for (int b = 0; b < W.nb; ++b) {
     if (W.ndof[b] == 0 || s.broken[b]) continue;

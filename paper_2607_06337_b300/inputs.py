@@ -18,7 +18,8 @@ per-apple descriptor values that the step takes as inputs:
   (Sec. IV-A), J the subtree's moment of inertia about the joint axes at rest;
 * rupture moment M_max = sigma_r pi r^3 / 4 (Sec. IV-B, Eq. 5);
 * apples on leaf spurs (Sec. IV-C): tether hang point 3 cm below the spur tip, k_s, c_s,
-  detach force, initial position at the rest sag m g / k_s below the hang point;
+  detach force, initial stem elongation at the rest sag m g / k_s (an attached apple's state
+  is its elongation x - x_hang; a detached apple's is its world position);
 * the external pull schedule on apples.
 
 Every value is derived in float64 from a ``numpy.random.Generator(PCG64(seed))`` with
@@ -89,7 +90,7 @@ class Forest:
     # initial state
     q0: np.ndarray = None     # (nv,)
     qd0: np.ndarray = None
-    apple_x0: np.ndarray = None   # (na,3)
+    apple_x0: np.ndarray = None   # (na,3) stem elongation x - x_hang while attached
     apple_v0: np.ndarray = None
     # external pull schedule: force applied from pull_start (inclusive) to pull_end (exclusive)
     pull_force: np.ndarray = None  # (na,3)
@@ -361,6 +362,10 @@ def _make_world(rng: np.random.Generator, rec: WorldRecipe) -> dict:
     elif rec.pulls == "fixed5" and n_a > 0:
         pull_force[0] = 5.0 * np.array([1.0, 0.0, -1.0]) / math.sqrt(2.0)
         pull_start[0] = 0
+    # apples sorted by their body (stable), so each body's apples form a contiguous range
+    order = np.argsort(abody, kind="stable")
+    abody, amass, fdet = abody[order], amass[order], fdet[order]
+    pull_force, pull_start, pull_end = pull_force[order], pull_start[order], pull_end[order]
     return dict(par=par, cidx=cidx, dep=dep, E=E, sigma_r=sigma_r, rho=rho, zeta=zeta,
                 length=length, phi=phi, angle=angle, abody=abody, amass=amass, fdet=fdet,
                 pull_force=pull_force, pull_start=pull_start, pull_end=pull_end, leaves=leaves)
@@ -469,7 +474,8 @@ def _pack(per: list) -> Forest:
     amass = cat("amass")
     k_s = np.full(NA, 1000.0)
     c_s = 2.0 * 0.2 * np.sqrt(k_s * amass)
-    x0 = hang_w - (amass * GRAVITY / k_s)[:, None] * np.array([0.0, 0.0, 1.0])
+    # attached apples carry their stem elongation u = x - x_hang; at rest it is the sag m g / k_s
+    x0 = -(amass * GRAVITY / k_s)[:, None] * np.array([0.0, 0.0, 1.0])
 
     # tips: the far end of every leaf segment
     tbody = cat("leaves").astype(np.int64) if W else np.zeros(0, np.int64)

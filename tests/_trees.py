@@ -28,7 +28,7 @@ def chain(n, seg_len, diam, rho, E, kd, ndof=1, apple=None, gravity=(0.0, 0.0, 0
     apples = []
     if apple is not None:
         apples.append(dict(body=n - 1, hang_local=(0.0, 0.0, seg_len), attach_local=(0.0, 0.0, seg_len),
-                           x0=(0.0, 0.0, n * seg_len), v0=(0.0, 0.0, 0.0), **apple))
+                           x0=(0.0, 0.0, 0.0), v0=(0.0, 0.0, 0.0), **apple))
     f = I.from_bodies(bodies, apples=apples, tips=[(n - 1, (0.0, 0.0, seg_len))], gravity=gravity)
     return f, k
 

@@ -46,10 +46,7 @@ def test_apples_at_rest_sag_do_not_load_a_tree_at_rest(implicit):
     fl = I.Flags(tether_implicit=implicit)
     bare.q0 = sb.q.copy()
     f.q0 = sb.q.copy()
-    ev = O.evaluate(f, fl, 0, sb.q, np.zeros(f.n_dofs))
-    b = f.apple_body
-    hang = ev["x"][b] + np.einsum("nij,nj->ni", ev["R"][b], f.hang_local)
-    f.apple_x0 = hang - (f.apple_mass * I.GRAVITY / f.k_s)[:, None] * np.array([0.0, 0.0, 1.0])
+    f.apple_x0 = -(f.apple_mass * I.GRAVITY / f.k_s)[:, None] * np.array([0.0, 0.0, 1.0])
     _, ra = O.rollout(f, fl, 300, record_q=True, n_threads=1)
     _, rb = O.rollout(bare, fl, 300, record_q=True, n_threads=1)
     np.testing.assert_allclose(ra["q"], rb["q"], atol=1e-12 * np.abs(rb["q"]).max())
@@ -75,6 +72,7 @@ def test_implicit_tether_keeps_the_bare_tree_rest_pose():
 # ------------------------------------------------------------------------------------------
 def _one_apple_on_a_post(m=0.2, k_s=1000.0, c_s=None, x0=(0, 0, 0), v0=(0, 0, 0), f_detach=1e9,
                          gravity=(0.0, 0.0, -I.GRAVITY)):
+    """An apple on a welded post; x0 is its stem elongation (its world position if detached)."""
     c_s = 2 * 0.2 * math.sqrt(k_s * m) if c_s is None else c_s
     mm, com, inertia = I.cylinder(0.05, 1.0, 700.0)
     post = dict(parent=-1, ndof=0, mass=mm, com=com, inertia=inertia, length=1.0, diam=0.05)
@@ -89,14 +87,14 @@ def test_attached_apple_is_the_implicit_damped_oscillator():
     m, k, c = 0.2, 1000.0, 0.8
     sag = m * I.GRAVITY / k
     y0 = -0.004
-    f = _one_apple_on_a_post(m=m, k_s=k, c_s=c, x0=(0.0, 0.0, 1.0 - sag + y0))
+    f = _one_apple_on_a_post(m=m, k_s=k, c_s=c, x0=(0.0, 0.0, -sag + y0))
     fl = I.Flags()
     n = 300
     ys = []
     st = None
     for t in range(n):
         st, _ = O.rollout(f, fl, 1, state=st, step0=t, n_threads=1)
-        ys.append(st.ax[0, 2] - (1.0 - sag))
+        ys.append(st.ax[0, 2] + sag)  # the state is the elongation below the hang point
     # the apple recurrence is the single-hinge one with J -> m, kd -> c, k -> k, alpha = 1
     ref = _closed_form_hinge(m, k, c, fl.dt, 1, y0, 0.0, n)
     np.testing.assert_allclose(ys, ref, atol=1e-13)
@@ -126,7 +124,7 @@ def test_pull_path_detach_step_from_ramp():
     fdet, rate = 14.3, 0.05
     m = 0.2
     sag = m * I.GRAVITY / 1000.0
-    f = _one_apple_on_a_post(m=m, x0=(0.0, 0.0, 1.0 - sag), f_detach=fdet)
+    f = _one_apple_on_a_post(m=m, x0=(0.0, 0.0, -sag), f_detach=fdet)
     fl = I.Flags()
     st = None
     for t in range(400):
@@ -146,7 +144,7 @@ def test_tension_path_detach_step_from_oscillator():
     fdet = 10.0
     sag = m * I.GRAVITY / k
     vkick = -1.25
-    f = _one_apple_on_a_post(m=m, k_s=k, c_s=c, x0=(0.0, 0.0, 1.0 - sag), v0=(0.0, 0.0, vkick), f_detach=fdet)
+    f = _one_apple_on_a_post(m=m, k_s=k, c_s=c, x0=(0.0, 0.0, -sag), v0=(0.0, 0.0, vkick), f_detach=fdet)
     fl = I.Flags()
     st, _ = O.rollout(f, fl, 200, n_threads=1)
     # closed form of the displacement from the sag equilibrium, state before each step
@@ -186,7 +184,7 @@ def test_quasi_static_break_step():
     body = dict(parent=-1, ndof=1, mass=m, com=com, inertia=inertia, k=k, kd=kd, m_max=mmax, length=l, diam=d)
     ma, ks = 0.002, 1000.0
     apple = dict(body=0, hang_local=(0.0, 0.0, l), attach_local=(0.0, 0.0, l), mass=ma, k_s=ks,
-                 c_s=2 * math.sqrt(ks * ma), f_detach=1e9, x0=(0.0, 0.0, l))
+                 c_s=2 * math.sqrt(ks * ma), f_detach=1e9, x0=(0.0, 0.0, 0.0))
     f = I.from_bodies([body], apples=[apple], gravity=(0.0, 0.0, 0.0))
     fl = I.Flags(clamp_factor=1e9)
     rate = 0.02 * mmax / l / fl.dt / 100  # reaches the break load in about 5000 steps
