@@ -1,0 +1,365 @@
+"""Benchmark of the batched compliant-tree step (body-steps/s) on 1..N GPUs.
+
+Default workload: 4096 uneven trees (100-600 segment bodies, L-system depth 6-8, 20-120
+apples, random 0-60 N pulls on a quarter of the apples), 1000 simulation steps per bench step,
+run as one persistent, size-sorted, graph-captured, autotuned launch. A bench step is one
+rollout of the whole hot path over the batch. Under torchrun every rank simulates its own
+4096 freshly seeded trees (weak scaling; no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "body-steps/s fwd & fwd+adjoint, batched vs plain on B300; frac of FP32/HBM roofline"
+UNIT = "body-steps/s"
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=1)
+    p.add_argument("--worlds", type=int, default=None, help="override the number of worlds")
+    p.add_argument("--sim-steps", type=int, default=1000)
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--plain-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    # 148 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.file.flush()
+        return False
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.file.name):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        finally:
+            os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("step_kernel.cu", "orchard_dev.h"):
+        h.update(open(os.path.join(ROOT, "paper_2607_06337_b300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(n_worlds):
+    """DRAM bytes per launch of the rollout kernel from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    per_world_step = d.get("dram_bytes_per_world_step")
+    return None if per_world_step is None else per_world_step
+
+
+def cpu_baseline(forest, flags, seconds):
+    """The oracle as it stands on the host cores, on a bounded sample of the same workload."""
+    import oracle as O
+    from paper_2607_06337_b300 import costs
+    cores = os.cpu_count() or 1
+    # stratified sample of worlds (by size), a few steps; grown until it takes ~`seconds`
+    sizes = np.diff(forest.body_off)
+    order = np.argsort(sizes)
+    n_w = min(max(cores, 8), forest.n_worlds)
+    pick = order[np.linspace(0, len(order) - 1, n_w).astype(int)]
+    sub = forest.subset(pick)
+    steps = 5
+    while True:
+        t = time.perf_counter()
+        O.rollout(sub, flags, steps, n_threads=cores)
+        dt = time.perf_counter() - t
+        if dt > seconds / 4 or steps >= 400:
+            break
+        steps = min(400, int(steps * max(2.0, seconds / 4 / max(dt, 1e-3))))
+    if dt < seconds / 2 and steps < 400:
+        steps = min(400, int(steps * seconds / max(dt, 1e-3)))
+        t = time.perf_counter()
+        O.rollout(sub, flags, steps, n_threads=cores)
+        dt = time.perf_counter() - t
+    bs = costs.body_count(sub) * steps / dt
+    return {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_w} worlds stratified by size x {steps} steps (FP64, {cores} threads), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    import oracle as O
+    nw = args.worlds or I.CONFIG_WORLDS[args.config]
+    fl = I.Flags()
+    cores = os.cpu_count() or 1
+    sample_w = min(max(cores, 8), nw)
+    forest = I.make_forest(args.config, n_worlds=nw, worlds=np.linspace(0, nw - 1, sample_w).astype(int))
+    steps = 10
+    for _ in range(args.warmup):
+        O.rollout(forest, fl, 2, n_threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        O.rollout(forest, fl, steps, n_threads=cores)
+        times.append(time.perf_counter() - t)
+    per = statistics.mean(times)
+    value = costs.body_count(forest) * steps / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"config {args.config} sample: {sample_w} of {nw} worlds x {steps} steps"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample_w} worlds x {steps} steps per bench step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+
+    nw = args.worlds or I.CONFIG_WORLDS[args.config]
+    fl = I.Flags()
+    forest = I.make_forest(args.config, n_worlds=nw, sweep=rank)
+    S = args.sim_steps
+    sim = B.Simulator(forest, fl, device=dev)
+    stream = torch.cuda.current_stream()
+    # pinned host copies of the initial state (inputs of every e2e step)
+    host_in = [torch.from_numpy(np.ascontiguousarray(a, np.float32).reshape(-1)).pin_memory()
+               for a in (forest.q0, forest.qd0, forest.apple_x0, forest.apple_v0)]
+    dev_in = [h.to(dev) for h in host_in]
+
+    def reset():
+        sim.reset_from_device(*dev_in)
+
+    if not args.no_autotune:
+        reset()
+        sim.autotune(n_steps=20)
+    scheds = [dict(threads_per_world=s.threads_per_world, worlds_per_block=s.worlds_per_block,
+                   global_workspace=s.global_workspace) for s in sim.schedules()]
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        reset()
+        sim.rollout(S)
+    torch.cuda.synchronize()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    B.launch_count(reset=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)  # evict the L2 between timed rollouts
+            reset()
+            e0[k].record(stream)
+            sim.rollout(S)
+            e1[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    launches = B.launch_count()
+    ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    ms_mean = statistics.mean(ms)
+    total_ms = sum(ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = sim.status.cpu().numpy()
+    bodies = costs.body_count(forest)
+    value = ws * bodies * S * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs in, final state and status out
+    host_q = torch.empty(forest.n_dofs, dtype=torch.float32).pin_memory()
+    host_st = torch.empty(forest.n_worlds, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for k in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for h, d in zip(host_in, dev_in):
+            d.copy_(h, non_blocking=True)
+        reset()
+        sim.rollout(S)
+        host_q.copy_(sim.q, non_blocking=True)
+        host_st.copy_(sim.status, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t)
+    h2d = sum(h.numel() * 4 for h in host_in)
+    d2h = host_q.numel() * 4 + host_st.numel() * 4
+    e2e_value = ws * bodies * S / statistics.mean(e2e_times)
+
+    # the plain form: one launch per world per step, no graph, no autotune
+    plain = None
+    if not args.no_plain:
+        reset()
+        torch.cuda.synchronize()
+        ps = args.plain_steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.rollout_plain(ps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        plain_value = bodies * ps / (pms / 1e3)
+        plain = {"value": plain_value, "unit": UNIT, "steps": ps, "launches": forest.n_worlds * ps,
+                 "batched_over_plain": value / ws / plain_value}
+
+    flops = costs.flops_per_step(forest) * S
+    pk, src = peaks()
+    clocks = clk.summary()
+    sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
+    peak_tf = fp32_peak_tflops(sm_mhz)
+    achieved_tf = flops / (ms_mean / 1e3) / 1e12
+    hbm_bytes = costs.hbm_bytes_per_rollout(forest)
+    traffic_per_ws = measured_traffic(nw)
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf,
+                "traffic": None if traffic_per_ws is None else traffic_per_ws * nw * S,
+                "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "flops_per_launch": flops}
+    hbm = {"achieved": hbm_bytes / (ms_mean / 1e3) / 1e9, "peak": float(pk.get("hbm_gbs", 6400.0)),
+           "unit": "GB/s", "bytes_per_launch": hbm_bytes}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(forest, fl, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"config {args.config}: {nw} uneven trees, {S} steps per bench step",
+                       "worlds_per_gpu": nw, "sim_steps": S, "bodies_per_gpu": bodies,
+                       "segment_bodies": forest.n_bodies, "apples": forest.n_apples, "dofs": forest.n_dofs,
+                       "l2": "flushed (256 MB write) before every timed rollout",
+                       "schedules": scheds},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "hbm": hbm,
+            "cpu_baseline": cpu,
+            "plain": plain,
+            "fwd_adj": None,
+            "clocks": clocks,
+            "frozen_worlds": int((status & 1).sum()),
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

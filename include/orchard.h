@@ -1,0 +1,243 @@
+/*
+ * orchard.h — C ABI of the batched compliant-tree step (liborchard.so, sm_103a).
+ *
+ * The library steps many independent worlds, each a kinematic tree of branch-segment bodies
+ * on compliant bending joints carrying apples on stem tethers (arxiv 2607.06337, Sec. IV):
+ *   - joint rest transform T = (0,0,l_parent) * q_rel, stress-free at rest (Sec. IV, Eq. 3);
+ *   - each compliant joint has up to two bending DOFs (Cardan x then y' of a twist-locked D6)
+ *     with torsional spring-damper tau = -k theta - kd omega, k = E I / l (Sec. IV-A, Eq. 4);
+ *   - rupture when k |theta| > sigma_r pi r^3 / 4 for N_b consecutive steps, after which the
+ *     joint is a free hinge (its gain rows zeroed in place, Sec. IV-B, Eq. 5);
+ *   - apples as 3-DOF free bodies on tethers f = -k_s (x - x_hang) - c_s v whose elastic part
+ *     minus the static weight reacts on the spur, clamped (Sec. IV-C, Eqs. 6-7); they detach
+ *     on a sustained pull above f_detach or a longer tension above gamma f_detach (Sec. IV-C).
+ * One step: forward kinematics, RNE bias forces, CRBA mass matrix, H = M + dt D' (+ dt^2 K'),
+ * tree-sparse LDL^T factor and solve, semi-implicit update, apple update, break and detach
+ * tests. Worlds may differ in topology, size and every parameter (Sec. IV-D generalised).
+ *
+ * Conventions
+ *   - Every call is asynchronous on the given CUDA stream (passed as void*, a cudaStream_t;
+ *     NULL is the legacy default stream), except ot_tree_model_upload's host validation and
+ *     the *_bytes size queries, which are host-only.
+ *   - The library never allocates device memory: every device buffer is allocated by the
+ *     caller (for example as a torch tensor) and passed as a pointer with its byte size.
+ *     Handles (ot_model, ot_state) are small host structs freed by *_release.
+ *   - Errors are negative ot_status codes; a call that fails leaves its outputs unchanged
+ *     unless stated. Per-world runtime faults (a non-finite state) do not fail a call: they
+ *     set bits in the per-world status word and freeze that world.
+ *   - Floating point on the device is FP32 (FMA contraction allowed). Descriptors are FP64
+ *     on the host and converted at upload.
+ *
+ * Layout of a descriptor (packed CSR over worlds; indices inside a world are world-local):
+ *   bodies of world w are [body_off[w], body_off[w+1]); they must be in breadth-first order:
+ *   parent[0] = -1 for the root, 0 <= parent[i] < i and parent non-decreasing for i >= 1
+ *   (so each level and each body's children are contiguous). Apples of world w are
+ *   [apple_off[w], apple_off[w+1]) sorted by apple_body (non-decreasing). Tips likewise.
+ *   The DOFs of a world are numbered body by body, each body's ndof DOFs consecutively.
+ */
+#ifndef ORCHARD_H
+#define ORCHARD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int ot_status;
+#define OT_OK 0
+#define OT_EINVAL (-1)      /* null pointer, size mismatch, buffer too small, bad flag value */
+#define OT_ETOPO (-2)       /* not breadth-first, parent out of range, ndof not in {0,1,2} */
+#define OT_ENONFINITE (-3)  /* a descriptor value is NaN or infinite, or a mass is not > 0 */
+#define OT_ECAPACITY (-4)   /* a world exceeds a hard limit (32767 DOFs, 255 children/apples per body) */
+#define OT_ECUDA (-5)       /* a CUDA call failed; ot_last_cuda_error() gives its code */
+#define OT_ESTATE (-6)      /* call out of order (e.g. backward without a recorded forward) */
+
+/* per-world status bits (ot_world_status) */
+#define OT_WORLD_NONFINITE 1u   /* the state became non-finite; the world is frozen */
+
+typedef struct ot_model ot_model; /* opaque: device layout of the uploaded forest (no ownership) */
+typedef struct ot_state ot_state; /* opaque: view over a caller-owned device state buffer */
+
+/* Host description of a forest (FP64). Per-body arrays have body_off[n_worlds] entries,
+ * per-apple arrays apple_off[n_worlds], per-tip arrays tip_off[n_worlds]. */
+typedef struct ot_tree_desc {
+  int32_t n_worlds;
+  const int32_t* body_off;   /* [W+1] */
+  const int32_t* apple_off;  /* [W+1] */
+  const int32_t* tip_off;    /* [W+1] */
+  const int32_t* parent;     /* world-local parent, -1 for the root */
+  const int32_t* ndof;       /* 0 (welded), 1 (hinge about x) or 2 (x then y') */
+  const double* jpos;        /* [nb][3] joint origin in the parent body frame */
+  const double* qrel;        /* [nb][4] rest rotation relative to the parent (w,x,y,z) */
+  const double* com;         /* [nb][3] centre of mass in the body frame */
+  const double* mass;        /* [nb] > 0 */
+  const double* inertia;     /* [nb][3] principal moments about the com along body axes */
+  const double* k;           /* [nb] joint stiffness (N m / rad), shared by the joint's DOFs */
+  const double* kd;          /* [nb] joint damping (N m s / rad) */
+  const double* armature;    /* [nb] added to the diagonal of H for the joint's DOFs */
+  const double* m_max;       /* [nb] rupture moment (N m) */
+  const int32_t* apple_body; /* [na] world-local body */
+  const double* hang_local;  /* [na][3] tether hang point in the body frame */
+  const double* apple_mass;  /* [na] > 0 */
+  const double* k_s;         /* [na] tether stiffness */
+  const double* c_s;         /* [na] tether damping (acts on the apple only) */
+  const double* f_detach;    /* [na] detach force */
+  const int32_t* tip_body;   /* [nt] world-local body of each recorded tip point */
+  const double* tip_local;   /* [nt][3] tip point in the body frame */
+  const double* gravity;     /* [W][3] */
+} ot_tree_desc;
+
+/* Switchable readings of the model (defaults in parentheses). */
+typedef struct ot_model_flags {
+  int32_t alpha_implicit_spring; /* (1) 1: springs implicit, H += dt^2 K'; 0: explicit */
+  int32_t tether_implicit;       /* (1) 1: tether by coupled backward Euler; 0: explicit reaction */
+  int32_t n_break;               /* (5) N_b */
+  int32_t n_pull;                /* (3) N_p */
+  int32_t n_tension;             /* (10) N_t */
+  double gamma_tension;          /* (1.2) tension threshold factor */
+  double clamp_factor;           /* (1.2) reaction clamp = clamp_factor * f_detach */
+} ot_model_flags;
+
+/* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */
+typedef struct ot_schedule {
+  int32_t threads_per_world;   /* 32, 64, 128 or 256 */
+  int32_t worlds_per_block;    /* groups of threads_per_world threads in one block */
+  int32_t blocks;              /* persistent grid size (0: enough for one wave) */
+  int32_t global_workspace;    /* 1: per-step temporaries in the state's scratch area */
+} ot_schedule;
+
+/* ---------------------------------------------------------------------------------------
+ * Model upload.
+ * ot_model_bytes: device bytes the packed model needs. Host only.
+ * ot_tree_model_upload: validates desc (topology, finiteness, limits), packs it to FP32 SoA,
+ *   sorts worlds by estimated cost into the work queue, splits them into size classes and
+ *   copies everything into dev_buf (caller-allocated, >= ot_model_bytes, 256-byte aligned)
+ *   on `stream`. The host call returns after the copies are enqueued; dev_buf must stay alive
+ *   while the model is used. On error *out is untouched and nothing is copied.
+ * ot_model_release: frees the host handle only. */
+ot_status ot_model_bytes(const ot_tree_desc* desc, size_t* bytes);
+ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* flags, void* dev_buf,
+                               size_t dev_bytes, void* stream, ot_model** out);
+void ot_model_release(ot_model* model);
+
+/* Counts of the uploaded forest: worlds, bodies, DOFs, apples, tips, size classes. */
+ot_status ot_model_counts(const ot_model* model, int64_t counts[6]);
+
+/* ---------------------------------------------------------------------------------------
+ * World state: q, qd (FP32 per DOF), apple positions and velocities, break and detach flags,
+ * counters and event steps, per-world status, plus the scratch area used by classes whose
+ * per-step temporaries do not fit in shared memory.
+ * ot_state_bytes: bytes of the state buffer (host only).
+ * ot_world_state_alloc: makes a state view over dev_buf (>= ot_state_bytes, 256-byte aligned).
+ *   Nothing is initialised: call ot_state_set. */
+ot_status ot_state_bytes(const ot_model* model, size_t* bytes);
+ot_status ot_world_state_alloc(const ot_model* model, void* dev_buf, size_t bytes, ot_state** out);
+void ot_state_release(ot_state* state);
+
+/* Initial state. q, qd: [n_dofs]; apple_x, apple_v: [n_apples][3]; FP32; host pointers when
+ * on_device == 0 (copied synchronously), device pointers otherwise (copied on `stream`).
+ * NULL q / qd / apple_v mean zeros; apple_x must be given when the forest has apples.
+ * Clears all flags, counters, event steps and status words. */
+typedef struct ot_state_init {
+  const float* q;
+  const float* qd;
+  const float* apple_x;
+  const float* apple_v;
+  int32_t on_device;
+} ot_state_init;
+ot_status ot_state_set(ot_state* state, const ot_state_init* init, void* stream);
+
+/* Device views of the state arrays (for reading results; same layout as ot_state_init plus
+ * int32 per-body broken flag and break step, per-apple detached flag and detach step,
+ * uint32 per-world status). Any pointer may be NULL. */
+typedef struct ot_state_view {
+  float* q;
+  float* qd;
+  float* apple_x;       /* [na][3] */
+  float* apple_v;       /* [na][3] */
+  int32_t* broken;      /* [nb] */
+  int32_t* break_step;  /* [nb] step index of the break, -1 if none */
+  int32_t* detached;    /* [na] */
+  int32_t* detach_step; /* [na] */
+  uint32_t* status;     /* [W] OT_WORLD_* bits */
+} ot_state_view;
+ot_status ot_state_get_view(const ot_state* state, ot_state_view* view);
+
+/* Per-world status words copied (device to device) into dev_status[W] on `stream`. */
+ot_status ot_world_status(const ot_state* state, uint32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Pull schedule on apples (device pointers): force [na][3] applied during steps
+ * start[a] <= step < end[a] (absolute step indices). NULL force means no pulls. */
+typedef struct ot_force_schedule {
+  const float* force;
+  const int32_t* start;
+  const int32_t* end;
+} ot_force_schedule;
+
+/* One step of every world (step index `step` for the pull schedule and the event records),
+ * with ext_force [na][3] (device, may be NULL) added to the scheduled pulls. */
+ot_status ot_step(ot_model* model, ot_state* state, const float* ext_force, const ot_force_schedule* pulls,
+                  int32_t step, double dt, void* stream);
+
+/* Record of a rollout (device buffers, any may be NULL):
+ *   tips: [n_steps][n_tips][3] tip positions after every step;
+ *   ckpt: state snapshots taken before steps 0, ckpt_every, 2 ckpt_every, ...
+ *         (ot_ckpt_bytes gives the size for n_steps). */
+typedef struct ot_record {
+  float* tips;
+  void* ckpt;
+  size_t ckpt_bytes;
+  int32_t ckpt_every;
+} ot_record;
+ot_status ot_ckpt_bytes(const ot_model* model, int32_t n_steps, int32_t ckpt_every, size_t* bytes);
+
+/* n_steps steps from absolute step index step0: one persistent launch per size class over a
+ * cost-sorted work queue (each group of threads pops a world and runs all its steps),
+ * captured once into a CUDA graph per (n_steps, record layout) and replayed. */
+ot_status ot_rollout(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
+                     const ot_force_schedule* pulls, const ot_record* record, void* stream);
+
+/* The plain form: one kernel launch per world per step (no queue, no graph, no autotune). */
+ot_status ot_rollout_plain(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
+                           const ot_force_schedule* pulls, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Adjoint of a recorded rollout with the break and detach masks frozen as recorded.
+ * Loss L = sum_t sum_tips |p_t - target_t|^2 / (n_steps * n_tips_of_world) per world; the
+ * caller gives dL/dtips [n_steps][n_tips][3] (device). Gradients (device, accumulated into,
+ * any may be NULL): dk, dkd [nb] per joint; dq0, dqd0 [n_dofs] of the initial state.
+ * Segments between checkpoints are recomputed forward, then swept in reverse. */
+typedef struct ot_grads {
+  float* dk;
+  float* dkd;
+  float* dq0;
+  float* dqd0;
+} ot_grads;
+ot_status ot_rollout_backward(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
+                              const ot_force_schedule* pulls, const ot_record* record, const float* dL_dtips,
+                              ot_grads* grads, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Schedules and autotuning. Size classes are formed at upload from the world sizes.
+ * ot_get_schedule / ot_set_schedule read or replace the schedule of class c.
+ * ot_autotune times every candidate schedule of every class on `n_steps` steps of the current
+ * state (restored afterwards) with CUDA events on `stream` and keeps the fastest. */
+ot_status ot_get_schedule(const ot_model* model, int32_t size_class, ot_schedule* sched);
+ot_status ot_set_schedule(ot_model* model, int32_t size_class, const ot_schedule* sched);
+ot_status ot_autotune(ot_model* model, ot_state* state, int32_t n_steps, double dt, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Diagnostics. */
+const char* ot_status_string(ot_status s);
+int32_t ot_last_cuda_error(void);
+/* Number of kernel launches the library issued since the last reset (graph replays count
+ * each kernel node once). */
+int64_t ot_launch_count(int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ORCHARD_H */

@@ -1,0 +1,933 @@
+// Host side of liborchard: the C ABI declared in include/orchard.h.
+//
+// Upload validates a forest descriptor, packs it into FP32 SoA arrays in the caller's device
+// buffer, builds the breadth-first level boundaries, the DOF ancestor rows (the storage of the
+// tree-sparse mass matrix), the per-world work queue sorted by size class and cost, and the
+// default launch schedule of every class. Rollouts launch one persistent kernel per class,
+// captured once into a CUDA graph and replayed. No device memory is ever allocated here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/orchard.h"
+#include "orchard_dev.h"
+
+using namespace orchard;
+
+namespace {
+
+std::atomic<int> g_last_cuda{0};
+std::atomic<long long> g_launches{0};
+
+ot_status cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  return OT_ECUDA;
+}
+#define OT_CUDA(call)                           \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t kSmemLimit = 226 * 1024;  // dynamic shared memory per block (opt-in 227 KB less static)
+
+// Bump allocator over a byte range; in sizing mode it only counts.
+struct Carver {
+  size_t off = 0;
+  template <class T> size_t take(size_t count) {
+    size_t o = off;
+    off = align_up(off + count * sizeof(T));
+    return o;
+  }
+};
+
+struct ClassInfo {
+  int q_begin, q_end;
+  int max_nb, max_nv, max_nm, max_na;
+  long long ws_floats;
+  ot_schedule sched;
+  size_t scratch_off;  // byte offset of this class's scratch in the state buffer (global workspace)
+  int scratch_slots;
+};
+
+// Host-side packed forest (FP32 device layout) plus bookkeeping.
+struct Packed {
+  int W = 0, NB = 0, NV = 0, NA = 0, NT = 0;
+  long long NM = 0;
+  std::vector<int> body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl;
+  std::vector<int4> bi;
+  std::vector<float4> bp0, bp1, bp2, bp3, bp4;
+  std::vector<int4> dinfo;
+  std::vector<unsigned short> anc;
+  std::vector<float4> ap0, ap1;
+  std::vector<int> apple_body, tip_body;
+  std::vector<float4> tip_local, gravity;
+  std::vector<int> queue;
+  std::vector<unsigned char> pairs;
+  std::vector<ClassInfo> classes;
+};
+
+bool finite_all(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+int num_sms() {
+  int dev = 0, n = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 148;
+}
+
+ot_schedule default_schedule(long long ws_floats, int max_nb) {
+  ot_schedule s{};
+  const size_t ws_bytes = (size_t)ws_floats * 4;
+  if (ws_bytes > kSmemLimit) {
+    s.threads_per_world = 256;
+    s.worlds_per_block = 1;
+    s.global_workspace = 1;
+  } else {
+    s.threads_per_world = max_nb <= 96 ? 32 : (max_nb <= 400 ? 64 : 128);
+    int g = (int)std::max<size_t>(1, std::min<size_t>(kSmemLimit / std::max<size_t>(ws_bytes, 1), 16));
+    if (s.threads_per_world > 32) g = std::min(g, 15);
+    g = std::min(g, 512 / s.threads_per_world);
+    s.worlds_per_block = std::max(1, std::min(g, s.threads_per_world == 32 ? 4 : 2));
+    s.global_workspace = 0;
+  }
+  s.blocks = 0;
+  return s;
+}
+
+ot_status pack(const ot_tree_desc* d, Packed& P) {
+  if (!d || d->n_worlds < 0 || !d->body_off || !d->apple_off || !d->tip_off) return OT_EINVAL;
+  const int W = d->n_worlds;
+  P.W = W;
+  for (int w = 0; w < W; ++w)
+    if (d->body_off[w + 1] < d->body_off[w] || d->apple_off[w + 1] < d->apple_off[w] ||
+        d->tip_off[w + 1] < d->tip_off[w])
+      return OT_EINVAL;
+  if (d->body_off[0] != 0 || d->apple_off[0] != 0 || d->tip_off[0] != 0) return OT_EINVAL;
+  const int NB = d->body_off[W], NA = d->apple_off[W], NT = d->tip_off[W];
+  if (NB > 0 && (!d->parent || !d->ndof || !d->jpos || !d->qrel || !d->com || !d->mass || !d->inertia || !d->k ||
+                 !d->kd || !d->armature || !d->m_max))
+    return OT_EINVAL;
+  if (NA > 0 && (!d->apple_body || !d->hang_local || !d->apple_mass || !d->k_s || !d->c_s || !d->f_detach))
+    return OT_EINVAL;
+  if (NT > 0 && (!d->tip_body || !d->tip_local)) return OT_EINVAL;
+  if (W > 0 && !d->gravity) return OT_EINVAL;
+  // finiteness
+  if (NB > 0 && !(finite_all(d->jpos, 3 * (size_t)NB) && finite_all(d->qrel, 4 * (size_t)NB) &&
+                  finite_all(d->com, 3 * (size_t)NB) && finite_all(d->mass, NB) &&
+                  finite_all(d->inertia, 3 * (size_t)NB) && finite_all(d->k, NB) && finite_all(d->kd, NB) &&
+                  finite_all(d->armature, NB) && finite_all(d->m_max, NB)))
+    return OT_ENONFINITE;
+  if (NA > 0 && !(finite_all(d->hang_local, 3 * (size_t)NA) && finite_all(d->apple_mass, NA) &&
+                  finite_all(d->k_s, NA) && finite_all(d->c_s, NA) && finite_all(d->f_detach, NA)))
+    return OT_ENONFINITE;
+  if (NT > 0 && !finite_all(d->tip_local, 3 * (size_t)NT)) return OT_ENONFINITE;
+  if (W > 0 && !finite_all(d->gravity, 3 * (size_t)W)) return OT_ENONFINITE;
+  for (int b = 0; b < NB; ++b)
+    if (!(d->mass[b] > 0)) return OT_ENONFINITE;
+  for (int a = 0; a < NA; ++a)
+    if (!(d->apple_mass[a] > 0)) return OT_ENONFINITE;
+
+  P.body_off.assign(d->body_off, d->body_off + W + 1);
+  P.apple_off.assign(d->apple_off, d->apple_off + W + 1);
+  P.tip_off.assign(d->tip_off, d->tip_off + W + 1);
+  P.dof_off.assign(W + 1, 0);
+  P.m_off.assign(W + 1, 0);
+  P.lvl_off.assign(W + 1, 0);
+  P.bi.resize(NB);
+  P.bp0.resize(NB); P.bp1.resize(NB); P.bp2.resize(NB); P.bp3.resize(NB); P.bp4.resize(NB);
+  P.lvl.clear();
+  P.dinfo.clear();
+  P.anc.clear();
+  std::vector<long long> ws(W);
+  std::vector<double> cost(W);
+  std::vector<int> wnb(W), wnv(W), wnm(W), wna(W);
+  for (int w = 0; w < W; ++w) {
+    const int b0 = d->body_off[w], nb = d->body_off[w + 1] - b0;
+    const int a0 = d->apple_off[w], na = d->apple_off[w + 1] - a0;
+    const int t0 = d->tip_off[w], nt = d->tip_off[w + 1] - t0;
+    // topology: breadth-first order
+    std::vector<int> depth(nb, 0), dof0(nb, 0), nd(nb, 0), cfirst(nb, -1), ccount(nb, 0);
+    int nv = 0;
+    for (int b = 0; b < nb; ++b) {
+      const int p = d->parent[b0 + b];
+      const int k = d->ndof[b0 + b];
+      if (k < 0 || k > 2) return OT_ETOPO;
+      if (b == 0) {
+        if (p != -1) return OT_ETOPO;
+      } else {
+        if (p < 0 || p >= b) return OT_ETOPO;
+        if (p < d->parent[b0 + b - 1]) return OT_ETOPO;  // not breadth-first
+        depth[b] = depth[p] + 1;
+        if (ccount[p] == 0) cfirst[p] = b;
+        ++ccount[p];
+        if (ccount[p] > 255) return OT_ECAPACITY;
+      }
+      dof0[b] = nv;
+      nd[b] = k;
+      nv += k;
+    }
+    if (nv > 32767) return OT_ECAPACITY;
+    // apples sorted by body
+    std::vector<int> afirst(nb, 0), acount(nb, 0);
+    for (int a = 0; a < na; ++a) {
+      const int b = d->apple_body[a0 + a];
+      if (b < 0 || b >= nb) return OT_ETOPO;
+      if (a > 0 && b < d->apple_body[a0 + a - 1]) return OT_ETOPO;
+      if (acount[b] == 0) afirst[b] = a;
+      if (++acount[b] > 255) return OT_ECAPACITY;
+    }
+    for (int t = 0; t < nt; ++t) {
+      const int b = d->tip_body[t0 + t];
+      if (b < 0 || b >= nb) return OT_ETOPO;
+    }
+    // levels
+    P.lvl_off[w] = (int)P.lvl.size();
+    if (nb > 0) {
+      P.lvl.push_back(0);
+      for (int b = 1; b < nb; ++b)
+        if (depth[b] != depth[b - 1]) P.lvl.push_back(b);
+      P.lvl.push_back(nb);
+    }
+    // DOF tree: parent DOF, depth, ancestor rows
+    std::vector<int> dpar(nv), ddep(nv), dbody(nv);
+    std::vector<int> last_dof(nb, -1);  // deepest DOF on the path root..b
+    for (int b = 0; b < nb; ++b) {
+      const int p = d->parent[b0 + b];
+      int prev = p >= 0 ? last_dof[p] : -1;
+      for (int j = 0; j < nd[b]; ++j) {
+        const int i = dof0[b] + j;
+        dpar[i] = prev;
+        ddep[i] = prev >= 0 ? ddep[prev] + 1 : 0;
+        if (ddep[i] > kMaxDepth) return OT_ECAPACITY;
+        dbody[i] = b;
+        prev = i;
+      }
+      last_dof[b] = prev;
+    }
+    P.dof_off[w] = (int)P.dinfo.size();
+    P.m_off[w] = (int)P.anc.size();
+    int row = 0;
+    for (int i = 0; i < nv; ++i) {
+      P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], 0));
+      int j = i;
+      for (int c = 0; c <= ddep[i]; ++c) {
+        P.anc.push_back((unsigned short)j);
+        j = dpar[j];
+      }
+      row += ddep[i] + 1;
+    }
+    const int nm = row;
+    for (int b = 0; b < nb; ++b) {
+      const int gb = b0 + b;
+      if (cfirst[b] < 0) cfirst[b] = 0;
+      P.bi[gb] = make_int4(d->parent[gb], dof0[b] | (nd[b] << 28), cfirst[b] | (ccount[b] << 24),
+                           afirst[b] | (acount[b] << 24));
+      P.bp0[gb] = make_float4((float)d->jpos[3 * gb], (float)d->jpos[3 * gb + 1], (float)d->jpos[3 * gb + 2],
+                              (float)d->mass[gb]);
+      P.bp1[gb] = make_float4((float)d->qrel[4 * gb], (float)d->qrel[4 * gb + 1], (float)d->qrel[4 * gb + 2],
+                              (float)d->qrel[4 * gb + 3]);
+      P.bp2[gb] = make_float4((float)d->com[3 * gb], (float)d->com[3 * gb + 1], (float)d->com[3 * gb + 2],
+                              (float)d->inertia[3 * gb]);
+      P.bp3[gb] = make_float4((float)d->inertia[3 * gb + 1], (float)d->inertia[3 * gb + 2], (float)d->k[gb],
+                              (float)d->kd[gb]);
+      P.bp4[gb] = make_float4((float)d->armature[gb], (float)d->m_max[gb], 0.f, 0.f);
+    }
+    wnb[w] = nb; wnv[w] = nv; wnm[w] = nm; wna[w] = na;
+    ws[w] = WsLayout::make(nb, nv, nm, na).total;
+    long long sumsq = 0;
+    for (int i = 0; i < nv; ++i) sumsq += (long long)ddep[i] * (ddep[i] + 1) / 2;
+    cost[w] = 700.0 * nb + 12.0 * nm + 2.0 * sumsq + 80.0 * na;
+  }
+  P.dof_off[W] = (int)P.dinfo.size();
+  P.m_off[W] = (int)P.anc.size();
+  P.lvl_off[W] = (int)P.lvl.size();
+  P.NB = NB; P.NA = NA; P.NT = NT; P.NV = P.dof_off[W]; P.NM = P.m_off[W];
+  if (P.NM > 0x7fffffffLL) return OT_ECAPACITY;
+  // apples, tips, gravity
+  P.ap0.resize(NA); P.ap1.resize(NA); P.apple_body.resize(NA);
+  for (int a = 0; a < NA; ++a) {
+    P.ap0[a] = make_float4((float)d->hang_local[3 * a], (float)d->hang_local[3 * a + 1],
+                           (float)d->hang_local[3 * a + 2], (float)d->apple_mass[a]);
+    P.ap1[a] = make_float4((float)d->k_s[a], (float)d->c_s[a], (float)d->f_detach[a], 0.f);
+    P.apple_body[a] = d->apple_body[a];
+  }
+  P.tip_body.resize(NT); P.tip_local.resize(NT);
+  for (int t = 0; t < NT; ++t) {
+    P.tip_body[t] = d->tip_body[t];
+    P.tip_local[t] = make_float4((float)d->tip_local[3 * t], (float)d->tip_local[3 * t + 1],
+                                 (float)d->tip_local[3 * t + 2], 0.f);
+  }
+  P.gravity.resize(W);
+  for (int w = 0; w < W; ++w)
+    P.gravity[w] = make_float4((float)d->gravity[3 * w], (float)d->gravity[3 * w + 1], (float)d->gravity[3 * w + 2], 0.f);
+  // size classes by workspace bytes, queue sorted by (class, cost descending)
+  const long long bounds[] = {6 * 1024, 14 * 1024, 28 * 1024, 55 * 1024, (long long)kSmemLimit / 4};
+  const int n_bounds = 5;
+  std::vector<int> cls(W);
+  for (int w = 0; w < W; ++w) {
+    int c = 0;
+    while (c < n_bounds && ws[w] > bounds[c]) ++c;
+    cls[w] = c;
+  }
+  std::vector<int> order(W);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    if (cls[x] != cls[y]) return cls[x] < cls[y];
+    return cost[x] > cost[y];
+  });
+  P.queue = order;
+  P.classes.clear();
+  for (int i = 0; i < W;) {
+    int j = i;
+    ClassInfo ci{};
+    ci.q_begin = i;
+    while (j < W && cls[order[j]] == cls[order[i]]) {
+      const int w = order[j];
+      ci.max_nb = std::max(ci.max_nb, wnb[w]);
+      ci.max_nv = std::max(ci.max_nv, wnv[w]);
+      ci.max_nm = std::max(ci.max_nm, wnm[w]);
+      ci.max_na = std::max(ci.max_na, wna[w]);
+      ci.ws_floats = std::max(ci.ws_floats, ws[w]);
+      ++j;
+    }
+    ci.q_end = j;
+    ci.ws_floats = (ci.ws_floats + 3) / 4 * 4;
+    ci.sched = default_schedule(ci.ws_floats, ci.max_nb);
+    P.classes.push_back(ci);
+    i = j;
+  }
+  // (c, c2) pair table
+  P.pairs.clear();
+  for (int c2 = 1; c2 <= kMaxDepth + 1; ++c2)
+    for (int c = 1; c <= c2; ++c) {
+      P.pairs.push_back((unsigned char)c);
+      P.pairs.push_back((unsigned char)c2);
+    }
+  return OT_OK;
+}
+
+template <class T> size_t vbytes(const std::vector<T>& v) { return v.size() * sizeof(T); }
+
+}  // namespace
+
+struct ot_model {
+  Packed P;
+  DevModel dev{};
+  ot_model_flags flags{};
+  int n_sm = 148;
+  cudaStream_t capture_stream = nullptr;
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  ~ot_model() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+  }
+};
+
+struct ot_state {
+  const ot_model* model = nullptr;
+  DevState dev{};
+  int* q_counters = nullptr;  // one per class
+  char* base = nullptr;
+  size_t bytes = 0;
+};
+
+namespace {
+
+// Layout of the packed model in the device buffer.
+struct ModelLayout {
+  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, ap0,
+      ap1, apple_body, tip_body, tip_local, gravity, queue, pairs, total;
+};
+
+ModelLayout model_layout(const Packed& P) {
+  Carver c;
+  ModelLayout L;
+  const size_t W1 = P.W + 1;
+  L.body_off = c.take<int>(W1); L.dof_off = c.take<int>(W1); L.apple_off = c.take<int>(W1);
+  L.tip_off = c.take<int>(W1); L.m_off = c.take<int>(W1); L.lvl_off = c.take<int>(W1);
+  L.lvl = c.take<int>(P.lvl.size());
+  L.bi = c.take<int4>(P.NB);
+  L.bp0 = c.take<float4>(P.NB); L.bp1 = c.take<float4>(P.NB); L.bp2 = c.take<float4>(P.NB);
+  L.bp3 = c.take<float4>(P.NB); L.bp4 = c.take<float4>(P.NB);
+  L.dinfo = c.take<int4>(P.NV);
+  L.anc = c.take<unsigned short>(P.NM);
+  L.ap0 = c.take<float4>(P.NA); L.ap1 = c.take<float4>(P.NA);
+  L.apple_body = c.take<int>(P.NA);
+  L.tip_body = c.take<int>(P.NT);
+  L.tip_local = c.take<float4>(P.NT);
+  L.gravity = c.take<float4>(P.W);
+  L.queue = c.take<int>(P.W);
+  L.pairs = c.take<unsigned char>(P.pairs.size());
+  L.total = c.off;
+  return L;
+}
+
+struct StateLayout {
+  size_t q, qd, ax, av, broken, bcnt, break_step, detached, pcnt, tcnt, detach_step, status, counters, total;
+  std::vector<size_t> scratch;
+};
+
+StateLayout state_layout(const ot_model* m) {
+  const Packed& P = m->P;
+  Carver c;
+  StateLayout L;
+  L.q = c.take<float>(P.NV); L.qd = c.take<float>(P.NV);
+  L.ax = c.take<float>(3 * (size_t)P.NA); L.av = c.take<float>(3 * (size_t)P.NA);
+  L.broken = c.take<int>(P.NB); L.bcnt = c.take<int>(P.NB); L.break_step = c.take<int>(P.NB);
+  L.detached = c.take<int>(P.NA); L.pcnt = c.take<int>(P.NA); L.tcnt = c.take<int>(P.NA);
+  L.detach_step = c.take<int>(P.NA);
+  L.status = c.take<unsigned>(P.W);
+  L.counters = c.take<int>(std::max<size_t>(P.classes.size(), 1) + 1);
+  // scratch: every class may run with global workspace; size for the slots its schedule can
+  // have (global classes: 4 blocks of one world per SM; the plain form uses slot 0)
+  size_t total_scratch_floats = 0;
+  for (const ClassInfo& ci : P.classes) {
+    size_t slots = ci.sched.global_workspace ? (size_t)m->n_sm * 4 : 1;
+    total_scratch_floats += slots * (size_t)ci.ws_floats;
+  }
+  L.scratch.push_back(c.take<float>(total_scratch_floats));
+  L.total = c.off;
+  return L;
+}
+
+size_t class_scratch_offset(const ot_model* m, int k, int* slots) {
+  size_t off = 0;
+  for (int i = 0; i < (int)m->P.classes.size(); ++i) {
+    const ClassInfo& ci = m->P.classes[i];
+    size_t s = ci.sched.global_workspace ? (size_t)m->n_sm * 4 : 1;
+    if (i == k) {
+      *slots = (int)s;
+      return off;
+    }
+    off += s * (size_t)ci.ws_floats;
+  }
+  *slots = 0;
+  return off;
+}
+
+long long ckpt_words(const Packed& P) { return 2LL * P.NV + 6LL * P.NA + 2LL * P.NB + 3LL * P.NA; }
+
+StepArgs base_args(const ot_model* m, double dt) {
+  StepArgs a{};
+  a.dt = (float)dt;
+  a.alpha = m->flags.alpha_implicit_spring;
+  a.tether_implicit = m->flags.tether_implicit;
+  a.n_break = m->flags.n_break;
+  a.n_pull = m->flags.n_pull;
+  a.n_tension = m->flags.n_tension;
+  a.gamma = (float)m->flags.gamma_tension;
+  a.clamp = (float)m->flags.clamp_factor;
+  a.single_world = -1;
+  a.NB = m->P.NB; a.NV = m->P.NV; a.NA = m->P.NA;
+  a.n_tips_total = m->P.NT;
+  a.ckpt_words = ckpt_words(m->P);
+  return a;
+}
+
+// Launch shape of a class under its current schedule (kernel attributes are set here, never
+// inside a stream capture).
+struct Shape {
+  size_t smem;
+  int blocks;
+  size_t scratch_off;
+};
+
+ot_status class_shape(ot_model* m, int k, Shape* out) {
+  ClassInfo& ci = m->P.classes[k];
+  const ot_schedule& sc = ci.sched;
+  const size_t smem = sc.global_workspace ? 0 : (size_t)ci.ws_floats * 4 * sc.worlds_per_block;
+  int bps = 0;
+  OT_CUDA(kernel_attributes(sc.threads_per_world, sc.worlds_per_block, std::max<size_t>(smem, 1), &bps));
+  if (bps < 1) return OT_ECAPACITY;
+  int slots = 0;
+  out->scratch_off = class_scratch_offset(m, k, &slots);
+  int blocks = sc.blocks > 0 ? sc.blocks : bps * m->n_sm;
+  const int worlds = ci.q_end - ci.q_begin;
+  blocks = std::min(blocks, (worlds + sc.worlds_per_block - 1) / sc.worlds_per_block);
+  if (sc.global_workspace) blocks = std::min(blocks, slots / std::max(1, sc.worlds_per_block));
+  out->smem = smem;
+  out->blocks = blocks;
+  return OT_OK;
+}
+
+// Launch one class of worlds (persistent, queue-driven) with a precomputed shape.
+ot_status launch_class_shaped(ot_model* m, ot_state* s, int k, StepArgs a, const Shape& sh, cudaStream_t st) {
+  ClassInfo& ci = m->P.classes[k];
+  const ot_schedule& sc = ci.sched;
+  if (sh.blocks < 1) return OT_OK;
+  a.q_begin = ci.q_begin;
+  a.q_end = ci.q_end;
+  a.q_counter = s->q_counters + k;
+  a.ws_floats = ci.ws_floats;
+  a.global_ws = sc.global_workspace;
+  DevState ds = s->dev;
+  ds.scratch = s->dev.scratch + sh.scratch_off;
+  OT_CUDA(cudaMemsetAsync(a.q_counter, 0, sizeof(int), st));
+  launch_rollout(sc.threads_per_world, sc.worlds_per_block, sh.blocks, sh.smem, st, m->dev, ds, a);
+  OT_CUDA(cudaGetLastError());
+  g_launches += 1;
+  return OT_OK;
+}
+
+ot_status launch_class(ot_model* m, ot_state* s, int k, StepArgs a, cudaStream_t st) {
+  Shape sh;
+  ot_status r = class_shape(m, k, &sh);
+  if (r != OT_OK) return r;
+  return launch_class_shaped(m, s, k, a, sh, st);
+}
+
+ot_status fill_pulls(StepArgs& a, const ot_force_schedule* pulls) {
+  if (pulls && pulls->force) {
+    if (!pulls->start || !pulls->end) return OT_EINVAL;
+    a.pull_force = pulls->force;
+    a.pull_start = pulls->start;
+    a.pull_end = pulls->end;
+  }
+  return OT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ot_status_string(ot_status s) {
+  switch (s) {
+    case OT_OK: return "ok";
+    case OT_EINVAL: return "invalid argument";
+    case OT_ETOPO: return "bad topology (bodies must be breadth-first, apples sorted by body)";
+    case OT_ENONFINITE: return "non-finite or non-positive descriptor value";
+    case OT_ECAPACITY: return "world exceeds a hard limit";
+    case OT_ECUDA: return "CUDA error";
+    case OT_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+int32_t ot_last_cuda_error(void) { return g_last_cuda.load(); }
+
+int64_t ot_launch_count(int32_t reset) {
+  if (reset) return g_launches.exchange(0);
+  return g_launches.load();
+}
+
+ot_status ot_model_bytes(const ot_tree_desc* desc, size_t* bytes) {
+  if (!bytes) return OT_EINVAL;
+  Packed P;
+  ot_status st = pack(desc, P);
+  if (st != OT_OK) return st;
+  *bytes = model_layout(P).total;
+  return OT_OK;
+}
+
+ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* flags, void* dev_buf,
+                               size_t dev_bytes, void* stream, ot_model** out) {
+  if (!out || !dev_buf || !flags) return OT_EINVAL;
+  if (((uintptr_t)dev_buf) % kAlign) return OT_EINVAL;
+  if (flags->n_break < 1 || flags->n_pull < 1 || flags->n_tension < 1 ||
+      (flags->alpha_implicit_spring != 0 && flags->alpha_implicit_spring != 1) ||
+      (flags->tether_implicit != 0 && flags->tether_implicit != 1) || !(flags->clamp_factor > 0) ||
+      !(flags->gamma_tension > 0))
+    return OT_EINVAL;
+  ot_model* m = new ot_model();
+  ot_status st = pack(desc, m->P);
+  if (st != OT_OK) {
+    delete m;
+    return st;
+  }
+  const Packed& P = m->P;
+  ModelLayout L = model_layout(P);
+  if (dev_bytes < L.total) {
+    delete m;
+    return OT_EINVAL;
+  }
+  m->flags = *flags;
+  m->n_sm = num_sms();
+  std::vector<char> host(L.total, 0);
+  auto put = [&](size_t off, const void* src, size_t n) {
+    if (n) std::memcpy(host.data() + off, src, n);
+  };
+  put(L.body_off, P.body_off.data(), vbytes(P.body_off));
+  put(L.dof_off, P.dof_off.data(), vbytes(P.dof_off));
+  put(L.apple_off, P.apple_off.data(), vbytes(P.apple_off));
+  put(L.tip_off, P.tip_off.data(), vbytes(P.tip_off));
+  put(L.m_off, P.m_off.data(), vbytes(P.m_off));
+  put(L.lvl_off, P.lvl_off.data(), vbytes(P.lvl_off));
+  put(L.lvl, P.lvl.data(), vbytes(P.lvl));
+  put(L.bi, P.bi.data(), vbytes(P.bi));
+  put(L.bp0, P.bp0.data(), vbytes(P.bp0)); put(L.bp1, P.bp1.data(), vbytes(P.bp1));
+  put(L.bp2, P.bp2.data(), vbytes(P.bp2)); put(L.bp3, P.bp3.data(), vbytes(P.bp3));
+  put(L.bp4, P.bp4.data(), vbytes(P.bp4));
+  put(L.dinfo, P.dinfo.data(), vbytes(P.dinfo));
+  put(L.anc, P.anc.data(), vbytes(P.anc));
+  put(L.ap0, P.ap0.data(), vbytes(P.ap0)); put(L.ap1, P.ap1.data(), vbytes(P.ap1));
+  put(L.apple_body, P.apple_body.data(), vbytes(P.apple_body));
+  put(L.tip_body, P.tip_body.data(), vbytes(P.tip_body));
+  put(L.tip_local, P.tip_local.data(), vbytes(P.tip_local));
+  put(L.gravity, P.gravity.data(), vbytes(P.gravity));
+  put(L.queue, P.queue.data(), vbytes(P.queue));
+  put(L.pairs, P.pairs.data(), vbytes(P.pairs));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dev_buf, host.data(), L.total, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    delete m;
+    return cuda_fail(e);
+  }
+  char* base = (char*)dev_buf;
+  DevModel& dm = m->dev;
+  dm.W = P.W;
+  dm.body_off = (const int*)(base + L.body_off);
+  dm.dof_off = (const int*)(base + L.dof_off);
+  dm.apple_off = (const int*)(base + L.apple_off);
+  dm.tip_off = (const int*)(base + L.tip_off);
+  dm.m_off = (const int*)(base + L.m_off);
+  dm.lvl_off = (const int*)(base + L.lvl_off);
+  dm.lvl = (const int*)(base + L.lvl);
+  dm.bi = (const int4*)(base + L.bi);
+  dm.bp0 = (const float4*)(base + L.bp0); dm.bp1 = (const float4*)(base + L.bp1);
+  dm.bp2 = (const float4*)(base + L.bp2); dm.bp3 = (const float4*)(base + L.bp3);
+  dm.bp4 = (const float4*)(base + L.bp4);
+  dm.dinfo = (const int4*)(base + L.dinfo);
+  dm.anc = (const unsigned short*)(base + L.anc);
+  dm.ap0 = (const float4*)(base + L.ap0); dm.ap1 = (const float4*)(base + L.ap1);
+  dm.apple_body = (const int*)(base + L.apple_body);
+  dm.tip_body = (const int*)(base + L.tip_body);
+  dm.tip_local = (const float4*)(base + L.tip_local);
+  dm.gravity = (const float4*)(base + L.gravity);
+  dm.queue = (const int*)(base + L.queue);
+  dm.pairs = (const unsigned char*)(base + L.pairs);
+  *out = m;
+  return OT_OK;
+}
+
+void ot_model_release(ot_model* model) { delete model; }
+
+ot_status ot_model_counts(const ot_model* m, int64_t counts[6]) {
+  if (!m || !counts) return OT_EINVAL;
+  counts[0] = m->P.W; counts[1] = m->P.NB; counts[2] = m->P.NV; counts[3] = m->P.NA; counts[4] = m->P.NT;
+  counts[5] = (int64_t)m->P.classes.size();
+  return OT_OK;
+}
+
+ot_status ot_state_bytes(const ot_model* m, size_t* bytes) {
+  if (!m || !bytes) return OT_EINVAL;
+  *bytes = state_layout(m).total;
+  return OT_OK;
+}
+
+ot_status ot_world_state_alloc(const ot_model* m, void* dev_buf, size_t bytes, ot_state** out) {
+  if (!m || !dev_buf || !out) return OT_EINVAL;
+  if (((uintptr_t)dev_buf) % kAlign) return OT_EINVAL;
+  StateLayout L = state_layout(m);
+  if (bytes < L.total) return OT_EINVAL;
+  ot_state* s = new ot_state();
+  s->model = m;
+  s->base = (char*)dev_buf;
+  s->bytes = bytes;
+  char* b = s->base;
+  s->dev.q = (float*)(b + L.q); s->dev.qd = (float*)(b + L.qd);
+  s->dev.ax = (float*)(b + L.ax); s->dev.av = (float*)(b + L.av);
+  s->dev.broken = (int*)(b + L.broken); s->dev.bcnt = (int*)(b + L.bcnt); s->dev.break_step = (int*)(b + L.break_step);
+  s->dev.detached = (int*)(b + L.detached); s->dev.pcnt = (int*)(b + L.pcnt); s->dev.tcnt = (int*)(b + L.tcnt);
+  s->dev.detach_step = (int*)(b + L.detach_step);
+  s->dev.status = (unsigned*)(b + L.status);
+  s->dev.scratch = (float*)(b + L.scratch[0]);
+  s->q_counters = (int*)(b + L.counters);
+  *out = s;
+  return OT_OK;
+}
+
+void ot_state_release(ot_state* s) { delete s; }
+
+ot_status ot_state_set(ot_state* s, const ot_state_init* init, void* stream) {
+  if (!s || !init) return OT_EINVAL;
+  const Packed& P = s->model->P;
+  if (P.NA > 0 && !init->apple_x) return OT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const cudaMemcpyKind kind = init->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  auto copy_or_zero = [&](void* dst, const void* src, size_t n) -> cudaError_t {
+    if (!n) return cudaSuccess;
+    if (src) return cudaMemcpyAsync(dst, src, n, kind, st);
+    return cudaMemsetAsync(dst, 0, n, st);
+  };
+  OT_CUDA(copy_or_zero(s->dev.q, init->q, sizeof(float) * P.NV));
+  OT_CUDA(copy_or_zero(s->dev.qd, init->qd, sizeof(float) * P.NV));
+  OT_CUDA(copy_or_zero(s->dev.ax, init->apple_x, sizeof(float) * 3 * P.NA));
+  OT_CUDA(copy_or_zero(s->dev.av, init->apple_v, sizeof(float) * 3 * P.NA));
+  const size_t nb = sizeof(int) * P.NB, na = sizeof(int) * P.NA;
+  if (nb) {
+    OT_CUDA(cudaMemsetAsync(s->dev.broken, 0, nb, st));
+    OT_CUDA(cudaMemsetAsync(s->dev.bcnt, 0, nb, st));
+    OT_CUDA(cudaMemsetAsync(s->dev.break_step, 0xff, nb, st));
+  }
+  if (na) {
+    OT_CUDA(cudaMemsetAsync(s->dev.detached, 0, na, st));
+    OT_CUDA(cudaMemsetAsync(s->dev.pcnt, 0, na, st));
+    OT_CUDA(cudaMemsetAsync(s->dev.tcnt, 0, na, st));
+    OT_CUDA(cudaMemsetAsync(s->dev.detach_step, 0xff, na, st));
+  }
+  if (P.W) OT_CUDA(cudaMemsetAsync(s->dev.status, 0, sizeof(unsigned) * P.W, st));
+  if (!init->on_device) OT_CUDA(cudaStreamSynchronize(st));
+  return OT_OK;
+}
+
+ot_status ot_state_get_view(const ot_state* s, ot_state_view* v) {
+  if (!s || !v) return OT_EINVAL;
+  v->q = s->dev.q; v->qd = s->dev.qd; v->apple_x = s->dev.ax; v->apple_v = s->dev.av;
+  v->broken = s->dev.broken; v->break_step = s->dev.break_step;
+  v->detached = s->dev.detached; v->detach_step = s->dev.detach_step;
+  v->status = s->dev.status;
+  return OT_OK;
+}
+
+ot_status ot_world_status(const ot_state* s, uint32_t* dev_status, void* stream) {
+  if (!s || !dev_status) return OT_EINVAL;
+  if (s->model->P.W)
+    OT_CUDA(cudaMemcpyAsync(dev_status, s->dev.status, sizeof(unsigned) * s->model->P.W, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+  return OT_OK;
+}
+
+ot_status ot_ckpt_bytes(const ot_model* m, int32_t n_steps, int32_t ckpt_every, size_t* bytes) {
+  if (!m || !bytes || n_steps < 0 || ckpt_every < 1) return OT_EINVAL;
+  const long long n_snap = (n_steps + ckpt_every - 1) / ckpt_every;
+  *bytes = (size_t)(n_snap * ckpt_words(m->P) * 4);
+  return OT_OK;
+}
+
+ot_status ot_step(ot_model* m, ot_state* s, const float* ext_force, const ot_force_schedule* pulls, int32_t step,
+                  double dt, void* stream) {
+  if (!m || !s || s->model != m || !(dt > 0)) return OT_EINVAL;
+  StepArgs a = base_args(m, dt);
+  a.step0 = step;
+  a.n_steps = 1;
+  a.ext_force = ext_force;
+  ot_status st = fill_pulls(a, pulls);
+  if (st != OT_OK) return st;
+  for (int k = 0; k < (int)m->P.classes.size(); ++k) {
+    st = launch_class(m, s, k, a, (cudaStream_t)stream);
+    if (st != OT_OK) return st;
+  }
+  return OT_OK;
+}
+
+ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                     const ot_force_schedule* pulls, const ot_record* rec, void* stream) {
+  if (!m || !s || s->model != m || n_steps < 0 || !(dt > 0)) return OT_EINVAL;
+  if (n_steps == 0) return OT_OK;
+  StepArgs a = base_args(m, dt);
+  a.step0 = step0;
+  a.n_steps = n_steps;
+  ot_status st = fill_pulls(a, pulls);
+  if (st != OT_OK) return st;
+  if (rec) {
+    a.tips = rec->tips;
+    if (rec->ckpt) {
+      if (rec->ckpt_every < 1) return OT_EINVAL;
+      size_t need = 0;
+      ot_ckpt_bytes(m, n_steps, rec->ckpt_every, &need);
+      if (rec->ckpt_bytes < need) return OT_EINVAL;
+      a.ckpt = (unsigned*)rec->ckpt;
+      a.ckpt_every = rec->ckpt_every;
+    }
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  // graph key: everything the captured launches depend on
+  char key[512];
+  std::snprintf(key, sizeof(key), "%p|%d|%d|%.17g|%p|%p|%p|%p|%p|%d", (void*)s->base, n_steps, step0, dt,
+                (const void*)a.pull_force, (const void*)a.pull_start, (const void*)a.tips, (void*)a.ckpt,
+                (const void*)a.pull_end, a.ckpt_every);
+  std::string skey = key;
+  std::string sched_sig;
+  for (const ClassInfo& ci : m->P.classes) {
+    char b[96];
+    std::snprintf(b, sizeof(b), "/%d,%d,%d,%d", ci.sched.threads_per_world, ci.sched.worlds_per_block,
+                  ci.sched.blocks, ci.sched.global_workspace);
+    sched_sig += b;
+  }
+  skey += sched_sig;
+  for (auto& g : m->graphs)
+    if (g.key == skey) {
+      OT_CUDA(cudaGraphLaunch(g.exec, user));
+      g_launches += g.kernels;
+      return OT_OK;
+    }
+  if (!m->capture_stream) OT_CUDA(cudaStreamCreateWithFlags(&m->capture_stream, cudaStreamNonBlocking));
+  cudaStream_t cs = m->capture_stream;
+  std::vector<Shape> shapes(m->P.classes.size());
+  for (int k = 0; k < (int)m->P.classes.size(); ++k) {
+    ot_status r = class_shape(m, k, &shapes[k]);
+    if (r != OT_OK) return r;
+  }
+  OT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const long long before = g_launches.load();
+  ot_status rst = OT_OK;
+  for (int k = 0; k < (int)m->P.classes.size() && rst == OT_OK; ++k)
+    rst = launch_class_shaped(m, s, k, a, shapes[k], cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  const int kernels = (int)(g_launches.load() - before);
+  g_launches -= kernels;  // capture is not execution
+  if (rst != OT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rst;
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (m->graphs.size() >= 8) {
+    cudaGraphExecDestroy(m->graphs.front().exec);
+    m->graphs.erase(m->graphs.begin());
+  }
+  m->graphs.push_back({skey, exec, kernels});
+  OT_CUDA(cudaGraphLaunch(exec, user));
+  g_launches += kernels;
+  return OT_OK;
+}
+
+ot_status ot_rollout_plain(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                           const ot_force_schedule* pulls, void* stream) {
+  if (!m || !s || s->model != m || n_steps < 0 || !(dt > 0)) return OT_EINVAL;
+  StepArgs a = base_args(m, dt);
+  ot_status st = fill_pulls(a, pulls);
+  if (st != OT_OK) return st;
+  a.n_steps = 1;
+  cudaStream_t cs = (cudaStream_t)stream;
+  // one fixed launch shape for every world: 64 threads, workspace in shared memory when it
+  // fits, else in the first scratch slot of the world's class
+  const Packed& P = m->P;
+  std::vector<int> cls_of(P.W);
+  for (int k = 0; k < (int)P.classes.size(); ++k)
+    for (int i = P.classes[k].q_begin; i < P.classes[k].q_end; ++i) cls_of[P.queue[i]] = k;
+  // the largest shared-memory size any world needs, set once
+  size_t smem_max = 1;
+  for (const ClassInfo& ci : P.classes)
+    if ((size_t)ci.ws_floats * 4 <= kSmemLimit) smem_max = std::max(smem_max, (size_t)ci.ws_floats * 4);
+  int bps = 0;
+  OT_CUDA(kernel_attributes(64, 1, smem_max, &bps));
+  for (int t = 0; t < n_steps; ++t) {
+    a.step0 = step0 + t;
+    for (int w = 0; w < P.W; ++w) {
+      const ClassInfo& ci = P.classes[cls_of[w]];
+      StepArgs b = a;
+      b.single_world = w;
+      b.ws_floats = ci.ws_floats;
+      const bool fits = (size_t)ci.ws_floats * 4 <= kSmemLimit;
+      b.global_ws = fits ? 0 : 1;
+      DevState ds = s->dev;
+      int slots = 0;
+      ds.scratch = s->dev.scratch + class_scratch_offset(m, cls_of[w], &slots);
+      const size_t smem = fits ? (size_t)ci.ws_floats * 4 : 0;
+      launch_rollout(64, 1, 1, smem, cs, m->dev, ds, b);
+      OT_CUDA(cudaGetLastError());
+      g_launches += 1;
+    }
+  }
+  return OT_OK;
+}
+
+ot_status ot_get_schedule(const ot_model* m, int32_t k, ot_schedule* sc) {
+  if (!m || !sc || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  *sc = m->P.classes[k].sched;
+  return OT_OK;
+}
+
+ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
+  if (!m || !sc || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  const ClassInfo& ci = m->P.classes[k];
+  const int t = sc->threads_per_world;
+  if (t != 32 && t != 64 && t != 128 && t != 256) return OT_EINVAL;
+  if (sc->worlds_per_block < 1 || t * sc->worlds_per_block > 512) return OT_EINVAL;
+  if (t > 32 && sc->worlds_per_block > 15) return OT_EINVAL;
+  if (t == 32 && sc->worlds_per_block > 16) return OT_EINVAL;
+  if (sc->blocks < 0) return OT_EINVAL;
+  // a class's global-workspace setting is fixed at upload (it sizes the state's scratch)
+  if (sc->global_workspace != ci.sched.global_workspace) return OT_EINVAL;
+  if (!sc->global_workspace && (size_t)ci.ws_floats * 4 * sc->worlds_per_block > kSmemLimit) return OT_EINVAL;
+  if (sc->global_workspace && sc->worlds_per_block * std::max(sc->blocks, 1) > m->n_sm * 4) return OT_EINVAL;
+  m->P.classes[k].sched = *sc;
+  return OT_OK;
+}
+
+ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void* stream) {
+  if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0)) return OT_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  OT_CUDA(cudaEventCreate(&e0));
+  OT_CUDA(cudaEventCreate(&e1));
+  StepArgs a = base_args(m, dt);
+  a.n_steps = n_steps;
+  ot_status result = OT_OK;
+  for (int k = 0; k < (int)m->P.classes.size() && result == OT_OK; ++k) {
+    ClassInfo& ci = m->P.classes[k];
+    const ot_schedule keep = ci.sched;
+    std::vector<ot_schedule> cands;
+    for (int t : {32, 64, 128, 256})
+      for (int g : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        ot_schedule c{t, g, 0, keep.global_workspace};
+        if (t * g > 512) continue;
+        if (t > 32 && g > 15) continue;
+        if (!c.global_workspace && (size_t)ci.ws_floats * 4 * g > kSmemLimit) continue;
+        if (c.global_workspace && g > 1) continue;
+        cands.push_back(c);
+      }
+    float best = 1e30f;
+    ot_schedule best_s = keep;
+    for (const ot_schedule& c : cands) {
+      ci.sched = c;
+      float ms = 0;
+      ot_status r = launch_class(m, s, k, a, st);  // warm-up and attribute set-up
+      if (r != OT_OK) continue;
+      cudaEventRecord(e0, st);
+      r = launch_class(m, s, k, a, st);
+      cudaEventRecord(e1, st);
+      if (r != OT_OK) continue;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        result = cuda_fail(cudaGetLastError());
+        break;
+      }
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_s = c;
+      }
+    }
+    ci.sched = best_s;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                              const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
+                              ot_grads* grads, void* stream) {
+  (void)m; (void)s; (void)n_steps; (void)step0; (void)dt; (void)pulls; (void)rec; (void)dL_dtips; (void)grads;
+  (void)stream;
+  return OT_ESTATE;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+"""The C-ABI library on the CPU: it loads, exports every declared symbol, and validates
+descriptors (host-only calls; no compute without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2607_06337_b300 import build as Bld
+from paper_2607_06337_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def orch():
+    Bld.build()
+    from paper_2607_06337_b300 import orchard
+    orchard.lib()
+    return orchard
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "orchard.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ot_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(orch):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = C.CDLL(orch.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+    # and the binding declares a signature for each of them
+    assert set(names) == set(orch._SIGS)
+
+
+def test_status_strings(orch):
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert orch.lib().ot_status_string(code)
+
+
+def test_model_bytes_of_a_generated_forest(orch):
+    f = I.make_forest(0, worlds=[0, 1])
+    n = orch.model_bytes(f)
+    assert n > 0 and n % 256 == 0
+
+
+def _status_of(orch, f):
+    keep = orch._Keep()
+    d = orch.make_desc(f, keep)
+    n = C.c_size_t(0)
+    return orch.lib().ot_model_bytes(C.byref(d), C.byref(n))
+
+
+def test_validation_rejects_bad_descriptors(orch):
+    good = I.make_forest(0, worlds=[0])
+    assert _status_of(orch, good) == orch.OT_OK
+    # not breadth-first: swap two parents so the parent array decreases
+    f = good.subset([0])
+    f.parent = f.parent.copy()
+    i = int(np.nonzero(np.diff(f.parent[1:]) > 0)[0][0]) + 1
+    f.parent[i], f.parent[i + 1] = f.parent[i + 1], f.parent[i]
+    assert _status_of(orch, f) == orch.OT_ETOPO
+    # parent out of range
+    f = good.subset([0])
+    f.parent = f.parent.copy()
+    f.parent[5] = 40
+    assert _status_of(orch, f) == orch.OT_ETOPO
+    # a second root
+    f = good.subset([0])
+    f.parent = f.parent.copy()
+    f.parent[0] = 3
+    assert _status_of(orch, f) == orch.OT_ETOPO
+    # ndof outside {0, 1, 2}
+    f = good.subset([0])
+    f.ndof = f.ndof.copy()
+    f.ndof[4] = 3
+    assert _status_of(orch, f) == orch.OT_ETOPO
+    # apples not sorted by body
+    f = good.subset([0])
+    f.apple_body = f.apple_body[::-1].copy()
+    assert _status_of(orch, f) == orch.OT_ETOPO
+    # non-finite and non-positive values
+    for name, val in (("mass", np.nan), ("k", np.inf), ("mass", 0.0), ("apple_mass", -1.0)):
+        f = good.subset([0])
+        a = getattr(f, name).copy()
+        a[1] = val
+        setattr(f, name, a)
+        assert _status_of(orch, f) == orch.OT_ENONFINITE, name
+    # too many DOFs in one world (more than 32767)
+    n = 16400
+    bodies = [dict(parent=max(i - 1, -1) if i < 2 else (i - 1) // 2, ndof=2, mass=1.0,
+                   inertia=(1.0, 1.0, 1.0)) for i in range(n)]
+    big = I.from_bodies(bodies)
+    assert _status_of(orch, big) == orch.OT_ECAPACITY
+
+
+def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
+    f = I.make_forest(0, worlds=[0])
+    keep = orch._Keep()
+    d = orch.make_desc(f, keep)
+    fl = orch.make_flags(I.Flags())
+    h = C.c_void_p()
+    # null device buffer
+    assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(fl), None, 0, None, C.byref(h)) == orch.OT_EINVAL
+    # misaligned device pointer (checked before any CUDA call)
+    assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(fl), C.c_void_p(4), 1 << 20, None,
+                                           C.byref(h)) == orch.OT_EINVAL
+    # invalid flags
+    bad = orch.make_flags(I.Flags(n_break=0))
+    assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(bad), C.c_void_p(256), 1 << 20, None,
+                                           C.byref(h)) == orch.OT_EINVAL
+    assert h.value is None
+
+
+def test_flop_count_scales_with_the_terms():
+    from paper_2607_06337_b300 import costs
+    f = I.make_forest(0, worlds=[0])
+    nb, nv, na, E, P = costs.world_terms(f)
+    assert nv[0] == 2 * (nb[0] - 1)
+    depth = costs.dof_depths(f)
+    assert E[0] == depth.sum() and P[0] == (depth * (depth + 1) // 2).sum()
+    per_body = costs.flops_per_step(f) / costs.body_count(f)
+    assert 500 < per_body < 5000  # of the order of a few kflop per body-step

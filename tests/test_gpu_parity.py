@@ -1,0 +1,157 @@
+"""GPU step (through the C ABI) against the FP64 oracle, element by element."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_06337_b300 import inputs as I
+from tests import parity as PAR
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _gpu_state(sim):
+    return dict(q=sim.q.cpu().numpy().astype(np.float64), qd=sim.qd.cpu().numpy().astype(np.float64),
+                ax=sim.apple_x.cpu().numpy().astype(np.float64), broken=sim.broken.cpu().numpy(),
+                break_step=sim.break_step.cpu().numpy(), detached=sim.detached.cpu().numpy(),
+                detach_step=sim.detach_step.cpu().numpy(), status=sim.status.cpu().numpy())
+
+
+def _run(f, flags, n_steps, form="batched", record_tips=False):
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Record, Simulator
+    sim = Simulator(f, flags)
+    sim.reset()
+    tips = None
+    rec = None
+    if record_tips:
+        tips = torch.zeros((n_steps, f.n_tips, 3), dtype=torch.float32, device="cuda")
+        rec = Record(tips.data_ptr(), None, 0, 0)
+    if form == "batched":
+        sim.rollout(n_steps, record=rec)
+    elif form == "plain":
+        sim.rollout_plain(n_steps)
+    elif form == "step":
+        for t in range(n_steps):
+            sim.step(t)
+    torch.cuda.synchronize()
+    out = _gpu_state(sim)
+    if tips is not None:
+        out["tips"] = tips.cpu().numpy().astype(np.float64)
+    return out
+
+
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_config0_plain_parity_1000_steps(form):
+    """16 worlds x 64 bodies x 8 apples, gravity only, 1000 steps (the plain-form workload)."""
+    f = I.make_forest(0)
+    fl = I.Flags()
+    g = _run(f, fl, 1000, form)
+    st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    assert max(r["ratio"] for r in rep) < 0.1  # ample margin in the smooth regime
+    assert (g["status"] == 0).all()
+
+
+def test_step_by_step_equals_rollout():
+    f = I.make_forest(1, worlds=[5, 6, 7])
+    fl = I.Flags()
+    a = _run(f, fl, 60, "batched")
+    b = _run(f, fl, 60, "step")
+    np.testing.assert_array_equal(a["q"], b["q"])
+    np.testing.assert_array_equal(a["broken"], b["broken"])
+
+
+def test_config1_subset_with_pulls_and_events():
+    """Uneven trees (100-600 bodies) with random pulls: q gate and identical event sets."""
+    f = I.make_forest(1, worlds=[0, 1, 2, 3, 17, 33, 64, 101])
+    fl = I.Flags()
+    g = _run(f, fl, 1000)
+    st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    assert sum(r["n_events"] for r in rep) > 10  # the workload does exercise breaks and detaches
+
+
+def test_tip_record_matches_oracle():
+    f = I.make_forest(3, worlds=[0, 1, 2])
+    fl = I.Flags()
+    g = _run(f, fl, 200, record_tips=True)
+    st, rec = O.rollout(f, fl, 200, record_tips=True)
+    err = np.abs(g["tips"] - rec["tips"]).max()
+    assert err < 1e-5, err
+
+
+def test_stress_classes_including_global_workspace():
+    """50 / 400 / 2000-body worlds (the 2000-body class runs with its workspace in global memory)."""
+    f = I.make_forest(4, worlds=[0, 4096, 8000])  # one world per size class
+    assert sorted(np.diff(f.body_off)) == [50, 400, 2000]
+    fl = I.Flags()
+    g = _run(f, fl, 150)
+    st, rec = O.rollout(f, fl, 150, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+
+
+def test_edge_cases_single_body_and_chain():
+    """Degenerate worlds in one batch: a welded post with an apple (no DOFs), a one-body hinge,
+    a 1-DOF chain, and a regular tree."""
+    from tests import _trees as T
+    post = I.from_bodies([dict(parent=-1, ndof=0, mass=1.0, com=(0, 0, 0.5), inertia=(0.1, 0.1, 0.01))],
+                         apples=[dict(body=0, hang_local=(0, 0, 1.0), mass=0.2, k_s=1000.0, c_s=5.0, f_detach=20.0,
+                                      x0=(0.0, 0.0, -0.01), v0=(0.0, 0.0, 0.0))])
+    hinge, _, _ = T.single_hinge(k=0.5, kd=0.01, gravity=(0.0, 0.0, -9.81))
+    hinge.q0[:] = 0.3
+    chain, _ = T.chain(12, 0.1, 0.01, 700.0, 1e9, kd=0.05, gravity=(0.0, 0.0, -9.81))
+    chain.q0[:] = np.linspace(0.05, -0.05, 12)
+    tree = I.make_forest(0, worlds=[0])
+    f = _concat([post, hinge, chain, tree])
+    fl = I.Flags()
+    g = _run(f, fl, 300)
+    st, rec = O.rollout(f, fl, 300, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    np.testing.assert_allclose(g["ax"], st.ax, atol=1e-5)
+
+
+def test_nonfinite_world_is_frozen_others_continue():
+    f = I.make_forest(0, worlds=[0, 1])
+    f.q0 = f.q0.copy()
+    f.q0[f.dof_off[1] + 3] = np.nan
+    fl = I.Flags()
+    g = _run(f, fl, 50)
+    assert g["status"][1] & 1 and g["status"][0] == 0
+    st, _ = O.rollout(f.subset([0]), fl, 50)
+    a, b = f.dof_off[0], f.dof_off[1]
+    assert np.abs(g["q"][a:b] - st.q).max() < 1e-4 * np.abs(st.q).max() + 1e-7
+
+
+def _concat(forests):
+    """Pack several one-or-more-world forests into one."""
+    from paper_2607_06337_b300.inputs import Forest
+    cat = lambda name: np.concatenate([getattr(x, name) for x in forests])
+
+    def offs(name):
+        out = [0]
+        for x in forests:
+            o = getattr(x, name)
+            out.extend((out[-1] + o[1:]).tolist())
+        return np.array(out, np.int32)
+
+    return Forest(
+        n_worlds=sum(x.n_worlds for x in forests), body_off=offs("body_off"), apple_off=offs("apple_off"),
+        tip_off=offs("tip_off"), parent=cat("parent"), ndof=cat("ndof"), jpos=cat("jpos"), qrel=cat("qrel"),
+        length=cat("length"), diam=cat("diam"), mass=cat("mass"), com=cat("com"), inertia=cat("inertia"),
+        k=cat("k"), kd=cat("kd"), armature=cat("armature"), m_max=cat("m_max"), apple_body=cat("apple_body"),
+        hang_local=cat("hang_local"), attach_local=cat("attach_local"), apple_mass=cat("apple_mass"),
+        k_s=cat("k_s"), c_s=cat("c_s"), f_detach=cat("f_detach"), tip_body=cat("tip_body"),
+        tip_local=cat("tip_local"), gravity=cat("gravity"), q0=cat("q0"), qd0=cat("qd0"),
+        apple_x0=cat("apple_x0"), apple_v0=cat("apple_v0"), pull_force=cat("pull_force"),
+        pull_start=cat("pull_start"), pull_end=cat("pull_end"))
