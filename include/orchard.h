@@ -7,7 +7,9 @@
  *   - each compliant joint has up to two bending DOFs (Cardan x then y' of a twist-locked D6)
  *     with torsional spring-damper tau = -k theta - kd omega, k = E I / l (Sec. IV-A, Eq. 4);
  *   - rupture when k |theta| > sigma_r pi r^3 / 4 for N_b consecutive steps, after which the
- *     joint is a free hinge (its gain rows zeroed in place, Sec. IV-B, Eq. 5);
+ *     joint is a free hinge (its gain rows zeroed in place, Sec. IV-B, Eq. 5) whose torn-fibre
+ *     friction ramps up over about 1.5 s (read as an implicit viscous damper), and the apples
+ *     of the snapped sub-tree no longer load it (applied forces disabled, App. B);
  *   - apples as 3-DOF free bodies on tethers f = -k_s (x - x_hang) - c_s v whose elastic part
  *     minus the static weight reacts on the spur, clamped (Sec. IV-C, Eqs. 6-7); they detach
  *     on a sustained pull above f_detach or a longer tension above gamma f_detach (Sec. IV-C).
@@ -98,6 +100,8 @@ typedef struct ot_model_flags {
   int32_t n_tension;             /* (10) N_t */
   double gamma_tension;          /* (1.2) tension threshold factor */
   double clamp_factor;           /* (1.2) reaction clamp = clamp_factor * f_detach */
+  double break_ramp_s;           /* (1.5) a broken joint keeps a friction surrogate: a viscous */
+  double break_ramp_factor;      /* (5.0) damper ramping from kd to factor * kd over ramp_s (s) */
 } ot_model_flags;
 
 /* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */

@@ -127,6 +127,8 @@ typedef struct {
   int32_t alpha_implicit_spring, tether_implicit, n_break, n_pull, n_tension;
   double gamma_tension, clamp_factor;
   int32_t dense_limit;  // solve densely when n_v <= dense_limit, else by tree LTDL
+  double break_ramp_s;      // post-break friction surrogate ramps over this time (s)
+  double break_ramp_factor; // ... from kd to this multiple of kd
 } OFlags;
 
 typedef struct {
@@ -284,8 +286,11 @@ template <class T> inline V3<T> jac_point(const World& W, const Kin<T>& K, int i
 // v' = a + beta v_hang' with a = (m v + dt (f_ext + m g + f_s)) / D, beta = dt^2 k_s / D,
 // D = m + dt c_s + dt^2 k_s; eliminating it leaves the tree with the force
 // f_react + dt k_s a - dt kappa v_hang at the hang point and dt^2 kappa J_h^T J_h in H,
-// kappa = k_s (1 - beta). A clamped (or explicit-mode) apple gives the plain f_react and
-// v' = a. Detached apples give nothing.
+// kappa = k_s (1 - beta). Reading of the clamp (Eq. 7, "clamped to a maximum"): when
+// |f_react| > F_clamp the coupled reaction, force and stiffness alike, is scaled by
+// F_clamp / |f_react| (continuous at the threshold). In the explicit mode the plain clamped
+// f_react is applied and v' = a. Detached apples, and apples on a snapped sub-tree (whose
+// applied forces are disabled, App. B), give nothing.
 template <class T> struct AppleLoads {
   std::vector<V3<T>> hang;     // world hang point
   std::vector<V3<T>> vhang;    // its velocity at the start of the step
@@ -296,10 +301,18 @@ template <class T> struct AppleLoads {
   std::vector<T> tension, pull;
 };
 
+// A body is on a snapped sub-tree when its own joint or any joint above it is broken.
+std::vector<int> snapped_bodies(const World& W, const int32_t* broken) {
+  std::vector<int> s(W.nb, 0);
+  for (int b = 0; b < W.nb; ++b) s[b] = (broken && broken[b]) || (W.parent[b] >= 0 && s[W.parent[b]]);
+  return s;
+}
+
 template <class T>
 void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax, const T* av,
-                 const int32_t* detached, const double* fext, AppleLoads<T>& A) {
+                 const int32_t* detached, const int32_t* broken, const double* fext, AppleLoads<T>& A) {
   int na = W.na;
+  const std::vector<int> snapped = snapped_bodies(W, broken);
   A.hang.resize(na); A.vhang.resize(na); A.fapp.resize(na); A.a.resize(na);
   A.beta.assign(na, T(0)); A.kappa.assign(na, T(0)); A.tension.resize(na); A.pull.resize(na);
   V3<T> g = dv<T>(W.g);
@@ -329,14 +342,18 @@ void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax,
     V3<T> fr = T(-1) * (fs + m * g);
     T n = sqrt(dot(fr, fr));
     double fc = fl.clamp_factor * W.fdet[a];
-    if (re(n) > fc) {
-      A.fapp[a] = (T(fc) / n) * fr;
+    if (snapped[b]) {
+      // debris: applied forces on a snapped sub-tree are disabled (App. B); the stem still
+      // acts on the apple
+      A.fapp[a] = zero;
     } else if (fl.tether_implicit) {
+      // the clamp scales the coupled reaction, force and stiffness alike, by F_clamp / |f_react|
+      T sc = re(n) > fc ? T(fc) / n : T(1);
       A.beta[a] = T(dt * dt * W.ks[a]) / D;
-      A.kappa[a] = T(W.ks[a]) * (T(1) - A.beta[a]);
-      A.fapp[a] = fr + T(dt * W.ks[a]) * A.a[a] - T(dt) * A.kappa[a] * A.vhang[a];
+      A.kappa[a] = sc * T(W.ks[a]) * (T(1) - A.beta[a]);
+      A.fapp[a] = sc * (fr + T(dt * W.ks[a]) * A.a[a]) - T(dt) * A.kappa[a] * A.vhang[a];
     } else {
-      A.fapp[a] = fr;
+      A.fapp[a] = re(n) > fc ? (T(fc) / n) * fr : fr;
     }
   }
 }
@@ -490,7 +507,7 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
     s.detached[a] = 1;
   }
   AppleLoads<T> A;
-  apple_loads(W, fl, K, s.ax.data(), s.av.data(), s.detached.data(), fext, A);
+  apple_loads(W, fl, K, s.ax.data(), s.av.data(), s.detached.data(), s.broken.data(), fext, A);
   std::vector<T> M, c;
   mass_matrix(W, fl, K, &A, s.detached.data(), M);
   bias_force(W, K, &A, c);
@@ -498,9 +515,16 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
   std::vector<T> r(n);
   for (int i = 0; i < n; ++i) {
     int b = W.dof_body[i];
-    // a broken joint is a free hinge: spring and damper removed (Sec. IV-B)
+    // a broken joint loses its spring and its damper (gain rows zeroed, Sec. IV-B); the
+    // friction of the torn fibres is introduced at the break and ramped up over break_ramp_s
+    // (Sec. IV-B), read as a viscous damper growing from kd to break_ramp_factor * kd
     T k = s.broken[b] ? T(0) : G.k[b];
-    T kd = s.broken[b] ? T(0) : G.kd[b];
+    T kd = G.kd[b];
+    if (s.broken[b]) {
+      double since = (step - s.break_step[b]) * dt;
+      double ramp = fl.break_ramp_s > 0 ? std::min(since / fl.break_ramp_s, 1.0) : 1.0;
+      kd = T(1.0 + (fl.break_ramp_factor - 1.0) * ramp) * G.kd[b];
+    }
     M[(size_t)i * n + i] += T(W.arm[b]) + T(dt) * kd + T(fl.alpha_implicit_spring * dt * dt) * k;
     r[i] = T(dt) * (T(-1) * k * (s.q[i] + T(fl.alpha_implicit_spring * dt) * s.qd[i]) - kd * s.qd[i] - c[i]);
   }
@@ -692,7 +716,7 @@ int oracle_eval(const OForest* f, const OFlags* fl, int w, const double* q, cons
   if (detached) det.assign(detached, detached + W.na);
   std::vector<double> zeros(3 * W.na, 0.0);
   AppleLoads<double> A;
-  apple_loads(W, *fl, K, ax ? ax : zeros.data(), av ? av : zeros.data(), det.data(), fext ? fext : zeros.data(), A);
+  apple_loads(W, *fl, K, ax ? ax : zeros.data(), av ? av : zeros.data(), det.data(), nullptr, fext ? fext : zeros.data(), A);
   std::vector<double> M, c;
   mass_matrix(W, *fl, K, ax ? &A : nullptr, det.data(), M);
   bias_force(W, K, ax ? &A : nullptr, c);

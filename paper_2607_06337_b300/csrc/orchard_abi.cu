@@ -40,7 +40,7 @@ ot_status cuda_fail(cudaError_t e) {
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-constexpr size_t kSmemLimit = 226 * 1024;  // dynamic shared memory per block (opt-in 227 KB less static)
+constexpr size_t kSmemLimit = kSmemLimitBytes;  // dynamic shared memory per block (opt-in 227 KB less static)
 
 // Bump allocator over a byte range; in sizing mode it only counts.
 struct Carver {
@@ -438,6 +438,8 @@ StepArgs base_args(const ot_model* m, double dt) {
   a.n_tension = m->flags.n_tension;
   a.gamma = (float)m->flags.gamma_tension;
   a.clamp = (float)m->flags.clamp_factor;
+  a.ramp_inv = m->flags.break_ramp_s > 0 ? (float)(dt / m->flags.break_ramp_s) : 0.f;
+  a.ramp_gain = (float)(m->flags.break_ramp_factor - 1.0);
   a.single_world = -1;
   a.NB = m->P.NB; a.NV = m->P.NV; a.NA = m->P.NA;
   a.n_tips_total = m->P.NT;
@@ -547,7 +549,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   if (flags->n_break < 1 || flags->n_pull < 1 || flags->n_tension < 1 ||
       (flags->alpha_implicit_spring != 0 && flags->alpha_implicit_spring != 1) ||
       (flags->tether_implicit != 0 && flags->tether_implicit != 1) || !(flags->clamp_factor > 0) ||
-      !(flags->gamma_tension > 0))
+      !(flags->gamma_tension > 0) || !(flags->break_ramp_s >= 0) || !(flags->break_ramp_factor >= 0))
     return OT_EINVAL;
   ot_model* m = new ot_model();
   ot_status st = pack(desc, m->P);

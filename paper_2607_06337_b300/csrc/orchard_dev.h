@@ -63,6 +63,8 @@ struct StepArgs {
   int tether_implicit;
   int n_break, n_pull, n_tension;
   float gamma, clamp;
+  float ramp_inv;       // 1 / (post-break ramp time in steps), 0: no ramp (full factor at once)
+  float ramp_gain;      // post-break damper factor minus one
   int step0;            // absolute index of the first step of this launch
   int n_steps;
   const float* pull_force;  // [NA*3] or null
@@ -84,7 +86,7 @@ struct StepArgs {
 
 // Workspace layout of one world (floats), a function of its sizes only.
 struct WsLayout {
-  int R, X, V, A, F, IC, E, M, r, AT, total;
+  int R, X, V, A, F, IC, E, M, r, AT, SN, total;
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
     L.R = 0;
@@ -97,11 +99,13 @@ struct WsLayout {
     L.M = L.E + 3 * nv;
     L.r = L.M + nm;
     L.AT = L.r + nv;
-    L.total = L.AT + 8 * na;
+    L.SN = L.AT + 8 * na;  // per body: 1 when on a snapped sub-tree
+    L.total = L.SN + nb;
     return L;
   }
 };
 
+constexpr size_t kSmemLimitBytes = 226 * 1024;  // dynamic shared memory per block we use at most
 constexpr int kMaxDepth = 63;  // DOF depth limit (pair table size)
 constexpr int kPairCount = (kMaxDepth + 1) * (kMaxDepth + 2) / 2;
 

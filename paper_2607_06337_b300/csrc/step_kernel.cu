@@ -182,6 +182,20 @@ HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
   return f;
 }
 
+// Joint gains of this step: a broken joint has no spring and keeps the torn-fibre friction,
+// a damper growing from kd to (1 + ramp_gain) kd over the ramp time (Sec. IV-B).
+HD void joint_gains(const DevState& s, const StepArgs& a, int gb, float4 P3, int t_abs, float* k, float* kd) {
+  if (!s.broken[gb]) {
+    *k = P3.z;
+    *kd = P3.w;
+    return;
+  }
+  const float since = (float)(t_abs - s.break_step[gb]);
+  const float ramp = a.ramp_inv > 0.f ? fminf(since * a.ramp_inv, 1.f) : 1.f;
+  *k = 0.f;
+  *kd = (1.f + a.ramp_gain * ramp) * P3.w;
+}
+
 // Phase 1 for one body: kinematics, velocities, bias acceleration, own force, apple loads.
 HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
                                              const WorldView& v, const WsLayout& L, float* ws, int b,
@@ -228,6 +242,9 @@ HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
   }
   stm(ws + L.R + 9 * b, R);
   st3(ws + L.X + 3 * b, xb);
+  // on a snapped sub-tree (this joint or one above broken): applied forces disabled (App. B)
+  const bool snapped = s.broken[gb] || (p >= 0 && ws[L.SN + p] != 0.f);
+  ws[L.SN + b] = snapped ? 1.f : 0.f;
   st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vin);
   st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
 
@@ -284,15 +301,17 @@ HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
       const f3 fr = (-1.f) * (fs + ma * g);
       const float nfr = sqrtf(dot(fr, fr));
       const float fc = a.clamp * fdet;
-      if (nfr > fc) {
-        fapp = (fc / nfr) * fr;
+      if (snapped) {
+        // debris: no reaction on the tree; the stem still acts on the apple
       } else if (a.tether_implicit) {
+        // the clamp scales the coupled reaction, force and stiffness alike
+        const float sc = nfr > fc ? fc / nfr : 1.f;
         beta = dt * dt * ks / D;
-        kappa = ks * (1.f - beta);
+        kappa = sc * ks * (1.f - beta);
         const f3 vh = vin + cross(w, rh);
-        fapp = fr + (dt * ks) * avec - (dt * kappa) * vh;
+        fapp = sc * (fr + (dt * ks) * avec) - (dt * kappa) * vh;
       } else {
-        fapp = fr;
+        fapp = nfr > fc ? (fc / nfr) * fr : fr;
       }
     }
     n = n - cross(rh, fapp);
@@ -308,7 +327,7 @@ HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
 
 // Phase 2 for one body: pull children, bias and right-hand side of its DOFs.
 HD void backward_body(const DevModel& m, const DevState& s, const StepArgs& a,
-                                              const WorldView& v, const WsLayout& L, float* ws, int b) {
+                                              const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs) {
   const int gb = v.b0 + b;
   const int4 bi = m.bi[gb];
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
@@ -328,8 +347,8 @@ HD void backward_body(const DevModel& m, const DevState& s, const StepArgs& a,
   st_in(ws + L.IC + 10 * b, I);
   if (nd) {
     const float4 P3 = m.bp3[gb];
-    const bool on = !s.broken[gb];
-    const float k = on ? P3.z : 0.f, kd = on ? P3.w : 0.f;
+    float k, kd;
+    joint_gains(s, a, gb, P3, t_abs, &k, &kd);
     const float dt = a.dt, adt = a.alpha ? dt : 0.f;
     for (int j = 0; j < nd; ++j) {
       const int i = dof0 + j;
@@ -531,7 +550,7 @@ HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w
     // 2. leaf-to-root: forces and composite inertias, right-hand side
     for (int l = v.nL - 1; l >= 0; --l) {
       const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-      for (int b = lo + g.lane; b < hi; b += TPW) backward_body(m, s, a, v, L, ws, b);
+      for (int b = lo + g.lane; b < hi; b += TPW) backward_body(m, s, a, v, L, ws, b, t_abs);
       g.sync();
     }
     // 3. CRBA rows and the implicit diagonal
@@ -546,8 +565,8 @@ HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w
       float* row = ws + L.M + di.x;
       const unsigned short* an = m.anc + v.m0 + di.x;
       const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
-      const bool on = !s.broken[gb];
-      const float k = on ? P3.z : 0.f, kd = on ? P3.w : 0.f;
+      float k, kd;
+      joint_gains(s, a, gb, P3, t_abs, &k, &kd);
       row[0] = dot(e, n) + P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
       for (int c = 1; c <= di.z; ++c) {
         const int j = an[c];
@@ -645,7 +664,9 @@ cudaError_t kernel_attributes(int tpw, int groups_per_block, size_t smem_bytes, 
     case 256: fn = (const void*)rollout_kernel<256>; break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
+  // the attribute belongs to the instantiation, shared by every class using it: always the limit
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimitBytes);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, tpw * groups_per_block, smem_bytes);
 }

@@ -49,6 +49,8 @@ class Flags:
     n_tension: int = 10              # N_t: steps of tension > gamma f_det before detach
     gamma_tension: float = 1.2       # tension threshold factor (and reaction clamp factor)
     clamp_factor: float = 1.2        # reaction clamp F_clamp = clamp_factor * f_det
+    break_ramp_s: float = 1.5        # post-break friction surrogate: ramp time (s)
+    break_ramp_factor: float = 5.0   # ... from kd up to this multiple of kd
     fp64_twig_diam: float = 0.0      # joints thinner than this use float64 pivots (0: none)
 
 

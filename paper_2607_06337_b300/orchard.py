@@ -53,7 +53,8 @@ class TreeDesc(C.Structure):
 class ModelFlags(C.Structure):
     _fields_ = [("alpha_implicit_spring", C.c_int32), ("tether_implicit", C.c_int32),
                 ("n_break", C.c_int32), ("n_pull", C.c_int32), ("n_tension", C.c_int32),
-                ("gamma_tension", C.c_double), ("clamp_factor", C.c_double)]
+                ("gamma_tension", C.c_double), ("clamp_factor", C.c_double),
+                ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -175,7 +176,8 @@ def make_desc(forest, keep: _Keep) -> TreeDesc:
 
 def make_flags(flags) -> ModelFlags:
     return ModelFlags(int(flags.alpha_implicit_spring), int(flags.tether_implicit), int(flags.n_break),
-                      int(flags.n_pull), int(flags.n_tension), float(flags.gamma_tension), float(flags.clamp_factor))
+                      int(flags.n_pull), int(flags.n_tension), float(flags.gamma_tension), float(flags.clamp_factor),
+                      float(flags.break_ramp_s), float(flags.break_ramp_factor))
 
 
 # ------------------------------------------------------------------------------------------

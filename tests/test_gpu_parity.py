@@ -155,3 +155,24 @@ def _concat(forests):
         tip_local=cat("tip_local"), gravity=cat("gravity"), q0=cat("q0"), qd0=cat("qd0"),
         apple_x0=cat("apple_x0"), apple_v0=cat("apple_v0"), pull_force=cat("pull_force"),
         pull_start=cat("pull_start"), pull_end=cat("pull_end"))
+
+
+def test_classes_sharing_a_kernel_instantiation():
+    """Several size classes launched with the same threads-per-world (default schedules, then
+    one uniform schedule set through the ABI) must all run and agree with the oracle."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    f = I.make_forest(1, worlds=list(range(0, 96, 2)))
+    fl = I.Flags()
+    st, rec = O.rollout(f, fl, 30, near_eps=PAR.NEAR)
+    sim = B.Simulator(f, fl)
+    assert sim.counts.classes >= 2
+    for uniform in (False, True):
+        if uniform:
+            for k, sc in enumerate(sim.schedules()):
+                B.set_schedule(sim.model, k, B.Schedule(64, 1, 0, sc.global_workspace))
+        sim.reset()
+        sim.rollout(30)
+        torch.cuda.synchronize()
+        rep = PAR.compare(f, fl, _gpu_state(sim), st, rec["near"])
+        PAR.assert_parity(rep)

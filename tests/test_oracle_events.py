@@ -210,7 +210,7 @@ def test_broken_joint_swings_as_a_physical_pendulum():
     d, l = 0.01, 0.2
     m, com, inertia = I.cylinder(d, l, 700.0)
     down = (0.0, 1.0, 0.0, 0.0)  # 180 degrees about x: the segment hangs straight down
-    body = dict(parent=-1, ndof=1, qrel=down, mass=m, com=com, inertia=inertia, k=50.0, kd=0.3, m_max=1e30,
+    body = dict(parent=-1, ndof=1, qrel=down, mass=m, com=com, inertia=inertia, k=50.0, kd=0.0, m_max=1e30,
                 length=l, diam=d)
     f = I.from_bodies([body], gravity=(0.0, 0.0, -I.GRAVITY))
     f.q0[0] = 0.01
@@ -255,3 +255,35 @@ def test_energy_bounded_and_first_order_in_dt():
         errs.append(np.abs(Es - E0).max())
         assert errs[-1] < 0.05 * scale
     assert errs[0] / errs[1] == pytest.approx(2.0, rel=0.2)
+
+
+def test_post_break_friction_ramp():
+    """After a break the joint keeps only the torn-fibre friction, read as an implicit viscous
+    damper ramping from kd to 5 kd over 1.5 s (Sec. IV-B). A single broken hinge hanging under
+    gravity then follows the scalar recurrence (J + dt c_n) D = dt (-m g (l/2) sin q - c_n qd),
+    c_n = kd (1 + 4 min(n dt / 1.5, 1)), with n counted from the break step."""
+    d, l, kd = 0.01, 0.2, 2e-3
+    m, com, inertia = I.cylinder(d, l, 700.0)
+    down = (0.0, 1.0, 0.0, 0.0)
+    body = dict(parent=-1, ndof=1, qrel=down, mass=m, com=com, inertia=inertia, k=50.0, kd=kd, m_max=1e30,
+                length=l, diam=d)
+    f = I.from_bodies([body], gravity=(0.0, 0.0, -I.GRAVITY))
+    f.q0[0] = 0.5
+    st = O.OracleState.initial(f)
+    st.broken[:] = 1
+    st.break_step[:] = -100
+    fl = I.Flags(dt=2e-3)
+    n = 1200
+    _, rec = O.rollout(f, fl, n, state=st, record_q=True, n_threads=1)
+    J = inertia[0] + m * (l / 2) ** 2
+    q, qd = 0.5, 0.0
+    ref = []
+    for t in range(n):
+        c = kd * (1 + 4 * min((t + 100) * fl.dt / 1.5, 1.0))
+        tau = -m * I.GRAVITY * (l / 2) * math.sin(q)
+        D = fl.dt * (tau - c * qd) / (J + fl.dt * c)
+        qd += D
+        q += fl.dt * qd
+        ref.append(q)
+    np.testing.assert_allclose(rec["q"][:, 0], ref, atol=1e-12)
+    assert abs(ref[-1]) < 0.3  # the swing decays
