@@ -69,12 +69,13 @@ struct Packed {
   std::vector<int4> bi;
   std::vector<float4> bp0, bp1, bp2, bp3, bp4;
   std::vector<int4> dinfo;
-  std::vector<unsigned short> anc;
+  std::vector<unsigned> anc;
+  std::vector<int> dl_off, dl_bound;
+  std::vector<unsigned short> dl_list;
   std::vector<float4> ap0, ap1;
   std::vector<int> apple_body, tip_body;
   std::vector<float4> tip_local, gravity;
   std::vector<int> queue;
-  std::vector<unsigned char> pairs;
   std::vector<ClassInfo> classes;
 };
 
@@ -153,6 +154,9 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
   P.lvl.clear();
   P.dinfo.clear();
   P.anc.clear();
+  P.dl_off.assign(W + 1, 0);
+  P.dl_bound.clear();
+  P.dl_list.clear();
   std::vector<long long> ws(W);
   std::vector<double> cost(W);
   std::vector<int> wnb(W), wnv(W), wnm(W), wna(W);
@@ -181,7 +185,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
       nd[b] = k;
       nv += k;
     }
-    if (nv > 32767) return OT_ECAPACITY;
+    if (nv > 32767 || nb > 65535) return OT_ECAPACITY;
     // apples sorted by body
     std::vector<int> afirst(nb, 0), acount(nb, 0);
     for (int a = 0; a < na; ++a) {
@@ -226,12 +230,39 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
       P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], 0));
       int j = i;
       for (int c = 0; c <= ddep[i]; ++c) {
-        P.anc.push_back((unsigned short)j);
+        P.anc.push_back((unsigned)j | ((unsigned)dbody[j] << 16));
         j = dpar[j];
       }
       row += ddep[i] + 1;
     }
     const int nm = row;
+    // DOFs by depth, each depth in depth-first preorder (children in index order), so the
+    // DOFs of one depth below any given DOF are contiguous
+    {
+      std::vector<int> pre;
+      pre.reserve(nv);
+      std::vector<int> stack;
+      if (nb > 0) stack.push_back(0);
+      while (!stack.empty()) {
+        const int b = stack.back();
+        stack.pop_back();
+        for (int j = 0; j < nd[b]; ++j) pre.push_back(dof0[b] + j);
+        for (int c = ccount[b] - 1; c >= 0; --c) stack.push_back(cfirst[b] + c);
+      }
+      int maxd = -1;
+      for (int i = 0; i < nv; ++i) maxd = std::max(maxd, ddep[i]);
+      P.dl_off[w] = (int)P.dl_bound.size();
+      int pos = 0;
+      for (int l = 0; l <= maxd; ++l) {
+        P.dl_bound.push_back(pos);
+        for (int i : pre)
+          if (ddep[i] == l) {
+            P.dl_list.push_back((unsigned short)i);
+            ++pos;
+          }
+      }
+      P.dl_bound.push_back(pos);
+    }
     for (int b = 0; b < nb; ++b) {
       const int gb = b0 + b;
       if (cfirst[b] < 0) cfirst[b] = 0;
@@ -256,6 +287,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
   P.dof_off[W] = (int)P.dinfo.size();
   P.m_off[W] = (int)P.anc.size();
   P.lvl_off[W] = (int)P.lvl.size();
+  P.dl_off[W] = (int)P.dl_bound.size();
   P.NB = NB; P.NA = NA; P.NT = NT; P.NV = P.dof_off[W]; P.NM = P.m_off[W];
   if (P.NM > 0x7fffffffLL) return OT_ECAPACITY;
   // apples, tips, gravity
@@ -311,13 +343,6 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     P.classes.push_back(ci);
     i = j;
   }
-  // (c, c2) pair table
-  P.pairs.clear();
-  for (int c2 = 1; c2 <= kMaxDepth + 1; ++c2)
-    for (int c = 1; c <= c2; ++c) {
-      P.pairs.push_back((unsigned char)c);
-      P.pairs.push_back((unsigned char)c2);
-    }
   return OT_OK;
 }
 
@@ -356,8 +381,8 @@ namespace {
 
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
-  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, ap0,
-      ap1, apple_body, tip_body, tip_local, gravity, queue, pairs, total;
+  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, dl_off,
+      dl_bound, dl_list, ap0, ap1, apple_body, tip_body, tip_local, gravity, queue, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -371,14 +396,16 @@ ModelLayout model_layout(const Packed& P) {
   L.bp0 = c.take<float4>(P.NB); L.bp1 = c.take<float4>(P.NB); L.bp2 = c.take<float4>(P.NB);
   L.bp3 = c.take<float4>(P.NB); L.bp4 = c.take<float4>(P.NB);
   L.dinfo = c.take<int4>(P.NV);
-  L.anc = c.take<unsigned short>(P.NM);
+  L.anc = c.take<unsigned>(P.NM);
+  L.dl_off = c.take<int>(W1);
+  L.dl_bound = c.take<int>(P.dl_bound.size());
+  L.dl_list = c.take<unsigned short>(P.dl_list.size());
   L.ap0 = c.take<float4>(P.NA); L.ap1 = c.take<float4>(P.NA);
   L.apple_body = c.take<int>(P.NA);
   L.tip_body = c.take<int>(P.NT);
   L.tip_local = c.take<float4>(P.NT);
   L.gravity = c.take<float4>(P.W);
   L.queue = c.take<int>(P.W);
-  L.pairs = c.take<unsigned char>(P.pairs.size());
   L.total = c.off;
   return L;
 }
@@ -582,13 +609,15 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.bp4, P.bp4.data(), vbytes(P.bp4));
   put(L.dinfo, P.dinfo.data(), vbytes(P.dinfo));
   put(L.anc, P.anc.data(), vbytes(P.anc));
+  put(L.dl_off, P.dl_off.data(), vbytes(P.dl_off));
+  put(L.dl_bound, P.dl_bound.data(), vbytes(P.dl_bound));
+  put(L.dl_list, P.dl_list.data(), vbytes(P.dl_list));
   put(L.ap0, P.ap0.data(), vbytes(P.ap0)); put(L.ap1, P.ap1.data(), vbytes(P.ap1));
   put(L.apple_body, P.apple_body.data(), vbytes(P.apple_body));
   put(L.tip_body, P.tip_body.data(), vbytes(P.tip_body));
   put(L.tip_local, P.tip_local.data(), vbytes(P.tip_local));
   put(L.gravity, P.gravity.data(), vbytes(P.gravity));
   put(L.queue, P.queue.data(), vbytes(P.queue));
-  put(L.pairs, P.pairs.data(), vbytes(P.pairs));
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dev_buf, host.data(), L.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -611,14 +640,16 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.bp2 = (const float4*)(base + L.bp2); dm.bp3 = (const float4*)(base + L.bp3);
   dm.bp4 = (const float4*)(base + L.bp4);
   dm.dinfo = (const int4*)(base + L.dinfo);
-  dm.anc = (const unsigned short*)(base + L.anc);
+  dm.anc = (const unsigned*)(base + L.anc);
+  dm.dl_off = (const int*)(base + L.dl_off);
+  dm.dl_bound = (const int*)(base + L.dl_bound);
+  dm.dl_list = (const unsigned short*)(base + L.dl_list);
   dm.ap0 = (const float4*)(base + L.ap0); dm.ap1 = (const float4*)(base + L.ap1);
   dm.apple_body = (const int*)(base + L.apple_body);
   dm.tip_body = (const int*)(base + L.tip_body);
   dm.tip_local = (const float4*)(base + L.tip_local);
   dm.gravity = (const float4*)(base + L.gravity);
   dm.queue = (const int*)(base + L.queue);
-  dm.pairs = (const unsigned char*)(base + L.pairs);
   *out = m;
   return OT_OK;
 }

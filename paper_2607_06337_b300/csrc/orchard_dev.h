@@ -28,7 +28,10 @@ struct DevModel {
   const float4* bp3;     // Iyy, Izz, k, kd
   const float4* bp4;     // armature, m_max, -, -
   const int4* dinfo;     // per DOF: row start (world-local), body, depth d_i, -
-  const unsigned short* anc;  // per row entry c of DOF i: world-local DOF id of its c-th ancestor
+  const unsigned* anc;   // per row entry c of DOF i: its c-th ancestor DOF j | (body of j) << 16
+  const int* dl_off;     // [W+1] start of the world's DOF-depth level boundaries in dl_bound
+  const int* dl_bound;   // world-local position in dl_list of each DOF depth's first DOF (+ end)
+  const unsigned short* dl_list;  // per world: DOFs sorted by (depth, depth-first preorder)
   const float4* ap0;     // hang point in the body frame (xyz), apple mass (w)
   const float4* ap1;     // k_s, c_s, f_detach, -
   const int* apple_body; // world-local body of each apple
@@ -36,7 +39,6 @@ struct DevModel {
   const float4* tip_local;
   const float4* gravity; // per world
   const int* queue;      // world ids sorted by (size class, cost descending)
-  const unsigned char* pairs;  // (c, c2) pairs 1 <= c <= c2 <= d, ordered by c2 then c
 };
 
 // State arrays in device memory (views into the caller's state buffer).
@@ -84,30 +86,34 @@ struct StepArgs {
   int global_ws;            // 1: workspace in DevState::scratch, slot = global group index
 };
 
-// Workspace layout of one world (floats), a function of its sizes only.
+// Workspace layout of one world (floats), a function of its sizes only. Rotations, bias
+// accelerations and forces (live in the two sweeps) share space with the mass-matrix rows
+// (live from the mass matrix to the end of the step).
 struct WsLayout {
-  int R, X, V, A, F, IC, E, M, r, AT, SN, total;
+  int X, E, IC, r, AT, V, SN, R, A, F, M, total;
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
-    L.R = 0;
-    L.X = L.R + 9 * nb;
-    L.V = L.X + 3 * nb;
-    L.A = L.V + 6 * nb;
+    L.X = 0;                 // joint origins
+    L.E = L.X + 3 * nb;      // DOF axes
+    L.IC = L.E + 3 * nv;     // spatial (then composite) inertias about x_b
+    L.r = L.IC + 10 * nb;    // right-hand side, then the solution
+    L.AT = L.r + nv;         // per apple: velocity with the hang point frozen, beta, tension,
+                             // pull, hang offset r_h (10 floats)
+    L.V = L.AT + 10 * na;    // body velocities (start of step, then end of step)
+    L.SN = L.V + 6 * nb;     // 1 on a snapped sub-tree
+    const int u = L.SN + nb; // shared region
+    L.R = u;
+    L.A = L.R + 9 * nb;
     L.F = L.A + 6 * nb;
-    L.IC = L.F + 6 * nb;
-    L.E = L.IC + 10 * nb;
-    L.M = L.E + 3 * nv;
-    L.r = L.M + nm;
-    L.AT = L.r + nv;
-    L.SN = L.AT + 8 * na;  // per body: 1 when on a snapped sub-tree
-    L.total = L.SN + nb;
+    L.M = u;
+    const int end_sweeps = L.F + 6 * nb, end_m = L.M + nm;
+    L.total = end_sweeps > end_m ? end_sweeps : end_m;
     return L;
   }
 };
 
 constexpr size_t kSmemLimitBytes = 226 * 1024;  // dynamic shared memory per block we use at most
-constexpr int kMaxDepth = 63;  // DOF depth limit (pair table size)
-constexpr int kPairCount = (kMaxDepth + 1) * (kMaxDepth + 2) / 2;
+constexpr int kMaxDepth = 255;  // DOF depth limit
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);

@@ -161,7 +161,7 @@ struct Group {
 };
 
 struct WorldView {
-  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL;
+  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, DL0, nDL;
 };
 
 HD WorldView world_view(const DevModel& m, int w) {
@@ -172,6 +172,7 @@ HD WorldView world_view(const DevModel& m, int w) {
   v.t0 = m.tip_off[w]; v.nt = m.tip_off[w + 1] - v.t0;
   v.m0 = m.m_off[w]; v.nm = m.m_off[w + 1] - v.m0;
   v.L0 = m.lvl_off[w]; v.nL = m.lvl_off[w + 1] - v.L0 - 1;
+  v.DL0 = m.dl_off[w]; v.nDL = m.dl_off[w + 1] - v.DL0 - 1;
   return v;
 }
 
@@ -317,9 +318,10 @@ HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
     n = n - cross(rh, fapp);
     f = f - fapp;
     if (kappa > 0.f) add_point(I, dt * dt * kappa, rh);
-    float* at = ws + L.AT + 8 * ai;
+    float* at = ws + L.AT + 10 * ai;
     st3(at, avec);
     at[3] = beta; at[4] = T; at[5] = P;
+    st3(at + 6, rh);
   }
   st3(ws + L.F + 6 * b, n); st3(ws + L.F + 6 * b + 3, f);
   st_in(ws + L.IC + 10 * b, I);
@@ -383,9 +385,9 @@ HD void update_body(const DevModel& m, const DevState& s, const StepArgs& a,
     const int i = dof0 + j;
     const int4 di = m.dinfo[v.d0 + i];
     const float* row = ws + L.M + di.x;
-    const unsigned short* an = m.anc + v.m0 + di.x;
+    const unsigned* an = m.anc + v.m0 + di.x;
     float acc = 0.f;
-    for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], ws[L.r + an[c]], acc);
+    for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], ws[L.r + (an[c] & 0xffffu)], acc);
     const float x = ws[L.r + i] - acc / row[0];
     ws[L.r + i] = x;
     const float qd = s.qd[v.d0 + i] + x;
@@ -400,12 +402,11 @@ HD void update_body(const DevModel& m, const DevState& s, const StepArgs& a,
 
   const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
   if (acount) {
-    const m3 R = ldm(ws + L.R + 9 * b);
     for (int k = 0; k < acount; ++k) {
       const int ai = afirst + k, ga = v.a0 + ai;
-      const float* at = ws + L.AT + 8 * ai;
+      const float* at = ws + L.AT + 10 * ai;
       const bool det = s.detached[ga] != 0;
-      const f3 rh = mul(R, xyz(m.ap0[ga]));
+      const f3 rh = ld3(at + 6);
       const f3 vh = det ? mk(0, 0, 0) : vl + cross(w, rh);
       const f3 vn = ld3(at) + at[3] * vh;
       // attached: u' = u + dt (v' - v_hang'); detached: x' = x + dt v'
@@ -525,6 +526,108 @@ HD void record_tips(const DevModel& m, const StepArgs& a, const WorldView& v, co
   }
 }
 
+#ifdef __CUDA_ARCH__
+// Inclusive sum over the lanes [first, lane] of a warp (the lane's segment).
+__device__ __forceinline__ float seg_scan(float v, int lane, int first) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane - o >= first) v += t;
+  }
+  return v;
+}
+#endif
+
+// Tree-sparse LDL^T of H (rows kept unscaled, U = D L) and the L^T sweep of the solve.
+// All DOFs of one depth are eliminated together (their rows are final once every deeper DOF
+// is done, and none is an ancestor of another). A DOF k of depth l adds
+// -U_k[c] U_k[c2] / D_k to entry (anc_c(k), c2 - c) and -U_k[c] y_k / D_k to y of anc_c(k).
+// Listed in depth-first order, the DOFs of one depth that share their c-th ancestor are
+// contiguous, so each target's contributions are a segmented sum over consecutive lanes:
+// shuffle scans, deterministic, no atomics. The c values are split over the group's warps
+// (different c means different target rows). y_k / D_k is stored once the level is done.
+template <int TPW>
+HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, const Group<TPW>& g) {
+#ifdef __CUDA_ARCH__
+  constexpr int NW = TPW / 32;
+  const int warp = g.lane >> 5, lane = g.lane & 31;
+  for (int l = v.nDL - 1; l >= 0; --l) {
+    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+    if (l > 0) {
+      for (int base = lo; base < hi; base += 32) {
+        const int idx = base + lane;
+        const bool valid = idx < hi;
+        int rowk = 0;
+        float dinv = 0.f, yk = 0.f;
+        if (valid) {
+          const int k = m.dl_list[v.d0 + idx];
+          rowk = m.dinfo[v.d0 + k].x;
+          dinv = 1.f / ws[L.M + rowk];
+          yk = ws[L.r + k];
+        }
+        const float* row = ws + L.M + rowk;
+        const unsigned* an = m.anc + v.m0 + rowk;
+        for (int c = 1 + warp; c <= l; c += NW) {
+          const int key = valid ? (int)(an[c] & 0xffffu) : -1 - lane;
+          const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+          const int next = __shfl_down_sync(0xffffffffu, key, 1);
+          const bool head = lane == 0 || prev != key;
+          const bool tail = lane == 31 || next != key;
+          const unsigned heads = __ballot_sync(0xffffffffu, head);
+          const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+          const float uc = valid ? row[c] * dinv : 0.f;
+          const int trow = valid ? m.dinfo[v.d0 + key].x : 0;
+          const float sy = seg_scan(uc * yk, lane, first);
+          if (valid && tail) ws[L.r + key] -= sy;
+          for (int c2 = c; c2 <= l; ++c2) {
+            const float sm = seg_scan(valid ? uc * row[c2] : 0.f, lane, first);
+            if (valid && tail) ws[L.M + trow + (c2 - c)] -= sm;
+          }
+        }
+      }
+    }
+    g.sync();
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) {
+      const int k = m.dl_list[v.d0 + idx];
+      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
+    }
+  }
+  g.sync();
+#else
+  // one serial lane: the same updates, segment by segment in list order
+  for (int l = v.nDL - 1; l >= 0; --l) {
+    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+    for (int c = 1; c <= l; ++c) {
+      for (int c2 = c - 1; c2 <= l; ++c2) {  // c2 = c - 1 stands for the right-hand side
+        float acc = 0.f;
+        for (int idx = lo; idx < hi; ++idx) {
+          const int k = m.dl_list[v.d0 + idx];
+          const int rowk = m.dinfo[v.d0 + k].x;
+          const float* row = ws + L.M + rowk;
+          const int key = (int)(m.anc[v.m0 + rowk + c] & 0xffffu);
+          const float uc = row[c] / row[0];
+          acc += uc * (c2 < c ? ws[L.r + k] : row[c2]);
+          int next = -1;
+          if (idx + 1 < hi) {
+            const int k2 = m.dl_list[v.d0 + idx + 1];
+            next = (int)(m.anc[v.m0 + m.dinfo[v.d0 + k2].x + c] & 0xffffu);
+          }
+          if (next != key) {
+            if (c2 < c) ws[L.r + key] -= acc;
+            else ws[L.M + m.dinfo[v.d0 + key].x + (c2 - c)] -= acc;
+            acc = 0.f;
+          }
+        }
+      }
+    }
+    for (int idx = lo; idx < hi; ++idx) {
+      const int k = m.dl_list[v.d0 + idx];
+      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
+    }
+  }
+#endif
+}
+
 // All steps of one world.
 template <int TPW>
 HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w, float* ws,
@@ -563,38 +666,21 @@ HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w
       const f3 n = mul(I.I, e), f = cross(e, I.h);
       const f3 xb = ld3(ws + L.X + 3 * b);
       float* row = ws + L.M + di.x;
-      const unsigned short* an = m.anc + v.m0 + di.x;
+      const unsigned* an = m.anc + v.m0 + di.x;
       const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
       float k, kd;
       joint_gains(s, a, gb, P3, t_abs, &k, &kd);
       row[0] = dot(e, n) + P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
       for (int c = 1; c <= di.z; ++c) {
-        const int j = an[c];
-        const int bj = m.dinfo[v.d0 + j].y;
+        const unsigned ab = an[c];
+        const int j = ab & 0xffffu, bj = ab >> 16;
         const f3 lev = xb - ld3(ws + L.X + 3 * bj);
         row[c] = dot(ld3(ws + L.E + 3 * j), n + cross(lev, f));
       }
     }
     g.sync();
-    // 4. LDL^T, leaves to root, with the L^T sweep of the solve
-    for (int k = v.nv - 1; k >= 0; --k) {
-      const int4 dk = m.dinfo[v.d0 + k];
-      const float* row = ws + L.M + dk.x;
-      const unsigned short* an = m.anc + v.m0 + dk.x;
-      const float inv = 1.f / row[0];
-      const int np = dk.z * (dk.z + 1) / 2;
-      for (int pi = g.lane; pi < np; pi += TPW) {
-        const int c = m.pairs[2 * pi], c2 = m.pairs[2 * pi + 1];
-        const int j = an[c];
-        const int rj = m.dinfo[v.d0 + j].x;
-        ws[L.M + rj + (c2 - c)] -= row[c] * inv * row[c2];
-      }
-      const float rk = ws[L.r + k] * inv;
-      for (int c = 1 + g.lane; c <= dk.z; c += TPW) ws[L.r + an[c]] -= row[c] * rk;
-      g.sync();
-    }
-    for (int i = g.lane; i < v.nv; i += TPW) ws[L.r + i] /= ws[L.M + m.dinfo[v.d0 + i].x];
-    g.sync();
+    // 4. LDL^T by DOF depth, deepest first, with the L^T sweep of the solve
+    factor_levels<TPW>(m, v, L, ws, g);
     // 5. root-to-leaf: L sweep, update, velocities, apples, events
     for (int l = 0; l < v.nL; ++l) {
       const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
