@@ -415,6 +415,14 @@ struct StateLayout {
   std::vector<size_t> scratch;
 };
 
+// Workspace slots of a class in the state's scratch area: classes in shared memory keep one
+// (for the plain form); global-workspace classes get four per SM, or one per SM for worlds
+// whose temporaries exceed 2 MB.
+size_t scratch_slots(const ot_model* m, const ClassInfo& ci) {
+  if (!ci.sched.global_workspace) return 1;
+  return (size_t)m->n_sm * ((size_t)ci.ws_floats * 4 > (2u << 20) ? 1 : 4);
+}
+
 StateLayout state_layout(const ot_model* m) {
   const Packed& P = m->P;
   Carver c;
@@ -429,10 +437,7 @@ StateLayout state_layout(const ot_model* m) {
   // scratch: every class may run with global workspace; size for the slots its schedule can
   // have (global classes: 4 blocks of one world per SM; the plain form uses slot 0)
   size_t total_scratch_floats = 0;
-  for (const ClassInfo& ci : P.classes) {
-    size_t slots = ci.sched.global_workspace ? (size_t)m->n_sm * 4 : 1;
-    total_scratch_floats += slots * (size_t)ci.ws_floats;
-  }
+  for (const ClassInfo& ci : P.classes) total_scratch_floats += scratch_slots(m, ci) * (size_t)ci.ws_floats;
   L.scratch.push_back(c.take<float>(total_scratch_floats));
   L.total = c.off;
   return L;
@@ -442,7 +447,7 @@ size_t class_scratch_offset(const ot_model* m, int k, int* slots) {
   size_t off = 0;
   for (int i = 0; i < (int)m->P.classes.size(); ++i) {
     const ClassInfo& ci = m->P.classes[i];
-    size_t s = ci.sched.global_workspace ? (size_t)m->n_sm * 4 : 1;
+    size_t s = scratch_slots(m, ci);
     if (i == k) {
       *slots = (int)s;
       return off;
@@ -900,7 +905,8 @@ ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
   // a class's global-workspace setting is fixed at upload (it sizes the state's scratch)
   if (sc->global_workspace != ci.sched.global_workspace) return OT_EINVAL;
   if (!sc->global_workspace && (size_t)ci.ws_floats * 4 * sc->worlds_per_block > kSmemLimit) return OT_EINVAL;
-  if (sc->global_workspace && sc->worlds_per_block * std::max(sc->blocks, 1) > m->n_sm * 4) return OT_EINVAL;
+  if (sc->global_workspace && (size_t)sc->worlds_per_block * std::max(sc->blocks, 1) > scratch_slots(m, ci))
+    return OT_EINVAL;
   m->P.classes[k].sched = *sc;
   return OT_OK;
 }
