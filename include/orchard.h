@@ -234,6 +234,27 @@ ot_status ot_set_schedule(ot_model* model, int32_t size_class, const ot_schedule
 ot_status ot_autotune(ot_model* model, ot_state* state, int32_t n_steps, double dt, void* stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Allocation-free step (the paper has no counterpart; this is a library convenience).
+ * ot_step_static_scratch does what ot_step does, but the per-world temporaries of the step
+ * live in a fixed array compiled into the library instead of the state's scratch area, so a
+ * caller that cannot allocate device memory while it steps (a control loop that must not
+ * stall or fail on an allocation mid-run, or a host program with a fixed device-memory
+ * budget that only holds the model and state buffers) needs nothing more. The caller still
+ * passes the model, the state, the forces and the stream.
+ *   - Size: OT_STATIC_SCRATCH_BYTES per GPU, held from library load until process exit. A
+ *     world whose temporaries exceed it (minus 256 bytes of counters) is rejected with
+ *     OT_ECAPACITY before any work is queued.
+ *   - The array's device address is looked up with cudaGetSymbolAddress on the first call on
+ *     each device (with that device current); make that first call outside any stream capture.
+ *   - Every call uses the same array and leaves its contents behind; the call clears what must
+ *     start at zero. Calls that overlap on the GPU (other streams, other host threads) race:
+ *     serialise them.
+ *   - No device memory is allocated or freed. */
+#define OT_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ot_status ot_step_static_scratch(ot_model* model, ot_state* state, const float* ext_force,
+                                 const ot_force_schedule* pulls, int32_t step, double dt, void* stream);
+
+/* ---------------------------------------------------------------------------------------
  * Diagnostics. */
 const char* ot_status_string(ot_status s);
 int32_t ot_last_cuda_error(void);

@@ -970,3 +970,53 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Helpers of ot_step_static_scratch (static_scratch.cu): the per-class launch of one step with
+// the workspace in memory the caller of these helpers provides.
+// ------------------------------------------------------------------------------------------
+namespace orchard {
+
+ot_status static_step_plan(const ot_model* m, int* n_classes, size_t* max_ws_floats) {
+  if (!m || !n_classes || !max_ws_floats) return OT_EINVAL;
+  *n_classes = (int)m->P.classes.size();
+  *max_ws_floats = 0;
+  for (const ClassInfo& ci : m->P.classes) *max_ws_floats = std::max(*max_ws_floats, (size_t)ci.ws_floats);
+  return OT_OK;
+}
+
+ot_status static_step_class(ot_model* m, ot_state* s, int k, const float* ext_force, const ot_force_schedule* pulls,
+                            int32_t step, double dt, float* scratch, size_t scratch_floats, int* counter,
+                            void* stream) {
+  if (!m || !s || s->model != m || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  const ClassInfo& ci = m->P.classes[k];
+  const ot_schedule& sc = ci.sched;
+  if ((size_t)ci.ws_floats > scratch_floats) return OT_ECAPACITY;  // one world does not fit
+  const long long slots = (long long)(scratch_floats / (size_t)ci.ws_floats);
+  StepArgs a = base_args(m, dt);
+  a.step0 = step;
+  a.n_steps = 1;
+  a.ext_force = ext_force;
+  ot_status st = fill_pulls(a, pulls);
+  if (st != OT_OK) return st;
+  a.q_begin = ci.q_begin;
+  a.q_end = ci.q_end;
+  a.q_counter = counter;
+  a.ws_floats = ci.ws_floats;
+  a.global_ws = 1;
+  int bps = 0;
+  OT_CUDA(kernel_attributes(sc.threads_per_world, sc.worlds_per_block, 1, &bps));
+  if (bps < 1) return OT_ECAPACITY;
+  const int worlds = ci.q_end - ci.q_begin;
+  long long blocks = std::min<long long>((long long)bps * m->n_sm, (worlds + sc.worlds_per_block - 1) / sc.worlds_per_block);
+  blocks = std::min<long long>(blocks, slots / sc.worlds_per_block);
+  if (blocks < 1) return OT_ECAPACITY;
+  DevState ds = s->dev;
+  ds.scratch = scratch;
+  launch_rollout(sc.threads_per_world, sc.worlds_per_block, (int)blocks, 0, (cudaStream_t)stream, m->dev, ds, a);
+  OT_CUDA(cudaGetLastError());
+  g_launches += 1;
+  return OT_OK;
+}
+
+}  // namespace orchard

@@ -115,6 +115,19 @@ struct WsLayout {
 constexpr size_t kSmemLimitBytes = 226 * 1024;  // dynamic shared memory per block we use at most
 constexpr int kMaxDepth = 255;  // DOF depth limit
 
+}  // namespace orchard
+
+struct ot_model;
+struct ot_state;
+struct ot_force_schedule;
+
+namespace orchard {
+
+// One step of size class k with its workspace in `scratch` (used by the static-scratch entry).
+int static_step_plan(const ot_model* m, int* n_classes, size_t* max_ws_floats);
+int static_step_class(ot_model* m, ot_state* s, int k, const float* ext_force, const ot_force_schedule* pulls,
+                      int step, double dt, float* scratch, size_t scratch_floats, int* counter, void* stream);
+
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);
 cudaError_t kernel_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);

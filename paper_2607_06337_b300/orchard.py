@@ -111,6 +111,8 @@ _SIGS = {
     "ot_get_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
+    "ot_step_static_scratch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ForceSchedule), C.c_int32,
+                                         C.c_double, C.c_void_p]),
     "ot_status_string": (C.c_char_p, [C.c_int]),
     "ot_last_cuda_error": (C.c_int32, []),
     "ot_launch_count": (C.c_int64, [C.c_int32]),
