@@ -387,6 +387,7 @@ HD void update_body(const DevModel& m, const DevState& s, const StepArgs& a,
     const float* row = ws + L.M + di.x;
     const unsigned* an = m.anc + v.m0 + di.x;
     float acc = 0.f;
+#pragma unroll 4
     for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], ws[L.r + (an[c] & 0xffffu)], acc);
     const float x = ws[L.r + i] - acc / row[0];
     ws[L.r + i] = x;
@@ -527,14 +528,21 @@ HD void record_tips(const DevModel& m, const StepArgs& a, const WorldView& v, co
 }
 
 #ifdef __CUDA_ARCH__
-// Inclusive sum over the lanes [first, lane] of a warp (the lane's segment).
-__device__ __forceinline__ float seg_scan(float v, int lane, int first) {
+// Four independent segmented scans interleaved, so their shuffle latencies overlap.
+__device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d, int lane, int first) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const float t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane - o >= first) v += t;
+    const float ta = __shfl_up_sync(0xffffffffu, a, o);
+    const float tb = __shfl_up_sync(0xffffffffu, b, o);
+    const float tc = __shfl_up_sync(0xffffffffu, c, o);
+    const float td = __shfl_up_sync(0xffffffffu, d, o);
+    if (lane - o >= first) {
+      a += ta;
+      b += tb;
+      c += tc;
+      d += td;
+    }
   }
-  return v;
 }
 #endif
 
@@ -577,11 +585,31 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
           const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
           const float uc = valid ? row[c] * dinv : 0.f;
           const int trow = valid ? m.dinfo[v.d0 + key].x : 0;
-          const float sy = seg_scan(uc * yk, lane, first);
-          if (valid && tail) ws[L.r + key] -= sy;
-          for (int c2 = c; c2 <= l; ++c2) {
-            const float sm = seg_scan(valid ? uc * row[c2] : 0.f, lane, first);
-            if (valid && tail) ws[L.M + trow + (c2 - c)] -= sm;
+          float* tgt = ws + L.M + trow - c;  // entry (anc_c(k), c2 - c) is tgt[c2]
+          int c2 = c;
+          for (; c2 + 4 <= l + 1; c2 += 4) {
+            float s0 = valid ? uc * row[c2] : 0.f, s1 = valid ? uc * row[c2 + 1] : 0.f;
+            float s2 = valid ? uc * row[c2 + 2] : 0.f, s3 = valid ? uc * row[c2 + 3] : 0.f;
+            seg_scan4(s0, s1, s2, s3, lane, first);
+            if (valid && tail) {
+              tgt[c2] -= s0;
+              tgt[c2 + 1] -= s1;
+              tgt[c2 + 2] -= s2;
+              tgt[c2 + 3] -= s3;
+            }
+          }
+          // the last up-to-three entries of the row together with the right-hand side
+          const int rem = l + 1 - c2;
+          float s0 = valid && rem > 0 ? uc * row[c2] : 0.f;
+          float s1 = valid && rem > 1 ? uc * row[c2 + 1] : 0.f;
+          float s2 = valid && rem > 2 ? uc * row[c2 + 2] : 0.f;
+          float sy = uc * yk;
+          seg_scan4(s0, s1, s2, sy, lane, first);
+          if (valid && tail) {
+            if (rem > 0) tgt[c2] -= s0;
+            if (rem > 1) tgt[c2 + 1] -= s1;
+            if (rem > 2) tgt[c2 + 2] -= s2;
+            ws[L.r + key] -= sy;
           }
         }
       }
@@ -671,6 +699,7 @@ HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w
       float k, kd;
       joint_gains(s, a, gb, P3, t_abs, &k, &kd);
       row[0] = dot(e, n) + P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
+#pragma unroll 4
       for (int c = 1; c <= di.z; ++c) {
         const unsigned ab = an[c];
         const int j = ab & 0xffffu, bj = ab >> 16;
