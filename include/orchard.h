@@ -209,20 +209,26 @@ ot_status ot_rollout_plain(ot_model* model, ot_state* state, int32_t n_steps, in
                            const ot_force_schedule* pulls, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * Adjoint of a recorded rollout with the break and detach masks frozen as recorded.
- * Loss L = sum_t sum_tips |p_t - target_t|^2 / (n_steps * n_tips_of_world) per world; the
- * caller gives dL/dtips [n_steps][n_tips][3] (device). Gradients (device, accumulated into,
- * any may be NULL): dk, dkd [nb] per joint; dq0, dqd0 [n_dofs] of the initial state.
- * Segments between checkpoints are recomputed forward, then swept in reverse. */
+ * Adjoint of a recorded rollout with the break and detach masks frozen as recorded (the
+ * gradient the spec differentiation pattern asks for; the paper never differentiates).
+ * The forward must have been run by ot_rollout with the same model, n_steps, step0, dt and
+ * pulls, and a record holding checkpoints (ckpt, ckpt_every). The caller gives the cotangent
+ * of the recorded tips, dL_dtips [n_steps][n_tips][3] (device); for the tip-tracking loss
+ * L = sum_t sum_tips |p_t - p*_t|^2 / (n_steps n_tips_of_world) it is 2 (p - p*) / (...).
+ * Gradients (device, any may be NULL): dk, dkd [nb] per joint are ACCUMULATED into; dq0,
+ * dqd0 [n_dofs] (the initial state) are written. Each segment between checkpoints is
+ * recomputed forward (bitwise as in the forward) and then swept in reverse step by step.
+ * workspace: device buffer of at least ot_backward_workspace_bytes bytes (256-byte aligned). */
 typedef struct ot_grads {
   float* dk;
   float* dkd;
   float* dq0;
   float* dqd0;
 } ot_grads;
+ot_status ot_backward_workspace_bytes(const ot_model* model, int32_t ckpt_every, size_t* bytes);
 ot_status ot_rollout_backward(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
                               const ot_force_schedule* pulls, const ot_record* record, const float* dL_dtips,
-                              ot_grads* grads, void* stream);
+                              ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Schedules and autotuning. Size classes are formed at upload from the world sizes.

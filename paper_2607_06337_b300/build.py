@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC_DIR = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "liborchard.so")
-SOURCES = ["step_kernel.cu", "orchard_abi.cu", "static_scratch.cu"]
+SOURCES = ["step_kernel.cu", "adjoint_kernel.cu", "orchard_abi.cu", "static_scratch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

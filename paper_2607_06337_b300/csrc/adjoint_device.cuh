@@ -1,0 +1,795 @@
+// Adjoint of the batched compliant-tree step (device code, also compilable for the host as a
+// serial group). Masks (breaks, detachments) are frozen as the forward recorded them.
+//
+// One step maps (q, qd, u, v) to (q', qd', u', v') through Delta = H^-1 r, qd' = qd + Delta,
+// q' = q + dt qd', and the coupled apple update. With Delta-bar the cotangent of Delta and
+// lambda = H^-1 Delta-bar, the cotangents of the step inputs are the direct terms of the update
+// equations plus the gradient, with Delta held fixed, of
+//   psi = lambda^T (r - H Delta)
+//       = -dt sum_i lambda_i [k'_i (q_i + alpha dt qd'_i) + kd'_i qd'_i]
+//         - dt lambda^T ID(q, qd, Delta / dt)
+//         + dt sum_apples [ w_a . P0_a - dt kappa_a w_a . v_hang'_a ],
+// where ID is the inverse dynamics (inertia, velocity products, gravity), w_a = J_h lambda is
+// the virtual velocity of the hang point and P0_a the clamped reaction of the coupled tether.
+// lambda^T ID = sum_b Lambda_b . F_b (virtual work of each body's Newton-Euler force under the
+// virtual velocity Lambda_b of lambda), so the q and qd gradients come from one reverse sweep
+// over a per-body tape of the forward kinematics, velocities, accelerations and the virtual
+// velocities of lambda and of qd'. Tip cotangents enter as point loads at the configuration
+// they were recorded in.
+#pragma once
+#include "step_device.cuh"
+
+namespace orchard {
+namespace {
+
+HD float u2f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+
+// Backward workspace of one world (floats), after the forward workspace.
+struct AdjLayout {
+  int T;          // tape, 36 per body: R, x, w, v, alpha, a, Lw, Lv, Ow, Ov (see tape_body)
+  int C;          // 42 per body: cotangents a body sends to its parent's tape outputs (36),
+                  // plus the hang-velocity channel of Ow, Ov (6; it feeds q, not qd)
+  int AF;         // 6 per body: force sweep accumulator
+  int qb, qdb;    // per DOF: cotangents of the step-start q, qd being built
+  int qb1, qdb1;  // per DOF: cotangents of the step-end q', qd'
+  int lam;        // per DOF: lambda (first Delta-bar)
+  int qd1;        // per DOF: qd' of the step being reversed
+  int zero;       // per DOF: zeros
+  int ub, vb;     // per apple x3: cotangents of the step-start u (or x), v
+  int ub1, vb1;   // per apple x3: of the step-end u', v'
+  int vh;         // per apple x3: cotangent of the new hang-point velocity
+  int ps;         // private state floats: q, qd (nv), ax, av (3 na)
+  int pi;         // private state ints: broken, bcnt, break_step (nb), detached, pcnt, tcnt,
+                  // detach_step (na), status (1)
+  int seg;        // snapshots of the private state at the start of each step of a segment
+  int snap;       // words per snapshot
+  int total;
+  HD static AdjLayout make(int fwd_total, int nb, int nv, int na, int seg_len) {
+    AdjLayout A;
+    int o = fwd_total;
+    A.T = o; o += 36 * nb;
+    A.C = o; o += 42 * nb;
+    A.AF = o; o += 6 * nb;
+    A.qb = o; o += nv;
+    A.qdb = o; o += nv;
+    A.qb1 = o; o += nv;
+    A.qdb1 = o; o += nv;
+    A.lam = o; o += nv;
+    A.qd1 = o; o += nv;
+    A.zero = o; o += nv;
+    A.ub = o; o += 3 * na;
+    A.vb = o; o += 3 * na;
+    A.ub1 = o; o += 3 * na;
+    A.vb1 = o; o += 3 * na;
+    A.vh = o; o += 3 * na;
+    A.ps = o; o += 2 * nv + 6 * na;
+    A.pi = o; o += 3 * nb + 4 * na + 1;
+    A.snap = 2 * nv + 6 * na + 3 * nb + 4 * na + 1;
+    A.seg = o; o += seg_len * A.snap;
+    A.total = o;
+    return A;
+  }
+};
+
+HD WState private_state(float* ws, const AdjLayout& A, int nb, int nv, int na) {
+  WState s;
+  float* f = ws + A.ps;
+  s.q = f; s.qd = f + nv; s.ax = f + 2 * nv; s.av = f + 2 * nv + 3 * na;
+  int* i = (int*)(ws + A.pi);
+  s.broken = i; s.bcnt = i + nb; s.break_step = i + 2 * nb;
+  s.detached = i + 3 * nb; s.pcnt = s.detached + na; s.tcnt = s.pcnt + na; s.detach_step = s.tcnt + na;
+  s.status = (unsigned*)(s.detach_step + na);
+  return s;
+}
+
+// Copy the private state to or from snapshot `k` of the segment buffer (group-parallel).
+template <int TPW>
+HD void snapshot(float* ws, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
+  float* src = ws + A.ps;  // private floats and ints are contiguous: ps then pi
+  float* dst = ws + A.seg + (long long)k * A.snap;
+  for (int i = g.lane; i < A.snap; i += TPW) {
+    if (save) dst[i] = src[i];
+    else src[i] = dst[i];
+  }
+  g.sync();
+}
+
+// Load checkpoint `slot` of the forward record into the private state (its world's ranges).
+template <int TPW>
+HD void load_ckpt(const StepArgs& a, const WorldView& v, const WState& s, int slot, const Group<TPW>& g) {
+  const unsigned* base = a.ckpt + (long long)slot * a.ckpt_words;
+  const unsigned* q = base;
+  const unsigned* qd = q + a.NV;
+  const unsigned* ax = qd + a.NV;
+  const unsigned* av = ax + 3 * a.NA;
+  const unsigned* br = av + 3 * a.NA;
+  const unsigned* bc = br + a.NB;
+  const unsigned* bs = bc + a.NB;
+  const unsigned* de = bs + a.NB;
+  const unsigned* pc = de + a.NA;
+  const unsigned* tc = pc + a.NA;
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    s.q[i] = u2f(q[v.d0 + i]);
+    s.qd[i] = u2f(qd[v.d0 + i]);
+  }
+  for (int i = g.lane; i < 3 * v.na; i += TPW) {
+    s.ax[i] = u2f(ax[3 * v.a0 + i]);
+    s.av[i] = u2f(av[3 * v.a0 + i]);
+  }
+  for (int i = g.lane; i < v.nb; i += TPW) {
+    s.broken[i] = (int)br[v.b0 + i];
+    s.bcnt[i] = (int)bc[v.b0 + i];
+    s.break_step[i] = (int)bs[v.b0 + i];
+  }
+  for (int i = g.lane; i < v.na; i += TPW) {
+    s.detached[i] = (int)de[v.a0 + i];
+    s.pcnt[i] = (int)pc[v.a0 + i];
+    s.tcnt[i] = (int)tc[v.a0 + i];
+    s.detach_step[i] = -1;
+  }
+  if (g.lane == 0) *s.status = 0u;
+  g.sync();
+}
+
+// Tape of one body: forward kinematics at q, body velocity (w, v at x_b), full spatial
+// acceleration (alpha, a) with qdd = Delta / dt, and the virtual velocities of lambda (Lw, Lv)
+// and of qd' (Ow, Ov).
+HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const AdjLayout& A, float* ws,
+                  const float* delta, float inv_dt, const float* lam, const float* qd1, int b, f3 g) {
+  const int gb = v.b0 + b;
+  const int4 bi = m.bi[gb];
+  const int p = bi.x;
+  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+  m3 Rp;
+  f3 xp, wp, vp, alp, ap, lwp, lvp, owp, ovp;
+  if (p >= 0) {
+    const float* tp = ws + A.T + 36 * p;
+    Rp = ldm(tp);
+    xp = ld3(tp + 9); wp = ld3(tp + 12); vp = ld3(tp + 15); alp = ld3(tp + 18); ap = ld3(tp + 21);
+    lwp = ld3(tp + 24); lvp = ld3(tp + 27); owp = ld3(tp + 30); ovp = ld3(tp + 33);
+  } else {
+    Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
+    xp = wp = vp = alp = lwp = lvp = owp = ovp = mk(0, 0, 0);
+    ap = (-1.f) * g;
+  }
+  m3 R = mul(Rp, quat_mat(m.bp1[gb]));
+  const f3 xb = xp + mul(Rp, xyz(m.bp0[gb]));
+  const f3 d = xb - xp;
+  const f3 vin = vp + cross(wp, d), lvin = lvp + cross(lwp, d), ovin = ovp + cross(owp, d);
+  f3 w = wp, al = alp, aa = ap + cross(alp, d), lw = lwp, ow = owp;
+  for (int j = 0; j < nd; ++j) {
+    const int i = dof0 + j;
+    const f3 e = j == 0 ? R.c0 : R.c1;
+    al = al + s.qd[i] * cross(w, e) + (delta[i] * inv_dt) * e;
+    aa = aa + s.qd[i] * cross(vin, e);
+    w = w + s.qd[i] * e;
+    lw = lw + lam[i] * e;
+    ow = ow + qd1[i] * e;
+    float sn, cs;
+    sin_cos(s.q[i], &sn, &cs);
+    if (j == 0) {
+      const f3 c1 = cs * R.c1 + sn * R.c2, c2 = cs * R.c2 - sn * R.c1;
+      R.c1 = c1; R.c2 = c2;
+    } else {
+      const f3 c0 = cs * R.c0 - sn * R.c2, c2 = sn * R.c0 + cs * R.c2;
+      R.c0 = c0; R.c2 = c2;
+    }
+  }
+  float* t = ws + A.T + 36 * b;
+  stm(t, R);
+  st3(t + 9, xb); st3(t + 12, w); st3(t + 15, vin); st3(t + 18, al); st3(t + 21, aa);
+  st3(t + 24, lw); st3(t + 27, lvin); st3(t + 30, ow); st3(t + 33, ovin);
+}
+
+// Reverse of a 3x3 symmetric-product term: G accumulates d(phi)/d(Io) as a general matrix.
+struct g33 {
+  f3 c0, c1, c2;  // columns
+};
+HD void g_add_outer(g33& G, f3 u, f3 v) {  // G += u v^T
+  G.c0 = G.c0 + v.x * u; G.c1 = G.c1 + v.y * u; G.c2 = G.c2 + v.z * u;
+}
+HD f3 g_mulT_plus(const g33& G, f3 x) {  // (G + G^T) x
+  const f3 gx = x.x * G.c0 + x.y * G.c1 + x.z * G.c2;
+  const f3 gtx = mk(dot(G.c0, x), dot(G.c1, x), dot(G.c2, x));
+  return gx + gtx;
+}
+
+struct RevArgs {
+  int dyn;               // 1: include the step's dynamics terms; 0: only tip / point seeds
+  const float* delta;    // per DOF: the step's Delta
+  const float* lam;      // per DOF
+  const float* qd1;      // per DOF: qd'
+  const float* tipbar;   // [n_tips_total][3] cotangents of this configuration's tips, or null
+  float sphi;            // scale of the virtual-work term (-dt)
+};
+
+// Reverse of one body's tape (leaf-to-root): consumes the cotangents its children sent (C
+// slots) plus its own seeds, adds the q / qd cotangents of its DOFs, writes its C slot.
+HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v,
+                     const WsLayout& L, const AdjLayout& A, float* ws, const RevArgs& ra, int b, f3 g, int t_abs) {
+  const int gb = v.b0 + b;
+  const int4 bi = m.bi[gb];
+  const int p = bi.x;
+  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+  const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
+  const float dt = a.dt;
+  // cotangents of this body's tape outputs, summed over its children
+  float cb[42];
+  for (int k = 0; k < 42; ++k) cb[k] = 0.f;
+  for (int k = 0; k < ccount; ++k) {
+    const float* c = ws + A.C + 42 * (cfirst + k);
+    for (int j = 0; j < 42; ++j) cb[j] += c[j];
+  }
+  m3 Rb_ = {mk(cb[0], cb[1], cb[2]), mk(cb[3], cb[4], cb[5]), mk(cb[6], cb[7], cb[8])};
+  f3 xbb = mk(cb[9], cb[10], cb[11]), wb_ = mk(cb[12], cb[13], cb[14]), vb_ = mk(cb[15], cb[16], cb[17]);
+  f3 alb = mk(cb[18], cb[19], cb[20]), ab_ = mk(cb[21], cb[22], cb[23]), lwb = mk(cb[24], cb[25], cb[26]);
+  f3 lvb = mk(cb[27], cb[28], cb[29]), owb = mk(cb[30], cb[31], cb[32]), ovb = mk(cb[33], cb[34], cb[35]);
+  // cotangents of J_h qd' seen by the apple update: their qd' part is already in Delta-bar
+  // (hang_load_sweep), so this channel only reaches q (through the axes and hang offsets)
+  f3 owh = mk(cb[36], cb[37], cb[38]), ovh = mk(cb[39], cb[40], cb[41]);
+
+  // own forward values
+  const float* t = ws + A.T + 36 * b;
+  const m3 R = ldm(t);
+  const f3 w = ld3(t + 12), vin = ld3(t + 15), al = ld3(t + 18), aa = ld3(t + 21);
+  const f3 lw = ld3(t + 24), lv = ld3(t + 27), ow = ld3(t + 30), ov = ld3(t + 33);
+
+  // seeds: virtual work of the body's own Newton-Euler force
+  if (ra.dyn) {
+    const float4 P0 = m.bp0[gb], P2 = m.bp2[gb], P3 = m.bp3[gb];
+    const float mb = P0.w;
+    const f3 com = xyz(P2);
+    const float Di[3] = {P2.w, P3.x, P3.y};
+    const f3 r = mul(R, com);
+    const f3 h = mb * r;
+    sym3 Io;
+    {
+      const float rr = dot(r, r);
+      const f3 c0 = R.c0, c1 = R.c1, c2 = R.c2;
+      Io.xx = Di[0] * c0.x * c0.x + Di[1] * c1.x * c1.x + Di[2] * c2.x * c2.x + mb * (rr - r.x * r.x);
+      Io.yy = Di[0] * c0.y * c0.y + Di[1] * c1.y * c1.y + Di[2] * c2.y * c2.y + mb * (rr - r.y * r.y);
+      Io.zz = Di[0] * c0.z * c0.z + Di[1] * c1.z * c1.z + Di[2] * c2.z * c2.z + mb * (rr - r.z * r.z);
+      Io.xy = Di[0] * c0.x * c0.y + Di[1] * c1.x * c1.y + Di[2] * c2.x * c2.y - mb * r.x * r.y;
+      Io.xz = Di[0] * c0.x * c0.z + Di[1] * c1.x * c1.z + Di[2] * c2.x * c2.z - mb * r.x * r.z;
+      Io.yz = Di[0] * c0.y * c0.z + Di[1] * c1.y * c1.z + Di[2] * c2.y * c2.z - mb * r.y * r.z;
+    }
+    const f3 p2 = mul(Io, w) + cross(h, vin);
+    const f3 l2 = mb * vin - cross(h, w);
+    const f3 n = mul(Io, al) + cross(h, aa) + cross(w, p2) + cross(vin, l2);
+    const f3 f = mb * aa - cross(h, al) + cross(w, l2);
+    const float sp = ra.sphi;
+    lwb = lwb + sp * n;
+    lvb = lvb + sp * f;
+    const f3 nb = sp * lw, fb = sp * lv;
+    g33 G = {mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0)};
+    f3 hb = mk(0, 0, 0), p2b = mk(0, 0, 0), l2b = mk(0, 0, 0);
+    // n = Io al + h x aa + w x p2 + vin x l2
+    g_add_outer(G, nb, al);
+    alb = alb + mul(Io, nb);
+    hb = hb + cross(aa, nb);
+    ab_ = ab_ + cross(nb, h);
+    wb_ = wb_ + cross(p2, nb);
+    p2b = p2b + cross(nb, w);
+    vb_ = vb_ + cross(l2, nb);
+    l2b = l2b + cross(nb, vin);
+    // f = m aa - h x al + w x l2
+    ab_ = ab_ + mb * fb;
+    hb = hb - cross(al, fb);
+    alb = alb - cross(fb, h);
+    wb_ = wb_ + cross(l2, fb);
+    l2b = l2b + cross(fb, w);
+    // p2 = Io w + h x vin
+    g_add_outer(G, p2b, w);
+    wb_ = wb_ + mul(Io, p2b);
+    hb = hb + cross(vin, p2b);
+    vb_ = vb_ + cross(p2b, h);
+    // l2 = m vin - h x w
+    vb_ = vb_ + mb * l2b;
+    hb = hb - cross(w, l2b);
+    wb_ = wb_ - cross(l2b, h);
+    // Io = R D R^T + m (|r|^2 1 - r r^T), h = m r, r = R com
+    const float trG = G.c0.x + G.c1.y + G.c2.z;
+    const f3 rb = mb * hb + mb * (2.f * trG * r - g_mulT_plus(G, r));
+    Rb_.c0 = Rb_.c0 + com.x * rb + Di[0] * g_mulT_plus(G, R.c0);
+    Rb_.c1 = Rb_.c1 + com.y * rb + Di[1] * g_mulT_plus(G, R.c1);
+    Rb_.c2 = Rb_.c2 + com.z * rb + Di[2] * g_mulT_plus(G, R.c2);
+  }
+
+  // apples hanging from this body
+  const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
+  for (int k = 0; k < acount; ++k) {
+    const int ai = afirst + k, ga = v.a0 + ai;
+    const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
+    const f3 hl = xyz(A0);
+    const f3 rh = mul(R, hl);
+    f3 rhb = mk(0, 0, 0);
+    const int det = s.detached[ai];
+    if (ra.dyn && det == 0) {
+      // the new hang-point velocity seen by the apple update
+      const f3 vhb = ld3(ws + A.vh + 3 * ai);
+      ovh = ovh + vhb;
+      owh = owh + cross(rh, vhb);
+      rhb = rhb + cross(vhb, ow);
+      // the coupled reaction on the tree (unless on a snapped sub-tree or explicit mode)
+      const bool snapped = ws[L.SN + b] != 0.f;
+      if (!snapped) {
+        const float ma = A0.w, ks = A1.x, csd = A1.y, fdet = A1.z;
+        const f3 u = ld3(s.ax + 3 * ai), vv = ld3(s.av + 3 * ai);
+        const f3 fe = apple_force(a, ga, t_abs);
+        const float D = ma + dt * csd + dt * dt * ks;
+        const float beta = dt * dt * ks / D;
+        const f3 fr = ks * u - ma * g;
+        const f3 avec = (1.f / D) * (ma * vv + dt * (fe + ma * g - ks * u));
+        (void)beta;
+        const float nfr = sqrtf(dot(fr, fr)), fc = a.clamp * fdet;
+        const bool clamped = nfr > fc;
+        const float sc = clamped ? fc / nfr : 1.f;
+        const f3 wv = lv + cross(lw, rh);
+        f3 wbar, ubar, vbar;
+        if (a.tether_implicit) {
+          // psi_a = dt sc [ w.G - dt kap0 w.vh1 ], G = fr + dt k_s avec, kap0 = k_s (1 - beta)
+          const f3 G = fr + (dt * ks) * avec;
+          const float kap0 = ks * (1.f - beta);
+          const f3 vh1 = ov + cross(ow, rh);
+          wbar = (dt * sc) * (G - (dt * kap0) * vh1);
+          const f3 vh1b = (-dt * dt * sc * kap0) * wv;
+          ovb = ovb + vh1b;
+          owb = owb + cross(rh, vh1b);
+          rhb = rhb + cross(vh1b, ow);
+          const float psi_core = dot(wv, G) - dt * kap0 * dot(wv, vh1);
+          ubar = (dt * sc * kap0) * wv;
+          if (clamped) ubar = ubar + (dt * psi_core * (-sc * ks / (nfr * nfr))) * fr;
+          vbar = (dt * sc * dt * ks * ma / D) * wv;
+        } else {
+          // psi_a = dt w . (sc fr)
+          wbar = (dt * sc) * fr;
+          ubar = (dt * sc * ks) * wv;
+          if (clamped) ubar = ubar + (dt * dot(wv, fr) * (-sc * ks / (nfr * nfr))) * fr;
+          vbar = mk(0, 0, 0);
+        }
+        lvb = lvb + wbar;
+        lwb = lwb + cross(rh, wbar);
+        rhb = rhb + cross(wbar, lw);
+        float* ub = ws + A.ub + 3 * ai;
+        float* vb = ws + A.vb + 3 * ai;
+        st3(ub, ld3(ub) + ubar);
+        st3(vb, ld3(vb) + vbar);
+      }
+    }
+    if (ra.dyn && det == 2) {
+      // converted at this step's start: x = x_hang + u
+      const f3 xb_ = ld3(ws + A.ub + 3 * ai);  // cotangent of x (the step-start position)
+      xbb = xbb + xb_;
+      rhb = rhb + xb_;
+    }
+    Rb_.c0 = Rb_.c0 + hl.x * rhb;
+    Rb_.c1 = Rb_.c1 + hl.y * rhb;
+    Rb_.c2 = Rb_.c2 + hl.z * rhb;
+  }
+  // tips on this body
+  if (ra.tipbar) {
+    const int tr = m.btip[gb];
+    const int tfirst = tr & 0x00ffffff, tcount = (unsigned)tr >> 24;
+    for (int k = tfirst; k < tfirst + tcount; ++k) {
+      const f3 pb = ld3(ra.tipbar + 3 * (v.t0 + k));
+      const f3 tl = xyz(m.tip_local[v.t0 + k]);
+      xbb = xbb + pb;
+      Rb_.c0 = Rb_.c0 + tl.x * pb;
+      Rb_.c1 = Rb_.c1 + tl.y * pb;
+      Rb_.c2 = Rb_.c2 + tl.z * pb;
+    }
+  }
+
+  // reverse of the DOF loop: recompute its intermediates from the parent's tape
+  m3 Rp;
+  f3 wp, alp, lwp, owp;
+  if (p >= 0) {
+    const float* tp = ws + A.T + 36 * p;
+    Rp = ldm(tp);
+    wp = ld3(tp + 12); alp = ld3(tp + 18); lwp = ld3(tp + 24); owp = ld3(tp + 30);
+  } else {
+    Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
+    wp = alp = lwp = owp = mk(0, 0, 0);
+  }
+  const m3 Q = quat_mat(m.bp1[gb]);
+  m3 Rs[3];
+  f3 ws_[3];
+  Rs[0] = mul(Rp, Q);
+  ws_[0] = wp;
+  float sn_[2], cs_[2];
+  for (int j = 0; j < nd; ++j) {
+    const int i = dof0 + j;
+    const f3 e = j == 0 ? Rs[j].c0 : Rs[j].c1;
+    ws_[j + 1] = ws_[j] + s.qd[i] * e;
+    sin_cos(s.q[i], &sn_[j], &cs_[j]);
+    m3 Rn = Rs[j];
+    if (j == 0) {
+      Rn.c1 = cs_[j] * Rs[j].c1 + sn_[j] * Rs[j].c2;
+      Rn.c2 = cs_[j] * Rs[j].c2 - sn_[j] * Rs[j].c1;
+    } else {
+      Rn.c0 = cs_[j] * Rs[j].c0 - sn_[j] * Rs[j].c2;
+      Rn.c2 = sn_[j] * Rs[j].c0 + cs_[j] * Rs[j].c2;
+    }
+    Rs[j + 1] = Rn;
+  }
+  for (int j = nd - 1; j >= 0; --j) {
+    const int i = dof0 + j;
+    const m3& Rn = Rs[j + 1];
+    const m3& Ro = Rs[j];
+    // R_new = R_old Rot(q): rotation-angle cotangent and R_old cotangent
+    float qbar = 0.f;
+    m3 Rob = Rb_;
+    if (j == 0) {
+      qbar += dot(Rb_.c1, Rn.c2) - dot(Rb_.c2, Rn.c1);
+      Rob.c1 = cs_[j] * Rb_.c1 - sn_[j] * Rb_.c2;
+      Rob.c2 = sn_[j] * Rb_.c1 + cs_[j] * Rb_.c2;
+    } else {
+      qbar += -dot(Rb_.c0, Rn.c2) + dot(Rb_.c2, Rn.c0);
+      Rob.c0 = cs_[j] * Rb_.c0 + sn_[j] * Rb_.c2;
+      Rob.c2 = -sn_[j] * Rb_.c0 + cs_[j] * Rb_.c2;
+    }
+    Rb_ = Rob;
+    const f3 e = j == 0 ? Ro.c0 : Ro.c1;
+    const f3 wo = ws_[j];
+    const float qd = s.qd[i];
+    f3 eb = mk(0, 0, 0);
+    float qdbar = 0.f;
+    // alpha += qd (w x e) + qdd e ; a += qd (vin x e) ; w += qd e ; Lw += lam e ; Ow += qd1 e
+    if (ra.dyn) {
+      const float qdd = ra.delta[i] / dt;
+      qdbar += dot(alb, cross(wo, e));
+      wb_ = wb_ + qd * cross(e, alb);
+      eb = eb + qd * cross(alb, wo) + qdd * alb;
+      qdbar += dot(ab_, cross(vin, e));
+      vb_ = vb_ + qd * cross(e, ab_);
+      eb = eb + qd * cross(ab_, vin);
+      eb = eb + ra.lam[i] * lwb;
+    }
+    qdbar += dot(wb_, e);
+    eb = eb + qd * wb_;
+    qdbar += dot(owb, e);  // qd' = qd + Delta with Delta fixed
+    eb = eb + ra.qd1[i] * (owb + owh);
+    if (j == 0) Rb_.c0 = Rb_.c0 + eb;
+    else Rb_.c1 = Rb_.c1 + eb;
+    ws[A.qb + i] += qbar;
+    ws[A.qdb + i] += qdbar;
+  }
+  // prefix: R0 = Rp Q, xb = xp + Rp j, d = xb - xp, vin/ain/Lvin/Ovin shifts
+  const f3 jb = xyz(m.bp0[gb]);
+  const f3 d = mul(Rp, jb);
+  f3 db = mk(0, 0, 0);
+  // vin = vp + wp x d
+  f3 vpb = vb_, wpb = wb_ + cross(d, vb_);
+  db = db + cross(vb_, wp);
+  // ain = ap + alp x d (a starts at ain; alpha starts at alp)
+  f3 apb = ab_, alpb = alb + cross(d, ab_);
+  db = db + cross(ab_, alp);
+  // Lvin = Lvp + Lwp x d, Ovin = Ovp + Owp x d
+  f3 lvpb = lvb, lwpb = lwb + cross(d, lvb);
+  db = db + cross(lvb, lwp);
+  f3 ovpb = ovb, owpb = owb + cross(d, ovb);
+  db = db + cross(ovb, owp);
+  f3 ovph = ovh, owph = owh + cross(d, ovh);
+  db = db + cross(ovh, owp);
+  // d = Rp jb and xb = xp + d
+  f3 xpb = xbb;
+  db = db + xbb;
+  m3 Rpb;
+  Rpb.c0 = jb.x * db + (Q.c0.x * Rb_.c0 + Q.c1.x * Rb_.c1 + Q.c2.x * Rb_.c2);
+  Rpb.c1 = jb.y * db + (Q.c0.y * Rb_.c0 + Q.c1.y * Rb_.c1 + Q.c2.y * Rb_.c2);
+  Rpb.c2 = jb.z * db + (Q.c0.z * Rb_.c0 + Q.c1.z * Rb_.c1 + Q.c2.z * Rb_.c2);
+  float* c = ws + A.C + 42 * b;
+  stm(c, Rpb);
+  st3(c + 9, xpb); st3(c + 12, wpb); st3(c + 15, vpb); st3(c + 18, alpb); st3(c + 21, apb);
+  st3(c + 24, lwpb); st3(c + 27, lvpb); st3(c + 30, owpb); st3(c + 33, ovpb);
+  st3(c + 36, owph); st3(c + 39, ovph);
+}
+
+// L^T sweep, D scaling and L sweep of a solve with the step's factors (rows U = D L in M):
+// y <- H^-1 y, in place.
+template <int TPW>
+HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, float* y,
+                       const Group<TPW>& g) {
+#ifdef __CUDA_ARCH__
+  constexpr int NW = TPW / 32;
+  const int warp = g.lane >> 5, lane = g.lane & 31;
+  for (int l = v.nDL - 1; l >= 0; --l) {
+    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+    if (l > 0) {
+      for (int base = lo; base < hi; base += 32) {
+        const int idx = base + lane;
+        const bool valid = idx < hi;
+        int rowk = 0;
+        float dinv = 0.f, yk = 0.f;
+        if (valid) {
+          const int k = m.dl_list[v.d0 + idx];
+          rowk = m.dinfo[v.d0 + k].x;
+          dinv = 1.f / ws[L.M + rowk];
+          yk = y[k];
+        }
+        const float* row = ws + L.M + rowk;
+        const unsigned* an = m.anc + v.m0 + rowk;
+        for (int c = 1 + warp; c <= l; c += NW) {
+          const int key = valid ? (int)(an[c] & 0xffffu) : -1 - lane;
+          const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+          const int next = __shfl_down_sync(0xffffffffu, key, 1);
+          const bool head = lane == 0 || prev != key;
+          const bool tail = lane == 31 || next != key;
+          const unsigned heads = __ballot_sync(0xffffffffu, head);
+          const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+          float s0 = valid ? row[c] * dinv * yk : 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+          seg_scan4(s0, s1, s2, s3, lane, first);
+          if (valid && tail) y[key] -= s0;
+        }
+      }
+    }
+    g.sync();
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) {
+      const int k = m.dl_list[v.d0 + idx];
+      y[k] /= ws[L.M + m.dinfo[v.d0 + k].x];
+    }
+  }
+  g.sync();
+#else
+  for (int l = v.nDL - 1; l >= 0; --l) {
+    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+    for (int c = 1; c <= l; ++c) {
+      float acc = 0.f;
+      for (int idx = lo; idx < hi; ++idx) {
+        const int k = m.dl_list[v.d0 + idx];
+        const int rowk = m.dinfo[v.d0 + k].x;
+        const float* row = ws + L.M + rowk;
+        const int key = (int)(m.anc[v.m0 + rowk + c] & 0xffffu);
+        acc += row[c] / row[0] * y[k];
+        int next = -1;
+        if (idx + 1 < hi) {
+          const int k2 = m.dl_list[v.d0 + idx + 1];
+          next = (int)(m.anc[v.m0 + m.dinfo[v.d0 + k2].x + c] & 0xffffu);
+        }
+        if (next != key) {
+          y[key] -= acc;
+          acc = 0.f;
+        }
+      }
+    }
+    for (int idx = lo; idx < hi; ++idx) {
+      const int k = m.dl_list[v.d0 + idx];
+      y[k] /= ws[L.M + m.dinfo[v.d0 + k].x];
+    }
+  }
+#endif
+  // L sweep, root to leaf by body level
+  for (int l = 0; l < v.nL; ++l) {
+    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) {
+      const int4 bi = m.bi[v.b0 + b];
+      const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+      for (int j = 0; j < nd; ++j) {
+        const int i = dof0 + j;
+        const int4 di = m.dinfo[v.d0 + i];
+        const float* row = ws + L.M + di.x;
+        const unsigned* an = m.anc + v.m0 + di.x;
+        float acc = 0.f;
+        for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], y[an[c] & 0xffffu], acc);
+        y[i] -= acc / row[0];
+      }
+    }
+    g.sync();
+  }
+}
+
+// Leaf-to-root sweep of point loads at the apples' hang points (cotangents vh of the new
+// hang-point velocities): adds J_h^T vh to out (per DOF).
+template <int TPW>
+HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L,
+                        const AdjLayout& A, float* ws, float* out, const Group<TPW>& g) {
+  for (int l = v.nL - 1; l >= 0; --l) {
+    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) {
+      const int4 bi = m.bi[v.b0 + b];
+      const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+      const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
+      const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
+      f3 n = mk(0, 0, 0), f = mk(0, 0, 0);
+      const f3 xb = ld3(ws + L.X + 3 * b);
+      for (int k = 0; k < acount; ++k) {
+        const int ai = afirst + k;
+        if (s.detached[ai]) continue;
+        const f3 rh = ld3(ws + L.AT + 10 * ai + 6);
+        const f3 fv = ld3(ws + A.vh + 3 * ai);
+        n = n + cross(rh, fv);
+        f = f + fv;
+      }
+      for (int k = 0; k < ccount; ++k) {
+        const int c = cfirst + k;
+        const f3 sft = ld3(ws + L.X + 3 * c) - xb;
+        const f3 fc = ld3(ws + A.AF + 6 * c + 3);
+        n = n + ld3(ws + A.AF + 6 * c) + cross(sft, fc);
+        f = f + fc;
+      }
+      st3(ws + A.AF + 6 * b, n);
+      st3(ws + A.AF + 6 * b + 3, f);
+      for (int j = 0; j < nd; ++j) out[dof0 + j] += dot(ld3(ws + L.E + 3 * (dof0 + j)), n);
+    }
+    g.sync();
+  }
+}
+
+}  // namespace
+}  // namespace orchard
+
+namespace orchard {
+namespace {
+
+// Cotangents of one step (t) of one world: the private state holds the step's start state,
+// the forward workspace holds that step's recomputed forward (factors, Delta, apple data), and
+// A.qb1 / qdb1 / ub1 / vb1 hold the cotangents of its end state. Leaves the cotangents of its
+// start state in A.qb / qdb / ub / vb.
+template <int TPW>
+HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
+                     const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, const Group<TPW>& g,
+                     int t, f3 gv) {
+  const float dt = a.dt;
+  const int t_abs = a.step0 + t;
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    ws[A.qb + i] = ws[A.qb1 + i];                                  // q' = q + dt qd'
+    ws[A.lam + i] = ws[A.qdb1 + i] + dt * ws[A.qb1 + i];           // qd'-bar (first part)
+  }
+  // the apple update: u' = u + dt (v' - v_hang'), v' = a + beta v_hang' (attached), or
+  // x' = x + dt v', v' = v + dt (g + f / m) (detached)
+  for (int ai = g.lane; ai < v.na; ai += TPW) {
+    const int ga = v.a0 + ai;
+    const f3 u1b = ld3(ws + A.ub1 + 3 * ai), v1b = ld3(ws + A.vb1 + 3 * ai);
+    const f3 vtot = v1b + dt * u1b;
+    if (s.detached[ai] == 0) {
+      const float beta = ws[L.AT + 10 * ai + 3];
+      const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
+      const float ma = A0.w, ks = A1.x, csd = A1.y;
+      const float D = ma + dt * csd + dt * dt * ks;
+      st3(ws + A.vh + 3 * ai, beta * vtot - dt * u1b);
+      st3(ws + A.ub + 3 * ai, u1b - (dt * ks / D) * vtot);
+      st3(ws + A.vb + 3 * ai, (ma / D) * vtot);
+    } else {
+      st3(ws + A.vh + 3 * ai, mk(0, 0, 0));
+      st3(ws + A.ub + 3 * ai, u1b);
+      st3(ws + A.vb + 3 * ai, vtot);
+    }
+  }
+  g.sync();
+  hang_load_sweep<TPW>(m, s, v, L, A, ws, ws + A.lam, g);  // qd'-bar += J_h^T vh-bar
+  for (int i = g.lane; i < v.nv; i += TPW) ws[A.qdb + i] = ws[A.lam + i];  // qd' = qd + Delta
+  g.sync();
+  solve_factored<TPW>(m, v, L, ws, ws + A.lam, g);  // lambda = H^-1 Delta-bar
+  // springs and dampers (diagonal terms of r and H)
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    const int b = m.dinfo[v.d0 + i].y;
+    const int gb = v.b0 + b;
+    const float4 P3 = m.bp3[gb];
+    float k, kd;
+    joint_gains(s, a, b, P3, t_abs, &k, &kd);
+    const float lam = ws[A.lam + i];
+    const float adt = a.alpha ? dt : 0.f;
+    ws[A.qb + i] += -dt * k * lam;
+    ws[A.qdb + i] += -dt * (adt * k + kd) * lam;
+    const float kfac = s.broken[b] ? 0.f : 1.f;
+    const float kdfac = P3.w != 0.f ? kd / P3.w : 0.f;
+    // one writer per joint: the joint's first DOF adds both DOFs' terms
+    const int dof0 = m.bi[gb].y & 0x0fffffff, nd = (unsigned)m.bi[gb].y >> 28;
+    if (i == dof0) {
+      float sk = 0.f, skd = 0.f;
+      for (int j = 0; j < nd; ++j) {
+        const float lj = ws[A.lam + dof0 + j], qj = s.q[dof0 + j], q1j = ws[A.qd1 + dof0 + j];
+        sk += lj * (qj + adt * q1j);
+        skd += lj * q1j;
+      }
+      if (ba.dk) ba.dk[gb] += -dt * kfac * sk;
+      if (ba.dkd) ba.dkd[gb] += -dt * kdfac * skd;
+    }
+  }
+  g.sync();
+  // tape at the step start, then the reverse sweep
+  for (int l = 0; l < v.nL; ++l) {
+    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW)
+      tape_body(m, s, v, A, ws, ws + L.r, 1.f / dt, ws + A.lam, ws + A.qd1, b, gv);
+    g.sync();
+  }
+  RevArgs ra;
+  ra.dyn = 1;
+  ra.delta = ws + L.r;
+  ra.lam = ws + A.lam;
+  ra.qd1 = ws + A.qd1;
+  ra.tipbar = t >= 1 ? ba.dtips + (long long)(t - 1) * a.n_tips_total * 3 : nullptr;
+  ra.sphi = -dt;
+  for (int l = v.nL - 1; l >= 0; --l) {
+    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, ra, b, gv, t_abs);
+    g.sync();
+  }
+}
+
+// Backward pass of one world over a recorded rollout.
+template <int TPW>
+HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws,
+                       const Group<TPW>& g) {
+  const WorldView v = world_view(m, w);
+  const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
+  const AdjLayout A = AdjLayout::make(L.total, v.nb, v.nv, v.na, a.ckpt_every);
+  const WState s = private_state(ws, A, v.nb, v.nv, v.na);
+  const float4 g4 = m.gravity[w];
+  const f3 gv = mk(g4.x, g4.y, g4.z);
+  const float dt = a.dt;
+  const int T = a.n_steps, ce = a.ckpt_every;
+  const int nseg = (T + ce - 1) / ce;
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    ws[A.qb1 + i] = 0.f; ws[A.qdb1 + i] = 0.f; ws[A.zero + i] = 0.f; ws[A.qb + i] = 0.f; ws[A.qdb + i] = 0.f;
+  }
+  for (int i = g.lane; i < 3 * v.na; i += TPW) { ws[A.ub1 + i] = 0.f; ws[A.vb1 + i] = 0.f; }
+  g.sync();
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int t0 = seg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
+    load_ckpt(a, v, s, seg, g);
+    for (int t = t0; t < t1; ++t) {
+      snapshot(ws, A, t - t0, true, g);
+      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
+    }
+    if (seg == nseg - 1) {
+      // the last record's tips at the final configuration
+      for (int l = 0; l < v.nL; ++l) {
+        const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+        for (int b = lo + g.lane; b < hi; b += TPW)
+          tape_body(m, s, v, A, ws, ws + A.zero, 0.f, ws + A.zero, ws + A.zero, b, gv);
+        g.sync();
+      }
+      RevArgs ra;
+      ra.dyn = 0;
+      ra.delta = ws + A.zero; ra.lam = ws + A.zero; ra.qd1 = ws + A.zero;
+      ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
+      ra.sphi = 0.f;
+      for (int l = v.nL - 1; l >= 0; --l) {
+        const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+        for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, ra, b, gv, a.step0 + T);
+        g.sync();
+      }
+      for (int i = g.lane; i < v.nv; i += TPW) {
+        ws[A.qb1 + i] = ws[A.qb + i];
+        ws[A.qb + i] = 0.f;
+      }
+      g.sync();
+    }
+    for (int t = t1 - 1; t >= t0; --t) {
+      snapshot(ws, A, t - t0, false, g);
+      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
+      for (int i = g.lane; i < v.nv; i += TPW) ws[A.qd1 + i] = s.qd[i];
+      g.sync();
+      snapshot(ws, A, t - t0, false, g);
+      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, g, t, gv);
+      for (int i = g.lane; i < v.nv; i += TPW) {
+        ws[A.qb1 + i] = ws[A.qb + i];
+        ws[A.qdb1 + i] = ws[A.qdb + i];
+      }
+      for (int i = g.lane; i < 3 * v.na; i += TPW) {
+        ws[A.ub1 + i] = ws[A.ub + i];
+        ws[A.vb1 + i] = ws[A.vb + i];
+      }
+      g.sync();
+    }
+  }
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    if (ba.dq0) ba.dq0[v.d0 + i] = ws[A.qb1 + i];
+    if (ba.dqd0) ba.dqd0[v.d0 + i] = ws[A.qdb1 + i];
+  }
+  g.sync();
+  (void)dt;
+}
+
+}  // namespace
+}  // namespace orchard

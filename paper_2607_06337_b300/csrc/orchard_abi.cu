@@ -73,7 +73,7 @@ struct Packed {
   std::vector<int> dl_off, dl_bound;
   std::vector<unsigned short> dl_list;
   std::vector<float4> ap0, ap1;
-  std::vector<int> apple_body, tip_body;
+  std::vector<int> apple_body, tip_body, btip;
   std::vector<float4> tip_local, gravity;
   std::vector<int> queue;
   std::vector<ClassInfo> classes;
@@ -157,6 +157,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
   P.dl_off.assign(W + 1, 0);
   P.dl_bound.clear();
   P.dl_list.clear();
+  P.btip.clear();
   std::vector<long long> ws(W);
   std::vector<double> cost(W);
   std::vector<int> wnb(W), wnv(W), wnm(W), wna(W);
@@ -198,6 +199,16 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     for (int t = 0; t < nt; ++t) {
       const int b = d->tip_body[t0 + t];
       if (b < 0 || b >= nb) return OT_ETOPO;
+      if (t > 0 && b < d->tip_body[t0 + t - 1]) return OT_ETOPO;  // tips sorted by body
+    }
+    {
+      std::vector<int> tf(nb, 0), tc(nb, 0);
+      for (int t = 0; t < nt; ++t) {
+        const int b = d->tip_body[t0 + t];
+        if (tc[b] == 0) tf[b] = t;
+        if (++tc[b] > 255) return OT_ECAPACITY;
+      }
+      for (int b = 0; b < nb; ++b) P.btip.push_back(tf[b] | (tc[b] << 24));
     }
     // levels
     P.lvl_off[w] = (int)P.lvl.size();
@@ -382,7 +393,7 @@ namespace {
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
   size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, dl_off,
-      dl_bound, dl_list, ap0, ap1, apple_body, tip_body, tip_local, gravity, queue, total;
+      dl_bound, dl_list, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -403,6 +414,7 @@ ModelLayout model_layout(const Packed& P) {
   L.ap0 = c.take<float4>(P.NA); L.ap1 = c.take<float4>(P.NA);
   L.apple_body = c.take<int>(P.NA);
   L.tip_body = c.take<int>(P.NT);
+  L.btip = c.take<int>(P.NB);
   L.tip_local = c.take<float4>(P.NT);
   L.gravity = c.take<float4>(P.W);
   L.queue = c.take<int>(P.W);
@@ -458,7 +470,7 @@ size_t class_scratch_offset(const ot_model* m, int k, int* slots) {
   return off;
 }
 
-long long ckpt_words(const Packed& P) { return 2LL * P.NV + 6LL * P.NA + 2LL * P.NB + 3LL * P.NA; }
+long long ckpt_words(const Packed& P) { return 2LL * P.NV + 6LL * P.NA + 3LL * P.NB + 3LL * P.NA; }
 
 StepArgs base_args(const ot_model* m, double dt) {
   StepArgs a{};
@@ -620,6 +632,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.ap0, P.ap0.data(), vbytes(P.ap0)); put(L.ap1, P.ap1.data(), vbytes(P.ap1));
   put(L.apple_body, P.apple_body.data(), vbytes(P.apple_body));
   put(L.tip_body, P.tip_body.data(), vbytes(P.tip_body));
+  put(L.btip, P.btip.data(), vbytes(P.btip));
   put(L.tip_local, P.tip_local.data(), vbytes(P.tip_local));
   put(L.gravity, P.gravity.data(), vbytes(P.gravity));
   put(L.queue, P.queue.data(), vbytes(P.queue));
@@ -652,6 +665,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.ap0 = (const float4*)(base + L.ap0); dm.ap1 = (const float4*)(base + L.ap1);
   dm.apple_body = (const int*)(base + L.apple_body);
   dm.tip_body = (const int*)(base + L.tip_body);
+  dm.btip = (const int*)(base + L.btip);
   dm.tip_local = (const float4*)(base + L.tip_local);
   dm.gravity = (const float4*)(base + L.gravity);
   dm.queue = (const int*)(base + L.queue);
@@ -961,12 +975,68 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
   return result;
 }
 
+namespace {
+// Backward workspace: per class, two slots per SM of one world's backward layout.
+long long back_ws_floats(const ClassInfo& ci, int ce) {
+  return (backward_ws_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na, ce) + 63) / 64 * 64;
+}
+size_t back_slots(const ot_model* m, const ClassInfo& ci) {
+  return std::min<size_t>((size_t)m->n_sm * 2, (size_t)(ci.q_end - ci.q_begin));
+}
+int back_tpw(const ClassInfo& ci) { return std::max(32, std::min(ci.sched.threads_per_world, 256)); }
+}  // namespace
+
+ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, size_t* bytes) {
+  if (!m || !bytes || ckpt_every < 1) return OT_EINVAL;
+  size_t total = 0;
+  for (const ClassInfo& ci : m->P.classes) total += back_slots(m, ci) * (size_t)back_ws_floats(ci, ckpt_every) * 4;
+  *bytes = total;
+  return OT_OK;
+}
+
 ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
                               const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
-                              ot_grads* grads, void* stream) {
-  (void)m; (void)s; (void)n_steps; (void)step0; (void)dt; (void)pulls; (void)rec; (void)dL_dtips; (void)grads;
-  (void)stream;
-  return OT_ESTATE;
+                              ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
+  if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0) || !rec || !dL_dtips || !grads || !workspace)
+    return OT_EINVAL;
+  if (!rec->ckpt || rec->ckpt_every < 1) return OT_ESTATE;
+  if (((uintptr_t)workspace) % kAlign) return OT_EINVAL;
+  size_t need = 0;
+  ot_ckpt_bytes(m, n_steps, rec->ckpt_every, &need);
+  if (rec->ckpt_bytes < need) return OT_EINVAL;
+  ot_backward_workspace_bytes(m, rec->ckpt_every, &need);
+  if (workspace_bytes < need) return OT_EINVAL;
+  StepArgs a = base_args(m, dt);
+  a.step0 = step0;
+  a.n_steps = n_steps;
+  ot_status st = fill_pulls(a, pulls);
+  if (st != OT_OK) return st;
+  a.ckpt = (unsigned*)rec->ckpt;
+  a.ckpt_every = rec->ckpt_every;
+  BackArgs ba{dL_dtips, grads->dk, grads->dkd, grads->dq0, grads->dqd0};
+  cudaStream_t cs = (cudaStream_t)stream;
+  float* work = (float*)workspace;
+  for (int k = 0; k < (int)m->P.classes.size(); ++k) {
+    const ClassInfo& ci = m->P.classes[k];
+    const long long wsf = back_ws_floats(ci, rec->ckpt_every);
+    const size_t slots = back_slots(m, ci);
+    const int tpw = back_tpw(ci);
+    int bps = 0;
+    OT_CUDA(backward_attributes(tpw, 1, &bps));
+    const int blocks = (int)std::min<size_t>(slots, (size_t)std::max(bps, 1) * m->n_sm);
+    StepArgs b = a;
+    b.q_begin = ci.q_begin;
+    b.q_end = ci.q_end;
+    b.q_counter = s->q_counters + k;
+    OT_CUDA(cudaMemsetAsync(b.q_counter, 0, sizeof(int), cs));
+    if (blocks > 0) {
+      launch_backward(tpw, 1, blocks, cs, m->dev, b, ba, work, wsf);
+      OT_CUDA(cudaGetLastError());
+      g_launches += 1;
+    }
+    work += slots * (size_t)wsf;
+  }
+  return OT_OK;
 }
 
 }  // extern "C"

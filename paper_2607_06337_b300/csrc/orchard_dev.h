@@ -36,6 +36,7 @@ struct DevModel {
   const float4* ap1;     // k_s, c_s, f_detach, -
   const int* apple_body; // world-local body of each apple
   const int* tip_body;   // world-local body of each tip
+  const int* btip;       // per body: first tip (world-local) | tip count << 24 (tips sorted by body)
   const float4* tip_local;
   const float4* gravity; // per world
   const int* queue;      // world ids sorted by (size class, cost descending)
@@ -127,6 +128,19 @@ namespace orchard {
 int static_step_plan(const ot_model* m, int* n_classes, size_t* max_ws_floats);
 int static_step_class(ot_model* m, ot_state* s, int k, const float* ext_force, const ot_force_schedule* pulls,
                       int step, double dt, float* scratch, size_t scratch_floats, int* counter, void* stream);
+
+// Outputs and inputs of a backward pass beyond the forward's StepArgs.
+struct BackArgs {
+  const float* dtips;  // [n_steps][n_tips_total][3]
+  float* dk;           // [NB] accumulated
+  float* dkd;          // [NB] accumulated
+  float* dq0;          // [NV] written
+  float* dqd0;         // [NV] written
+};
+void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
+                     const StepArgs& a, const BackArgs& ba, float* work, long long ws_floats);
+cudaError_t backward_attributes(int tpw, int groups_per_block, int* blocks_per_sm);
+long long backward_ws_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);

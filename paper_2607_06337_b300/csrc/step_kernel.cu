@@ -1,728 +1,10 @@
-// Batched compliant-tree step for sm_103a: one group of TPW threads per world.
-//
-// Spatial algebra is written in world orientation with each body's own joint origin x_b as
-// the reference point (so a hinge's motion subspace is (e_i; 0) and lever arms stay
-// segment-sized, which keeps twig inertias well conditioned in FP32). Per step and world:
-//   1. root-to-leaf level sweep: forward kinematics (Sec. IV Eq. 3, two Cardan DOFs per
-//      joint), body velocities and velocity-product accelerations (RNE forward pass, base
-//      acceleration -g), the body's own Newton-Euler force, apple tether loads (Sec. IV-C
-//      Eqs. 6-7) and the body's spatial inertia (plus the tether coupling point masses);
-//   2. leaf-to-root level sweep: RNE force accumulation and CRBA composite inertias; bias
-//      c_i = e_i . n_b and the right-hand side r = dt(-K'(q + alpha dt qd) - D' qd - c);
-//   3. CRBA rows in ancestor-row storage M_ij = e_j . (n_i + (x_b(i) - x_b(j)) x f_i) with
-//      (n_i; f_i) = I^c_b(i) (e_i; 0), plus the implicit diagonal (armature, dt kd', dt^2 k');
-//   4. tree-sparse LDL^T: DOFs eliminated from the last to the first (children have larger
-//      indices), each a rank-1 update of its ancestor rows; the L^T sweep of the solve rides
-//      along; rows are kept unscaled (U = D L);
-//   5. root-to-leaf level sweep: the L sweep of the solve, qd += Delta, q += dt qd, the new
-//      body velocities, the coupled apple update, and the rupture / detachment tests with
-//      their hysteresis counters (Sec. IV-B Eq. 5, Sec. IV-C).
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <cstring>
-
-#include "orchard_dev.h"
-
-// Helpers are __host__ __device__ so the per-world step also compiles for the host (a serial
-// group of one thread), which is how its logic is debugged without a GPU.
-#define HD __host__ __device__ __forceinline__
+// Batched compliant-tree forward rollout kernel for sm_103a (the per-world step is in
+// step_device.cuh): a persistent grid whose thread groups pop worlds from a cost-sorted queue
+// and run all their steps.
+#include "step_device.cuh"
 
 namespace orchard {
 namespace {
-
-HD float rsq(float x) {
-#ifdef __CUDA_ARCH__
-  return rsqrtf(x);
-#else
-  return 1.f / std::sqrt(x);
-#endif
-}
-HD unsigned f2u(float x) {
-#ifdef __CUDA_ARCH__
-  return __float_as_uint(x);
-#else
-  unsigned u;
-  std::memcpy(&u, &x, 4);
-  return u;
-#endif
-}
-HD void atomic_or(unsigned* p, unsigned v) {
-#ifdef __CUDA_ARCH__
-  atomicOr(p, v);
-#else
-  *p |= v;
-#endif
-}
-HD void sin_cos(float x, float* s, float* c) {
-#ifdef __CUDA_ARCH__
-  sincosf(x, s, c);
-#else
-  *s = std::sin(x);
-  *c = std::cos(x);
-#endif
-}
-HD bool finite(float x) {
-#ifdef __CUDA_ARCH__
-  return isfinite(x);
-#else
-  return std::isfinite(x);
-#endif
-}
-
-struct f3 {
-  float x, y, z;
-};
-HD f3 mk(float x, float y, float z) { return {x, y, z}; }
-HD f3 operator+(f3 a, f3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-HD f3 operator-(f3 a, f3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-HD f3 operator*(float s, f3 a) { return {s * a.x, s * a.y, s * a.z}; }
-HD float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
-HD f3 cross(f3 a, f3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-HD f3 ld3(const float* p) { return {p[0], p[1], p[2]}; }
-HD void st3(float* p, f3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
-HD f3 xyz(float4 v) { return {v.x, v.y, v.z}; }
-
-// 3x3 rotation, column-major storage c0, c1, c2 (columns are the frame axes).
-struct m3 {
-  f3 c0, c1, c2;
-};
-HD f3 mul(const m3& R, f3 v) { return v.x * R.c0 + v.y * R.c1 + v.z * R.c2; }
-HD m3 mul(const m3& A, const m3& B) { return {mul(A, B.c0), mul(A, B.c1), mul(A, B.c2)}; }
-HD m3 ldm(const float* p) { return {ld3(p), ld3(p + 3), ld3(p + 6)}; }
-HD void stm(float* p, const m3& R) { st3(p, R.c0); st3(p + 3, R.c1); st3(p + 6, R.c2); }
-HD m3 quat_mat(float4 q) {
-  float n = rsq(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-  float w = q.x * n, x = q.y * n, y = q.z * n, z = q.w * n;
-  return {mk(1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)),
-          mk(2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)),
-          mk(2 * (x * z + w * y), 2 * (y * z - w * x), 1 - 2 * (x * x + y * y))};
-}
-
-// Symmetric 3x3 (xx, yy, zz, xy, xz, yz) and the 10-number spatial inertia about a point.
-struct sym3 {
-  float xx, yy, zz, xy, xz, yz;
-};
-HD f3 mul(const sym3& I, f3 v) {
-  return {I.xx * v.x + I.xy * v.y + I.xz * v.z, I.xy * v.x + I.yy * v.y + I.yz * v.z,
-          I.xz * v.x + I.yz * v.y + I.zz * v.z};
-}
-struct sinertia {
-  float m;
-  f3 h;     // m (com - O)
-  sym3 I;   // rotational inertia about O
-};
-HD void st_in(float* p, const sinertia& s) {
-  p[0] = s.m; p[1] = s.h.x; p[2] = s.h.y; p[3] = s.h.z;
-  p[4] = s.I.xx; p[5] = s.I.yy; p[6] = s.I.zz; p[7] = s.I.xy; p[8] = s.I.xz; p[9] = s.I.yz;
-}
-HD sinertia ld_in(const float* p) {
-  return {p[0], mk(p[1], p[2], p[3]), {p[4], p[5], p[6], p[7], p[8], p[9]}};
-}
-// add a point mass mp at offset r from O
-HD void add_point(sinertia& s, float mp, f3 r) {
-  float rr = dot(r, r);
-  s.m += mp;
-  s.h = s.h + mp * r;
-  s.I.xx += mp * (rr - r.x * r.x); s.I.yy += mp * (rr - r.y * r.y); s.I.zz += mp * (rr - r.z * r.z);
-  s.I.xy -= mp * r.x * r.y; s.I.xz -= mp * r.x * r.z; s.I.yz -= mp * r.y * r.z;
-}
-// add inertia c expressed about O + s (child origin) into acc expressed about O:
-// h' = h + m s, I' = I + (2 h.s + m |s|^2) 1 - (h s^T + s h^T) - m s s^T
-HD void add_shifted(sinertia& acc, const sinertia& c, f3 s) {
-  float hs = dot(c.h, s), ss = dot(s, s);
-  float d = 2.f * hs + c.m * ss;
-  acc.m += c.m;
-  acc.h = acc.h + c.h + c.m * s;
-  acc.I.xx += c.I.xx + d - 2.f * c.h.x * s.x - c.m * s.x * s.x;
-  acc.I.yy += c.I.yy + d - 2.f * c.h.y * s.y - c.m * s.y * s.y;
-  acc.I.zz += c.I.zz + d - 2.f * c.h.z * s.z - c.m * s.z * s.z;
-  acc.I.xy += c.I.xy - (c.h.x * s.y + s.x * c.h.y) - c.m * s.x * s.y;
-  acc.I.xz += c.I.xz - (c.h.x * s.z + s.x * c.h.z) - c.m * s.x * s.z;
-  acc.I.yz += c.I.yz - (c.h.y * s.z + s.y * c.h.z) - c.m * s.y * s.z;
-}
-
-template <int TPW>
-struct Group {
-  int lane;
-  int id;      // group index inside the block
-  int* flag;   // per-group shared word: 1 once the current world is frozen
-  HD void sync() const {
-#ifdef __CUDA_ARCH__
-    if (TPW == 32) {
-      __syncwarp();
-    } else {
-      asm volatile("bar.sync %0, %1;" ::"r"(id + 1), "r"(TPW) : "memory");
-    }
-#endif
-  }
-};
-
-struct WorldView {
-  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, DL0, nDL;
-};
-
-HD WorldView world_view(const DevModel& m, int w) {
-  WorldView v;
-  v.b0 = m.body_off[w]; v.nb = m.body_off[w + 1] - v.b0;
-  v.d0 = m.dof_off[w]; v.nv = m.dof_off[w + 1] - v.d0;
-  v.a0 = m.apple_off[w]; v.na = m.apple_off[w + 1] - v.a0;
-  v.t0 = m.tip_off[w]; v.nt = m.tip_off[w + 1] - v.t0;
-  v.m0 = m.m_off[w]; v.nm = m.m_off[w + 1] - v.m0;
-  v.L0 = m.lvl_off[w]; v.nL = m.lvl_off[w + 1] - v.L0 - 1;
-  v.DL0 = m.dl_off[w]; v.nDL = m.dl_off[w + 1] - v.DL0 - 1;
-  return v;
-}
-
-HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
-  f3 f = mk(0.f, 0.f, 0.f);
-  if (a.pull_force && t_abs >= a.pull_start[ga] && t_abs < a.pull_end[ga]) f = ld3(a.pull_force + 3 * ga);
-  if (a.ext_force) f = f + ld3(a.ext_force + 3 * ga);
-  return f;
-}
-
-// Joint gains of this step: a broken joint has no spring and keeps the torn-fibre friction,
-// a damper growing from kd to (1 + ramp_gain) kd over the ramp time (Sec. IV-B).
-HD void joint_gains(const DevState& s, const StepArgs& a, int gb, float4 P3, int t_abs, float* k, float* kd) {
-  if (!s.broken[gb]) {
-    *k = P3.z;
-    *kd = P3.w;
-    return;
-  }
-  const float since = (float)(t_abs - s.break_step[gb]);
-  const float ramp = a.ramp_inv > 0.f ? fminf(since * a.ramp_inv, 1.f) : 1.f;
-  *k = 0.f;
-  *kd = (1.f + a.ramp_gain * ramp) * P3.w;
-}
-
-// Phase 1 for one body: kinematics, velocities, bias acceleration, own force, apple loads.
-HD void forward_body(const DevModel& m, const DevState& s, const StepArgs& a,
-                                             const WorldView& v, const WsLayout& L, float* ws, int b,
-                                             int t_abs, f3 g) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
-  const int p = bi.x;
-  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const float4 P0 = m.bp0[gb], P1 = m.bp1[gb], P2 = m.bp2[gb], P3 = m.bp3[gb];
-  m3 Rp;
-  f3 xp, wp, vp, alp, ap;
-  if (p >= 0) {
-    Rp = ldm(ws + L.R + 9 * p);
-    xp = ld3(ws + L.X + 3 * p);
-    wp = ld3(ws + L.V + 6 * p); vp = ld3(ws + L.V + 6 * p + 3);
-    alp = ld3(ws + L.A + 6 * p); ap = ld3(ws + L.A + 6 * p + 3);
-  } else {
-    Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
-    xp = wp = vp = alp = mk(0, 0, 0);
-    ap = (-1.f) * g;  // gravity as a base acceleration
-  }
-  m3 R = mul(Rp, quat_mat(P1));
-  const f3 xb = xp + mul(Rp, xyz(P0));
-  const f3 d = xb - xp;
-  const f3 vin = vp + cross(wp, d);
-  f3 w = wp, al = alp, aa = ap + cross(alp, d);
-  for (int j = 0; j < nd; ++j) {
-    const int i = dof0 + j;
-    const f3 e = j == 0 ? R.c0 : R.c1;
-    st3(ws + L.E + 3 * i, e);
-    const float qdj = s.qd[v.d0 + i], qj = s.q[v.d0 + i];
-    al = al + qdj * cross(w, e);
-    aa = aa + qdj * cross(vin, e);
-    w = w + qdj * e;
-    float sn, cs;
-    sin_cos(qj, &sn, &cs);
-    if (j == 0) {  // R <- R Rx(q)
-      const f3 c1 = cs * R.c1 + sn * R.c2, c2 = cs * R.c2 - sn * R.c1;
-      R.c1 = c1; R.c2 = c2;
-    } else {       // R <- R Ry(q)
-      const f3 c0 = cs * R.c0 - sn * R.c2, c2 = sn * R.c0 + cs * R.c2;
-      R.c0 = c0; R.c2 = c2;
-    }
-  }
-  stm(ws + L.R + 9 * b, R);
-  st3(ws + L.X + 3 * b, xb);
-  // on a snapped sub-tree (this joint or one above broken): applied forces disabled (App. B)
-  const bool snapped = s.broken[gb] || (p >= 0 && ws[L.SN + p] != 0.f);
-  ws[L.SN + b] = snapped ? 1.f : 0.f;
-  st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vin);
-  st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
-
-  // spatial inertia of the body about x_b
-  const float mb = P0.w;
-  const f3 r = mul(R, xyz(P2));
-  sinertia I;
-  I.m = mb;
-  I.h = mb * r;
-  {
-    const float i0 = P2.w, i1 = P3.x, i2 = P3.y, rr = dot(r, r);
-    const f3 c0 = R.c0, c1 = R.c1, c2 = R.c2;
-    I.I.xx = i0 * c0.x * c0.x + i1 * c1.x * c1.x + i2 * c2.x * c2.x + mb * (rr - r.x * r.x);
-    I.I.yy = i0 * c0.y * c0.y + i1 * c1.y * c1.y + i2 * c2.y * c2.y + mb * (rr - r.y * r.y);
-    I.I.zz = i0 * c0.z * c0.z + i1 * c1.z * c1.z + i2 * c2.z * c2.z + mb * (rr - r.z * r.z);
-    I.I.xy = i0 * c0.x * c0.y + i1 * c1.x * c1.y + i2 * c2.x * c2.y - mb * r.x * r.y;
-    I.I.xz = i0 * c0.x * c0.z + i1 * c1.x * c1.z + i2 * c2.x * c2.z - mb * r.x * r.z;
-    I.I.yz = i0 * c0.y * c0.z + i1 * c1.y * c1.z + i2 * c2.y * c2.z - mb * r.y * r.z;
-  }
-  // own Newton-Euler force at x_b: I (al; aa) + (w; vin) x* I (w; vin)
-  const f3 n1 = mul(I.I, al) + cross(I.h, aa), f1 = mb * aa - cross(I.h, al);
-  const f3 n2 = mul(I.I, w) + cross(I.h, vin), f2 = mb * vin - cross(I.h, w);
-  f3 n = n1 + cross(w, n2) + cross(vin, f2);
-  f3 f = f1 + cross(w, f2);
-
-  // apples hanging from this body
-  const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
-  const float dt = a.dt;
-  for (int k = 0; k < acount; ++k) {
-    const int ai = afirst + k, ga = v.a0 + ai;
-    const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
-    const float ma = A0.w, ks = A1.x, csd = A1.y, fdet = A1.z;
-    const f3 rh = mul(R, xyz(A0));
-    const f3 xh = xb + rh;
-    // attached: the state is the stem elongation u = x - x_hang; detached: the position
-    f3 ua = ld3(s.ax + 3 * ga);
-    const f3 va = ld3(s.av + 3 * ga);
-    int det = s.detached[ga];
-    if (det == 2) {  // detached during the last step: elongation -> world position
-      ua = ua + xh;
-      st3(s.ax + 3 * ga, ua);
-      s.detached[ga] = det = 1;
-    }
-    const f3 fe = apple_force(a, ga, t_abs);
-    const f3 fs = det ? mk(0, 0, 0) : (-ks) * ua;
-    const float T = sqrtf(dot(fs, fs)), P = sqrtf(dot(fe, fe));
-    f3 avec, fapp = mk(0, 0, 0);
-    float beta = 0.f, kappa = 0.f;
-    if (det) {
-      avec = va + dt * (g + (1.f / ma) * fe);
-    } else {
-      const float D = ma + dt * csd + dt * dt * ks;
-      avec = (1.f / D) * (ma * va + dt * (fe + ma * g + fs));
-      const f3 fr = (-1.f) * (fs + ma * g);
-      const float nfr = sqrtf(dot(fr, fr));
-      const float fc = a.clamp * fdet;
-      if (snapped) {
-        // debris: no reaction on the tree; the stem still acts on the apple
-      } else if (a.tether_implicit) {
-        // the clamp scales the coupled reaction, force and stiffness alike
-        const float sc = nfr > fc ? fc / nfr : 1.f;
-        beta = dt * dt * ks / D;
-        kappa = sc * ks * (1.f - beta);
-        const f3 vh = vin + cross(w, rh);
-        fapp = sc * (fr + (dt * ks) * avec) - (dt * kappa) * vh;
-      } else {
-        fapp = nfr > fc ? (fc / nfr) * fr : fr;
-      }
-    }
-    n = n - cross(rh, fapp);
-    f = f - fapp;
-    if (kappa > 0.f) add_point(I, dt * dt * kappa, rh);
-    float* at = ws + L.AT + 10 * ai;
-    st3(at, avec);
-    at[3] = beta; at[4] = T; at[5] = P;
-    st3(at + 6, rh);
-  }
-  st3(ws + L.F + 6 * b, n); st3(ws + L.F + 6 * b + 3, f);
-  st_in(ws + L.IC + 10 * b, I);
-}
-
-// Phase 2 for one body: pull children, bias and right-hand side of its DOFs.
-HD void backward_body(const DevModel& m, const DevState& s, const StepArgs& a,
-                                              const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
-  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
-  f3 n = ld3(ws + L.F + 6 * b), f = ld3(ws + L.F + 6 * b + 3);
-  sinertia I = ld_in(ws + L.IC + 10 * b);
-  const f3 xb = ld3(ws + L.X + 3 * b);
-  for (int k = 0; k < ccount; ++k) {
-    const int c = cfirst + k;
-    const f3 sft = ld3(ws + L.X + 3 * c) - xb;
-    const f3 nc = ld3(ws + L.F + 6 * c), fc = ld3(ws + L.F + 6 * c + 3);
-    n = n + nc + cross(sft, fc);
-    f = f + fc;
-    add_shifted(I, ld_in(ws + L.IC + 10 * c), sft);
-  }
-  st3(ws + L.F + 6 * b, n); st3(ws + L.F + 6 * b + 3, f);
-  st_in(ws + L.IC + 10 * b, I);
-  if (nd) {
-    const float4 P3 = m.bp3[gb];
-    float k, kd;
-    joint_gains(s, a, gb, P3, t_abs, &k, &kd);
-    const float dt = a.dt, adt = a.alpha ? dt : 0.f;
-    for (int j = 0; j < nd; ++j) {
-      const int i = dof0 + j;
-      const float c = dot(ld3(ws + L.E + 3 * i), n);
-      const float qi = s.q[v.d0 + i], qdi = s.qd[v.d0 + i];
-      ws[L.r + i] = dt * (-k * (qi + adt * qdi) - kd * qdi - c);
-    }
-  }
-}
-
-// Phase 5 for one body: finish the solve, update, velocities, apples, events.
-HD void update_body(const DevModel& m, const DevState& s, const StepArgs& a,
-                                            const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs,
-                                            unsigned w_idx, int* frozen) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
-  const int p = bi.x;
-  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const float dt = a.dt;
-  const f3 xb = ld3(ws + L.X + 3 * b);
-  f3 w, vl;
-  if (p >= 0) {
-    const f3 wp = ld3(ws + L.V + 6 * p), vp = ld3(ws + L.V + 6 * p + 3);
-    w = wp;
-    vl = vp + cross(wp, xb - ld3(ws + L.X + 3 * p));
-  } else {
-    w = vl = mk(0, 0, 0);
-  }
-  bool bad = false;
-  float th2 = 0.f;
-  for (int j = 0; j < nd; ++j) {
-    const int i = dof0 + j;
-    const int4 di = m.dinfo[v.d0 + i];
-    const float* row = ws + L.M + di.x;
-    const unsigned* an = m.anc + v.m0 + di.x;
-    float acc = 0.f;
-#pragma unroll 4
-    for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], ws[L.r + (an[c] & 0xffffu)], acc);
-    const float x = ws[L.r + i] - acc / row[0];
-    ws[L.r + i] = x;
-    const float qd = s.qd[v.d0 + i] + x;
-    const float q = s.q[v.d0 + i] + dt * qd;
-    s.qd[v.d0 + i] = qd;
-    s.q[v.d0 + i] = q;
-    bad |= !finite(q) || !finite(qd);
-    th2 = fmaf(q, q, th2);
-    w = w + qd * ld3(ws + L.E + 3 * i);
-  }
-  st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vl);
-
-  const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
-  if (acount) {
-    for (int k = 0; k < acount; ++k) {
-      const int ai = afirst + k, ga = v.a0 + ai;
-      const float* at = ws + L.AT + 10 * ai;
-      const bool det = s.detached[ga] != 0;
-      const f3 rh = ld3(at + 6);
-      const f3 vh = det ? mk(0, 0, 0) : vl + cross(w, rh);
-      const f3 vn = ld3(at) + at[3] * vh;
-      // attached: u' = u + dt (v' - v_hang'); detached: x' = x + dt v'
-      const f3 xn = ld3(s.ax + 3 * ga) + dt * (vn - vh);
-      st3(s.av + 3 * ga, vn);
-      st3(s.ax + 3 * ga, xn);
-      bad |= !finite(xn.x) || !finite(xn.y) || !finite(xn.z);
-      if (!det) {
-        const float fdet = m.ap1[ga].z;
-        const int cp = at[5] > fdet ? s.pcnt[ga] + 1 : 0;
-        const int ct = at[4] > a.gamma * fdet ? s.tcnt[ga] + 1 : 0;
-        s.pcnt[ga] = cp;
-        s.tcnt[ga] = ct;
-        if (cp >= a.n_pull || ct >= a.n_tension) {
-          s.detached[ga] = 2;  // becomes a world position at the next step's kinematics
-          s.detach_step[ga] = t_abs;
-        }
-      }
-    }
-  }
-  if (nd && !s.broken[gb]) {
-    const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
-    const float mom = P3.z * sqrtf(th2);
-    const int cnt = mom > P4.y ? s.bcnt[gb] + 1 : 0;
-    s.bcnt[gb] = cnt;
-    if (cnt >= a.n_break) {
-      s.broken[gb] = 1;
-      s.break_step[gb] = t_abs;
-    }
-  }
-  if (bad) {
-    atomic_or(s.status + w_idx, 1u);
-    *frozen = 1;  // every lane reads it after the group barrier that ends the sweep
-  }
-}
-
-template <int TPW>
-HD void write_ckpt(const DevState& s, const StepArgs& a, const WorldView& v, int slot, const Group<TPW>& g) {
-  unsigned* base = a.ckpt + (long long)slot * a.ckpt_words;
-  unsigned* q = base;
-  unsigned* qd = q + a.NV;
-  unsigned* ax = qd + a.NV;
-  unsigned* av = ax + 3 * a.NA;
-  unsigned* br = av + 3 * a.NA;
-  unsigned* bc = br + a.NB;
-  unsigned* de = bc + a.NB;
-  unsigned* pc = de + a.NA;
-  unsigned* tc = pc + a.NA;
-  for (int i = g.lane; i < v.nv; i += TPW) {
-    q[v.d0 + i] = f2u(s.q[v.d0 + i]);
-    qd[v.d0 + i] = f2u(s.qd[v.d0 + i]);
-  }
-  for (int i = g.lane; i < 3 * v.na; i += TPW) {
-    ax[3 * v.a0 + i] = f2u(s.ax[3 * v.a0 + i]);
-    av[3 * v.a0 + i] = f2u(s.av[3 * v.a0 + i]);
-  }
-  for (int i = g.lane; i < v.nb; i += TPW) {
-    br[v.b0 + i] = s.broken[v.b0 + i];
-    bc[v.b0 + i] = s.bcnt[v.b0 + i];
-  }
-  for (int i = g.lane; i < v.na; i += TPW) {
-    de[v.a0 + i] = s.detached[v.a0 + i];
-    pc[v.a0 + i] = s.pcnt[v.a0 + i];
-    tc[v.a0 + i] = s.tcnt[v.a0 + i];
-  }
-}
-
-// Forward kinematics only (positions), for the tip record after the last step.
-template <int TPW>
-HD void fk_only(const DevModel& m, const DevState& s, const WorldView& v, const WsLayout& L, float* ws,
-                        const Group<TPW>& g) {
-  for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) {
-      const int gb = v.b0 + b;
-      const int4 bi = m.bi[gb];
-      const int p = bi.x;
-      const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-      m3 Rp;
-      f3 xp;
-      if (p >= 0) {
-        Rp = ldm(ws + L.R + 9 * p);
-        xp = ld3(ws + L.X + 3 * p);
-      } else {
-        Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
-        xp = mk(0, 0, 0);
-      }
-      m3 R = mul(Rp, quat_mat(m.bp1[gb]));
-      const f3 xb = xp + mul(Rp, xyz(m.bp0[gb]));
-      for (int j = 0; j < nd; ++j) {
-        float sn, cs;
-        sin_cos(s.q[v.d0 + dof0 + j], &sn, &cs);
-        if (j == 0) {
-          const f3 c1 = cs * R.c1 + sn * R.c2, c2 = cs * R.c2 - sn * R.c1;
-          R.c1 = c1; R.c2 = c2;
-        } else {
-          const f3 c0 = cs * R.c0 - sn * R.c2, c2 = sn * R.c0 + cs * R.c2;
-          R.c0 = c0; R.c2 = c2;
-        }
-      }
-      stm(ws + L.R + 9 * b, R);
-      st3(ws + L.X + 3 * b, xb);
-    }
-    g.sync();
-  }
-}
-
-template <int TPW>
-HD void record_tips(const DevModel& m, const StepArgs& a, const WorldView& v, const WsLayout& L,
-                            const float* ws, int slot, const Group<TPW>& g) {
-  float* out = a.tips + (long long)slot * a.n_tips_total * 3;
-  for (int t = g.lane; t < v.nt; t += TPW) {
-    const int b = m.tip_body[v.t0 + t];
-    const m3 R = ldm(ws + L.R + 9 * b);
-    const f3 p = ld3(ws + L.X + 3 * b) + mul(R, xyz(m.tip_local[v.t0 + t]));
-    st3(out + 3 * (v.t0 + t), p);
-  }
-}
-
-#ifdef __CUDA_ARCH__
-// Four independent segmented scans interleaved, so their shuffle latencies overlap.
-__device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d, int lane, int first) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float ta = __shfl_up_sync(0xffffffffu, a, o);
-    const float tb = __shfl_up_sync(0xffffffffu, b, o);
-    const float tc = __shfl_up_sync(0xffffffffu, c, o);
-    const float td = __shfl_up_sync(0xffffffffu, d, o);
-    if (lane - o >= first) {
-      a += ta;
-      b += tb;
-      c += tc;
-      d += td;
-    }
-  }
-}
-#endif
-
-// Tree-sparse LDL^T of H (rows kept unscaled, U = D L) and the L^T sweep of the solve.
-// All DOFs of one depth are eliminated together (their rows are final once every deeper DOF
-// is done, and none is an ancestor of another). A DOF k of depth l adds
-// -U_k[c] U_k[c2] / D_k to entry (anc_c(k), c2 - c) and -U_k[c] y_k / D_k to y of anc_c(k).
-// Listed in depth-first order, the DOFs of one depth that share their c-th ancestor are
-// contiguous, so each target's contributions are a segmented sum over consecutive lanes:
-// shuffle scans, deterministic, no atomics. The c values are split over the group's warps
-// (different c means different target rows). y_k / D_k is stored once the level is done.
-template <int TPW>
-HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, const Group<TPW>& g) {
-#ifdef __CUDA_ARCH__
-  constexpr int NW = TPW / 32;
-  const int warp = g.lane >> 5, lane = g.lane & 31;
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
-    if (l > 0) {
-      for (int base = lo; base < hi; base += 32) {
-        const int idx = base + lane;
-        const bool valid = idx < hi;
-        int rowk = 0;
-        float dinv = 0.f, yk = 0.f;
-        if (valid) {
-          const int k = m.dl_list[v.d0 + idx];
-          rowk = m.dinfo[v.d0 + k].x;
-          dinv = 1.f / ws[L.M + rowk];
-          yk = ws[L.r + k];
-        }
-        const float* row = ws + L.M + rowk;
-        const unsigned* an = m.anc + v.m0 + rowk;
-        for (int c = 1 + warp; c <= l; c += NW) {
-          const int key = valid ? (int)(an[c] & 0xffffu) : -1 - lane;
-          const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-          const int next = __shfl_down_sync(0xffffffffu, key, 1);
-          const bool head = lane == 0 || prev != key;
-          const bool tail = lane == 31 || next != key;
-          const unsigned heads = __ballot_sync(0xffffffffu, head);
-          const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-          const float uc = valid ? row[c] * dinv : 0.f;
-          const int trow = valid ? m.dinfo[v.d0 + key].x : 0;
-          float* tgt = ws + L.M + trow - c;  // entry (anc_c(k), c2 - c) is tgt[c2]
-          int c2 = c;
-          for (; c2 + 4 <= l + 1; c2 += 4) {
-            float s0 = valid ? uc * row[c2] : 0.f, s1 = valid ? uc * row[c2 + 1] : 0.f;
-            float s2 = valid ? uc * row[c2 + 2] : 0.f, s3 = valid ? uc * row[c2 + 3] : 0.f;
-            seg_scan4(s0, s1, s2, s3, lane, first);
-            if (valid && tail) {
-              tgt[c2] -= s0;
-              tgt[c2 + 1] -= s1;
-              tgt[c2 + 2] -= s2;
-              tgt[c2 + 3] -= s3;
-            }
-          }
-          // the last up-to-three entries of the row together with the right-hand side
-          const int rem = l + 1 - c2;
-          float s0 = valid && rem > 0 ? uc * row[c2] : 0.f;
-          float s1 = valid && rem > 1 ? uc * row[c2 + 1] : 0.f;
-          float s2 = valid && rem > 2 ? uc * row[c2 + 2] : 0.f;
-          float sy = uc * yk;
-          seg_scan4(s0, s1, s2, sy, lane, first);
-          if (valid && tail) {
-            if (rem > 0) tgt[c2] -= s0;
-            if (rem > 1) tgt[c2 + 1] -= s1;
-            if (rem > 2) tgt[c2 + 2] -= s2;
-            ws[L.r + key] -= sy;
-          }
-        }
-      }
-    }
-    g.sync();
-    for (int idx = lo + g.lane; idx < hi; idx += TPW) {
-      const int k = m.dl_list[v.d0 + idx];
-      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
-  }
-  g.sync();
-#else
-  // one serial lane: the same updates, segment by segment in list order
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
-    for (int c = 1; c <= l; ++c) {
-      for (int c2 = c - 1; c2 <= l; ++c2) {  // c2 = c - 1 stands for the right-hand side
-        float acc = 0.f;
-        for (int idx = lo; idx < hi; ++idx) {
-          const int k = m.dl_list[v.d0 + idx];
-          const int rowk = m.dinfo[v.d0 + k].x;
-          const float* row = ws + L.M + rowk;
-          const int key = (int)(m.anc[v.m0 + rowk + c] & 0xffffu);
-          const float uc = row[c] / row[0];
-          acc += uc * (c2 < c ? ws[L.r + k] : row[c2]);
-          int next = -1;
-          if (idx + 1 < hi) {
-            const int k2 = m.dl_list[v.d0 + idx + 1];
-            next = (int)(m.anc[v.m0 + m.dinfo[v.d0 + k2].x + c] & 0xffffu);
-          }
-          if (next != key) {
-            if (c2 < c) ws[L.r + key] -= acc;
-            else ws[L.M + m.dinfo[v.d0 + key].x + (c2 - c)] -= acc;
-            acc = 0.f;
-          }
-        }
-      }
-    }
-    for (int idx = lo; idx < hi; ++idx) {
-      const int k = m.dl_list[v.d0 + idx];
-      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
-  }
-#endif
-}
-
-// All steps of one world.
-template <int TPW>
-HD void run_world(const DevModel& m, const DevState& s, const StepArgs& a, int w, float* ws,
-                          const Group<TPW>& g) {
-  const WorldView v = world_view(m, w);
-  const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
-  const float4 g4 = m.gravity[w];
-  const f3 gv = mk(g4.x, g4.y, g4.z);
-  const float dt = a.dt;
-  if (g.lane == 0) *g.flag = (int)(s.status[w] & 1u);
-  g.sync();
-  for (int t = 0; t < a.n_steps; ++t) {
-    const int t_abs = a.step0 + t;
-    if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
-    if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
-    // 1. root-to-leaf: kinematics, velocities, own forces, apple loads
-    for (int l = 0; l < v.nL; ++l) {
-      const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-      for (int b = lo + g.lane; b < hi; b += TPW) forward_body(m, s, a, v, L, ws, b, t_abs, gv);
-      g.sync();
-    }
-    if (a.tips && t > 0) record_tips(m, a, v, L, ws, t - 1, g);
-    // 2. leaf-to-root: forces and composite inertias, right-hand side
-    for (int l = v.nL - 1; l >= 0; --l) {
-      const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-      for (int b = lo + g.lane; b < hi; b += TPW) backward_body(m, s, a, v, L, ws, b, t_abs);
-      g.sync();
-    }
-    // 3. CRBA rows and the implicit diagonal
-    for (int i = g.lane; i < v.nv; i += TPW) {
-      const int4 di = m.dinfo[v.d0 + i];
-      const int b = di.y;
-      const int gb = v.b0 + b;
-      const f3 e = ld3(ws + L.E + 3 * i);
-      const sinertia I = ld_in(ws + L.IC + 10 * b);
-      const f3 n = mul(I.I, e), f = cross(e, I.h);
-      const f3 xb = ld3(ws + L.X + 3 * b);
-      float* row = ws + L.M + di.x;
-      const unsigned* an = m.anc + v.m0 + di.x;
-      const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
-      float k, kd;
-      joint_gains(s, a, gb, P3, t_abs, &k, &kd);
-      row[0] = dot(e, n) + P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
-#pragma unroll 4
-      for (int c = 1; c <= di.z; ++c) {
-        const unsigned ab = an[c];
-        const int j = ab & 0xffffu, bj = ab >> 16;
-        const f3 lev = xb - ld3(ws + L.X + 3 * bj);
-        row[c] = dot(ld3(ws + L.E + 3 * j), n + cross(lev, f));
-      }
-    }
-    g.sync();
-    // 4. LDL^T by DOF depth, deepest first, with the L^T sweep of the solve
-    factor_levels<TPW>(m, v, L, ws, g);
-    // 5. root-to-leaf: L sweep, update, velocities, apples, events
-    for (int l = 0; l < v.nL; ++l) {
-      const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-      for (int b = lo + g.lane; b < hi; b += TPW) update_body(m, s, a, v, L, ws, b, t_abs, (unsigned)w, g.flag);
-      g.sync();
-    }
-  }
-  if (a.tips && a.n_steps > 0) {
-    fk_only(m, s, v, L, ws, g);
-    record_tips(m, a, v, L, ws, a.n_steps - 1, g);
-    g.sync();
-  }
-}
 
 template <int TPW>
 __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, StepArgs a) {

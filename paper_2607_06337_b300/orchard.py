@@ -105,9 +105,10 @@ _SIGS = {
                              C.POINTER(Record), C.c_void_p]),
     "ot_rollout_plain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
                                    C.POINTER(ForceSchedule), C.c_void_p]),
+    "ot_backward_workspace_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_size_t)]),
     "ot_rollout_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
                                       C.POINTER(ForceSchedule), C.POINTER(Record), C.c_void_p, C.POINTER(Grads),
-                                      C.c_void_p]),
+                                      C.c_void_p, C.c_size_t, C.c_void_p]),
     "ot_get_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
@@ -235,10 +236,17 @@ def rollout_plain(model, state, n_steps, step0=0, dt=2e-3, pulls=None, stream=No
                                   _stream_handle(stream)), "ot_rollout_plain")
 
 
-def rollout_backward(model, state, n_steps, step0, dt, pulls, record, dL_dtips, grads, stream=None):
+def backward_workspace_bytes(model, ckpt_every) -> int:
+    n = C.c_size_t(0)
+    _check(lib().ot_backward_workspace_bytes(model, int(ckpt_every), C.byref(n)), "ot_backward_workspace_bytes")
+    return n.value
+
+
+def rollout_backward(model, state, n_steps, step0, dt, pulls, record, dL_dtips, grads, workspace, stream=None):
     fs = pulls if pulls is not None else ForceSchedule(None, None, None)
     _check(lib().ot_rollout_backward(model, state, int(n_steps), int(step0), float(dt), C.byref(fs),
-                                     C.byref(record), _ptr(dL_dtips), C.byref(grads), _stream_handle(stream)),
+                                     C.byref(record), _ptr(dL_dtips), C.byref(grads), _ptr(workspace),
+                                     workspace.numel() * workspace.element_size(), _stream_handle(stream)),
            "ot_rollout_backward")
 
 
