@@ -1,12 +1,18 @@
 """Benchmark of the batched compliant-tree step (body-steps/s) on 1..N GPUs.
 
-Default workload: 4096 uneven trees (100-600 segment bodies, L-system depth 6-8, 20-120
-apples, random 0-60 N pulls on a quarter of the apples), 1000 simulation steps per bench step,
-run as one persistent, size-sorted, graph-captured, autotuned launch. A bench step is one
-rollout of the whole hot path over the batch. Under torchrun every rank simulates its own
-4096 freshly seeded trees (weak scaling; no collective on the data path).
+Default workload (batch4096): 4096 uneven trees (100-600 segment bodies, L-system depth 6-8,
+20-120 apples, random 0-60 N pulls on a quarter of the apples), 1000 simulation steps per
+bench step, run as one persistent, size-sorted, graph-captured, autotuned launch per size
+class. A bench step is one rollout of the whole hot path over the batch. Under torchrun every
+rank simulates its own freshly seeded trees (weak scaling; no collective on the data path).
+
+Beside the headline forward number the line carries: the plain form (one launch per world per
+step) on the same batch, the forward + adjoint leg on the differentiation workload (diff1024:
+1024 trees x 200 bodies x 30 apples, 200 steps, checkpoints every 20), the FP32 roofline
+fractions, and the FP64 oracle timed on the host cores on a bounded sample.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch4096|sweep16384|stress8192|plain16] [--worlds W]
 """
 from __future__ import annotations
 
@@ -39,14 +45,19 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", type=int, default=1)
+    p.add_argument("--workload", default="batch4096",
+                   help="batch4096 (default), sweep16384, stress8192 or plain16")
     p.add_argument("--worlds", type=int, default=None, help="override the number of worlds")
-    p.add_argument("--sim-steps", type=int, default=1000)
+    p.add_argument("--sim-steps", type=int, default=None, help="default: the workload's step count")
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--plain-steps", type=int, default=2)
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adj-worlds", type=int, default=None)
+    p.add_argument("--adj-steps", type=int, default=200)
+    p.add_argument("--adj-ckpt", type=int, default=20)
     return p.parse_args()
 
 
@@ -142,33 +153,37 @@ def measured_traffic(n_worlds):
     return None if per_world_step is None else per_world_step
 
 
-def cpu_baseline(forest, flags, seconds):
-    """The oracle as it stands on the host cores, on a bounded sample of the same workload."""
+def cpu_baseline(forest, flags, seconds, sim_steps):
+    """The oracle as it stands on the host cores, on a bounded sample of the same workload:
+    worlds stratified by size, the workload's own step count (capped at 1000), as many worlds
+    as fit in about `seconds` of host time."""
     import oracle as O
     from paper_2607_06337_b300 import costs
     cores = os.cpu_count() or 1
-    # stratified sample of worlds (by size), a few steps; grown until it takes ~`seconds`
     sizes = np.diff(forest.body_off)
     order = np.argsort(sizes)
-    n_w = min(max(cores, 8), forest.n_worlds)
-    pick = order[np.linspace(0, len(order) - 1, n_w).astype(int)]
-    sub = forest.subset(pick)
-    steps = 5
-    while True:
-        t = time.perf_counter()
-        O.rollout(sub, flags, steps, n_threads=cores)
-        dt = time.perf_counter() - t
-        if dt > seconds / 4 or steps >= 400:
-            break
-        steps = min(400, int(steps * max(2.0, seconds / 4 / max(dt, 1e-3))))
-    if dt < seconds / 2 and steps < 400:
-        steps = min(400, int(steps * seconds / max(dt, 1e-3)))
-        t = time.perf_counter()
-        O.rollout(sub, flags, steps, n_threads=cores)
-        dt = time.perf_counter() - t
+
+    def sample(n_w):
+        pick = np.sort(order[np.linspace(0, len(order) - 1, n_w).astype(int)])
+        return forest.subset(pick)
+
+    n_w = min(2 * cores, forest.n_worlds)
+    sub = sample(n_w)
+    probe_steps = 10
+    t = time.perf_counter()
+    O.rollout(sub, flags, probe_steps, n_threads=cores)
+    rate = costs.body_count(sub) * probe_steps / max(time.perf_counter() - t, 1e-6)
+    steps = min(sim_steps, 1000)
+    want = rate * seconds  # body-steps that fit in the time
+    n_w = int(min(forest.n_worlds, max(n_w, want / steps / max(costs.body_count(sub) / n_w, 1))))
+    sub = sample(n_w)
+    t = time.perf_counter()
+    O.rollout(sub, flags, steps, n_threads=cores)
+    dt = time.perf_counter() - t
     bs = costs.body_count(sub) * steps / dt
     return {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_w} worlds stratified by size x {steps} steps (FP64, {cores} threads), {dt:.1f} s"}
+            "sample": f"{n_w} of {forest.n_worlds} worlds stratified by size x {steps} steps "
+                      f"(FP64, {cores} threads), {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -178,11 +193,11 @@ def run_reference(args):
     from paper_2607_06337_b300 import costs
     from paper_2607_06337_b300 import inputs as I
     import oracle as O
-    nw = args.worlds or I.CONFIG_WORLDS[args.config]
+    nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
     fl = I.Flags()
     cores = os.cpu_count() or 1
     sample_w = min(max(cores, 8), nw)
-    forest = I.make_forest(args.config, n_worlds=nw, worlds=np.linspace(0, nw - 1, sample_w).astype(int))
+    forest = I.make_forest(args.workload, n_worlds=nw, worlds=np.linspace(0, nw - 1, sample_w).astype(int))
     steps = 10
     for _ in range(args.warmup):
         O.rollout(forest, fl, 2, n_threads=cores)
@@ -196,11 +211,113 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"config {args.config} sample: {sample_w} of {nw} worlds x {steps} steps"},
+            "config": {"workload": f"{args.workload} sample: {sample_w} of {nw} worlds x {steps} steps"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample_w} worlds x {steps} steps per bench step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fwd_adjoint(args, dev, rank, ws):
+    """Forward + adjoint body-steps/s on the differentiation workload: 1024 trees of 200
+    segment bodies and 30 apples, a 200-step rollout under a fixed 5 N pull on one apple per
+    tree, tip positions recorded, checkpoints every 20 steps; the loss is the squared error of
+    the tips against a target rollout, and the backward gives dL/dk, dL/dkd, dL/dq0, dL/dqd0.
+
+    The target here is this library's own rollout with every k scaled by U(0.8, 1.2) (the
+    timing does not depend on it; the tests take the target from the oracle)."""
+    import torch
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+    name = I.DIFF
+    nw = args.adj_worlds or I.WORKLOAD_WORLDS[name]
+    fl = I.Flags()
+    f = I.make_forest(name, n_worlds=nw, sweep=rank)
+    n, ce = args.adj_steps, args.adj_ckpt
+    sim = B.Simulator(f, fl, device=dev)
+    stream = torch.cuda.current_stream()
+    dev_in = [torch.as_tensor(np.ascontiguousarray(a, np.float32).reshape(-1), device=dev)
+              for a in (f.q0, f.qd0, f.apple_x0, f.apple_v0)]
+    k0 = torch.as_tensor(np.asarray(f.k, np.float32), device=dev)
+    rng = np.random.default_rng(4321 + rank)
+    kp = torch.as_tensor(np.asarray(f.k * rng.uniform(0.8, 1.2, f.n_bodies), np.float32), device=dev)
+    tips, ckpt, rec = sim.record_buffers(n, ce)
+    sim.set_gains(kp)
+    sim.reset_from_device(*dev_in)
+    sim.rollout(n, record=rec)
+    target = tips.clone()
+    sim.set_gains(k0)
+    if not args.no_autotune:
+        sim.reset_from_device(*dev_in)
+        sim.autotune(n_steps=20)
+    counts = np.diff(f.tip_off)
+    w_tip = torch.as_tensor(np.repeat(2.0 / (n * np.maximum(counts, 1)), counts).astype(np.float32),
+                            device=dev)[None, :, None]
+    work = torch.empty(B.backward_workspace_bytes(sim.model, ce), dtype=torch.uint8, device=dev)
+    grads = tuple(torch.zeros(m, dtype=torch.float32, device=dev) for m in (f.n_bodies, f.n_bodies, f.n_dofs,
+                                                                           f.n_dofs))
+    dtips = torch.empty_like(tips)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def one(k, ev=None):
+        flush.fill_(k & 0xff)
+        sim.reset_from_device(*dev_in)
+        if ev:
+            ev[0].record(stream)
+        sim.rollout(n, record=rec)
+        if ev:
+            ev[1].record(stream)
+        torch.sub(tips, target, out=dtips)
+        dtips.mul_(w_tip)
+        grads[0].zero_()
+        grads[1].zero_()
+        if ev:
+            ev[2].record(stream)
+        sim.backward(n, rec, dtips, grads=grads, workspace=work)
+        if ev:
+            ev[3].record(stream)
+
+    for k in range(args.warmup):
+        one(k)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    B.launch_count(reset=True)
+    for k in range(args.steps):
+        one(k, evs[k])
+    torch.cuda.synchronize()
+    launches = B.launch_count()
+    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    bwd_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    tot_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    bodies = costs.body_count(f)
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
+    peak_tf = fp32_peak_tflops(sm_mhz)
+    fwd_fl = costs.flops_per_step(f) * n
+    bwd_fl = costs.adjoint_flops_per_step(f) * n
+    g_ok = all(bool(torch.isfinite(g).all()) for g in grads)
+    return {
+        "workload": f"{nw} trees x 200 segment bodies x 30 apples, {n} steps, fixed 5 N pull, "
+                    f"checkpoints every {ce} steps, tip-tracking loss",
+        "value": ws * bodies * n / (tot_ms / 1e3), "unit": UNIT,
+        "ms_per_step": tot_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+        "fwd_only_value": ws * bodies * n / (fwd_ms / 1e3),
+        "gpu_launches": launches, "grads_finite": g_ok,
+        "roofline_backward": {"bound": "alu", "achieved": bwd_fl / (bwd_ms / 1e3) / 1e12, "peak": peak_tf,
+                              "unit": "TFLOP/s", "frac": bwd_fl / (bwd_ms / 1e3) / 1e12 / peak_tf,
+                              "flops_per_launch": bwd_fl},
+        "roofline_forward": {"bound": "alu", "achieved": fwd_fl / (fwd_ms / 1e3) / 1e12, "peak": peak_tf,
+                             "unit": "TFLOP/s", "frac": fwd_fl / (fwd_ms / 1e3) / 1e12 / peak_tf},
+        "l2": "flushed (256 MB write) before every timed step",
+    }
 
 
 def run_ours(args):
@@ -215,10 +332,10 @@ def run_ours(args):
     from paper_2607_06337_b300 import inputs as I
     from paper_2607_06337_b300 import orchard as B
 
-    nw = args.worlds or I.CONFIG_WORLDS[args.config]
+    nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
     fl = I.Flags()
-    forest = I.make_forest(args.config, n_worlds=nw, sweep=rank)
-    S = args.sim_steps
+    forest = I.make_forest(args.workload, n_worlds=nw, sweep=rank)
+    S = args.sim_steps or I.WORKLOAD_STEPS[args.workload]
     sim = B.Simulator(forest, fl, device=dev)
     stream = torch.cuda.current_stream()
     # pinned host copies of the initial state (inputs of every e2e step)
@@ -322,16 +439,18 @@ def run_ours(args):
            "unit": "GB/s", "bytes_per_launch": hbm_bytes}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
 
+    adj = None if args.no_adjoint else fwd_adjoint(args, dev, rank, ws)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(forest, fl, args.cpu_seconds)
+        cpu = cpu_baseline(forest, fl, args.cpu_seconds, S)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_mean, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"config {args.config}: {nw} uneven trees, {S} steps per bench step",
+            "config": {"workload": f"{args.workload}: {nw} trees, {S} steps per bench step",
                        "worlds_per_gpu": nw, "sim_steps": S, "bodies_per_gpu": bodies,
                        "segment_bodies": forest.n_bodies, "apples": forest.n_apples, "dofs": forest.n_dofs,
                        "l2": "flushed (256 MB write) before every timed rollout",
@@ -342,7 +461,7 @@ def run_ours(args):
             "hbm": hbm,
             "cpu_baseline": cpu,
             "plain": plain,
-            "fwd_adj": None,
+            "fwd_adj": adj,
             "clocks": clocks,
             "frozen_worlds": int((status & 1).sum()),
             "wall_s": wall,

@@ -129,6 +129,14 @@ void ot_model_release(ot_model* model);
 /* Counts of the uploaded forest: worlds, bodies, DOFs, apples, tips, size classes. */
 ot_status ot_model_counts(const ot_model* model, int64_t counts[6]);
 
+/* Replace the joint stiffness k and damping kd of every body (Sec. IV-A, Eq. 4 and the damping
+ * that follows it) in the uploaded model, in place, on `stream`: k, kd are device arrays [nb]
+ * in the forest's body order (either may be NULL to keep the current values). Values are
+ * taken as given (no check for sign or finiteness: that is the caller's). Steps and graphs
+ * enqueued after this call see the new values; nothing else of the model changes. This is
+ * how the differentiable rollout feeds k and kd from tensors. */
+ot_status ot_model_set_gains(ot_model* model, const float* k, const float* kd, void* stream);
+
 /* ---------------------------------------------------------------------------------------
  * World state: q, qd (FP32 per DOF), apple positions and velocities, break and detach flags,
  * counters and event steps, per-world status, plus the scratch area used by classes whose
@@ -209,15 +217,16 @@ ot_status ot_rollout_plain(ot_model* model, ot_state* state, int32_t n_steps, in
                            const ot_force_schedule* pulls, void* stream);
 
 /* ---------------------------------------------------------------------------------------
- * Adjoint of a recorded rollout with the break and detach masks frozen as recorded (the
- * gradient the spec differentiation pattern asks for; the paper never differentiates).
+ * Adjoint of a recorded rollout with the break and detach masks frozen as recorded (an
+ * addition: the paper simulates forward only and never differentiates the step).
  * The forward must have been run by ot_rollout with the same model, n_steps, step0, dt and
  * pulls, and a record holding checkpoints (ckpt, ckpt_every). The caller gives the cotangent
  * of the recorded tips, dL_dtips [n_steps][n_tips][3] (device); for the tip-tracking loss
  * L = sum_t sum_tips |p_t - p*_t|^2 / (n_steps n_tips_of_world) it is 2 (p - p*) / (...).
  * Gradients (device, any may be NULL): dk, dkd [nb] per joint are ACCUMULATED into; dq0,
  * dqd0 [n_dofs] (the initial state) are written. Each segment between checkpoints is
- * recomputed forward (bitwise as in the forward) and then swept in reverse step by step.
+ * recomputed forward with the forward's step code (equal to the recorded run up to the last
+ * bits: it is compiled into another kernel) and then swept in reverse step by step.
  * workspace: device buffer of at least ot_backward_workspace_bytes bytes (256-byte aligned). */
 typedef struct ot_grads {
   float* dk;

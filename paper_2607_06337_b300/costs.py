@@ -14,6 +14,16 @@ of DOF ancestors of DOF i):
 
   flops = 589 n_b + 182 n_a + 48 n_v + 24 E + 3 P.
 
+Adjoint, per world and step of the backward pass (n_t tips): the segment replay and the
+recompute that supplies the step's factors run the forward step twice, then
+
+  tape            138 / body + 75 / DOF   (kinematics, accelerations, virtual velocities)
+  reverse sweep   978 / body + 189 / DOF + 246 / apple + 21 / tip
+  apple update, springs, hang-load sweep and the solve with the step's factors:
+                   21 / body + 30 / DOF + 48 / apple + 5 / ancestor entry
+
+  flops = 2 * forward + 1137 n_b + 294 n_v + 294 n_a + 5 E + 21 n_t.
+
 Bytes: the persistent rollout keeps a world's temporaries on chip and re-reads its model from
 L2, so the unavoidable HBM traffic per rollout is one read of the model and one read and write
 of the state.
@@ -27,6 +37,12 @@ F_APPLE = 182
 F_DOF = 48
 F_ENTRY = 24
 F_PAIR = 3
+
+A_BODY = 1137
+A_DOF = 294
+A_APPLE = 294
+A_ENTRY = 5
+A_TIP = 21
 
 MODEL_BYTES_PER_BODY = 6 * 16   # int4 + 5 float4
 MODEL_BYTES_PER_DOF = 16        # int4
@@ -71,6 +87,14 @@ def world_terms(forest):
 def flops_per_step(forest) -> float:
     nb, nv, na, E, P = world_terms(forest)
     return float(np.sum(F_BODY * nb + F_APPLE * na + F_DOF * nv + F_ENTRY * E + F_PAIR * P))
+
+
+def adjoint_flops_per_step(forest) -> float:
+    """Flops of one step of the backward pass (two forward recomputations included)."""
+    nb, nv, na, E, P = world_terms(forest)
+    nt = np.diff(forest.tip_off).astype(np.int64)
+    return 2.0 * flops_per_step(forest) + float(np.sum(A_BODY * nb + A_DOF * nv + A_APPLE * na + A_ENTRY * E +
+                                                        A_TIP * nt))
 
 
 def hbm_bytes_per_rollout(forest) -> float:

@@ -442,7 +442,11 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
     const float qd = s.qd[i];
     f3 eb = mk(0, 0, 0);
     float qdbar = 0.f;
-    // alpha += qd (w x e) + qdd e ; a += qd (vin x e) ; w += qd e ; Lw += lam e ; Ow += qd1 e
+    // forward order: alpha += qd (w x e) + qdd e ; a += qd (vin x e) (both with the w before
+    // this DOF) ; w += qd e ; Lw += lam e ; Ow += qd1 e. Reversed last to first, so the w
+    // update is undone before the alpha term adds its part to w-bar.
+    qdbar += dot(wb_, e);
+    eb = eb + qd * wb_;
     if (ra.dyn) {
       const float qdd = ra.delta[i] / dt;
       qdbar += dot(alb, cross(wo, e));
@@ -453,8 +457,6 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
       eb = eb + qd * cross(ab_, vin);
       eb = eb + ra.lam[i] * lwb;
     }
-    qdbar += dot(wb_, e);
-    eb = eb + qd * wb_;
     qdbar += dot(owb, e);  // qd' = qd + Delta with Delta fixed
     eb = eb + ra.qd1[i] * (owb + owh);
     if (j == 0) Rb_.c0 = Rb_.c0 + eb;

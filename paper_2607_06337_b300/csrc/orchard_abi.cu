@@ -361,6 +361,18 @@ template <class T> size_t vbytes(const std::vector<T>& v) { return v.size() * si
 
 }  // namespace
 
+namespace orchard {
+// k and kd live in the z and w lanes of the per-body record bp3.
+__global__ void set_gains_kernel(float4* bp3, const float* k, const float* kd, int nb) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  float4 v = bp3[b];
+  if (k) v.z = k[b];
+  if (kd) v.w = kd[b];
+  bp3[b] = v;
+}
+}  // namespace orchard
+
 struct ot_model {
   Packed P;
   DevModel dev{};
@@ -674,6 +686,18 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
 }
 
 void ot_model_release(ot_model* model) { delete model; }
+
+ot_status ot_model_set_gains(ot_model* m, const float* k, const float* kd, void* stream) {
+  if (!m) return OT_EINVAL;
+  if (!k && !kd) return OT_OK;
+  const int nb = m->P.NB;
+  if (nb == 0) return OT_OK;
+  const int threads = 256, blocks = (nb + threads - 1) / threads;
+  set_gains_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(const_cast<float4*>(m->dev.bp3), k, kd, nb);
+  OT_CUDA(cudaGetLastError());
+  g_launches += 1;
+  return OT_OK;
+}
 
 ot_status ot_model_counts(const ot_model* m, int64_t counts[6]) {
   if (!m || !counts) return OT_EINVAL;

@@ -23,7 +23,8 @@ per-apple descriptor values that the step takes as inputs:
 * the external pull schedule on apples.
 
 Every value is derived in float64 from a ``numpy.random.Generator(PCG64(seed))`` with
-seed = 1_000_003 * config + world, so both sides receive bit-identical inputs.
+seed = 1_000_003 * (the workload's position in WORKLOADS) + world, so both sides receive
+bit-identical inputs.
 """
 from __future__ import annotations
 
@@ -278,20 +279,30 @@ class WorldRecipe:
     pulls: str = "none"           # "none" | "random25" | "fixed5"
 
 
-CONFIG_STEPS = {0: 1000, 1: 1000, 2: 1000, 3: 200, 4: 500}
+# The workloads, by name. The position of a name in WORKLOADS is its seed stream.
+PLAIN = "plain16"        # 16 trees x 64 bodies (depth 5) x 8 apples, gravity only, 1000 steps
+BATCH = "batch4096"      # 4096 uneven trees: 100-600 bodies, depth 6-8, 20-120 apples,
+                         # random 0-60 N pulls on a quarter of the apples, 1000 steps
+SWEEP = "sweep16384"     # 16384 trees x 300 bodies (depth 8) x 60 apples, 1000 steps
+DIFF = "diff1024"        # 1024 trees x 200 bodies (depth 8) x 30 apples, a fixed 5 N pull, 200 steps
+STRESS = "stress8192"    # 8192 mixed trees: half 50 bodies, 40% 400, 10% 2000 (depth 6/8/10),
+                         # 10-200 apples, 500 steps
+WORKLOADS = (PLAIN, BATCH, SWEEP, DIFF, STRESS)
+WORKLOAD_WORLDS = {PLAIN: 16, BATCH: 4096, SWEEP: 16384, DIFF: 1024, STRESS: 8192}
+WORKLOAD_STEPS = {PLAIN: 1000, BATCH: 1000, SWEEP: 1000, DIFF: 200, STRESS: 500}
 
 
-def world_recipe(config: int, w: int, n_worlds: int, rng: np.random.Generator) -> WorldRecipe:
-    if config == 0:
+def world_recipe(workload: str, w: int, n_worlds: int, rng: np.random.Generator) -> WorldRecipe:
+    if workload == PLAIN:
         return WorldRecipe(64, 5, 8)
-    if config == 1:
+    if workload == BATCH:
         return WorldRecipe(int(rng.integers(100, 601)), int(rng.integers(6, 9)),
                            int(rng.integers(20, 121)), "random25")
-    if config == 2:
+    if workload == SWEEP:
         return WorldRecipe(300, 8, 60)
-    if config == 3:
+    if workload == DIFF:
         return WorldRecipe(200, 8, 30, "fixed5")
-    if config == 4:
+    if workload == STRESS:
         frac = (w + 0.5) / n_worlds
         n_a = int(rng.integers(10, 201))
         if frac < 0.5:
@@ -299,33 +310,32 @@ def world_recipe(config: int, w: int, n_worlds: int, rng: np.random.Generator) -
         if frac < 0.9:
             return WorldRecipe(400, 8, n_a)
         return WorldRecipe(2000, 10, n_a)
-    raise ValueError(f"unknown config {config}")
+    raise ValueError(f"unknown workload {workload!r}")
 
 
-CONFIG_WORLDS = {0: 16, 1: 4096, 2: 16384, 3: 1024, 4: 8192}
+def world_seed(workload: str, w: int, sweep: int = 0) -> int:
+    return 1_000_003 * WORKLOADS.index(workload) + w + 10_000_019 * sweep
 
 
-def world_seed(config: int, w: int, sweep: int = 0) -> int:
-    return 1_000_003 * config + w + 10_000_019 * sweep
-
-
-def make_forest(config: int, n_worlds: int | None = None, worlds=None, sweep: int = 0,
+def make_forest(workload: str, n_worlds: int | None = None, worlds=None, sweep: int = 0,
                 recipe_override: WorldRecipe | None = None) -> Forest:
-    """Generate the synthetic workload of a config (optionally a subset of its worlds).
+    """Generate a named workload (optionally a subset of its worlds).
 
-    ``worlds`` picks world indices of the full config (the seeds do not change), so a subset
+    ``worlds`` picks world indices of the full workload (the seeds do not change), so a subset
     holds exactly the same trees as the full batch. ``sweep`` > 0 draws fresh seeds of the
-    same distribution (the world-count sweep).
+    same distribution (the world-count sweep, and one batch per rank).
     """
-    full = CONFIG_WORLDS[config] if n_worlds is None else n_worlds
+    if workload not in WORKLOADS:
+        raise ValueError(f"unknown workload {workload!r}; one of {WORKLOADS}")
+    full = WORKLOAD_WORLDS[workload] if n_worlds is None else n_worlds
     worlds = list(range(full)) if worlds is None else [int(w) for w in worlds]
     per = []
     for w in worlds:
-        rng = np.random.Generator(np.random.PCG64(world_seed(config, w, sweep)))
-        rec = recipe_override or world_recipe(config, w, full, rng)
+        rng = np.random.Generator(np.random.PCG64(world_seed(workload, w, sweep)))
+        rec = recipe_override or world_recipe(workload, w, full, rng)
         per.append(_make_world(rng, rec))
     forest = _pack(per)
-    forest.meta.update(config=config, n_worlds_full=full, worlds=worlds, sweep=sweep)
+    forest.meta.update(workload=workload, n_worlds_full=full, worlds=worlds, sweep=sweep)
     return forest
 
 

@@ -92,6 +92,7 @@ _SIGS = {
                                        C.c_void_p, C.POINTER(C.c_void_p)]),
     "ot_model_release": (None, [C.c_void_p]),
     "ot_model_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "ot_model_set_gains": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ot_state_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "ot_world_state_alloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
     "ot_state_release": (None, [C.c_void_p]),
@@ -205,6 +206,14 @@ def tree_model_upload(forest, flags, dev_buf, stream=None):
     return h
 
 
+def model_set_gains(model, k=None, kd=None, stream=None):
+    """Write per-body k and kd (float32 device tensors [nb], either may be None) into the model."""
+    for t in (k, kd):
+        if t is not None and (t.dtype.itemsize != 4 or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("gains must be contiguous float32 CUDA tensors")
+    _check(lib().ot_model_set_gains(model, _ptr(k), _ptr(kd), _stream_handle(stream)), "ot_model_set_gains")
+
+
 def state_bytes(model) -> int:
     n = C.c_size_t(0)
     _check(lib().ot_state_bytes(model, C.byref(n)), "ot_state_bytes")
@@ -295,6 +304,8 @@ class Simulator:
         self.forest = forest
         self.flags = flags
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.model_buf = torch.empty(model_bytes(forest), dtype=torch.uint8, device=self.device)
         self.model = tree_model_upload(forest, flags, self.model_buf, stream)
         cnt = (C.c_int64 * 6)()
@@ -360,6 +371,36 @@ class Simulator:
     def step(self, step_index=0, ext_force=None, dt=None, stream=None):
         step(self.model, self.state, ext_force, self.pulls, step_index, self.flags.dt if dt is None else dt,
              stream)
+
+    def set_gains(self, k=None, kd=None, stream=None):
+        """Per-body joint stiffness and damping from float32 device tensors [bodies]."""
+        model_set_gains(self.model, k, kd, stream)
+
+    def record_buffers(self, n_steps, ckpt_every, tips=True):
+        """Device buffers for a recorded rollout: tips [n_steps, n_tips, 3] and checkpoints."""
+        import torch
+        t = torch.empty((n_steps, self.counts.tips, 3), dtype=torch.float32, device=self.device) if tips else None
+        nb = ckpt_bytes(self.model, n_steps, ckpt_every)
+        ck = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        rec = Record(None if t is None else t.data_ptr(), ck.data_ptr(), nb, ckpt_every)
+        return t, ck, rec
+
+    def backward(self, n_steps, record, dL_dtips, step0=0, dt=None, grads=None, workspace=None, stream=None):
+        """Adjoint of a recorded rollout. Returns (dk, dkd, dq0, dqd0) as float32 device tensors.
+
+        dk and dkd are accumulated into when given in ``grads``; fresh zeroed ones otherwise."""
+        import torch
+        c = self.counts
+        if grads is None:
+            grads = tuple(torch.zeros(n, dtype=torch.float32, device=self.device)
+                          for n in (c.bodies, c.bodies, c.dofs, c.dofs))
+        if workspace is None:
+            workspace = torch.empty(backward_workspace_bytes(self.model, record.ckpt_every), dtype=torch.uint8,
+                                    device=self.device)
+        g = Grads(*[t.data_ptr() if t.numel() else None for t in grads])
+        rollout_backward(self.model, self.state, n_steps, step0, self.flags.dt if dt is None else dt, self.pulls,
+                         record, dL_dtips.contiguous(), g, workspace, stream)
+        return grads
 
     def schedules(self):
         return [get_schedule(self.model, k) for k in range(self.counts.classes)]

@@ -36,7 +36,7 @@ def chain(n, seg_len, diam, rho, E, kd, ndof=1, apple=None, gravity=(0.0, 0.0, 0
 def small_random_tree(seed, n_b=6, depth=3, n_a=0, ndof=2, root_ndof=0):
     """A generated world of a few bodies (same recipe as the configs, smaller)."""
     rec = I.WorldRecipe(n_b, depth, n_a)
-    f = I.make_forest(0, n_worlds=1, worlds=[0], sweep=1000 + seed, recipe_override=rec)
+    f = I.make_forest(I.PLAIN, n_worlds=1, worlds=[0], sweep=1000 + seed, recipe_override=rec)
     if ndof != 2 or root_ndof != 0:
         nd = np.where(f.parent >= 0, ndof, root_ndof).astype(np.int32)
         f.ndof = nd

@@ -43,7 +43,7 @@ def test_status_strings(orch):
 
 
 def test_model_bytes_of_a_generated_forest(orch):
-    f = I.make_forest(0, worlds=[0, 1])
+    f = I.make_forest(I.PLAIN, worlds=[0, 1])
     n = orch.model_bytes(f)
     assert n > 0 and n % 256 == 0
 
@@ -56,7 +56,7 @@ def _status_of(orch, f):
 
 
 def test_validation_rejects_bad_descriptors(orch):
-    good = I.make_forest(0, worlds=[0])
+    good = I.make_forest(I.PLAIN, worlds=[0])
     assert _status_of(orch, good) == orch.OT_OK
     # not breadth-first: swap two parents so the parent array decreases
     f = good.subset([0])
@@ -99,7 +99,7 @@ def test_validation_rejects_bad_descriptors(orch):
 
 
 def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
-    f = I.make_forest(0, worlds=[0])
+    f = I.make_forest(I.PLAIN, worlds=[0])
     keep = orch._Keep()
     d = orch.make_desc(f, keep)
     fl = orch.make_flags(I.Flags())
@@ -118,7 +118,7 @@ def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
 
 def test_flop_count_scales_with_the_terms():
     from paper_2607_06337_b300 import costs
-    f = I.make_forest(0, worlds=[0])
+    f = I.make_forest(I.PLAIN, worlds=[0])
     nb, nv, na, E, P = costs.world_terms(f)
     assert nv[0] == 2 * (nb[0] - 1)
     depth = costs.dof_depths(f)

@@ -1,0 +1,172 @@
+"""Adjoint kernel (ot_rollout_backward, and the autograd wrapper over it) against the FP64
+oracle's complex-step derivative and central finite differences of the tip-tracking loss.
+
+Tolerance, per kind of coordinate (k, kd, q0, qd0) and per world, relative to the largest
+sampled magnitude of that kind: 2e-3 against the complex-step derivative, 3e-3 against central
+differences (which add their own O(h^2) error). Derivation: the loss is a sum of squared
+residuals p - p*, and the FP32 tips differ from the FP64 ones by about 5e-4 of the rms residual
+for the +-20% stiffness target over 200 steps; the serial FP32 evaluation of the same adjoint
+arithmetic lands within 3e-4 of the complex-step derivative on that workload, so 2e-3 leaves a
+factor of about 7 for the GPU's different summation order.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2607_06337_b300 import inputs as I
+from tests import parity as PAR
+from tests.test_oracle_grad import fd_steps, sample_coords
+
+pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
+
+TOL_CS = 2e-3
+TOL_FD = 3e-3
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def perturbed_target(f, fl, n, seed=7):
+    """Target tips: the oracle's rollout of the same forest with every k scaled by U(0.8, 1.2)."""
+    rng = np.random.default_rng(seed)
+    g = dataclasses.replace(f, k=f.k * rng.uniform(0.8, 1.2, f.n_bodies))
+    _, rec = O.rollout(g, fl, n, record_tips=True)
+    return rec["tips"]
+
+
+def tip_cotangent(f, tips, target):
+    """dL/dtips (float64 tensors) of L = sum over worlds of sum_t sum_tips |p - p*|^2 / (n_steps
+    n_tips_of_world)."""
+    torch = _torch()
+    n = tips.shape[0]
+    counts = np.diff(f.tip_off)
+    scale = torch.as_tensor(np.repeat(1.0 / (n * np.maximum(counts, 1)), counts), device=tips.device)
+    return 2.0 * (tips - target) * scale[None, :, None]
+
+
+def gpu_gradients(f, fl, n, ckpt_every, target, sim=None):
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Simulator
+    sim = sim or Simulator(f, fl)
+    sim.reset()
+    tips, ck, rec = sim.record_buffers(n, ckpt_every)
+    sim.rollout(n, record=rec)
+    tg = torch.as_tensor(np.asarray(target, np.float32), device="cuda")
+    dt = tip_cotangent(f, tips.double(), tg.double()).float()
+    grads = sim.backward(n, rec, dt)
+    torch.cuda.synchronize()
+    g = [x.cpu().numpy().astype(np.float64) for x in grads]
+    ev = dict(broken=sim.broken.cpu().numpy(), break_step=sim.break_step.cpu().numpy(),
+              detached=sim.detached.cpu().numpy(), detach_step=sim.detach_step.cpu().numpy())
+    return g, ev, sim
+
+
+def pick(f, w, g, kinds, idx):
+    b0, d0 = f.body_off[w], f.dof_off[w]
+    return np.array([g[k][(b0 if k < 2 else d0) + i] for k, i in zip(kinds, idx)])
+
+
+def assert_close_per_kind(got, ref, kinds, tol, what):
+    for kind in range(4):
+        s = kinds == kind
+        if not s.any():
+            continue
+        scale = np.abs(ref[s]).max()
+        err = np.abs(got[s] - ref[s]).max()
+        assert err <= tol * scale + 1e-30, (
+            f"{what}: {['k', 'kd', 'q0', 'qd0'][kind]} max err {err:.3e} vs scale {scale:.3e}\n"
+            f"got {got[s]}\nref {ref[s]}")
+
+
+def test_adjoint_differentiation_workload_against_oracle():
+    """Four worlds of the differentiation workload (200 bodies, 30 apples, a fixed 5 N pull),
+    200 steps, checkpoints every 20 steps; target from the oracle with k perturbed by +-20%."""
+    f = I.make_forest(I.DIFF, worlds=[0, 1, 2, 3])
+    fl = I.Flags()
+    n = 200
+    target = perturbed_target(f, fl, n)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    rng = np.random.default_rng(5)
+    for w in range(f.n_worlds):
+        kinds, idx = sample_coords(f, w, 4, rng)
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+        got = pick(f, w, g, kinds, idx)
+        assert_close_per_kind(got, g_cs, kinds, TOL_CS, f"world {w} vs complex step")
+        if w == 0:
+            g_fd, _ = O.grad(f, fl, w, n, tw, kinds, idx, fd_steps(f, w, kinds, idx), mode=1)
+            assert_close_per_kind(got, g_fd, kinds, TOL_FD, f"world {w} vs central differences")
+
+
+def test_adjoint_with_breaks_and_detaches_masks_frozen():
+    """Worlds of the batching workload in which a branch breaks and apples detach within 200
+    steps: with the masks frozen as recorded, the adjoint matches the oracle's complex-step
+    derivative (whose real part, and so every event, is that of the unperturbed rollout)."""
+    f = I.make_forest(I.BATCH, worlds=[23, 79])
+    fl = I.Flags()
+    n = 200
+    st, rec = O.rollout(f, fl, n, record_tips=True, near_eps=PAR.NEAR)
+    assert st.broken.sum() > 0 and (st.detached > 0).sum() > 0
+    rng = np.random.default_rng(2)
+    target = rec["tips"] + rng.normal(0.0, 0.02, rec["tips"].shape)
+    g, ev, _ = gpu_gradients(f, fl, n, 25, target)
+    for w in range(f.n_worlds):
+        ref_ev = PAR.events(st.broken, st.break_step, st.detached, st.detach_step, f, w)
+        got_ev = PAR.events(ev["broken"], ev["break_step"], ev["detached"], ev["detach_step"], f, w)
+        assert got_ev == ref_ev, f"world {w}: event sets differ, the gradients are not comparable"
+        kinds, idx = sample_coords(f, w, 4, rng)
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, TOL_CS, f"world {w} with events")
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    """Every checkpoint interval, including one that does not divide the step count and one
+    longer than the rollout, gives the same gradient: the replayed segments run the forward's
+    step code (compiled into another kernel, so equal up to the last bits of each step, not
+    bitwise), and the gradients agree to 1e-5 of each kind's largest entry."""
+    f = I.make_forest(I.DIFF, worlds=[7, 8])
+    fl = I.Flags()
+    n = 50
+    target = perturbed_target(f, fl, n)
+    ref, _, sim = gpu_gradients(f, fl, n, 1, target)
+    for ce in (7, 20, 50, 64):
+        got, _, _ = gpu_gradients(f, fl, n, ce, target, sim=sim)
+        for a, b in zip(got, ref):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
+
+
+def test_autograd_function_matches_the_direct_call():
+    """tip_rollout + tip_loss + loss.backward() gives the gradients of ot_rollout_backward, and
+    the forward returns the tips of a plain recorded rollout."""
+    torch = _torch()
+    from paper_2607_06337_b300.autograd import tip_loss, tip_rollout
+    f = I.make_forest(I.DIFF, worlds=[9, 10, 11])
+    fl = I.Flags()
+    n = 60
+    target = perturbed_target(f, fl, n).astype(np.float32).astype(np.float64)  # same bits on both paths
+    g_ref, _, sim = gpu_gradients(f, fl, n, 20, target)
+    dev = "cuda"
+    k = torch.tensor(f.k, dtype=torch.float32, device=dev, requires_grad=True)
+    kd = torch.tensor(f.kd, dtype=torch.float32, device=dev, requires_grad=True)
+    q0 = torch.tensor(f.q0, dtype=torch.float32, device=dev, requires_grad=True)
+    qd0 = torch.tensor(f.qd0, dtype=torch.float32, device=dev, requires_grad=True)
+    tips = tip_rollout(sim, k, kd, q0, qd0, n, ckpt_every=20)
+    loss = tip_loss(tips.double(), torch.as_tensor(target, device=dev), f.tip_off)
+    loss.backward()
+    for t, r in zip((k, kd, q0, qd0), g_ref):
+        np.testing.assert_allclose(t.grad.cpu().numpy(), r, rtol=0, atol=1e-5 * np.abs(r).max())
+    # the loss itself agrees with the oracle's at the unperturbed gains
+    lo = sum(O.grad(f, fl, w, n, target[:, f.tip_off[w]:f.tip_off[w + 1]], [2], [0], [1e-20], mode=0)[1]
+             for w in range(f.n_worlds))
+    assert float(loss) == pytest.approx(lo, rel=1e-3)
+    # a second forward with scaled gains changes the tips; its backward uses its own gains
+    k2 = (k.detach() * 1.1).requires_grad_(True)
+    tips2 = tip_rollout(sim, k2, kd.detach(), q0.detach(), qd0.detach(), n, ckpt_every=20)
+    assert not torch.equal(tips2, tips)

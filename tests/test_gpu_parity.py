@@ -50,7 +50,7 @@ def _run(f, flags, n_steps, form="batched", record_tips=False):
 @pytest.mark.parametrize("form", ["batched", "plain"])
 def test_config0_plain_parity_1000_steps(form):
     """16 worlds x 64 bodies x 8 apples, gravity only, 1000 steps (the plain-form workload)."""
-    f = I.make_forest(0)
+    f = I.make_forest(I.PLAIN)
     fl = I.Flags()
     g = _run(f, fl, 1000, form)
     st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
@@ -61,7 +61,7 @@ def test_config0_plain_parity_1000_steps(form):
 
 
 def test_step_by_step_equals_rollout():
-    f = I.make_forest(1, worlds=[5, 6, 7])
+    f = I.make_forest(I.BATCH, worlds=[5, 6, 7])
     fl = I.Flags()
     a = _run(f, fl, 60, "batched")
     b = _run(f, fl, 60, "step")
@@ -71,7 +71,7 @@ def test_step_by_step_equals_rollout():
 
 def test_config1_subset_with_pulls_and_events():
     """Uneven trees (100-600 bodies) with random pulls: q gate and identical event sets."""
-    f = I.make_forest(1, worlds=[0, 1, 2, 3, 17, 33, 64, 101])
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 3, 17, 33, 64, 101])
     fl = I.Flags()
     g = _run(f, fl, 1000)
     st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
@@ -81,7 +81,7 @@ def test_config1_subset_with_pulls_and_events():
 
 
 def test_tip_record_matches_oracle():
-    f = I.make_forest(3, worlds=[0, 1, 2])
+    f = I.make_forest(I.DIFF, worlds=[0, 1, 2])
     fl = I.Flags()
     g = _run(f, fl, 200, record_tips=True)
     st, rec = O.rollout(f, fl, 200, record_tips=True)
@@ -91,7 +91,7 @@ def test_tip_record_matches_oracle():
 
 def test_stress_classes_including_global_workspace():
     """50 / 400 / 2000-body worlds (the 2000-body class runs with its workspace in global memory)."""
-    f = I.make_forest(4, worlds=[0, 4096, 8000])  # one world per size class
+    f = I.make_forest(I.STRESS, worlds=[0, 4096, 8000])  # one world per size class
     assert sorted(np.diff(f.body_off)) == [50, 400, 2000]
     fl = I.Flags()
     g = _run(f, fl, 150)
@@ -111,7 +111,7 @@ def test_edge_cases_single_body_and_chain():
     hinge.q0[:] = 0.3
     chain, _ = T.chain(12, 0.1, 0.01, 700.0, 1e9, kd=0.05, gravity=(0.0, 0.0, -9.81))
     chain.q0[:] = np.linspace(0.05, -0.05, 12)
-    tree = I.make_forest(0, worlds=[0])
+    tree = I.make_forest(I.PLAIN, worlds=[0])
     f = _concat([post, hinge, chain, tree])
     fl = I.Flags()
     g = _run(f, fl, 300)
@@ -122,7 +122,7 @@ def test_edge_cases_single_body_and_chain():
 
 
 def test_nonfinite_world_is_frozen_others_continue():
-    f = I.make_forest(0, worlds=[0, 1])
+    f = I.make_forest(I.PLAIN, worlds=[0, 1])
     f.q0 = f.q0.copy()
     f.q0[f.dof_off[1] + 3] = np.nan
     fl = I.Flags()
@@ -162,7 +162,7 @@ def test_classes_sharing_a_kernel_instantiation():
     one uniform schedule set through the ABI) must all run and agree with the oracle."""
     torch = _torch()
     from paper_2607_06337_b300 import orchard as B
-    f = I.make_forest(1, worlds=list(range(0, 96, 2)))
+    f = I.make_forest(I.BATCH, worlds=list(range(0, 96, 2)))
     fl = I.Flags()
     st, rec = O.rollout(f, fl, 30, near_eps=PAR.NEAR)
     sim = B.Simulator(f, fl)

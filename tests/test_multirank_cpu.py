@@ -25,7 +25,7 @@ def _free_port():
 def _worker(rank, ws, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
-    f = I.make_forest(1, n_worlds=8, worlds=range(8), sweep=rank)  # the bench seeds rank r with sweep r
+    f = I.make_forest(I.BATCH, n_worlds=8, worlds=range(8), sweep=rank)  # the bench seeds rank r with sweep r
     bodies = torch.tensor([costs.body_count(f)], dtype=torch.float64)
     t = torch.tensor([1.0 + rank], dtype=torch.float64)  # a rank's timed milliseconds
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -44,7 +44,7 @@ def test_two_rank_weak_scaling_host_logic():
     t1, b1, nb1, k1 = out[1]
     assert t0 == t1 == 2.0                     # max over ranks
     assert b0 == b1                            # every rank sees the total
-    f0 = I.make_forest(1, n_worlds=8, worlds=range(8), sweep=0)
-    f1 = I.make_forest(1, n_worlds=8, worlds=range(8), sweep=1)
+    f0 = I.make_forest(I.BATCH, n_worlds=8, worlds=range(8), sweep=0)
+    f1 = I.make_forest(I.BATCH, n_worlds=8, worlds=range(8), sweep=1)
     assert b0 == costs.body_count(f0) + costs.body_count(f1)
     assert k0 != k1                            # the ranks hold different trees

@@ -26,7 +26,7 @@ def _without_apples(f):
 # Apple at rest: the reaction vanishes, the tree behaves as if it bore no fruit (Sec. IV-C)
 # ------------------------------------------------------------------------------------------
 def test_reaction_vanishes_at_rest_sag():
-    f = I.make_forest(0, worlds=[0])
+    f = I.make_forest(I.PLAIN, worlds=[0])
     ev = O.evaluate(f, I.Flags(), 0, np.zeros(f.n_dofs), np.zeros(f.n_dofs), ax=f.apple_x0, av=f.apple_v0,
                     detached=np.zeros(f.n_apples, np.int32), fext=np.zeros((f.n_apples, 3)))
     assert np.abs(ev["fapp"]).max() < 1e-12
@@ -38,7 +38,7 @@ def test_apples_at_rest_sag_do_not_load_a_tree_at_rest(implicit):
     """Sec. IV-C: only the elastic perturbation beyond rest is transmitted, so apples hanging at
     their rest sag below a tree in equilibrium leave its trajectory that of the bare tree (to
     rounding), with the reaction taken explicitly or implicitly."""
-    f = I.make_forest(0, worlds=[1])
+    f = I.make_forest(I.PLAIN, worlds=[1])
     bare = _without_apples(f)
     settle = I.Flags(dt=0.01)
     sb, _ = O.rollout(bare, settle, 4000, n_threads=1)
@@ -55,7 +55,7 @@ def test_apples_at_rest_sag_do_not_load_a_tree_at_rest(implicit):
 def test_implicit_tether_keeps_the_bare_tree_rest_pose():
     """With the coupled backward-Euler tether the dynamics feel the apple's inertia, but the
     settled pose under gravity is still exactly the bare tree's."""
-    f = I.make_forest(0, worlds=[2])
+    f = I.make_forest(I.PLAIN, worlds=[2])
     fl = I.Flags(tether_implicit=1, dt=0.01)
     sa, _ = O.rollout(f, fl, 4000, n_threads=1)
     sb, _ = O.rollout(_without_apples(f), fl, 4000, n_threads=1)

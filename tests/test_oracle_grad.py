@@ -1,0 +1,121 @@
+"""Pins of the oracle's loss gradient (the reference for the adjoint kernel), CPU only.
+
+The oracle differentiates the tip-tracking loss by complex step (every function is templated
+on the scalar, so the same step code runs in std::complex<double>), exact to rounding as long
+as the arithmetic is holomorphic in the perturbed inputs. These tests pin that derivative to
+two things outside the oracle: the hand-differentiated closed-form recurrence of a single
+hinge, and central finite differences on a full generated world with apples and a pull.
+"""
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle as O
+from paper_2607_06337_b300 import inputs as I
+from tests import _trees as T
+
+pytestmark = pytest.mark.usefixtures("oracle_lib")
+
+
+def _hinge_recurrence_and_derivatives(J, dt, alpha):
+    """A(k, kd) of the single-hinge recurrence x' = A x, x = (q, qd) (the semi-implicit step with
+    implicit damping and, for alpha = 1, implicit springs; Sec. IV-A), and dA/dk, dA/dkd by
+    symbolic differentiation."""
+    k, kd = sp.symbols("k kd", positive=True)
+    H = J + dt * kd + alpha * dt * dt * k
+    a = dt * (alpha * dt * k + kd) / H
+    A = sp.Matrix([[1 - dt * dt * k / H, dt * (1 - a)], [-dt * k / H, 1 - a]])
+    f = sp.lambdify((k, kd), A, "numpy")
+    fk = sp.lambdify((k, kd), A.diff(k), "numpy")
+    fkd = sp.lambdify((k, kd), A.diff(kd), "numpy")
+    return (lambda kv, kdv: np.array(f(kv, kdv), float), lambda kv, kdv: np.array(fk(kv, kdv), float),
+            lambda kv, kdv: np.array(fkd(kv, kdv), float))
+
+
+@pytest.mark.parametrize("alpha", [0, 1])
+def test_single_hinge_gradient_closed_form(alpha):
+    """One body on a hinge about x, no gravity, tip at (0, 0, l): p(q) = (0, -l sin q, l cos q).
+    The loss sum_t |p(q_t) - p*_t|^2 / n is differentiated by forward-mode propagation of the
+    2x2 recurrence (dx_(t+1) = A dx_t + dA x_t) and compared with the oracle's derivative."""
+    kval, kdval, length = 50.0, 0.3, 0.2
+    f, J, m = T.single_hinge(k=kval, kd=kdval, length=length)
+    q0, qd0 = 0.05, -0.4
+    f.q0[0], f.qd0[0] = q0, qd0
+    fl = I.Flags(alpha_implicit_spring=alpha)
+    n = 120
+    rng = np.random.default_rng(3)
+    target = rng.normal(0.0, 0.05, (n, 1, 3)) + np.array([0.0, 0.0, length])
+
+    A, dAk, dAkd = _hinge_recurrence_and_derivatives(J, fl.dt, alpha)
+    Am, Ak, Akd = A(kval, kdval), dAk(kval, kdval), dAkd(kval, kdval)
+    x = np.array([q0, qd0])
+    dx = {"k": np.zeros(2), "kd": np.zeros(2), "q0": np.array([1.0, 0.0]), "qd0": np.array([0.0, 1.0])}
+    grad = dict.fromkeys(dx, 0.0)
+    loss = 0.0
+    for t in range(n):
+        dx = {"k": Am @ dx["k"] + Ak @ x, "kd": Am @ dx["kd"] + Akd @ x, "q0": Am @ dx["q0"], "qd0": Am @ dx["qd0"]}
+        x = Am @ x
+        p = np.array([0.0, -length * np.sin(x[0]), length * np.cos(x[0])])
+        dp = np.array([0.0, -length * np.cos(x[0]), -length * np.sin(x[0])])
+        r = p - target[t, 0]
+        loss += r @ r / n
+        for key in grad:
+            grad[key] += 2.0 * (r @ dp) * dx[key][0] / n
+
+    kinds, idx = [0, 1, 2, 3], [0, 0, 0, 0]
+    g, lo = O.grad(f, fl, 0, n, target, kinds, idx, [1e-20] * 4, mode=0, n_threads=1)
+    assert lo == pytest.approx(loss, rel=1e-11)
+    ref = np.array([grad["k"], grad["kd"], grad["q0"], grad["qd0"]])
+    np.testing.assert_allclose(g, ref, rtol=1e-8, atol=1e-14 * np.abs(ref).max())
+
+
+def fd_steps(f, w, kinds, idx, rel=1e-3):
+    """Central-difference steps of 1e-3 relative: of k and kd for the gains; for the initial
+    state (zero in the generated workloads) of 1 mrad and 1 mrad/s, or the value when larger.
+    (A step of 1e-3 rad would move the tips by as much as the loss residual itself.)"""
+    b0 = f.body_off[w]
+    d0 = f.dof_off[w]
+    h = []
+    for kind, i in zip(kinds, idx):
+        if kind == 0:
+            h.append(rel * f.k[b0 + i])
+        elif kind == 1:
+            h.append(rel * f.kd[b0 + i])
+        elif kind == 2:
+            h.append(rel * max(1e-3, abs(f.q0[d0 + i])))
+        else:
+            h.append(rel * max(1e-3, abs(f.qd0[d0 + i])))
+    return np.array(h)
+
+
+def sample_coords(f, w, per_kind, rng):
+    """World-local (kind, index) pairs: k and kd of jointed bodies, q0 and qd0 entries."""
+    b0, b1 = f.body_off[w], f.body_off[w + 1]
+    nv = int(f.dof_off[w + 1] - f.dof_off[w])
+    jb = np.nonzero(f.ndof[b0:b1] > 0)[0]
+    kinds, idx = [], []
+    for kind, pool in ((0, jb), (1, jb), (2, np.arange(nv)), (3, np.arange(nv))):
+        sel = rng.choice(pool, min(per_kind, len(pool)), replace=False)
+        kinds += [kind] * len(sel)
+        idx += [int(i) for i in sel]
+    return np.array(kinds), np.array(idx)
+
+
+def test_complex_step_agrees_with_central_differences():
+    """A 200-body world of the differentiation workload (30 apples, a fixed 5 N pull on one),
+    60 steps: the complex-step derivative matches central differences with 1e-3 relative steps
+    to the differences' own truncation error, for every kind of coordinate."""
+    f = I.make_forest(I.DIFF, worlds=[5])
+    fl = I.Flags()
+    n = 60
+    _, rec = O.rollout(f, fl, n, record_tips=True)
+    rng = np.random.default_rng(11)
+    target = rec["tips"] + rng.normal(0.0, 0.01, rec["tips"].shape)
+    kinds, idx = sample_coords(f, 0, 3, rng)
+    g_cs, _ = O.grad(f, fl, 0, n, target, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+    g_fd, _ = O.grad(f, fl, 0, n, target, kinds, idx, fd_steps(f, 0, kinds, idx), mode=1)
+    for kind in range(4):
+        s = kinds == kind
+        scale = np.abs(g_cs[s]).max()
+        assert scale > 0
+        np.testing.assert_allclose(g_fd[s], g_cs[s], rtol=0, atol=1e-4 * scale)

@@ -31,7 +31,7 @@ def test_paper_parameter_closed_forms():
         assert I.beam_stiffness(case["E_Pa"], d, case["l_m"]) == pytest.approx(case["k_Nm_per_rad"], rel=1e-4)
         assert I.rupture_moment(case["sigma_r_Pa"], d) == pytest.approx(case["M_max_Nm"], rel=1e-4)
     # generated descriptors obey the same closed forms body by body
-    f = I.make_forest(0, worlds=[0, 1])
+    f = I.make_forest(I.PLAIN, worlds=[0, 1])
     wid = np.repeat(np.arange(2), np.diff(f.body_off))
     E = f.meta["E"][wid]
     sig = f.meta["sigma_r"][wid]
@@ -55,7 +55,7 @@ def test_paper_parameter_closed_forms():
 # ------------------------------------------------------------------------------------------
 def test_rest_pose_reproduces_skeleton():
     """Sec. IV Eq. 3: at q = 0 the articulation reproduces the generated skeleton exactly."""
-    f = I.make_forest(0, worlds=[0, 3])
+    f = I.make_forest(I.PLAIN, worlds=[0, 3])
     fl = I.Flags()
     for w in range(2):
         b0, b1 = f.body_off[w], f.body_off[w + 1]
@@ -66,7 +66,7 @@ def test_rest_pose_reproduces_skeleton():
 
 
 def test_frames_orthonormal_random_q():
-    f = I.make_forest(0, worlds=[1])
+    f = I.make_forest(I.PLAIN, worlds=[1])
     rng = np.random.default_rng(0)
     q = rng.uniform(-1, 1, f.n_dofs)
     ev = O.evaluate(f, I.Flags(), 0, q, np.zeros(f.n_dofs))
@@ -77,7 +77,7 @@ def test_frames_orthonormal_random_q():
 
 def test_rest_is_stress_free_without_gravity():
     """No gravity, q = 0, qd = 0: the bias force vanishes (stress-free rest, Sec. IV Eq. 3)."""
-    f = I.make_forest(0, worlds=[2])
+    f = I.make_forest(I.PLAIN, worlds=[2])
     f.gravity[:] = 0
     ev = O.evaluate(f, I.Flags(), 0, np.zeros(f.n_dofs), np.zeros(f.n_dofs))
     assert np.abs(ev["c"]).max() == 0.0
@@ -367,7 +367,7 @@ def test_tree_ldlt_matches_dense():
         np.testing.assert_allclose(x_tree, x_np, rtol=1e-10, atol=1e-12)
         np.testing.assert_allclose(x_dense, x_np, rtol=1e-10, atol=1e-12)
     # and on a real H of a generated tree
-    f = I.make_forest(0, worlds=[0])
+    f = I.make_forest(I.PLAIN, worlds=[0])
     ev = O.evaluate(f, I.Flags(), 0, np.zeros(f.n_dofs), np.zeros(f.n_dofs))
     H = ev["M"] + np.diag(np.repeat(f.kd[f.parent >= 0], 2) * 2e-3)
     dof_par = []

@@ -27,7 +27,7 @@ def test_static_scratch_step_matches_regular_step_twice():
         pytest.skip("no CUDA device")
     from paper_2607_06337_b300 import orchard as B
     # uneven worlds across several size classes, with pulls active from step 0
-    f = I.make_forest(1, worlds=[0, 1, 2, 3, 40, 41])
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 3, 40, 41])
     f.pull_start = np.minimum(f.pull_start, 0).astype(np.int32)
     fl = I.Flags()
     ref = B.Simulator(f, fl)
