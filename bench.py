@@ -135,7 +135,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("step_kernel.cu", "orchard_dev.h"):
+    for name in ("step_kernel.cu", "step_device.cuh", "orchard_dev.h"):
         h.update(open(os.path.join(ROOT, "paper_2607_06337_b300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -167,19 +167,16 @@ def cpu_baseline(forest, flags, seconds, sim_steps):
         pick = np.sort(order[np.linspace(0, len(order) - 1, n_w).astype(int)])
         return forest.subset(pick)
 
-    n_w = min(2 * cores, forest.n_worlds)
-    sub = sample(n_w)
-    probe_steps = 10
-    t = time.perf_counter()
-    O.rollout(sub, flags, probe_steps, n_threads=cores)
-    rate = costs.body_count(sub) * probe_steps / max(time.perf_counter() - t, 1e-6)
     steps = min(sim_steps, 1000)
-    want = rate * seconds  # body-steps that fit in the time
-    n_w = int(min(forest.n_worlds, max(n_w, want / steps / max(costs.body_count(sub) / n_w, 1))))
-    sub = sample(n_w)
-    t = time.perf_counter()
-    O.rollout(sub, flags, steps, n_threads=cores)
-    dt = time.perf_counter() - t
+    n_w = min(cores, forest.n_worlds)
+    while True:  # grow the sample until it takes at least half of `seconds`
+        sub = sample(n_w)
+        t = time.perf_counter()
+        O.rollout(sub, flags, steps, n_threads=cores)
+        dt = time.perf_counter() - t
+        if dt >= seconds / 2 or n_w >= forest.n_worlds:
+            break
+        n_w = int(min(forest.n_worlds, max(n_w + 1, n_w * 1.1 * seconds / max(dt, 1e-3))))
     bs = costs.body_count(sub) * steps / dt
     return {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_w} of {forest.n_worlds} worlds stratified by size x {steps} steps "
@@ -404,6 +401,8 @@ def run_ours(args):
     d2h = host_q.numel() * 4 + host_st.numel() * 4
     e2e_value = ws * bodies * S / statistics.mean(e2e_times)
 
+    adj = None if args.no_adjoint else fwd_adjoint(args, dev, rank, ws)
+
     # the plain form: one launch per world per step, no graph, no autotune
     plain = None
     if not args.no_plain:
@@ -438,8 +437,6 @@ def run_ours(args):
     hbm = {"achieved": hbm_bytes / (ms_mean / 1e3) / 1e9, "peak": float(pk.get("hbm_gbs", 6400.0)),
            "unit": "GB/s", "bytes_per_launch": hbm_bytes}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
-
-    adj = None if args.no_adjoint else fwd_adjoint(args, dev, rank, ws)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -1,13 +1,18 @@
 """Adjoint kernel (ot_rollout_backward, and the autograd wrapper over it) against the FP64
 oracle's complex-step derivative and central finite differences of the tip-tracking loss.
 
-Tolerance, per kind of coordinate (k, kd, q0, qd0) and per world, relative to the largest
-sampled magnitude of that kind: 2e-3 against the complex-step derivative, 3e-3 against central
-differences (which add their own O(h^2) error). Derivation: the loss is a sum of squared
-residuals p - p*, and the FP32 tips differ from the FP64 ones by about 5e-4 of the rms residual
-for the +-20% stiffness target over 200 steps; the serial FP32 evaluation of the same adjoint
-arithmetic lands within 3e-4 of the complex-step derivative on that workload, so 2e-3 leaves a
-factor of about 7 for the GPU's different summation order.
+Tolerances, per kind of coordinate (k, kd, q0, qd0) and per world, relative to the largest
+sampled magnitude of that kind:
+
+* far target (tips + 1 cm noise): 1e-3 against the complex-step derivative. With residuals of
+  1 cm the FP32 tip error (~1e-7 m) is irrelevant, so this bounds the adjoint's own rounding;
+  the serial FP32 evaluation of the same arithmetic lands within 2.4e-4.
+* the differentiation workload's target (the oracle's rollout with k scaled by U(0.8, 1.2)):
+  residuals are ~2e-4 m, so the loss is resolved only to the ratio r of the FP32 tips' error
+  to the residual (rms over the rollout, measured per world in the test, ~7e-4), and the
+  gradient, a sum of residual-weighted terms that partly cancel, to a multiple of it:
+  max(2e-3, 10 r) against complex step, and 1.5 times that against central differences
+  (which add their own O(h^2) error).
 """
 import dataclasses
 
@@ -21,8 +26,7 @@ from tests.test_oracle_grad import fd_steps, sample_coords
 
 pytestmark = [pytest.mark.gpu, pytest.mark.usefixtures("oracle_lib")]
 
-TOL_CS = 2e-3
-TOL_FD = 3e-3
+TOL_FAR = 1e-3
 
 
 def _torch():
@@ -61,6 +65,7 @@ def gpu_gradients(f, fl, n, ckpt_every, target, sim=None):
     dt = tip_cotangent(f, tips.double(), tg.double()).float()
     grads = sim.backward(n, rec, dt)
     torch.cuda.synchronize()
+    sim.last_tips = tips.cpu().numpy().astype(np.float64)
     g = [x.cpu().numpy().astype(np.float64) for x in grads]
     ev = dict(broken=sim.broken.cpu().numpy(), break_step=sim.break_step.cpu().numpy(),
               detached=sim.detached.cpu().numpy(), detach_step=sim.detach_step.cpu().numpy())
@@ -91,17 +96,40 @@ def test_adjoint_differentiation_workload_against_oracle():
     fl = I.Flags()
     n = 200
     target = perturbed_target(f, fl, n)
-    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    _, rec0 = O.rollout(f, fl, n, record_tips=True)
+    g, _, sim = gpu_gradients(f, fl, n, 20, target)
     rng = np.random.default_rng(5)
     for w in range(f.n_worlds):
+        t0, t1 = f.tip_off[w], f.tip_off[w + 1]
+        tw = target[:, t0:t1]
+        tips_gpu = sim.last_tips[:, t0:t1]
+        r = np.sqrt(((tips_gpu - rec0["tips"][:, t0:t1]) ** 2).mean() / ((rec0["tips"][:, t0:t1] - tw) ** 2).mean())
+        assert r < 2e-3, f"world {w}: FP32 tips off by {r:.2e} of the residual"
+        tol = max(2e-3, 10 * r)
         kinds, idx = sample_coords(f, w, 4, rng)
-        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
         g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
         got = pick(f, w, g, kinds, idx)
-        assert_close_per_kind(got, g_cs, kinds, TOL_CS, f"world {w} vs complex step")
+        assert_close_per_kind(got, g_cs, kinds, tol, f"world {w} vs complex step (r = {r:.2e})")
         if w == 0:
             g_fd, _ = O.grad(f, fl, w, n, tw, kinds, idx, fd_steps(f, w, kinds, idx), mode=1)
-            assert_close_per_kind(got, g_fd, kinds, TOL_FD, f"world {w} vs central differences")
+            assert_close_per_kind(got, g_fd, kinds, 1.5 * tol, f"world {w} vs central differences")
+
+
+def test_adjoint_far_target_bounds_the_adjoint_rounding():
+    """The same worlds against a target 1 cm away (noise on the oracle's own tips): the loss is
+    well resolved in FP32, so the adjoint must match the complex-step derivative to 1e-3."""
+    f = I.make_forest(I.DIFF, worlds=[0, 1, 2, 3])
+    fl = I.Flags()
+    n = 200
+    _, rec0 = O.rollout(f, fl, n, record_tips=True)
+    rng = np.random.default_rng(3)
+    target = rec0["tips"] + rng.normal(0.0, 0.01, rec0["tips"].shape)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    for w in range(f.n_worlds):
+        kinds, idx = sample_coords(f, w, 6, rng)
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, TOL_FAR, f"world {w} far target")
 
 
 def test_adjoint_with_breaks_and_detaches_masks_frozen():
@@ -123,7 +151,7 @@ def test_adjoint_with_breaks_and_detaches_masks_frozen():
         kinds, idx = sample_coords(f, w, 4, rng)
         tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
         g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
-        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, TOL_CS, f"world {w} with events")
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, 2e-3, f"world {w} with events")
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
