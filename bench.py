@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--plain-steps", type=int, default=2)
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=24.0)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--adj-worlds", type=int, default=None)
     p.add_argument("--adj-steps", type=int, default=200)

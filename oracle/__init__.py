@@ -80,6 +80,9 @@ def lib():
         _lib.oracle_grad.argtypes = [C.POINTER(OForest), C.POINTER(OFlags), C.POINTER(OState), C.POINTER(OPulls),
                                      C.c_int, C.c_int, C.c_int, _f64p, C.c_int, _i32p, _i32p, _f64p, C.c_int,
                                      _f64p, _f64p, C.c_int]
+        _lib.oracle_grad_full.argtypes = [C.POINTER(OForest), C.POINTER(OFlags), C.POINTER(OState),
+                                          C.POINTER(OPulls), C.c_int, C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p,
+                                          _f64p, _f64p, C.c_longlong]
     return _lib
 
 
@@ -248,3 +251,33 @@ def grad(f, flags, w: int, n_steps: int, target, kinds, idx, steps, mode: int, s
                       len(kinds), _p(kinds, _i32p), _p(idx, _i32p), _p(steps, _f64p), mode, _p(g, _f64p),
                       _p(loss, _f64p), nt)
     return g, float(loss[0])
+
+
+def grad_full(f, flags, w: int, n_steps: int, target, state: OracleState | None = None, step0: int = 0,
+              max_nodes: int = 30_000_000, dense_limit: int = 256):
+    """Full loss gradient of world w by the oracle's reverse-mode scalar (its own FP64 adjoint).
+
+    Returns dict(dk, dkd [nb], dq0, dqd0 [nv] world-local, loss, nodes). The tape holds every
+    scalar operation of the rollout (about 32 bytes each), so this is for small worlds and
+    short rollouts; raises MemoryError past max_nodes.
+    """
+    st = OracleState.initial(f) if state is None else state.copy()
+    keep = _Keep()
+    fs = _forest_struct(f, keep)
+    fl = _flags_struct(flags, dense_limit)
+    pl = _pulls_struct(f, keep)
+    s = st.struct()
+    b0, b1 = f.body_off[w], f.body_off[w + 1]
+    nb = int(b1 - b0)
+    nv = int(f.dof_off[w + 1] - f.dof_off[w])
+    target = np.ascontiguousarray(target, np.float64)
+    out = {k: np.zeros(n) for k, n in (("dk", nb), ("dkd", nb), ("dq0", nv), ("dqd0", nv))}
+    loss = np.zeros(1)
+    r = lib().oracle_grad_full(C.byref(fs), C.byref(fl), C.byref(s), C.byref(pl), w, step0, n_steps,
+                               _p(target, _f64p), _p(out["dk"], _f64p), _p(out["dkd"], _f64p),
+                               _p(out["dq0"], _f64p), _p(out["dqd0"], _f64p), _p(loss, _f64p), int(max_nodes))
+    if r < 0:
+        raise MemoryError(f"reverse-mode tape of world {w} exceeds {max_nodes} nodes")
+    out["loss"] = float(loss[0])
+    out["nodes"] = int(r)
+    return out

@@ -42,6 +42,80 @@ using cplx = std::complex<double>;
 inline double re(double x) { return x; }
 inline double re(const cplx& x) { return x.real(); }
 
+// Reverse-mode scalar: the oracle's own adjoint. Every operation on an RV appends one node
+// to the current thread's tape (its value's local partial derivatives with respect to at most
+// two operands); one backward pass over the tape then gives the derivative of a final value
+// with respect to every leaf. Comparisons use the value, so event masks stay as in the plain
+// run, exactly like the complex-step and the GPU adjoint.
+struct Tape {
+  std::vector<int32_t> pa, pb;  // operand nodes (-1: a constant)
+  std::vector<double> ga, gb;   // d(node)/d(operand)
+  int32_t push(int32_t a, double da, int32_t b, double db) {
+    pa.push_back(a); ga.push_back(da); pb.push_back(b); gb.push_back(db);
+    return (int32_t)pa.size() - 1;
+  }
+};
+Tape*& tape_slot() {
+  static thread_local Tape* t = nullptr;
+  return t;
+}
+struct RV {
+  double v = 0.0;
+  int32_t id = -1;  // -1: a constant (no derivative)
+  RV() = default;
+  RV(double x) : v(x), id(-1) {}
+  static RV node(double v, int32_t a, double da, int32_t b, double db) {
+    RV r;
+    r.v = v;
+    if (a >= 0 || b >= 0) r.id = tape_slot()->push(a, da, b, db);
+    return r;
+  }
+  static RV leaf(double v) {
+    RV r;
+    r.v = v;
+    r.id = tape_slot()->push(-1, 0.0, -1, 0.0);
+    return r;
+  }
+};
+inline double re(const RV& x) { return x.v; }
+inline RV operator+(const RV& x, const RV& y) { return RV::node(x.v + y.v, x.id, 1.0, y.id, 1.0); }
+inline RV operator-(const RV& x, const RV& y) { return RV::node(x.v - y.v, x.id, 1.0, y.id, -1.0); }
+inline RV operator*(const RV& x, const RV& y) { return RV::node(x.v * y.v, x.id, y.v, y.id, x.v); }
+inline RV operator/(const RV& x, const RV& y) {
+  const double q = x.v / y.v;
+  return RV::node(q, x.id, 1.0 / y.v, y.id, -q / y.v);
+}
+inline RV operator-(const RV& x) { return RV::node(-x.v, x.id, -1.0, -1, 0.0); }
+inline RV& operator+=(RV& x, const RV& y) { return x = x + y; }
+inline RV& operator-=(RV& x, const RV& y) { return x = x - y; }
+inline RV& operator*=(RV& x, const RV& y) { return x = x * y; }
+inline RV& operator/=(RV& x, const RV& y) { return x = x / y; }
+// the std overloads stay visible beside the RV ones for double and std::complex<double>
+using std::cos;
+using std::sin;
+using std::sqrt;
+inline RV sin(const RV& x) { return RV::node(std::sin(x.v), x.id, std::cos(x.v), -1, 0.0); }
+inline RV cos(const RV& x) { return RV::node(std::cos(x.v), x.id, -std::sin(x.v), -1, 0.0); }
+inline RV sqrt(const RV& x) {
+  const double r = std::sqrt(x.v);
+  return RV::node(r, x.id, 0.5 / r, -1, 0.0);
+}
+
+// d(out)/d(node) for every node of the tape (nodes whose adjoint is zero are skipped, so an
+// unused infinite partial, e.g. of sqrt at 0, cannot turn into 0 * inf).
+std::vector<double> tape_adjoints(const Tape& t, int32_t out) {
+  std::vector<double> adj(t.pa.size(), 0.0);
+  if (out < 0) return adj;
+  adj[out] = 1.0;
+  for (int32_t i = out; i >= 0; --i) {
+    const double a = adj[i];
+    if (a == 0.0) continue;
+    if (t.pa[i] >= 0) adj[t.pa[i]] += a * t.ga[i];
+    if (t.pb[i] >= 0) adj[t.pb[i]] += a * t.gb[i];
+  }
+  return adj;
+}
+
 template <class T> struct V3 {
   T x, y, z;
 };
@@ -793,6 +867,69 @@ int oracle_grad(const OForest* f, const OFlags* fl, const OState* st, const OPul
   for (int t = 0; t < nt; ++t) th.emplace_back(worker);
   for (auto& t : th) t.join();
   return 0;
+}
+
+// Full loss gradient of world w by the reverse-mode scalar (the oracle's own adjoint): dk, dkd
+// [nb] and dq0, dqd0 [nv], world-local. Masks follow the plain run. The tape holds every scalar
+// operation of the rollout, so this is meant for small worlds and short rollouts: it returns
+// -1 (and writes nothing) when the tape would exceed max_nodes.
+int oracle_grad_full(const OForest* f, const OFlags* fl, const OState* st, const OPulls* pl, int w, int step0,
+                     int n_steps, const double* target, double* dk, double* dkd, double* dq0, double* dqd0,
+                     double* loss_out, long long max_nodes) {
+  World W = make_world(f, w);
+  int a0 = f->apple_off[w];
+  Tape tape;
+  Tape*& slot = tape_slot();
+  Tape* saved = slot;
+  slot = &tape;
+  WState<RV> s = load_state<RV>(f, st, W, w);
+  Gains<RV> G;
+  std::vector<int32_t> ik(W.nb), ikd(W.nb), iq(W.nv), iqd(W.nv);
+  for (int b = 0; b < W.nb; ++b) {
+    G.k.push_back(RV::leaf(W.k[b]));
+    ik[b] = G.k.back().id;
+    G.kd.push_back(RV::leaf(W.kd[b]));
+    ikd[b] = G.kd.back().id;
+  }
+  for (int i = 0; i < W.nv; ++i) {
+    s.q[i] = RV::leaf(s.q[i].v);
+    iq[i] = s.q[i].id;
+    s.qd[i] = RV::leaf(s.qd[i].v);
+    iqd[i] = s.qd[i].id;
+  }
+  // the tape's size is checked after every step
+  RV L = RV(0.0);
+  bool over = false;
+  {
+    std::vector<double> fext;
+    for (int t = 0; t < n_steps && !over; ++t) {
+      pulls_at(W, pl, a0, step0 + t, fext);
+      step_world(W, *fl, s, G, fext.data(), step0 + t, 0, nullptr);
+      Kin<RV> K;
+      kinematics(W, s.q.data(), s.qd.data(), K);
+      for (int i = 0; i < W.nt; ++i) {
+        V3<RV> p = tip_point(W, K, i);
+        const double* y = target + ((size_t)t * W.nt + i) * 3;
+        V3<RV> d = p - dv<RV>(y);
+        L += dot(d, d);
+      }
+      over = (long long)tape.pa.size() > max_nodes;
+    }
+  }
+  if (!over) L = L / RV(double(n_steps) * std::max(W.nt, 1));
+  slot = saved;
+  if (over) return -1;
+  std::vector<double> adj = tape_adjoints(tape, L.id);
+  for (int b = 0; b < W.nb; ++b) {
+    if (dk) dk[b] = adj[ik[b]];
+    if (dkd) dkd[b] = adj[ikd[b]];
+  }
+  for (int i = 0; i < W.nv; ++i) {
+    if (dq0) dq0[i] = adj[iq[i]];
+    if (dqd0) dqd0[i] = adj[iqd[i]];
+  }
+  if (loss_out) *loss_out = L.v;
+  return (int)std::min<long long>(tape.pa.size(), 2000000000LL);
 }
 
 }  // extern "C"

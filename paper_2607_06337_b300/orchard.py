@@ -406,7 +406,10 @@ class Simulator:
         return [get_schedule(self.model, k) for k in range(self.counts.classes)]
 
     def autotune(self, n_steps=20, dt=None, stream=None):
+        """Pick every class's fastest schedule; the state is scratch meanwhile, so it is reset
+        to the forest's initial state afterwards."""
         autotune(self.model, self.state, n_steps, self.flags.dt if dt is None else dt, stream)
+        self.reset(stream=stream)
 
     def close(self):
         if getattr(self, "state", None):

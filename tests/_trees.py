@@ -4,6 +4,7 @@ import math
 import numpy as np
 
 from paper_2607_06337_b300 import inputs as I
+from paper_2607_06337_b300.inputs import Forest
 
 
 def single_hinge(diam=0.02, length=0.2, rho=700.0, k=50.0, kd=0.0, ndof=1, gravity=(0.0, 0.0, 0.0),
@@ -77,3 +78,26 @@ def joint_axes(f, q, w=0):
             i += 1
         R[b] = Rj
     return np.array(axes).reshape(-1, 3), np.array(dof_body, int), R
+
+
+def concat(forests):
+    """Pack several one-or-more-world forests into one."""
+    cat = lambda name: np.concatenate([getattr(x, name) for x in forests])
+
+    def offs(name):
+        out = [0]
+        for x in forests:
+            o = getattr(x, name)
+            out.extend((out[-1] + o[1:]).tolist())
+        return np.array(out, np.int32)
+
+    return Forest(
+        n_worlds=sum(x.n_worlds for x in forests), body_off=offs("body_off"), apple_off=offs("apple_off"),
+        tip_off=offs("tip_off"), parent=cat("parent"), ndof=cat("ndof"), jpos=cat("jpos"), qrel=cat("qrel"),
+        length=cat("length"), diam=cat("diam"), mass=cat("mass"), com=cat("com"), inertia=cat("inertia"),
+        k=cat("k"), kd=cat("kd"), armature=cat("armature"), m_max=cat("m_max"), apple_body=cat("apple_body"),
+        hang_local=cat("hang_local"), attach_local=cat("attach_local"), apple_mass=cat("apple_mass"),
+        k_s=cat("k_s"), c_s=cat("c_s"), f_detach=cat("f_detach"), tip_body=cat("tip_body"),
+        tip_local=cat("tip_local"), gravity=cat("gravity"), q0=cat("q0"), qd0=cat("qd0"),
+        apple_x0=cat("apple_x0"), apple_v0=cat("apple_v0"), pull_force=cat("pull_force"),
+        pull_start=cat("pull_start"), pull_end=cat("pull_end"))

@@ -8,11 +8,13 @@ sampled magnitude of that kind:
   1 cm the FP32 tip error (~1e-7 m) is irrelevant, so this bounds the adjoint's own rounding;
   the serial FP32 evaluation of the same arithmetic lands within 2.4e-4.
 * the differentiation workload's target (the oracle's rollout with k scaled by U(0.8, 1.2)):
-  residuals are ~2e-4 m, so the loss is resolved only to the ratio r of the FP32 tips' error
-  to the residual (rms over the rollout, measured per world in the test, ~7e-4), and the
-  gradient, a sum of residual-weighted terms that partly cancel, to a multiple of it:
-  max(2e-3, 10 r) against complex step, and 1.5 times that against central differences
-  (which add their own O(h^2) error).
+  residuals are only ~2e-4 m, so the loss is resolved only to the ratio r of the FP32 tips'
+  error to the residual (rms over the rollout, measured per world, ~3e-4), and the gradient is
+  a sum of per-step residual-weighted terms that cancel heavily for some coordinates (q0
+  above all), which multiplies the adjoint's own ~1e-4 rounding. Measured: up to 4.4e-3 on
+  q0 with r = 2.9e-4 (the serial FP32 evaluation of the same arithmetic: 4.7e-3). Bound:
+  1e-2 against complex step, 1.5e-2 against central differences (which add their own
+  O(h^2) error). The far-target test above is the sharp check of the adjoint.
 """
 import dataclasses
 
@@ -105,7 +107,7 @@ def test_adjoint_differentiation_workload_against_oracle():
         tips_gpu = sim.last_tips[:, t0:t1]
         r = np.sqrt(((tips_gpu - rec0["tips"][:, t0:t1]) ** 2).mean() / ((rec0["tips"][:, t0:t1] - tw) ** 2).mean())
         assert r < 2e-3, f"world {w}: FP32 tips off by {r:.2e} of the residual"
-        tol = max(2e-3, 10 * r)
+        tol = 1e-2
         kinds, idx = sample_coords(f, w, 4, rng)
         g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
         got = pick(f, w, g, kinds, idx)
@@ -198,3 +200,36 @@ def test_autograd_function_matches_the_direct_call():
     k2 = (k.detach() * 1.1).requires_grad_(True)
     tips2 = tip_rollout(sim, k2, kd.detach(), q0.detach(), qd0.detach(), n, ckpt_every=20)
     assert not torch.equal(tips2, tips)
+
+
+def test_full_gradient_against_the_oracle_reverse_mode():
+    """Every coordinate of the gradient against the oracle's own FP64 adjoint (its reverse-mode
+    tape): six generated 24-body trees with 6 apples each and a 12-body tree in which a joint
+    breaks and an apple detaches (masks frozen as recorded), 150 steps, checkpoints every 16,
+    a target 1 cm away. Per world and kind: |g - g_ref|_2 <= 1e-3 |g_ref|_2, and the largest
+    entry error within 2e-3 of the kind's largest entry."""
+    from tests import _trees as T
+    from tests.test_oracle_grad import event_tree
+    trees = []
+    for seed in range(20, 26):
+        t = T.small_random_tree(seed, n_b=24, depth=5, n_a=6)
+        t.qd0[:] = np.random.default_rng(seed).uniform(-0.3, 0.3, t.n_dofs)
+        trees.append(t)
+    trees.append(event_tree())
+    f = T.concat(trees)
+    fl = I.Flags()
+    n = 150
+    st, rec0 = O.rollout(f, fl, n, record_tips=True)
+    target = rec0["tips"] + np.random.default_rng(4).normal(0.0, 0.01, rec0["tips"].shape)
+    g, ev, _ = gpu_gradients(f, fl, n, 16, target)
+    for w in range(f.n_worlds):
+        assert PAR.events(ev["broken"], ev["break_step"], ev["detached"], ev["detach_step"], f, w) == \
+            PAR.events(st.broken, st.break_step, st.detached, st.detach_step, f, w)
+        ref = O.grad_full(f, fl, w, n, target[:, f.tip_off[w]:f.tip_off[w + 1]])
+        b0, b1, d0, d1 = f.body_off[w], f.body_off[w + 1], f.dof_off[w], f.dof_off[w + 1]
+        for name, got in (("dk", g[0][b0:b1]), ("dkd", g[1][b0:b1]), ("dq0", g[2][d0:d1]), ("dqd0", g[3][d0:d1])):
+            r = ref[name]
+            nrm = np.linalg.norm(r)
+            assert nrm > 0
+            assert np.linalg.norm(got - r) <= 1e-3 * nrm, f"world {w} {name}: normwise {np.linalg.norm(got - r) / nrm:.2e}"
+            assert np.abs(got - r).max() <= 2e-3 * np.abs(r).max(), f"world {w} {name}"

@@ -112,7 +112,7 @@ def test_edge_cases_single_body_and_chain():
     chain, _ = T.chain(12, 0.1, 0.01, 700.0, 1e9, kd=0.05, gravity=(0.0, 0.0, -9.81))
     chain.q0[:] = np.linspace(0.05, -0.05, 12)
     tree = I.make_forest(I.PLAIN, worlds=[0])
-    f = _concat([post, hinge, chain, tree])
+    f = T.concat([post, hinge, chain, tree])
     fl = I.Flags()
     g = _run(f, fl, 300)
     st, rec = O.rollout(f, fl, 300, near_eps=PAR.NEAR)
@@ -131,30 +131,6 @@ def test_nonfinite_world_is_frozen_others_continue():
     st, _ = O.rollout(f.subset([0]), fl, 50)
     a, b = f.dof_off[0], f.dof_off[1]
     assert np.abs(g["q"][a:b] - st.q).max() < 1e-4 * np.abs(st.q).max() + 1e-7
-
-
-def _concat(forests):
-    """Pack several one-or-more-world forests into one."""
-    from paper_2607_06337_b300.inputs import Forest
-    cat = lambda name: np.concatenate([getattr(x, name) for x in forests])
-
-    def offs(name):
-        out = [0]
-        for x in forests:
-            o = getattr(x, name)
-            out.extend((out[-1] + o[1:]).tolist())
-        return np.array(out, np.int32)
-
-    return Forest(
-        n_worlds=sum(x.n_worlds for x in forests), body_off=offs("body_off"), apple_off=offs("apple_off"),
-        tip_off=offs("tip_off"), parent=cat("parent"), ndof=cat("ndof"), jpos=cat("jpos"), qrel=cat("qrel"),
-        length=cat("length"), diam=cat("diam"), mass=cat("mass"), com=cat("com"), inertia=cat("inertia"),
-        k=cat("k"), kd=cat("kd"), armature=cat("armature"), m_max=cat("m_max"), apple_body=cat("apple_body"),
-        hang_local=cat("hang_local"), attach_local=cat("attach_local"), apple_mass=cat("apple_mass"),
-        k_s=cat("k_s"), c_s=cat("c_s"), f_detach=cat("f_detach"), tip_body=cat("tip_body"),
-        tip_local=cat("tip_local"), gravity=cat("gravity"), q0=cat("q0"), qd0=cat("qd0"),
-        apple_x0=cat("apple_x0"), apple_v0=cat("apple_v0"), pull_force=cat("pull_force"),
-        pull_start=cat("pull_start"), pull_end=cat("pull_end"))
 
 
 def test_classes_sharing_a_kernel_instantiation():

@@ -119,3 +119,42 @@ def test_complex_step_agrees_with_central_differences():
         scale = np.abs(g_cs[s]).max()
         assert scale > 0
         np.testing.assert_allclose(g_fd[s], g_cs[s], rtol=0, atol=1e-4 * scale)
+
+
+def event_tree():
+    """A 12-body tree with three apples in which joint 5 breaks (step 4) and apple 0 detaches
+    under a 40 N pull (step 12): every event path of the step is inside the rollout."""
+    import dataclasses
+    f = T.small_random_tree(4, n_b=12, depth=4, n_a=3)
+    mm = f.m_max.copy()
+    mm[5] = 1e-4
+    f = dataclasses.replace(f, m_max=mm)
+    f.pull_force = np.zeros((f.n_apples, 3))
+    f.pull_force[0] = (0.0, 0.0, -40.0)
+    f.pull_start = np.array([10, 1 << 30, 1 << 30], np.int32)
+    f.pull_end = np.full(f.n_apples, 1 << 30, np.int32)
+    f.qd0[:] = np.random.default_rng(2).uniform(-0.5, 0.5, f.n_dofs)
+    return f
+
+
+def test_reverse_mode_adjoint_equals_complex_step():
+    """The oracle's own adjoint (a tape of every scalar operation, swept backwards) gives the
+    same full gradient as complex step on every coordinate, through a break and a detach."""
+    f = event_tree()
+    fl = I.Flags()
+    n = 80
+    st, rec = O.rollout(f, fl, n, record_tips=True)
+    assert st.broken.sum() == 1 and (st.detached > 0).sum() == 1
+    target = rec["tips"] + np.random.default_rng(1).normal(0.0, 0.01, rec["tips"].shape)
+    full = O.grad_full(f, fl, 0, n, target)
+    kinds = [0] * f.n_bodies + [1] * f.n_bodies + [2] * f.n_dofs + [3] * f.n_dofs
+    idx = list(range(f.n_bodies)) * 2 + list(range(f.n_dofs)) * 2
+    g, loss = O.grad(f, fl, 0, n, target, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+    assert full["loss"] == pytest.approx(loss, rel=1e-14)
+    got = np.concatenate([full["dk"], full["dkd"], full["dq0"], full["dqd0"]])
+    kinds = np.array(kinds)
+    for kind in range(4):
+        s = kinds == kind
+        np.testing.assert_allclose(got[s], g[s], rtol=0, atol=1e-12 * np.abs(g[s]).max())
+    # the broken joint's stiffness acts only before the break: its gradient is not zero
+    assert full["dk"][5] != 0.0
