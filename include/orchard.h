@@ -106,7 +106,7 @@ typedef struct ot_model_flags {
 
 /* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */
 typedef struct ot_schedule {
-  int32_t threads_per_world;   /* 32, 64, 128 or 256 */
+  int32_t threads_per_world;   /* 32, 64, 128, 256 or 512 */
   int32_t worlds_per_block;    /* groups of threads_per_world threads in one block */
   int32_t blocks;              /* persistent grid size (0: enough for one wave) */
   int32_t global_workspace;    /* 1: per-step temporaries in the state's scratch area */

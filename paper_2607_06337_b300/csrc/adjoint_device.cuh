@@ -32,7 +32,8 @@ HD float u2f(unsigned u) {
 #endif
 }
 
-// Backward workspace of one world (floats), after the forward workspace.
+// Backward temporaries of one world (floats), at their own base `wa` (shared or global
+// memory), and the snapshots of one checkpoint segment (global memory, `seg`).
 struct AdjLayout {
   int T;          // tape, 36 per body: R, x, w, v, alpha, a, Lw, Lv, Ow, Ov (see tape_body)
   int C;          // 42 per body: cotangents a body sends to its parent's tape outputs (36),
@@ -49,12 +50,11 @@ struct AdjLayout {
   int ps;         // private state floats: q, qd (nv), ax, av (3 na)
   int pi;         // private state ints: broken, bcnt, break_step (nb), detached, pcnt, tcnt,
                   // detach_step (na), status (1)
-  int seg;        // snapshots of the private state at the start of each step of a segment
-  int snap;       // words per snapshot
-  int total;
-  HD static AdjLayout make(int fwd_total, int nb, int nv, int na, int seg_len) {
+  int total;      // floats at wa
+  int snap;       // words per snapshot (the private state, ps then pi)
+  HD static AdjLayout make(int nb, int nv, int na) {
     AdjLayout A;
-    int o = fwd_total;
+    int o = 0;
     A.T = o; o += 36 * nb;
     A.C = o; o += 42 * nb;
     A.AF = o; o += 6 * nb;
@@ -73,17 +73,16 @@ struct AdjLayout {
     A.ps = o; o += 2 * nv + 6 * na;
     A.pi = o; o += 3 * nb + 4 * na + 1;
     A.snap = 2 * nv + 6 * na + 3 * nb + 4 * na + 1;
-    A.seg = o; o += seg_len * A.snap;
     A.total = o;
     return A;
   }
 };
 
-HD WState private_state(float* ws, const AdjLayout& A, int nb, int nv, int na) {
+HD WState private_state(float* wa, const AdjLayout& A, int nb, int nv, int na) {
   WState s;
-  float* f = ws + A.ps;
+  float* f = wa + A.ps;
   s.q = f; s.qd = f + nv; s.ax = f + 2 * nv; s.av = f + 2 * nv + 3 * na;
-  int* i = (int*)(ws + A.pi);
+  int* i = (int*)(wa + A.pi);
   s.broken = i; s.bcnt = i + nb; s.break_step = i + 2 * nb;
   s.detached = i + 3 * nb; s.pcnt = s.detached + na; s.tcnt = s.pcnt + na; s.detach_step = s.tcnt + na;
   s.status = (unsigned*)(s.detach_step + na);
@@ -92,9 +91,9 @@ HD WState private_state(float* ws, const AdjLayout& A, int nb, int nv, int na) {
 
 // Copy the private state to or from snapshot `k` of the segment buffer (group-parallel).
 template <int TPW>
-HD void snapshot(float* ws, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
-  float* src = ws + A.ps;  // private floats and ints are contiguous: ps then pi
-  float* dst = ws + A.seg + (long long)k * A.snap;
+HD void snapshot(float* wa, float* seg, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
+  float* src = wa + A.ps;  // private floats and ints are contiguous: ps then pi
+  float* dst = seg + (long long)k * A.snap;
   for (int i = g.lane; i < A.snap; i += TPW) {
     if (save) dst[i] = src[i];
     else src[i] = dst[i];
@@ -142,7 +141,7 @@ HD void load_ckpt(const StepArgs& a, const WorldView& v, const WState& s, int sl
 // Tape of one body: forward kinematics at q, body velocity (w, v at x_b), full spatial
 // acceleration (alpha, a) with qdd = Delta / dt, and the virtual velocities of lambda (Lw, Lv)
 // and of qd' (Ow, Ov).
-HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const AdjLayout& A, float* ws,
+HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const AdjLayout& A, float* wa,
                   const float* delta, float inv_dt, const float* lam, const float* qd1, int b, f3 g) {
   const int gb = v.b0 + b;
   const int4 bi = m.bi[gb];
@@ -151,7 +150,7 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
   m3 Rp;
   f3 xp, wp, vp, alp, ap, lwp, lvp, owp, ovp;
   if (p >= 0) {
-    const float* tp = ws + A.T + 36 * p;
+    const float* tp = wa + A.T + 36 * p;
     Rp = ldm(tp);
     xp = ld3(tp + 9); wp = ld3(tp + 12); vp = ld3(tp + 15); alp = ld3(tp + 18); ap = ld3(tp + 21);
     lwp = ld3(tp + 24); lvp = ld3(tp + 27); owp = ld3(tp + 30); ovp = ld3(tp + 33);
@@ -183,7 +182,7 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
       R.c0 = c0; R.c2 = c2;
     }
   }
-  float* t = ws + A.T + 36 * b;
+  float* t = wa + A.T + 36 * b;
   stm(t, R);
   st3(t + 9, xb); st3(t + 12, w); st3(t + 15, vin); st3(t + 18, al); st3(t + 21, aa);
   st3(t + 24, lw); st3(t + 27, lvin); st3(t + 30, ow); st3(t + 33, ovin);
@@ -214,7 +213,8 @@ struct RevArgs {
 // Reverse of one body's tape (leaf-to-root): consumes the cotangents its children sent (C
 // slots) plus its own seeds, adds the q / qd cotangents of its DOFs, writes its C slot.
 HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v,
-                     const WsLayout& L, const AdjLayout& A, float* ws, const RevArgs& ra, int b, f3 g, int t_abs) {
+                     const WsLayout& L, const AdjLayout& A, float* ws, float* wa, const RevArgs& ra, int b, f3 g,
+                     int t_abs) {
   const int gb = v.b0 + b;
   const int4 bi = m.bi[gb];
   const int p = bi.x;
@@ -225,7 +225,7 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   float cb[42];
   for (int k = 0; k < 42; ++k) cb[k] = 0.f;
   for (int k = 0; k < ccount; ++k) {
-    const float* c = ws + A.C + 42 * (cfirst + k);
+    const float* c = wa + A.C + 42 * (cfirst + k);
     for (int j = 0; j < 42; ++j) cb[j] += c[j];
   }
   m3 Rb_ = {mk(cb[0], cb[1], cb[2]), mk(cb[3], cb[4], cb[5]), mk(cb[6], cb[7], cb[8])};
@@ -237,7 +237,7 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   f3 owh = mk(cb[36], cb[37], cb[38]), ovh = mk(cb[39], cb[40], cb[41]);
 
   // own forward values
-  const float* t = ws + A.T + 36 * b;
+  const float* t = wa + A.T + 36 * b;
   const m3 R = ldm(t);
   const f3 w = ld3(t + 12), vin = ld3(t + 15), al = ld3(t + 18), aa = ld3(t + 21);
   const f3 lw = ld3(t + 24), lv = ld3(t + 27), ow = ld3(t + 30), ov = ld3(t + 33);
@@ -314,7 +314,7 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
     const int det = s.detached[ai];
     if (ra.dyn && det == 0) {
       // the new hang-point velocity seen by the apple update
-      const f3 vhb = ld3(ws + A.vh + 3 * ai);
+      const f3 vhb = ld3(wa + A.vh + 3 * ai);
       ovh = ovh + vhb;
       owh = owh + cross(rh, vhb);
       rhb = rhb + cross(vhb, ow);
@@ -358,15 +358,15 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
         lvb = lvb + wbar;
         lwb = lwb + cross(rh, wbar);
         rhb = rhb + cross(wbar, lw);
-        float* ub = ws + A.ub + 3 * ai;
-        float* vb = ws + A.vb + 3 * ai;
+        float* ub = wa + A.ub + 3 * ai;
+        float* vb = wa + A.vb + 3 * ai;
         st3(ub, ld3(ub) + ubar);
         st3(vb, ld3(vb) + vbar);
       }
     }
     if (ra.dyn && det == 2) {
       // converted at this step's start: x = x_hang + u
-      const f3 xb_ = ld3(ws + A.ub + 3 * ai);  // cotangent of x (the step-start position)
+      const f3 xb_ = ld3(wa + A.ub + 3 * ai);  // cotangent of x (the step-start position)
       xbb = xbb + xb_;
       rhb = rhb + xb_;
     }
@@ -392,7 +392,7 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   m3 Rp;
   f3 wp, alp, lwp, owp;
   if (p >= 0) {
-    const float* tp = ws + A.T + 36 * p;
+    const float* tp = wa + A.T + 36 * p;
     Rp = ldm(tp);
     wp = ld3(tp + 12); alp = ld3(tp + 18); lwp = ld3(tp + 24); owp = ld3(tp + 30);
   } else {
@@ -461,8 +461,8 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
     eb = eb + ra.qd1[i] * (owb + owh);
     if (j == 0) Rb_.c0 = Rb_.c0 + eb;
     else Rb_.c1 = Rb_.c1 + eb;
-    ws[A.qb + i] += qbar;
-    ws[A.qdb + i] += qdbar;
+    wa[A.qb + i] += qbar;
+    wa[A.qdb + i] += qdbar;
   }
   // prefix: R0 = Rp Q, xb = xp + Rp j, d = xb - xp, vin/ain/Lvin/Ovin shifts
   const f3 jb = xyz(m.bp0[gb]);
@@ -488,84 +488,80 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   Rpb.c0 = jb.x * db + (Q.c0.x * Rb_.c0 + Q.c1.x * Rb_.c1 + Q.c2.x * Rb_.c2);
   Rpb.c1 = jb.y * db + (Q.c0.y * Rb_.c0 + Q.c1.y * Rb_.c1 + Q.c2.y * Rb_.c2);
   Rpb.c2 = jb.z * db + (Q.c0.z * Rb_.c0 + Q.c1.z * Rb_.c1 + Q.c2.z * Rb_.c2);
-  float* c = ws + A.C + 42 * b;
+  float* c = wa + A.C + 42 * b;
   stm(c, Rpb);
   st3(c + 9, xpb); st3(c + 12, wpb); st3(c + 15, vpb); st3(c + 18, alpb); st3(c + 21, apb);
   st3(c + 24, lwpb); st3(c + 27, lvpb); st3(c + 30, owpb); st3(c + 33, ovpb);
   st3(c + 36, owph); st3(c + 39, ovph);
 }
 
-// L^T sweep, D scaling and L sweep of a solve with the step's factors (rows U = D L in M):
-// y <- H^-1 y, in place.
+// A solve with the step's factors (see Pivot): L^T sweep leaf to root by factorisation level,
+// the scaling z = P^-1 y, and the L sweep root to leaf by body level; y <- H^-1 y, in place.
 template <int TPW>
 HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, float* y,
                        const Group<TPW>& g) {
+  const float* M = ws + L.M;
 #ifdef __CUDA_ARCH__
   constexpr int NW = TPW / 32;
   const int warp = g.lane >> 5, lane = g.lane & 31;
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+  for (int l = v.nBL - 1; l >= 0; --l) {
+    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
     if (l > 0) {
+      const int count = hi - lo;
+      const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
       for (int base = lo; base < hi; base += 32) {
         const int idx = base + lane;
         const bool valid = idx < hi;
-        int rowk = 0;
-        float dinv = 0.f, yk = 0.f;
+        int4 info = make_int4(0, 0, 0, 0);
+        float zx = 0.f, zy = 0.f;
         if (valid) {
-          const int k = m.dl_list[v.d0 + idx];
-          rowk = m.dinfo[v.d0 + k].x;
-          dinv = 1.f / ws[L.M + rowk];
-          yk = y[k];
+          info = m.bl_info[v.b0 + idx];
+          const Pivot P = pivot_of(M, info.y, info.z, info.w);
+          const float yx = y[info.x], yy = info.w == 2 ? y[info.x + 1] : 0.f;
+          zx = P.p00 * yx + P.p01 * yy;  // P^-1 y of this joint
+          zy = P.p01 * yx + P.p11 * yy;
         }
-        const float* row = ws + L.M + rowk;
-        const unsigned* an = m.anc + v.m0 + rowk;
+        const bool two = info.w == 2;
+        const float* rowx = M + info.y;
+        const float* rowy = M + (two ? info.z + 1 : info.y);
+        const int2* fp = ft + (idx - lo);
         for (int c = 1 + warp; c <= l; c += NW) {
-          const int key = valid ? (int)(an[c] & 0xffffu) : -1 - lane;
+          const int key = valid ? fp[(c - 1) * count].y : -1 - lane;
           const int prev = __shfl_up_sync(0xffffffffu, key, 1);
           const int next = __shfl_down_sync(0xffffffffu, key, 1);
           const bool head = lane == 0 || prev != key;
           const bool tail = lane == 31 || next != key;
           const unsigned heads = __ballot_sync(0xffffffffu, head);
           const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-          float s0 = valid ? row[c] * dinv * yk : 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-          seg_scan4(s0, s1, s2, s3, lane, first);
-          if (valid && tail) y[key] -= s0;
+          const float val = valid ? fmaf(rowx[c], zx, two ? rowy[c] * zy : 0.f) : 0.f;
+          const float sum = seg_scan1(val, lane, first);
+          if (valid && tail) y[key] -= sum;
         }
       }
     }
     g.sync();
-    for (int idx = lo + g.lane; idx < hi; idx += TPW) {
-      const int k = m.dl_list[v.d0 + idx];
-      y[k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) pivot_scale(M, m.bl_info[v.b0 + idx], y);
   }
   g.sync();
 #else
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
-    for (int c = 1; c <= l; ++c) {
-      float acc = 0.f;
-      for (int idx = lo; idx < hi; ++idx) {
-        const int k = m.dl_list[v.d0 + idx];
-        const int rowk = m.dinfo[v.d0 + k].x;
-        const float* row = ws + L.M + rowk;
-        const int key = (int)(m.anc[v.m0 + rowk + c] & 0xffffu);
-        acc += row[c] / row[0] * y[k];
-        int next = -1;
-        if (idx + 1 < hi) {
-          const int k2 = m.dl_list[v.d0 + idx + 1];
-          next = (int)(m.anc[v.m0 + m.dinfo[v.d0 + k2].x + c] & 0xffffu);
-        }
-        if (next != key) {
-          y[key] -= acc;
-          acc = 0.f;
-        }
+  for (int l = v.nBL - 1; l >= 0; --l) {
+    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int count = hi - lo;
+    const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+    for (int idx = lo; idx < hi; ++idx) {
+      const int4 info = m.bl_info[v.b0 + idx];
+      const bool two = info.w == 2;
+      const Pivot P = pivot_of(M, info.y, info.z, info.w);
+      const float yx = y[info.x], yy = two ? y[info.x + 1] : 0.f;
+      const float zx = P.p00 * yx + P.p01 * yy, zy = P.p01 * yx + P.p11 * yy;
+      const float* rowx = M + info.y;
+      const float* rowy = M + (two ? info.z + 1 : info.y);
+      for (int c = 1; c <= l; ++c) {
+        const int2 tk = ft[(c - 1) * count + (idx - lo)];
+        y[tk.y] -= fmaf(rowx[c], zx, two ? rowy[c] * zy : 0.f);
       }
     }
-    for (int idx = lo; idx < hi; ++idx) {
-      const int k = m.dl_list[v.d0 + idx];
-      y[k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
+    for (int idx = lo; idx < hi; ++idx) pivot_scale(M, m.bl_info[v.b0 + idx], y);
   }
 #endif
   // L sweep, root to leaf by body level
@@ -573,16 +569,7 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
       const int4 bi = m.bi[v.b0 + b];
-      const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-      for (int j = 0; j < nd; ++j) {
-        const int i = dof0 + j;
-        const int4 di = m.dinfo[v.d0 + i];
-        const float* row = ws + L.M + di.x;
-        const unsigned* an = m.anc + v.m0 + di.x;
-        float acc = 0.f;
-        for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], y[an[c] & 0xffffu], acc);
-        y[i] -= acc / row[0];
-      }
+      lsweep_joint(m, v, L, ws, y, bi.y & 0x0fffffff, (unsigned)bi.y >> 28);
     }
     g.sync();
   }
@@ -592,7 +579,7 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
 // hang-point velocities): adds J_h^T vh to out (per DOF).
 template <int TPW>
 HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L,
-                        const AdjLayout& A, float* ws, float* out, const Group<TPW>& g) {
+                        const AdjLayout& A, float* ws, float* wa, float* out, const Group<TPW>& g) {
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
@@ -606,19 +593,19 @@ HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, 
         const int ai = afirst + k;
         if (s.detached[ai]) continue;
         const f3 rh = ld3(ws + L.AT + 10 * ai + 6);
-        const f3 fv = ld3(ws + A.vh + 3 * ai);
+        const f3 fv = ld3(wa + A.vh + 3 * ai);
         n = n + cross(rh, fv);
         f = f + fv;
       }
       for (int k = 0; k < ccount; ++k) {
         const int c = cfirst + k;
         const f3 sft = ld3(ws + L.X + 3 * c) - xb;
-        const f3 fc = ld3(ws + A.AF + 6 * c + 3);
-        n = n + ld3(ws + A.AF + 6 * c) + cross(sft, fc);
+        const f3 fc = ld3(wa + A.AF + 6 * c + 3);
+        n = n + ld3(wa + A.AF + 6 * c) + cross(sft, fc);
         f = f + fc;
       }
-      st3(ws + A.AF + 6 * b, n);
-      st3(ws + A.AF + 6 * b + 3, f);
+      st3(wa + A.AF + 6 * b, n);
+      st3(wa + A.AF + 6 * b + 3, f);
       for (int j = 0; j < nd; ++j) out[dof0 + j] += dot(ld3(ws + L.E + 3 * (dof0 + j)), n);
     }
     g.sync();
@@ -637,39 +624,39 @@ namespace {
 // start state in A.qb / qdb / ub / vb.
 template <int TPW>
 HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
-                     const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, const Group<TPW>& g,
-                     int t, f3 gv) {
+                     const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa,
+                     const Group<TPW>& g, int t, f3 gv) {
   const float dt = a.dt;
   const int t_abs = a.step0 + t;
   for (int i = g.lane; i < v.nv; i += TPW) {
-    ws[A.qb + i] = ws[A.qb1 + i];                                  // q' = q + dt qd'
-    ws[A.lam + i] = ws[A.qdb1 + i] + dt * ws[A.qb1 + i];           // qd'-bar (first part)
+    wa[A.qb + i] = wa[A.qb1 + i];                                  // q' = q + dt qd'
+    wa[A.lam + i] = wa[A.qdb1 + i] + dt * wa[A.qb1 + i];           // qd'-bar (first part)
   }
   // the apple update: u' = u + dt (v' - v_hang'), v' = a + beta v_hang' (attached), or
   // x' = x + dt v', v' = v + dt (g + f / m) (detached)
   for (int ai = g.lane; ai < v.na; ai += TPW) {
     const int ga = v.a0 + ai;
-    const f3 u1b = ld3(ws + A.ub1 + 3 * ai), v1b = ld3(ws + A.vb1 + 3 * ai);
+    const f3 u1b = ld3(wa + A.ub1 + 3 * ai), v1b = ld3(wa + A.vb1 + 3 * ai);
     const f3 vtot = v1b + dt * u1b;
     if (s.detached[ai] == 0) {
       const float beta = ws[L.AT + 10 * ai + 3];
       const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
       const float ma = A0.w, ks = A1.x, csd = A1.y;
       const float D = ma + dt * csd + dt * dt * ks;
-      st3(ws + A.vh + 3 * ai, beta * vtot - dt * u1b);
-      st3(ws + A.ub + 3 * ai, u1b - (dt * ks / D) * vtot);
-      st3(ws + A.vb + 3 * ai, (ma / D) * vtot);
+      st3(wa + A.vh + 3 * ai, beta * vtot - dt * u1b);
+      st3(wa + A.ub + 3 * ai, u1b - (dt * ks / D) * vtot);
+      st3(wa + A.vb + 3 * ai, (ma / D) * vtot);
     } else {
-      st3(ws + A.vh + 3 * ai, mk(0, 0, 0));
-      st3(ws + A.ub + 3 * ai, u1b);
-      st3(ws + A.vb + 3 * ai, vtot);
+      st3(wa + A.vh + 3 * ai, mk(0, 0, 0));
+      st3(wa + A.ub + 3 * ai, u1b);
+      st3(wa + A.vb + 3 * ai, vtot);
     }
   }
   g.sync();
-  hang_load_sweep<TPW>(m, s, v, L, A, ws, ws + A.lam, g);  // qd'-bar += J_h^T vh-bar
-  for (int i = g.lane; i < v.nv; i += TPW) ws[A.qdb + i] = ws[A.lam + i];  // qd' = qd + Delta
+  hang_load_sweep<TPW>(m, s, v, L, A, ws, wa, wa + A.lam, g);  // qd'-bar += J_h^T vh-bar
+  for (int i = g.lane; i < v.nv; i += TPW) wa[A.qdb + i] = wa[A.lam + i];  // qd' = qd + Delta
   g.sync();
-  solve_factored<TPW>(m, v, L, ws, ws + A.lam, g);  // lambda = H^-1 Delta-bar
+  solve_factored<TPW>(m, v, L, ws, wa + A.lam, g);  // lambda = H^-1 Delta-bar
   // springs and dampers (diagonal terms of r and H)
   for (int i = g.lane; i < v.nv; i += TPW) {
     const int b = m.dinfo[v.d0 + i].y;
@@ -677,10 +664,10 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
     const float4 P3 = m.bp3[gb];
     float k, kd;
     joint_gains(s, a, b, P3, t_abs, &k, &kd);
-    const float lam = ws[A.lam + i];
+    const float lam = wa[A.lam + i];
     const float adt = a.alpha ? dt : 0.f;
-    ws[A.qb + i] += -dt * k * lam;
-    ws[A.qdb + i] += -dt * (adt * k + kd) * lam;
+    wa[A.qb + i] += -dt * k * lam;
+    wa[A.qdb + i] += -dt * (adt * k + kd) * lam;
     const float kfac = s.broken[b] ? 0.f : 1.f;
     const float kdfac = P3.w != 0.f ? kd / P3.w : 0.f;
     // one writer per joint: the joint's first DOF adds both DOFs' terms
@@ -688,7 +675,7 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
     if (i == dof0) {
       float sk = 0.f, skd = 0.f;
       for (int j = 0; j < nd; ++j) {
-        const float lj = ws[A.lam + dof0 + j], qj = s.q[dof0 + j], q1j = ws[A.qd1 + dof0 + j];
+        const float lj = wa[A.lam + dof0 + j], qj = s.q[dof0 + j], q1j = wa[A.qd1 + dof0 + j];
         sk += lj * (qj + adt * q1j);
         skd += lj * q1j;
       }
@@ -701,93 +688,95 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   for (int l = 0; l < v.nL; ++l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW)
-      tape_body(m, s, v, A, ws, ws + L.r, 1.f / dt, ws + A.lam, ws + A.qd1, b, gv);
+      tape_body(m, s, v, A, wa, ws + L.r, 1.f / dt, wa + A.lam, wa + A.qd1, b, gv);
     g.sync();
   }
   RevArgs ra;
   ra.dyn = 1;
   ra.delta = ws + L.r;
-  ra.lam = ws + A.lam;
-  ra.qd1 = ws + A.qd1;
+  ra.lam = wa + A.lam;
+  ra.qd1 = wa + A.qd1;
   ra.tipbar = t >= 1 ? ba.dtips + (long long)(t - 1) * a.n_tips_total * 3 : nullptr;
   ra.sphi = -dt;
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, ra, b, gv, t_abs);
+    for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
     g.sync();
   }
 }
 
 // Backward pass of one world over a recorded rollout.
 template <int TPW>
-HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws,
-                       const Group<TPW>& g) {
+// ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
+// seg: ckpt_every snapshots; each may be in shared or global memory (seg is always global).
+HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
+                       float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
-  const AdjLayout A = AdjLayout::make(L.total, v.nb, v.nv, v.na, a.ckpt_every);
-  const WState s = private_state(ws, A, v.nb, v.nv, v.na);
+  const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
+  const WState s = private_state(wa, A, v.nb, v.nv, v.na);
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   const float dt = a.dt;
   const int T = a.n_steps, ce = a.ckpt_every;
   const int nseg = (T + ce - 1) / ce;
   for (int i = g.lane; i < v.nv; i += TPW) {
-    ws[A.qb1 + i] = 0.f; ws[A.qdb1 + i] = 0.f; ws[A.zero + i] = 0.f; ws[A.qb + i] = 0.f; ws[A.qdb + i] = 0.f;
+    wa[A.qb1 + i] = 0.f; wa[A.qdb1 + i] = 0.f; wa[A.zero + i] = 0.f; wa[A.qb + i] = 0.f; wa[A.qdb + i] = 0.f;
   }
-  for (int i = g.lane; i < 3 * v.na; i += TPW) { ws[A.ub1 + i] = 0.f; ws[A.vb1 + i] = 0.f; }
+  for (int i = g.lane; i < 3 * v.na; i += TPW) { wa[A.ub1 + i] = 0.f; wa[A.vb1 + i] = 0.f; }
   g.sync();
-  for (int seg = nseg - 1; seg >= 0; --seg) {
-    const int t0 = seg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
-    load_ckpt(a, v, s, seg, g);
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int t0 = sg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
+    load_ckpt(a, v, s, sg, g);
     for (int t = t0; t < t1; ++t) {
-      snapshot(ws, A, t - t0, true, g);
+      snapshot(wa, seg, A, t - t0, true, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
     }
-    if (seg == nseg - 1) {
+    if (sg == nseg - 1) {
       // the last record's tips at the final configuration
       for (int l = 0; l < v.nL; ++l) {
         const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
         for (int b = lo + g.lane; b < hi; b += TPW)
-          tape_body(m, s, v, A, ws, ws + A.zero, 0.f, ws + A.zero, ws + A.zero, b, gv);
+          tape_body(m, s, v, A, wa, wa + A.zero, 0.f, wa + A.zero, wa + A.zero, b, gv);
         g.sync();
       }
       RevArgs ra;
       ra.dyn = 0;
-      ra.delta = ws + A.zero; ra.lam = ws + A.zero; ra.qd1 = ws + A.zero;
+      ra.delta = wa + A.zero; ra.lam = wa + A.zero; ra.qd1 = wa + A.zero;
       ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
       ra.sphi = 0.f;
       for (int l = v.nL - 1; l >= 0; --l) {
         const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-        for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, ra, b, gv, a.step0 + T);
+        for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
         g.sync();
       }
       for (int i = g.lane; i < v.nv; i += TPW) {
-        ws[A.qb1 + i] = ws[A.qb + i];
-        ws[A.qb + i] = 0.f;
+        wa[A.qb1 + i] = wa[A.qb + i];
+        wa[A.qb + i] = 0.f;
       }
       g.sync();
     }
     for (int t = t1 - 1; t >= t0; --t) {
-      snapshot(ws, A, t - t0, false, g);
+      snapshot(wa, seg, A, t - t0, false, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
-      for (int i = g.lane; i < v.nv; i += TPW) ws[A.qd1 + i] = s.qd[i];
+      for (int i = g.lane; i < v.nv; i += TPW) wa[A.qd1 + i] = s.qd[i];
       g.sync();
-      snapshot(ws, A, t - t0, false, g);
-      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, g, t, gv);
+      snapshot(wa, seg, A, t - t0, false, g);
+      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, g, t, gv);
       for (int i = g.lane; i < v.nv; i += TPW) {
-        ws[A.qb1 + i] = ws[A.qb + i];
-        ws[A.qdb1 + i] = ws[A.qdb + i];
+        wa[A.qb1 + i] = wa[A.qb + i];
+        wa[A.qdb1 + i] = wa[A.qdb + i];
       }
       for (int i = g.lane; i < 3 * v.na; i += TPW) {
-        ws[A.ub1 + i] = ws[A.ub + i];
-        ws[A.vb1 + i] = ws[A.vb + i];
+        wa[A.ub1 + i] = wa[A.ub + i];
+        wa[A.vb1 + i] = wa[A.vb + i];
       }
       g.sync();
     }
   }
   for (int i = g.lane; i < v.nv; i += TPW) {
-    if (ba.dq0) ba.dq0[v.d0 + i] = ws[A.qb1 + i];
-    if (ba.dqd0) ba.dqd0[v.d0 + i] = ws[A.qdb1 + i];
+    if (ba.dq0) ba.dq0[v.d0 + i] = wa[A.qb1 + i];
+    if (ba.dqd0) ba.dqd0[v.d0 + i] = wa[A.qdb1 + i];
   }
   g.sync();
   (void)dt;

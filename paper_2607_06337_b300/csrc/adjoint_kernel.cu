@@ -1,6 +1,11 @@
 // Backward (adjoint) kernel of a recorded rollout for sm_103a: a persistent grid whose thread
-// groups pop worlds from the cost-sorted queue and run backward_world (adjoint_device.cuh),
-// each in its own slot of the caller's workspace.
+// groups pop worlds from the cost-sorted queue and run backward_world (adjoint_device.cuh).
+// Each group owns one slot of the caller's workspace (the snapshots of one checkpoint
+// segment, plus whatever of its temporaries is not in shared memory); BackShape::mode says
+// which temporaries live in the block's shared memory:
+//   0: none (forward and backward temporaries in the global slot),
+//   1: the forward step's temporaries (WsLayout),
+//   2: the forward step's and the backward's (WsLayout, then AdjLayout).
 #include "adjoint_device.cuh"
 
 namespace orchard {
@@ -8,7 +13,8 @@ namespace {
 
 template <int TPW>
 __global__ void __launch_bounds__(512) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
-                                                       long long ws_floats) {
+                                                       BackShape sh) {
+  extern __shared__ float smem[];
   __shared__ int frozen[16];
   __shared__ int next[16];
   Group<TPW> g;
@@ -16,47 +22,76 @@ __global__ void __launch_bounds__(512) backward_kernel(DevModel m, StepArgs a, B
   g.id = threadIdx.x / TPW;
   g.flag = &frozen[g.id];
   const int groups = blockDim.x / TPW;
-  float* ws = work + (long long)(blockIdx.x * groups + g.id) * ws_floats;
+  float* slot = work + (long long)(blockIdx.x * groups + g.id) * sh.global_floats;
+  float* local = smem + (long long)g.id * sh.smem_floats;
+  float *ws, *wa, *seg;
+  if (sh.mode == 2) {
+    ws = local;
+    wa = local + sh.fwd_floats;
+    seg = slot;
+  } else if (sh.mode == 1) {
+    ws = local;
+    wa = slot;
+    seg = slot + sh.adj_floats;
+  } else {
+    ws = slot;
+    wa = slot + sh.fwd_floats;
+    seg = wa + sh.adj_floats;
+  }
   for (;;) {
     if (g.lane == 0) next[g.id] = atomicAdd(a.q_counter, 1);
     g.sync();
     const int qi = next[g.id];
     g.sync();
     if (qi >= a.q_end - a.q_begin) break;
-    backward_world<TPW>(m, a, ba, m.queue[a.q_begin + qi], ws, g);
+    backward_world<TPW>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, seg, g);
+  }
+}
+
+template <int TPW>
+const void* backward_fn() {
+  return (const void*)backward_kernel<TPW>;
+}
+
+const void* backward_fn_of(int tpw) {
+  switch (tpw) {
+    case 32: return backward_fn<32>();
+    case 64: return backward_fn<64>();
+    case 128: return backward_fn<128>();
+    case 256: return backward_fn<256>();
+    default: return nullptr;
   }
 }
 
 }  // namespace
 
 void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
-                     const StepArgs& a, const BackArgs& ba, float* work, long long ws_floats) {
+                     const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh) {
   const int threads = tpw * groups_per_block;
+  const size_t smem = (size_t)sh.smem_floats * 4 * groups_per_block;
   switch (tpw) {
-    case 32: backward_kernel<32><<<blocks, threads, 0, st>>>(m, a, ba, work, ws_floats); break;
-    case 64: backward_kernel<64><<<blocks, threads, 0, st>>>(m, a, ba, work, ws_floats); break;
-    case 128: backward_kernel<128><<<blocks, threads, 0, st>>>(m, a, ba, work, ws_floats); break;
-    case 256: backward_kernel<256><<<blocks, threads, 0, st>>>(m, a, ba, work, ws_floats); break;
+    case 32: backward_kernel<32><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    case 64: backward_kernel<64><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    case 128: backward_kernel<128><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    case 256: backward_kernel<256><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
     default: break;
   }
 }
 
-cudaError_t backward_attributes(int tpw, int groups_per_block, int* blocks_per_sm) {
-  const void* fn = nullptr;
-  switch (tpw) {
-    case 32: fn = (const void*)backward_kernel<32>; break;
-    case 64: fn = (const void*)backward_kernel<64>; break;
-    case 128: fn = (const void*)backward_kernel<128>; break;
-    case 256: fn = (const void*)backward_kernel<256>; break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, tpw * groups_per_block, 0);
+cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
+  const void* fn = backward_fn_of(tpw);
+  if (!fn) return cudaErrorInvalidValue;
+  if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
+  // the attribute belongs to the instantiation, shared by every class using it: always the limit
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimitBytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, tpw * groups_per_block, smem_bytes);
 }
 
-// Floats of one world's backward workspace for the given sizes (forward part included).
-long long backward_ws_floats(int nb, int nv, int nm, int na, int ckpt_every) {
-  const WsLayout L = WsLayout::make(nb, nv, nm, na);
-  return AdjLayout::make(L.total, nb, nv, na, ckpt_every).total;
+long long backward_adj_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).total; }
+
+long long backward_seg_floats(int nb, int nv, int na, int ckpt_every) {
+  return (long long)ckpt_every * AdjLayout::make(nb, nv, na).snap;
 }
 
 }  // namespace orchard

@@ -70,8 +70,11 @@ struct Packed {
   std::vector<float4> bp0, bp1, bp2, bp3, bp4;
   std::vector<int4> dinfo;
   std::vector<unsigned> anc;
-  std::vector<int> dl_off, dl_bound;
-  std::vector<unsigned short> dl_list;
+  std::vector<int> bl_off, bl_bound;  // factorisation levels (bodies by first-DOF depth)
+  std::vector<int4> bl_info;          // per level position: first DOF, its row, second DOF's row, ndof
+  std::vector<int> bl_fbase;          // parallel to bl_bound: each level's start in fac_tgt
+  std::vector<int> fac_off;           // [W+1] start of each world's fac_tgt block
+  std::vector<int2> fac_tgt;          // per (level, c, position): {row start of the c-th ancestor - c, it}
   std::vector<float4> ap0, ap1;
   std::vector<int> apple_body, tip_body, btip;
   std::vector<float4> tip_local, gravity;
@@ -154,9 +157,12 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
   P.lvl.clear();
   P.dinfo.clear();
   P.anc.clear();
-  P.dl_off.assign(W + 1, 0);
-  P.dl_bound.clear();
-  P.dl_list.clear();
+  P.bl_off.assign(W + 1, 0);
+  P.bl_bound.clear();
+  P.bl_info.assign(NB, make_int4(0, 0, -1, 0));
+  P.bl_fbase.clear();
+  P.fac_off.assign(W + 1, 0);
+  P.fac_tgt.clear();
   P.btip.clear();
   std::vector<long long> ws(W);
   std::vector<double> cost(W);
@@ -237,7 +243,9 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     P.dof_off[w] = (int)P.dinfo.size();
     P.m_off[w] = (int)P.anc.size();
     int row = 0;
+    std::vector<int> rowstart(nv);
     for (int i = 0; i < nv; ++i) {
+      rowstart[i] = row;
       P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], 0));
       int j = i;
       for (int c = 0; c <= ddep[i]; ++c) {
@@ -247,32 +255,51 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
       row += ddep[i] + 1;
     }
     const int nm = row;
-    // DOFs by depth, each depth in depth-first preorder (children in index order), so the
-    // DOFs of one depth below any given DOF are contiguous
+    // Factorisation levels: the bodies with DOFs by the depth of their first DOF, each level in
+    // depth-first preorder (children in index order), so the bodies of one level below any
+    // given DOF are contiguous. Per (level l, ancestor distance c = 1..l, position p): the
+    // c-th ancestor of the p-th body's first DOF, as {its row start - c, it}, level-major.
     {
       std::vector<int> pre;
-      pre.reserve(nv);
+      pre.reserve(nb);
       std::vector<int> stack;
       if (nb > 0) stack.push_back(0);
       while (!stack.empty()) {
         const int b = stack.back();
         stack.pop_back();
-        for (int j = 0; j < nd[b]; ++j) pre.push_back(dof0[b] + j);
+        pre.push_back(b);
         for (int c = ccount[b] - 1; c >= 0; --c) stack.push_back(cfirst[b] + c);
       }
       int maxd = -1;
-      for (int i = 0; i < nv; ++i) maxd = std::max(maxd, ddep[i]);
-      P.dl_off[w] = (int)P.dl_bound.size();
-      int pos = 0;
+      for (int b = 0; b < nb; ++b)
+        if (nd[b] > 0) maxd = std::max(maxd, ddep[dof0[b]]);
+      P.bl_off[w] = (int)P.bl_bound.size();
+      P.fac_off[w] = (int)P.fac_tgt.size();
+      std::vector<int> first;  // first DOF of each level position
+      first.reserve(nb);
+      int pos = 0, fbase = 0;
       for (int l = 0; l <= maxd; ++l) {
-        P.dl_bound.push_back(pos);
-        for (int i : pre)
-          if (ddep[i] == l) {
-            P.dl_list.push_back((unsigned short)i);
+        P.bl_bound.push_back(pos);
+        P.bl_fbase.push_back(fbase);
+        const int lo = pos;
+        for (int b : pre)
+          if (nd[b] > 0 && ddep[dof0[b]] == l) {
+            const int i = dof0[b];
+            P.bl_info[b0 + pos] = make_int4(i, rowstart[i], nd[b] == 2 ? rowstart[i + 1] : -1, nd[b]);
+            first.push_back(i);
             ++pos;
           }
+        const int count = pos - lo;
+        for (int c = 1; c <= l; ++c)
+          for (int p = 0; p < count; ++p) {
+            int j = first[lo + p];
+            for (int s2 = 0; s2 < c; ++s2) j = dpar[j];
+            P.fac_tgt.push_back(make_int2(rowstart[j] - c, j));
+          }
+        fbase += count * l;
       }
-      P.dl_bound.push_back(pos);
+      P.bl_bound.push_back(pos);
+      P.bl_fbase.push_back(fbase);
     }
     for (int b = 0; b < nb; ++b) {
       const int gb = b0 + b;
@@ -298,7 +325,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
   P.dof_off[W] = (int)P.dinfo.size();
   P.m_off[W] = (int)P.anc.size();
   P.lvl_off[W] = (int)P.lvl.size();
-  P.dl_off[W] = (int)P.dl_bound.size();
+  P.bl_off[W] = (int)P.bl_bound.size();
+  P.fac_off[W] = (int)P.fac_tgt.size();
   P.NB = NB; P.NA = NA; P.NT = NT; P.NV = P.dof_off[W]; P.NM = P.m_off[W];
   if (P.NM > 0x7fffffffLL) return OT_ECAPACITY;
   // apples, tips, gravity
@@ -404,8 +432,8 @@ namespace {
 
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
-  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, dl_off,
-      dl_bound, dl_list, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue, total;
+  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, bl_off,
+      bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -420,9 +448,12 @@ ModelLayout model_layout(const Packed& P) {
   L.bp3 = c.take<float4>(P.NB); L.bp4 = c.take<float4>(P.NB);
   L.dinfo = c.take<int4>(P.NV);
   L.anc = c.take<unsigned>(P.NM);
-  L.dl_off = c.take<int>(W1);
-  L.dl_bound = c.take<int>(P.dl_bound.size());
-  L.dl_list = c.take<unsigned short>(P.dl_list.size());
+  L.bl_off = c.take<int>(W1);
+  L.bl_bound = c.take<int>(P.bl_bound.size());
+  L.bl_info = c.take<int4>(P.bl_info.size());
+  L.bl_fbase = c.take<int>(P.bl_fbase.size());
+  L.fac_off = c.take<int>(W1);
+  L.fac_tgt = c.take<int2>(P.fac_tgt.size());
   L.ap0 = c.take<float4>(P.NA); L.ap1 = c.take<float4>(P.NA);
   L.apple_body = c.take<int>(P.NA);
   L.tip_body = c.take<int>(P.NT);
@@ -638,9 +669,12 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.bp4, P.bp4.data(), vbytes(P.bp4));
   put(L.dinfo, P.dinfo.data(), vbytes(P.dinfo));
   put(L.anc, P.anc.data(), vbytes(P.anc));
-  put(L.dl_off, P.dl_off.data(), vbytes(P.dl_off));
-  put(L.dl_bound, P.dl_bound.data(), vbytes(P.dl_bound));
-  put(L.dl_list, P.dl_list.data(), vbytes(P.dl_list));
+  put(L.bl_off, P.bl_off.data(), vbytes(P.bl_off));
+  put(L.bl_bound, P.bl_bound.data(), vbytes(P.bl_bound));
+  put(L.bl_info, P.bl_info.data(), vbytes(P.bl_info));
+  put(L.bl_fbase, P.bl_fbase.data(), vbytes(P.bl_fbase));
+  put(L.fac_off, P.fac_off.data(), vbytes(P.fac_off));
+  put(L.fac_tgt, P.fac_tgt.data(), vbytes(P.fac_tgt));
   put(L.ap0, P.ap0.data(), vbytes(P.ap0)); put(L.ap1, P.ap1.data(), vbytes(P.ap1));
   put(L.apple_body, P.apple_body.data(), vbytes(P.apple_body));
   put(L.tip_body, P.tip_body.data(), vbytes(P.tip_body));
@@ -671,9 +705,12 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.bp4 = (const float4*)(base + L.bp4);
   dm.dinfo = (const int4*)(base + L.dinfo);
   dm.anc = (const unsigned*)(base + L.anc);
-  dm.dl_off = (const int*)(base + L.dl_off);
-  dm.dl_bound = (const int*)(base + L.dl_bound);
-  dm.dl_list = (const unsigned short*)(base + L.dl_list);
+  dm.bl_off = (const int*)(base + L.bl_off);
+  dm.bl_bound = (const int*)(base + L.bl_bound);
+  dm.bl_info = (const int4*)(base + L.bl_info);
+  dm.bl_fbase = (const int*)(base + L.bl_fbase);
+  dm.fac_off = (const int*)(base + L.fac_off);
+  dm.fac_tgt = (const int2*)(base + L.fac_tgt);
   dm.ap0 = (const float4*)(base + L.ap0); dm.ap1 = (const float4*)(base + L.ap1);
   dm.apple_body = (const int*)(base + L.apple_body);
   dm.tip_body = (const int*)(base + L.tip_body);
@@ -935,7 +972,7 @@ ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
   if (!m || !sc || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
   const ClassInfo& ci = m->P.classes[k];
   const int t = sc->threads_per_world;
-  if (t != 32 && t != 64 && t != 128 && t != 256) return OT_EINVAL;
+  if (t != 32 && t != 64 && t != 128 && t != 256 && t != 512) return OT_EINVAL;
   if (sc->worlds_per_block < 1 || t * sc->worlds_per_block > 512) return OT_EINVAL;
   if (t > 32 && sc->worlds_per_block > 15) return OT_EINVAL;
   if (t == 32 && sc->worlds_per_block > 16) return OT_EINVAL;
@@ -962,7 +999,7 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
     ClassInfo& ci = m->P.classes[k];
     const ot_schedule keep = ci.sched;
     std::vector<ot_schedule> cands;
-    for (int t : {32, 64, 128, 256})
+    for (int t : {32, 64, 128, 256, 512})
       for (int g : {1, 2, 3, 4, 6, 8, 12, 16}) {
         ot_schedule c{t, g, 0, keep.global_workspace};
         if (t * g > 512) continue;
@@ -1000,20 +1037,60 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
 }
 
 namespace {
-// Backward workspace: per class, two slots per SM of one world's backward layout.
-long long back_ws_floats(const ClassInfo& ci, int ce) {
-  return (backward_ws_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na, ce) + 63) / 64 * 64;
+// Backward launch plan of a class: threads per world as in the forward schedule (32..256);
+// the forward step's temporaries in shared memory when they fit, the backward's and the
+// segment snapshots in global memory; one workspace slot per group that can be resident at
+// once (bounded by shared memory, 2048 threads and 16 groups per SM).
+struct BackPlan {
+  int tpw, gpb, blocks;
+  size_t slots;
+  BackShape sh;
+};
+inline long long round16(long long f) { return (f + 15) / 16 * 16; }
+
+BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
+  BackPlan p{};
+  p.tpw = std::max(32, std::min(ci.sched.threads_per_world, 256));
+  BackShape& sh = p.sh;
+  sh.fwd_floats = round16(ci.ws_floats);
+  sh.adj_floats = round16(backward_adj_floats(ci.max_nb, ci.max_nv, ci.max_na));
+  const long long seg = round16(backward_seg_floats(ci.max_nb, ci.max_nv, ci.max_na, ce));
+  const long long lim = (long long)(kSmemLimit / 4);
+  // measured on B300 (diff1024 trees): the forward step's temporaries alone in shared memory,
+  // with more worlds resident per SM, beat keeping the backward's there too (one world per SM)
+  if (sh.fwd_floats <= lim) {
+    sh.mode = 1;
+    sh.smem_floats = sh.fwd_floats;
+    sh.global_floats = sh.adj_floats + seg;
+  } else {
+    sh.mode = 0;
+    sh.smem_floats = 0;
+    sh.global_floats = sh.fwd_floats + sh.adj_floats + seg;
+  }
+  sh.global_floats = (sh.global_floats + 63) / 64 * 64;
+  // groups per block: as many as share one block's shared memory (at most 512 threads)
+  p.gpb = sh.smem_floats > 0 ? (int)std::max<long long>(1, std::min<long long>(lim / sh.smem_floats, 512 / p.tpw))
+                             : 1;
+  p.gpb = std::min(p.gpb, 16);
+  // resident groups per SM
+  long long per_sm = std::min<long long>(2048 / p.tpw, 16);
+  if (sh.smem_floats > 0) per_sm = std::min<long long>(per_sm, (long long)(kSmemLimit / 4) / sh.smem_floats);
+  per_sm = std::max<long long>(per_sm, 1);
+  const size_t worlds = (size_t)(ci.q_end - ci.q_begin);
+  p.slots = std::min<size_t>(worlds, (size_t)m->n_sm * (size_t)per_sm);
+  p.slots = (p.slots + p.gpb - 1) / p.gpb * p.gpb;
+  p.blocks = (int)(p.slots / p.gpb);
+  return p;
 }
-size_t back_slots(const ot_model* m, const ClassInfo& ci) {
-  return std::min<size_t>((size_t)m->n_sm * 2, (size_t)(ci.q_end - ci.q_begin));
-}
-int back_tpw(const ClassInfo& ci) { return std::max(32, std::min(ci.sched.threads_per_world, 256)); }
 }  // namespace
 
 ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, size_t* bytes) {
   if (!m || !bytes || ckpt_every < 1) return OT_EINVAL;
   size_t total = 0;
-  for (const ClassInfo& ci : m->P.classes) total += back_slots(m, ci) * (size_t)back_ws_floats(ci, ckpt_every) * 4;
+  for (const ClassInfo& ci : m->P.classes) {
+    const BackPlan p = back_plan(m, ci, ckpt_every);
+    total += p.slots * (size_t)p.sh.global_floats * 4;
+  }
   *bytes = total;
   return OT_OK;
 }
@@ -1042,23 +1119,20 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
   float* work = (float*)workspace;
   for (int k = 0; k < (int)m->P.classes.size(); ++k) {
     const ClassInfo& ci = m->P.classes[k];
-    const long long wsf = back_ws_floats(ci, rec->ckpt_every);
-    const size_t slots = back_slots(m, ci);
-    const int tpw = back_tpw(ci);
+    const BackPlan p = back_plan(m, ci, rec->ckpt_every);
     int bps = 0;
-    OT_CUDA(backward_attributes(tpw, 1, &bps));
-    const int blocks = (int)std::min<size_t>(slots, (size_t)std::max(bps, 1) * m->n_sm);
+    OT_CUDA(backward_attributes(p.tpw, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps));
     StepArgs b = a;
     b.q_begin = ci.q_begin;
     b.q_end = ci.q_end;
     b.q_counter = s->q_counters + k;
     OT_CUDA(cudaMemsetAsync(b.q_counter, 0, sizeof(int), cs));
-    if (blocks > 0) {
-      launch_backward(tpw, 1, blocks, cs, m->dev, b, ba, work, wsf);
+    if (p.blocks > 0) {
+      launch_backward(p.tpw, p.gpb, p.blocks, cs, m->dev, b, ba, work, p.sh);
       OT_CUDA(cudaGetLastError());
       g_launches += 1;
     }
-    work += slots * (size_t)wsf;
+    work += p.slots * (size_t)p.sh.global_floats;
   }
   return OT_OK;
 }

@@ -29,9 +29,19 @@ struct DevModel {
   const float4* bp4;     // armature, m_max, -, -
   const int4* dinfo;     // per DOF: row start (world-local), body, depth d_i, -
   const unsigned* anc;   // per row entry c of DOF i: its c-th ancestor DOF j | (body of j) << 16
-  const int* dl_off;     // [W+1] start of the world's DOF-depth level boundaries in dl_bound
-  const int* dl_bound;   // world-local position in dl_list of each DOF depth's first DOF (+ end)
-  const unsigned short* dl_list;  // per world: DOFs sorted by (depth, depth-first preorder)
+  const int* bl_off;     // [W+1] start of the world's factorisation level boundaries in bl_bound
+  const int* bl_bound;   // world-local level position of each level's first body (+ end). A level
+                         // holds the bodies with DOFs whose first DOF has that depth, in
+                         // depth-first preorder
+  const int4* bl_info;   // per level position (world-local, at the world's body offset): the
+                         // body's first DOF, its row start, the second DOF's row start (-1 for a
+                         // one-DOF joint), the DOF count
+  const int* bl_fbase;   // parallel to bl_bound: each level's first entry in the fac_tgt block
+  const int* fac_off;    // [W+1] start of the world's fac_tgt block
+  const int2* fac_tgt;   // per level l, ancestor distance c (1..l), position p in the level:
+                         // entry (c - 1) * count_l + p = {row start of the c-th ancestor of the
+                         // p-th body's first DOF minus c (the factorisation's target base), that
+                         // ancestor}
   const float4* ap0;     // hang point in the body frame (xyz), apple mass (w)
   const float4* ap1;     // k_s, c_s, f_detach, -
   const int* apple_body; // world-local body of each apple
@@ -137,10 +147,21 @@ struct BackArgs {
   float* dq0;          // [NV] written
   float* dqd0;         // [NV] written
 };
+// Where a backward group keeps its temporaries (see adjoint_kernel.cu): mode 0 all in its
+// global slot, 1 the forward step's in shared memory, 2 the forward's and the backward's in
+// shared memory; the checkpoint segment's snapshots always in the global slot.
+struct BackShape {
+  int mode;
+  long long fwd_floats;     // forward temporaries of the class's largest world (WsLayout)
+  long long adj_floats;     // backward temporaries (AdjLayout)
+  long long smem_floats;    // per group in shared memory
+  long long global_floats;  // per slot of the workspace
+};
 void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
-                     const StepArgs& a, const BackArgs& ba, float* work, long long ws_floats);
-cudaError_t backward_attributes(int tpw, int groups_per_block, int* blocks_per_sm);
-long long backward_ws_floats(int nb, int nv, int nm, int na, int ckpt_every);
+                     const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
+cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
+long long backward_adj_floats(int nb, int nv, int na);
+long long backward_seg_floats(int nb, int nv, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);

@@ -162,7 +162,7 @@ struct Group {
 };
 
 struct WorldView {
-  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, DL0, nDL;
+  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, BL0, nBL, f0;
 };
 
 // One world's state arrays, indexed world-locally.
@@ -193,7 +193,8 @@ HD WorldView world_view(const DevModel& m, int w) {
   v.t0 = m.tip_off[w]; v.nt = m.tip_off[w + 1] - v.t0;
   v.m0 = m.m_off[w]; v.nm = m.m_off[w + 1] - v.m0;
   v.L0 = m.lvl_off[w]; v.nL = m.lvl_off[w + 1] - v.L0 - 1;
-  v.DL0 = m.dl_off[w]; v.nDL = m.dl_off[w + 1] - v.DL0 - 1;
+  v.BL0 = m.bl_off[w]; v.nBL = m.bl_off[w + 1] - v.BL0 - 1;
+  v.f0 = m.fac_off[w];
   return v;
 }
 
@@ -382,6 +383,74 @@ HD void backward_body(const DevModel& m, const WState& s, const StepArgs& a,
   }
 }
 
+// The factorisation eliminates a joint's DOFs (one or two) together, with the inverse of
+// their diagonal block P of H (1x1 or 2x2) taken after every deeper joint is eliminated:
+// rows stay unscaled (U), the Schur update of an ancestor pair (i, j) is U_i^T P^-1 U_j, and a
+// solve is an L^T sweep leaf to root, the scaling z = P^-1 r, and an L sweep root to leaf
+// x = z - P^-1 U x_ancestors. For a two-DOF joint (x, then y'): P = [[H_xx, H_yx], [H_yx, H_yy]]
+// and the y' row is the x row shifted by one (its first ancestor is x itself).
+struct Pivot {
+  float p00, p01, p11;  // P^-1 (symmetric)
+};
+HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
+  Pivot P;
+  const float a = M[rowx];
+  if (nd == 2) {
+    const float d = M[rowy], b = M[rowy + 1];
+    const float inv = 1.f / (a * d - b * b);
+    P.p00 = d * inv;
+    P.p01 = -b * inv;
+    P.p11 = a * inv;
+  } else {
+    P.p00 = 1.f / a;
+    P.p01 = 0.f;
+    P.p11 = 0.f;
+  }
+  return P;
+}
+
+// z = P^-1 r for one joint, in place in y.
+HD void pivot_scale(const float* M, int4 info, float* y) {
+  const Pivot P = pivot_of(M, info.y, info.z, info.w);
+  const float rx = y[info.x];
+  if (info.w == 2) {
+    const float ry = y[info.x + 1];
+    y[info.x] = P.p00 * rx + P.p01 * ry;
+    y[info.x + 1] = P.p01 * rx + P.p11 * ry;
+  } else {
+    y[info.x] = P.p00 * rx;
+  }
+}
+
+// L sweep of one joint (first DOF dof0, nd DOFs): x = z - P^-1 U x_ancestors, in place in y
+// (which holds z for this joint and the final x of every ancestor).
+HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, const float* ws, float* y, int dof0,
+                     int nd) {
+  if (nd == 0) return;
+  const int4 dx = m.dinfo[v.d0 + dof0];
+  const float* M = ws + L.M;
+  const float* rowx = M + dx.x;
+  const unsigned* an = m.anc + v.m0 + dx.x;
+  float sx = 0.f, sy = 0.f;
+  if (nd == 2) {
+    const int ry = m.dinfo[v.d0 + dof0 + 1].x;
+    const float* rowy = M + ry + 1;  // rowy[c]: the y' row's entry of the x row's c-th ancestor
+#pragma unroll 4
+    for (int c = 1; c <= dx.z; ++c) {
+      const float xa = y[an[c] & 0xffffu];
+      sx = fmaf(rowx[c], xa, sx);
+      sy = fmaf(rowy[c], xa, sy);
+    }
+    const Pivot P = pivot_of(M, dx.x, ry, 2);
+    y[dof0] -= P.p00 * sx + P.p01 * sy;
+    y[dof0 + 1] -= P.p01 * sx + P.p11 * sy;
+  } else {
+#pragma unroll 4
+    for (int c = 1; c <= dx.z; ++c) sx = fmaf(rowx[c], y[an[c] & 0xffffu], sx);
+    y[dof0] -= sx / rowx[0];
+  }
+}
+
 // Phase 5 for one body: finish the solve, update, velocities, apples, events.
 HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
                                             const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs,
@@ -402,16 +471,10 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
   }
   bool bad = false;
   float th2 = 0.f;
+  lsweep_joint(m, v, L, ws, ws + L.r, dof0, nd);
   for (int j = 0; j < nd; ++j) {
     const int i = dof0 + j;
-    const int4 di = m.dinfo[v.d0 + i];
-    const float* row = ws + L.M + di.x;
-    const unsigned* an = m.anc + v.m0 + di.x;
-    float acc = 0.f;
-#pragma unroll 4
-    for (int c = 1; c <= di.z; ++c) acc = fmaf(row[c], ws[L.r + (an[c] & 0xffffu)], acc);
-    const float x = ws[L.r + i] - acc / row[0];
-    ws[L.r + i] = x;
+    const float x = ws[L.r + i];
     const float qd = s.qd[i] + x;
     const float q = s.q[i] + dt * qd;
     s.qd[i] = qd;
@@ -551,6 +614,30 @@ HD void record_tips(const DevModel& m, const StepArgs& a, const WorldView& v, co
 }
 
 #ifdef __CUDA_ARCH__
+// Eight independent segmented scans interleaved, so their shuffle latencies overlap.
+__device__ __forceinline__ void seg_scan8(float (&v)[8], int lane, int first) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    float t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = __shfl_up_sync(0xffffffffu, v[j], o);
+    if (lane - o >= first) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] += t[j];
+    }
+  }
+}
+
+// One segmented scan.
+__device__ __forceinline__ float seg_scan1(float a, int lane, int first) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float t = __shfl_up_sync(0xffffffffu, a, o);
+    if (lane - o >= first) a += t;
+  }
+  return a;
+}
+
 // Four independent segmented scans interleaved, so their shuffle latencies overlap.
 __device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d, int lane, int first) {
 #pragma unroll
@@ -569,112 +656,128 @@ __device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d
 }
 #endif
 
-// Tree-sparse LDL^T of H (rows kept unscaled, U = D L) and the L^T sweep of the solve.
-// All DOFs of one depth are eliminated together (their rows are final once every deeper DOF
-// is done, and none is an ancestor of another). A DOF k of depth l adds
-// -U_k[c] U_k[c2] / D_k to entry (anc_c(k), c2 - c) and -U_k[c] y_k / D_k to y of anc_c(k).
-// Listed in depth-first order, the DOFs of one depth that share their c-th ancestor are
-// contiguous, so each target's contributions are a segmented sum over consecutive lanes:
-// shuffle scans, deterministic, no atomics. The c values are split over the group's warps
-// (different c means different target rows). y_k / D_k is stored once the level is done.
+// Tree-sparse LDL^T of H in joint blocks (see Pivot) with the L^T sweep of the solve fused in.
+// All joints of one level (the depth of their first DOF) are eliminated together, deepest first
+// (none is another's ancestor, and all their descendants are done). Joint k of level l adds
+// -a_c U_k,x[c2] - b_c U_k,y[c2] to entry (anc_c, c2 - c) and -a_c r_x - b_c r_y to r of anc_c,
+// for 1 <= c <= c2 <= l, with anc_c the c-th ancestor of k's first DOF and (a_c, b_c) =
+// (U_k,x[c], U_k,y[c]) P_k^-1. Listed in depth-first order, the joints of one level that share
+// their c-th ancestor are contiguous, so each target's contributions are a segmented sum over
+// consecutive lanes: shuffle scans, deterministic, no atomics. The c values are split over the
+// group's warps (different c means different target rows). z = P^-1 r is stored once the level
+// is done.
 template <int TPW>
 HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, const Group<TPW>& g) {
+  float* M = ws + L.M;
+  float* r = ws + L.r;
 #ifdef __CUDA_ARCH__
   constexpr int NW = TPW / 32;
   const int warp = g.lane >> 5, lane = g.lane & 31;
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
+  for (int l = v.nBL - 1; l >= 0; --l) {
+    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
     if (l > 0) {
+      const int count = hi - lo;
+      const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
       for (int base = lo; base < hi; base += 32) {
         const int idx = base + lane;
         const bool valid = idx < hi;
-        int rowk = 0;
-        float dinv = 0.f, yk = 0.f;
+        int4 info = make_int4(0, 0, 0, 0);
+        Pivot P{0.f, 0.f, 0.f};
+        float rx = 0.f, ry = 0.f;
         if (valid) {
-          const int k = m.dl_list[v.d0 + idx];
-          rowk = m.dinfo[v.d0 + k].x;
-          dinv = 1.f / ws[L.M + rowk];
-          yk = ws[L.r + k];
+          info = m.bl_info[v.b0 + idx];
+          P = pivot_of(M, info.y, info.z, info.w);
+          rx = r[info.x];
+          if (info.w == 2) ry = r[info.x + 1];
         }
-        const float* row = ws + L.M + rowk;
-        const unsigned* an = m.anc + v.m0 + rowk;
+        const bool two = info.w == 2;
+        const float* rowx = M + info.y;
+        const float* rowy = M + (two ? info.z + 1 : info.y);  // rowy[c]: entry of anc_c in the y' row
+        const int2* fp = ft + (idx - lo);
+        // this warp's first target; the next one is loaded while the current one is summed
+        int2 tk_next = (valid && 1 + warp <= l) ? fp[warp * count] : make_int2(0, -1 - lane);
         for (int c = 1 + warp; c <= l; c += NW) {
-          const int key = valid ? (int)(an[c] & 0xffffu) : -1 - lane;
+          const int2 tk = tk_next;
+          if (c + NW <= l) tk_next = valid ? fp[(c - 1 + NW) * count] : make_int2(0, -1 - lane);
+          const int key = tk.y;
           const int prev = __shfl_up_sync(0xffffffffu, key, 1);
           const int next = __shfl_down_sync(0xffffffffu, key, 1);
           const bool head = lane == 0 || prev != key;
           const bool tail = lane == 31 || next != key;
           const unsigned heads = __ballot_sync(0xffffffffu, head);
           const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-          const float uc = valid ? row[c] * dinv : 0.f;
-          const int trow = valid ? m.dinfo[v.d0 + key].x : 0;
-          float* tgt = ws + L.M + trow - c;  // entry (anc_c(k), c2 - c) is tgt[c2]
+          const float ux = valid ? rowx[c] : 0.f, uy = two ? rowy[c] : 0.f;
+          const float ac = ux * P.p00 + uy * P.p01, bc = ux * P.p01 + uy * P.p11;
+          float* tgt = M + tk.x;  // entry (anc_c, c2 - c) is tgt[c2]
           int c2 = c;
-          for (; c2 + 4 <= l + 1; c2 += 4) {
-            float s0 = valid ? uc * row[c2] : 0.f, s1 = valid ? uc * row[c2 + 1] : 0.f;
-            float s2 = valid ? uc * row[c2 + 2] : 0.f, s3 = valid ? uc * row[c2 + 3] : 0.f;
-            seg_scan4(s0, s1, s2, s3, lane, first);
+          for (; c2 + 8 <= l + 1; c2 += 8) {
+            float sv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sv[j] = valid ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
+            seg_scan8(sv, lane, first);
             if (valid && tail) {
-              tgt[c2] -= s0;
-              tgt[c2 + 1] -= s1;
-              tgt[c2 + 2] -= s2;
-              tgt[c2 + 3] -= s3;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) tgt[c2 + j] -= sv[j];
             }
           }
-          // the last up-to-three entries of the row together with the right-hand side
-          const int rem = l + 1 - c2;
-          float s0 = valid && rem > 0 ? uc * row[c2] : 0.f;
-          float s1 = valid && rem > 1 ? uc * row[c2 + 1] : 0.f;
-          float s2 = valid && rem > 2 ? uc * row[c2 + 2] : 0.f;
-          float sy = uc * yk;
-          seg_scan4(s0, s1, s2, sy, lane, first);
-          if (valid && tail) {
-            if (rem > 0) tgt[c2] -= s0;
-            if (rem > 1) tgt[c2 + 1] -= s1;
-            if (rem > 2) tgt[c2 + 2] -= s2;
-            ws[L.r + key] -= sy;
+          // the last up-to-seven entries of the row together with the right-hand side
+          const int rem = l + 1 - c2;  // the same for the whole warp
+          const float sr = fmaf(ac, rx, bc * ry);
+          if (rem <= 3) {
+            float s0 = valid && rem > 0 ? fmaf(ac, rowx[c2], two ? bc * rowy[c2] : 0.f) : 0.f;
+            float s1 = valid && rem > 1 ? fmaf(ac, rowx[c2 + 1], two ? bc * rowy[c2 + 1] : 0.f) : 0.f;
+            float s2 = valid && rem > 2 ? fmaf(ac, rowx[c2 + 2], two ? bc * rowy[c2 + 2] : 0.f) : 0.f;
+            float sy = sr;
+            seg_scan4(s0, s1, s2, sy, lane, first);
+            if (valid && tail) {
+              if (rem > 0) tgt[c2] -= s0;
+              if (rem > 1) tgt[c2 + 1] -= s1;
+              if (rem > 2) tgt[c2 + 2] -= s2;
+              r[key] -= sy;
+            }
+          } else {
+            float sv[8];
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+              sv[j] = valid && rem > j ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
+            sv[7] = sr;
+            seg_scan8(sv, lane, first);
+            if (valid && tail) {
+#pragma unroll
+              for (int j = 0; j < 7; ++j)
+                if (rem > j) tgt[c2 + j] -= sv[j];
+              r[key] -= sv[7];
+            }
           }
         }
       }
     }
     g.sync();
-    for (int idx = lo + g.lane; idx < hi; idx += TPW) {
-      const int k = m.dl_list[v.d0 + idx];
-      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) pivot_scale(M, m.bl_info[v.b0 + idx], r);
   }
   g.sync();
 #else
-  // one serial lane: the same updates, segment by segment in list order
-  for (int l = v.nDL - 1; l >= 0; --l) {
-    const int lo = m.dl_bound[v.DL0 + l], hi = m.dl_bound[v.DL0 + l + 1];
-    for (int c = 1; c <= l; ++c) {
-      for (int c2 = c - 1; c2 <= l; ++c2) {  // c2 = c - 1 stands for the right-hand side
-        float acc = 0.f;
-        for (int idx = lo; idx < hi; ++idx) {
-          const int k = m.dl_list[v.d0 + idx];
-          const int rowk = m.dinfo[v.d0 + k].x;
-          const float* row = ws + L.M + rowk;
-          const int key = (int)(m.anc[v.m0 + rowk + c] & 0xffffu);
-          const float uc = row[c] / row[0];
-          acc += uc * (c2 < c ? ws[L.r + k] : row[c2]);
-          int next = -1;
-          if (idx + 1 < hi) {
-            const int k2 = m.dl_list[v.d0 + idx + 1];
-            next = (int)(m.anc[v.m0 + m.dinfo[v.d0 + k2].x + c] & 0xffffu);
-          }
-          if (next != key) {
-            if (c2 < c) ws[L.r + key] -= acc;
-            else ws[L.M + m.dinfo[v.d0 + key].x + (c2 - c)] -= acc;
-            acc = 0.f;
-          }
-        }
+  // one serial lane: the same updates, joint by joint in list order
+  for (int l = v.nBL - 1; l >= 0; --l) {
+    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int count = hi - lo;
+    const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+    for (int idx = lo; idx < hi; ++idx) {
+      const int4 info = m.bl_info[v.b0 + idx];
+      const bool two = info.w == 2;
+      const Pivot P = pivot_of(M, info.y, info.z, info.w);
+      const float rx = r[info.x], ry = two ? r[info.x + 1] : 0.f;
+      const float* rowx = M + info.y;
+      const float* rowy = M + (two ? info.z + 1 : info.y);
+      for (int c = 1; c <= l; ++c) {
+        const int2 tk = ft[(c - 1) * count + (idx - lo)];
+        const float ux = rowx[c], uy = two ? rowy[c] : 0.f;
+        const float ac = ux * P.p00 + uy * P.p01, bc = ux * P.p01 + uy * P.p11;
+        for (int c2 = c; c2 <= l; ++c2) M[tk.x + c2] -= fmaf(ac, rowx[c2], two ? bc * rowy[c2] : 0.f);
+        r[tk.y] -= fmaf(ac, rx, bc * ry);
       }
     }
-    for (int idx = lo; idx < hi; ++idx) {
-      const int k = m.dl_list[v.d0 + idx];
-      ws[L.r + k] /= ws[L.M + m.dinfo[v.d0 + k].x];
-    }
+    for (int idx = lo; idx < hi; ++idx) pivot_scale(M, m.bl_info[v.b0 + idx], r);
   }
 #endif
 }

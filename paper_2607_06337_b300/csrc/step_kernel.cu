@@ -48,6 +48,7 @@ void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes
     case 64: rollout_kernel<64><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
     case 128: rollout_kernel<128><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
     case 256: rollout_kernel<256><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 512: rollout_kernel<512><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
     default: break;
   }
 }
@@ -59,6 +60,7 @@ cudaError_t kernel_attributes(int tpw, int groups_per_block, size_t smem_bytes, 
     case 64: fn = (const void*)rollout_kernel<64>; break;
     case 128: fn = (const void*)rollout_kernel<128>; break;
     case 256: fn = (const void*)rollout_kernel<256>; break;
+    case 512: fn = (const void*)rollout_kernel<512>; break;
     default: return cudaErrorInvalidValue;
   }
   if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
