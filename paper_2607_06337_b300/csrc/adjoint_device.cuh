@@ -47,11 +47,8 @@ struct AdjLayout {
   int ub, vb;     // per apple x3: cotangents of the step-start u (or x), v
   int ub1, vb1;   // per apple x3: of the step-end u', v'
   int vh;         // per apple x3: cotangent of the new hang-point velocity
-  int ps;         // private state floats: q, qd (nv), ax, av (3 na)
-  int pi;         // private state ints: broken, bcnt, break_step (nb), detached, pcnt, tcnt,
-                  // detach_step (na), status (1)
   int total;      // floats at wa
-  int snap;       // words per snapshot (the private state, ps then pi)
+  int snap;       // words per snapshot: the private state, staged in the forward workspace
   HD static AdjLayout make(int nb, int nv, int na) {
     AdjLayout A;
     int o = 0;
@@ -70,29 +67,16 @@ struct AdjLayout {
     A.ub1 = o; o += 3 * na;
     A.vb1 = o; o += 3 * na;
     A.vh = o; o += 3 * na;
-    A.ps = o; o += 2 * nv + 6 * na;
-    A.pi = o; o += 3 * nb + 4 * na + 1;
-    A.snap = 2 * nv + 6 * na + 3 * nb + 4 * na + 1;
+    A.snap = WsLayout::state_words(nb, nv, na);
     A.total = o;
     return A;
   }
 };
 
-HD WState private_state(float* wa, const AdjLayout& A, int nb, int nv, int na) {
-  WState s;
-  float* f = wa + A.ps;
-  s.q = f; s.qd = f + nv; s.ax = f + 2 * nv; s.av = f + 2 * nv + 3 * na;
-  int* i = (int*)(wa + A.pi);
-  s.broken = i; s.bcnt = i + nb; s.break_step = i + 2 * nb;
-  s.detached = i + 3 * nb; s.pcnt = s.detached + na; s.tcnt = s.pcnt + na; s.detach_step = s.tcnt + na;
-  s.status = (unsigned*)(s.detach_step + na);
-  return s;
-}
-
-// Copy the private state to or from snapshot `k` of the segment buffer (group-parallel).
+// Copy the private state (staged at ws + L.S) to or from snapshot `k` of the segment buffer.
 template <int TPW>
-HD void snapshot(float* wa, float* seg, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
-  float* src = wa + A.ps;  // private floats and ints are contiguous: ps then pi
+HD void snapshot(float* ws, const WsLayout& L, float* seg, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
+  float* src = ws + L.S;
   float* dst = seg + (long long)k * A.snap;
   for (int i = g.lane; i < A.snap; i += TPW) {
     if (save) dst[i] = src[i];
@@ -506,6 +490,7 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
   const int warp = g.lane >> 5, lane = g.lane & 31;
   for (int l = v.nBL - 1; l >= 0; --l) {
     const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    if (lo == hi) continue;  // uniform for the group
     if (l > 0) {
       const int count = hi - lo;
       const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
@@ -533,8 +518,9 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
           const bool tail = lane == 31 || next != key;
           const unsigned heads = __ballot_sync(0xffffffffu, head);
           const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+          const int span = __reduce_max_sync(0xffffffffu, (unsigned)(lane - first + 1));
           const float val = valid ? fmaf(rowx[c], zx, two ? rowy[c] * zy : 0.f) : 0.f;
-          const float sum = seg_scan1(val, lane, first);
+          const float sum = seg_scan1(val, lane, first, span);
           if (valid && tail) y[key] -= sum;
         }
       }
@@ -714,7 +700,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
   const WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
-  const WState s = private_state(wa, A, v.nb, v.nv, v.na);
+  const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);  // the world's private state
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   const float dt = a.dt;
@@ -729,7 +715,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     const int t0 = sg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
     load_ckpt(a, v, s, sg, g);
     for (int t = t0; t < t1; ++t) {
-      snapshot(wa, seg, A, t - t0, true, g);
+      snapshot(ws, L, seg, A, t - t0, true, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
     }
     if (sg == nseg - 1) {
@@ -757,11 +743,11 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       g.sync();
     }
     for (int t = t1 - 1; t >= t0; --t) {
-      snapshot(wa, seg, A, t - t0, false, g);
+      snapshot(ws, L, seg, A, t - t0, false, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
       for (int i = g.lane; i < v.nv; i += TPW) wa[A.qd1 + i] = s.qd[i];
       g.sync();
-      snapshot(wa, seg, A, t - t0, false, g);
+      snapshot(ws, L, seg, A, t - t0, false, g);
       reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, g, t, gv);
       for (int i = g.lane; i < v.nv; i += TPW) {
         wa[A.qb1 + i] = wa[A.qb + i];

@@ -99,9 +99,13 @@ struct StepArgs {
 
 // Workspace layout of one world (floats), a function of its sizes only. Rotations, bias
 // accelerations and forces (live in the two sweeps) share space with the mass-matrix rows
-// (live from the mass matrix to the end of the step).
+// (live from the mass matrix to the end of the step). S holds the world's state for the whole
+// rollout (see staged_view): the step reads and writes it there, not in global memory.
 struct WsLayout {
-  int X, E, IC, r, AT, V, SN, R, A, F, M, total;
+  int X, E, IC, r, AT, V, SN, S, R, A, F, M, total;
+  __host__ __device__ static int state_words(int nb, int nv, int na) {
+    return 2 * nv + 6 * na + 3 * nb + 4 * na + 1;
+  }
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
     L.X = 0;                 // joint origins
@@ -112,7 +116,8 @@ struct WsLayout {
                              // pull, hang offset r_h (10 floats)
     L.V = L.AT + 10 * na;    // body velocities (start of step, then end of step)
     L.SN = L.V + 6 * nb;     // 1 on a snapped sub-tree
-    const int u = L.SN + nb; // shared region
+    L.S = L.SN + nb;         // the staged state
+    const int u = L.S + state_words(nb, nv, na);  // shared region
     L.R = u;
     L.A = L.R + 9 * nb;
     L.F = L.A + 6 * nb;

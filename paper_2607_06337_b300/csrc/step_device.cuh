@@ -185,6 +185,19 @@ HD WState world_state(const DevState& S, const WorldView& v, int w) {
   return s;
 }
 
+// The state staged in a workspace (WsLayout::S): q, qd (nv) and the apples' u-or-x, v (3 na)
+// as floats, then broken, bcnt, break_step (nb), detached, pcnt, tcnt, detach_step (na) and
+// one status word as ints.
+HD WState staged_view(float* base, int nb, int nv, int na) {
+  WState s;
+  s.q = base; s.qd = base + nv; s.ax = base + 2 * nv; s.av = base + 2 * nv + 3 * na;
+  int* i = (int*)(base + 2 * nv + 6 * na);
+  s.broken = i; s.bcnt = i + nb; s.break_step = i + 2 * nb;
+  s.detached = i + 3 * nb; s.pcnt = s.detached + na; s.tcnt = s.pcnt + na; s.detach_step = s.tcnt + na;
+  s.status = (unsigned*)(s.detach_step + na);
+  return s;
+}
+
 HD WorldView world_view(const DevModel& m, int w) {
   WorldView v;
   v.b0 = m.body_off[w]; v.nb = m.body_off[w + 1] - v.b0;
@@ -614,10 +627,13 @@ HD void record_tips(const DevModel& m, const StepArgs& a, const WorldView& v, co
 }
 
 #ifdef __CUDA_ARCH__
-// Eight independent segmented scans interleaved, so their shuffle latencies overlap.
-__device__ __forceinline__ void seg_scan8(float (&v)[8], int lane, int first) {
+// Eight independent segmented scans interleaved, so their shuffle latencies overlap. `span`
+// is the longest segment in the warp (warp-uniform): rounds stop once they cover it, since the
+// shuffle unit's throughput, not its latency, bounds a block of scanning warps.
+__device__ __forceinline__ void seg_scan8(float (&v)[8], int lane, int first, int span) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;
     float t[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) t[j] = __shfl_up_sync(0xffffffffu, v[j], o);
@@ -628,20 +644,22 @@ __device__ __forceinline__ void seg_scan8(float (&v)[8], int lane, int first) {
   }
 }
 
-// One segmented scan.
-__device__ __forceinline__ float seg_scan1(float a, int lane, int first) {
+// One segmented scan (span as for seg_scan8).
+__device__ __forceinline__ float seg_scan1(float a, int lane, int first, int span) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;
     const float t = __shfl_up_sync(0xffffffffu, a, o);
     if (lane - o >= first) a += t;
   }
   return a;
 }
 
-// Four independent segmented scans interleaved, so their shuffle latencies overlap.
-__device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d, int lane, int first) {
+// Four independent segmented scans interleaved (span as for seg_scan8).
+__device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d, int lane, int first, int span) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
+    if (o >= span) break;
     const float ta = __shfl_up_sync(0xffffffffu, a, o);
     const float tb = __shfl_up_sync(0xffffffffu, b, o);
     const float tc = __shfl_up_sync(0xffffffffu, c, o);
@@ -675,17 +693,32 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
   const int warp = g.lane >> 5, lane = g.lane & 31;
   for (int l = v.nBL - 1; l >= 0; --l) {
     const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    if (lo == hi) continue;  // no joint has its first DOF at this depth (uniform for the group)
     if (l > 0) {
       const int count = hi - lo;
       const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+      // the first chunk's joint and first target; later chunks' are loaded one chunk ahead
+      int4 info_n = make_int4(0, 0, 0, 0);
+      int2 tk_n = make_int2(0, -1 - lane);
+      if (lo + lane < hi) {
+        info_n = m.bl_info[v.b0 + lo + lane];
+        if (1 + warp <= l) tk_n = ft[warp * count + lane];
+      }
       for (int base = lo; base < hi; base += 32) {
         const int idx = base + lane;
         const bool valid = idx < hi;
-        int4 info = make_int4(0, 0, 0, 0);
+        const int4 info = info_n;
+        int2 tk_next = tk_n;
+        if (base + 32 + lane < hi) {
+          info_n = m.bl_info[v.b0 + base + 32 + lane];
+          if (1 + warp <= l) tk_n = ft[warp * count + base + 32 + lane - lo];
+        } else {
+          info_n = make_int4(0, 0, 0, 0);
+          tk_n = make_int2(0, -1 - lane);
+        }
         Pivot P{0.f, 0.f, 0.f};
         float rx = 0.f, ry = 0.f;
         if (valid) {
-          info = m.bl_info[v.b0 + idx];
           P = pivot_of(M, info.y, info.z, info.w);
           rx = r[info.x];
           if (info.w == 2) ry = r[info.x + 1];
@@ -694,8 +727,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         const float* rowx = M + info.y;
         const float* rowy = M + (two ? info.z + 1 : info.y);  // rowy[c]: entry of anc_c in the y' row
         const int2* fp = ft + (idx - lo);
-        // this warp's first target; the next one is loaded while the current one is summed
-        int2 tk_next = (valid && 1 + warp <= l) ? fp[warp * count] : make_int2(0, -1 - lane);
+        // the next target is loaded while the current one is summed
         for (int c = 1 + warp; c <= l; c += NW) {
           const int2 tk = tk_next;
           if (c + NW <= l) tk_next = valid ? fp[(c - 1 + NW) * count] : make_int2(0, -1 - lane);
@@ -706,6 +738,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
           const bool tail = lane == 31 || next != key;
           const unsigned heads = __ballot_sync(0xffffffffu, head);
           const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+          const int span = __reduce_max_sync(0xffffffffu, (unsigned)(lane - first + 1));
           const float ux = valid ? rowx[c] : 0.f, uy = two ? rowy[c] : 0.f;
           const float ac = ux * P.p00 + uy * P.p01, bc = ux * P.p01 + uy * P.p11;
           float* tgt = M + tk.x;  // entry (anc_c, c2 - c) is tgt[c2]
@@ -714,7 +747,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
             float sv[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) sv[j] = valid ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
-            seg_scan8(sv, lane, first);
+            seg_scan8(sv, lane, first, span);
             if (valid && tail) {
 #pragma unroll
               for (int j = 0; j < 8; ++j) tgt[c2 + j] -= sv[j];
@@ -728,7 +761,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
             float s1 = valid && rem > 1 ? fmaf(ac, rowx[c2 + 1], two ? bc * rowy[c2 + 1] : 0.f) : 0.f;
             float s2 = valid && rem > 2 ? fmaf(ac, rowx[c2 + 2], two ? bc * rowy[c2 + 2] : 0.f) : 0.f;
             float sy = sr;
-            seg_scan4(s0, s1, s2, sy, lane, first);
+            seg_scan4(s0, s1, s2, sy, lane, first, span);
             if (valid && tail) {
               if (rem > 0) tgt[c2] -= s0;
               if (rem > 1) tgt[c2 + 1] -= s1;
@@ -741,7 +774,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
             for (int j = 0; j < 7; ++j)
               sv[j] = valid && rem > j ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
             sv[7] = sr;
-            seg_scan8(sv, lane, first);
+            seg_scan8(sv, lane, first, span);
             if (valid && tail) {
 #pragma unroll
               for (int j = 0; j < 7; ++j)
@@ -835,13 +868,41 @@ HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const 
   }
 }
 
-// All steps of one world (state in the global arrays).
+// Copy one world's state between two views (group-parallel), status word included.
+template <int TPW>
+HD void copy_state(const WState& d, const WState& src, const WorldView& v, const Group<TPW>& g) {
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    d.q[i] = src.q[i];
+    d.qd[i] = src.qd[i];
+  }
+  for (int i = g.lane; i < 3 * v.na; i += TPW) {
+    d.ax[i] = src.ax[i];
+    d.av[i] = src.av[i];
+  }
+  for (int i = g.lane; i < v.nb; i += TPW) {
+    d.broken[i] = src.broken[i];
+    d.bcnt[i] = src.bcnt[i];
+    d.break_step[i] = src.break_step[i];
+  }
+  for (int i = g.lane; i < v.na; i += TPW) {
+    d.detached[i] = src.detached[i];
+    d.pcnt[i] = src.pcnt[i];
+    d.tcnt[i] = src.tcnt[i];
+    d.detach_step[i] = src.detach_step[i];
+  }
+  if (g.lane == 0) *d.status = *src.status;
+  g.sync();
+}
+
+// All steps of one world: its state is staged in the workspace for the whole rollout.
 template <int TPW>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
                   const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
-  const WState s = world_state(S, v, w);
+  const WState sg = world_state(S, v, w);
+  const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);
+  copy_state<TPW>(s, sg, v, g);
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
@@ -856,6 +917,7 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);
     g.sync();
   }
+  copy_state<TPW>(sg, s, v, g);
 }
 
 }  // namespace
