@@ -85,6 +85,34 @@ HD void snapshot(float* ws, const WsLayout& L, float* seg, const AdjLayout& A, i
   g.sync();
 }
 
+// What the reverse of one step reads from that step's forward workspace, saved during the
+// segment's replay so the step need not run again: joint origins and DOF axes, the solution
+// Delta and the apple data, the snapped flags, the factors, and qd at the step's end.
+HD long long step_record_words(int nb, int nv, int nm, int na) {
+  return 3LL * nb + 3LL * nv + nv + 10LL * na + nb + nm + nv;
+}
+
+template <int TPW>
+HD void record_part(float* rec, long long& o, float* src, int n, bool save, const Group<TPW>& g) {
+  for (int i = g.lane; i < n; i += TPW) {
+    if (save) rec[o + i] = src[i];
+    else src[i] = rec[o + i];
+  }
+  o += n;
+}
+
+template <int TPW>
+HD void step_record(float* ws, const WsLayout& L, const WState& s, float* wa, const AdjLayout& A,
+                    const WorldView& v, float* rec, bool save, const Group<TPW>& g) {
+  long long o = 0;
+  record_part<TPW>(rec, o, ws + L.X, 3 * v.nb + 3 * v.nv, save, g);  // X, then E
+  record_part<TPW>(rec, o, ws + L.r, v.nv + 10 * v.na, save, g);     // r, then AT
+  record_part<TPW>(rec, o, ws + L.SN, v.nb, save, g);
+  record_part<TPW>(rec, o, ws + L.M, v.nm, save, g);
+  record_part<TPW>(rec, o, save ? s.qd : wa + A.qd1, v.nv, save, g);
+  g.sync();
+}
+
 // Load checkpoint `slot` of the forward record into the private state (its world's ranges).
 template <int TPW>
 HD void load_ckpt(const StepArgs& a, const WorldView& v, const WState& s, int slot, const Group<TPW>& g) {
@@ -694,13 +722,18 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
 // Backward pass of one world over a recorded rollout.
 template <int TPW>
 // ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
-// seg: ckpt_every snapshots; each may be in shared or global memory (seg is always global).
+// seg: ckpt_every snapshots and step records (global memory); ws and wa may be in shared or
+// global memory. Each segment is replayed once, forward, saving every step's start state and
+// its record; then its steps are reversed last to first from those.
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
                        float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);  // the world's private state
+  // the segment buffer: ckpt_every snapshots, then ckpt_every step records
+  const long long recw = step_record_words(v.nb, v.nv, v.nm, v.na);
+  float* recs = seg + (long long)a.ckpt_every * A.snap;
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   const float dt = a.dt;
@@ -717,6 +750,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     for (int t = t0; t < t1; ++t) {
       snapshot(ws, L, seg, A, t - t0, true, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
+      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
     }
     if (sg == nseg - 1) {
       // the last record's tips at the final configuration
@@ -744,10 +778,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     }
     for (int t = t1 - 1; t >= t0; --t) {
       snapshot(ws, L, seg, A, t - t0, false, g);
-      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
-      for (int i = g.lane; i < v.nv; i += TPW) wa[A.qd1 + i] = s.qd[i];
-      g.sync();
-      snapshot(ws, L, seg, A, t - t0, false, g);
+      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, false, g);
       reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, g, t, gv);
       for (int i = g.lane; i < v.nv; i += TPW) {
         wa[A.qb1 + i] = wa[A.qb + i];

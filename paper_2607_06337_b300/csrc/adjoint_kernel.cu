@@ -90,8 +90,8 @@ cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes
 
 long long backward_adj_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).total; }
 
-long long backward_seg_floats(int nb, int nv, int na, int ckpt_every) {
-  return (long long)ckpt_every * AdjLayout::make(nb, nv, na).snap;
+long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every) {
+  return (long long)ckpt_every * (AdjLayout::make(nb, nv, na).snap + step_record_words(nb, nv, nm, na));
 }
 
 }  // namespace orchard

@@ -1037,7 +1037,7 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
 }
 
 namespace {
-// Backward launch plan of a class: threads per world as in the forward schedule (32..256);
+// Backward launch plan of a class: threads per world by the class's largest tree;
 // the forward step's temporaries in shared memory when they fit, the backward's and the
 // segment snapshots in global memory; one workspace slot per group that can be resident at
 // once (bounded by shared memory, 2048 threads and 16 groups per SM).
@@ -1050,11 +1050,12 @@ inline long long round16(long long f) { return (f + 15) / 16 * 16; }
 
 BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
   BackPlan p{};
-  p.tpw = std::max(32, std::min(ci.sched.threads_per_world, 256));
+  // threads per world by tree size (measured on B300 with 200-body trees: 256 beat 128)
+  p.tpw = ci.max_nb <= 96 ? 64 : 256;
   BackShape& sh = p.sh;
   sh.fwd_floats = round16(ci.ws_floats);
   sh.adj_floats = round16(backward_adj_floats(ci.max_nb, ci.max_nv, ci.max_na));
-  const long long seg = round16(backward_seg_floats(ci.max_nb, ci.max_nv, ci.max_na, ce));
+  const long long seg = round16(backward_seg_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na, ce));
   const long long lim = (long long)(kSmemLimit / 4);
   // measured on B300 (diff1024 trees): the forward step's temporaries alone in shared memory,
   // with more worlds resident per SM, beat keeping the backward's there too (one world per SM)

@@ -166,7 +166,7 @@ void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st,
                      const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
 cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 long long backward_adj_floats(int nb, int nv, int na);
-long long backward_seg_floats(int nb, int nv, int na, int ckpt_every);
+long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);
