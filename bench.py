@@ -140,17 +140,18 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(n_worlds):
-    """DRAM bytes per launch of the rollout kernel from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def measured_traffic(workload, n_worlds, sim_steps):
+    """DRAM bytes of one timed rollout (all size classes) from the committed ncu summary, if it
+    was taken on the current kernel source and the same workload (else None)."""
     path = os.path.join(ROOT, "profiles", "rollout_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("kernel_source_hash") != kernel_source_hash():
         return None
-    per_world_step = d.get("dram_bytes_per_world_step")
-    return None if per_world_step is None else per_world_step
+    if (d.get("workload"), d.get("worlds"), d.get("sim_steps")) != (workload, n_worlds, sim_steps):
+        return None
+    return d.get("dram_bytes_per_rollout")
 
 
 def cpu_baseline(forest, flags, seconds, sim_steps):
@@ -365,9 +366,11 @@ def run_ours(args):
         for k in range(args.steps):
             flush.fill_(k & 0xff)  # evict the L2 between timed rollouts
             reset()
+            torch.cuda.nvtx.range_push("bench_timed")  # lets a profiler select the timed rollouts
             e0[k].record(stream)
             sim.rollout(S)
             e1[k].record(stream)
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     launches = B.launch_count()
@@ -427,10 +430,10 @@ def run_ours(args):
     peak_tf = fp32_peak_tflops(sm_mhz)
     achieved_tf = flops / (ms_mean / 1e3) / 1e12
     hbm_bytes = costs.hbm_bytes_per_rollout(forest)
-    traffic_per_ws = measured_traffic(nw)
+    traffic = measured_traffic(args.workload, nw, S)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf,
-                "traffic": None if traffic_per_ws is None else traffic_per_ws * nw * S,
+                "traffic": traffic,
                 "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
                                f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
                 "flops_per_launch": flops}

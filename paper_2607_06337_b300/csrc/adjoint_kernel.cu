@@ -12,7 +12,7 @@ namespace orchard {
 namespace {
 
 template <int TPW>
-__global__ void __launch_bounds__(512) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
+__global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
                                                        BackShape sh) {
   extern __shared__ float smem[];
   __shared__ int frozen[16];

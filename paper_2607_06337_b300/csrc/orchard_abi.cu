@@ -1040,7 +1040,7 @@ namespace {
 // Backward launch plan of a class: threads per world by the class's largest tree;
 // the forward step's temporaries in shared memory when they fit, the backward's and the
 // segment snapshots in global memory; one workspace slot per group that can be resident at
-// once (bounded by shared memory, 2048 threads and 16 groups per SM).
+// once (bounded by shared memory, registers and 16 groups per SM).
 struct BackPlan {
   int tpw, gpb, blocks;
   size_t slots;
@@ -1069,12 +1069,13 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
     sh.global_floats = sh.fwd_floats + sh.adj_floats + seg;
   }
   sh.global_floats = (sh.global_floats + 63) / 64 * 64;
-  // groups per block: as many as share one block's shared memory (at most 512 threads)
-  p.gpb = sh.smem_floats > 0 ? (int)std::max<long long>(1, std::min<long long>(lim / sh.smem_floats, 512 / p.tpw))
-                             : 1;
+  // groups per block: as many as share one block's shared memory (at most kBackMaxThreads threads)
+  p.gpb = sh.smem_floats > 0
+              ? (int)std::max<long long>(1, std::min<long long>(lim / sh.smem_floats, kBackMaxThreads / p.tpw))
+              : 1;
   p.gpb = std::min(p.gpb, 16);
-  // resident groups per SM
-  long long per_sm = std::min<long long>(2048 / p.tpw, 16);
+  // resident groups per SM (the kernel is built for 128 registers per thread)
+  long long per_sm = std::min<long long>(std::min<long long>(2048, 65536 / 128) / p.tpw, 16);
   if (sh.smem_floats > 0) per_sm = std::min<long long>(per_sm, (long long)(kSmemLimit / 4) / sh.smem_floats);
   per_sm = std::max<long long>(per_sm, 1);
   const size_t worlds = (size_t)(ci.q_end - ci.q_begin);

@@ -162,6 +162,9 @@ struct BackShape {
   long long smem_floats;    // per group in shared memory
   long long global_floats;  // per slot of the workspace
 };
+// Threads per block of the backward kernel at most (two such blocks per SM: 128 registers per
+// thread, which the reverse sweep needs without spilling; measured faster on B300 than 512).
+constexpr int kBackMaxThreads = 256;
 void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
                      const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
 cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);

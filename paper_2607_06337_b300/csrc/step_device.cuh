@@ -232,15 +232,15 @@ HD void joint_gains(const WState& s, const StepArgs& a, int b, float4 P3, int t_
   *kd = (1.f + a.ramp_gain * ramp) * P3.w;
 }
 
-// Phase 1 for one body: kinematics, velocities, bias acceleration, own force, apple loads.
-HD void forward_body(const DevModel& m, const WState& s, const StepArgs& a,
-                                             const WorldView& v, const WsLayout& L, float* ws, int b,
-                                             int t_abs, f3 g) {
+// Phase 1a for one body (root to leaf, level by level): kinematics, velocities, bias
+// acceleration, snapped flag.
+HD void forward_kin(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L, float* ws, int b,
+                    f3 g) {
   const int gb = v.b0 + b;
   const int4 bi = m.bi[gb];
   const int p = bi.x;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const float4 P0 = m.bp0[gb], P1 = m.bp1[gb], P2 = m.bp2[gb], P3 = m.bp3[gb];
+  const float4 P0 = m.bp0[gb], P1 = m.bp1[gb];
   m3 Rp;
   f3 xp, wp, vp, alp, ap;
   if (p >= 0) {
@@ -283,6 +283,20 @@ HD void forward_body(const DevModel& m, const WState& s, const StepArgs& a,
   ws[L.SN + b] = snapped ? 1.f : 0.f;
   st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vin);
   st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
+}
+
+// Phase 1b for one body (all bodies at once, after 1a): spatial inertia, own Newton-Euler
+// force, apple loads.
+HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                      float* ws, int b, int t_abs, f3 g) {
+  const int gb = v.b0 + b;
+  const int4 bi = m.bi[gb];
+  const float4 P0 = m.bp0[gb], P2 = m.bp2[gb], P3 = m.bp3[gb];
+  const m3 R = ldm(ws + L.R + 9 * b);
+  const f3 xb = ld3(ws + L.X + 3 * b);
+  const f3 w = ld3(ws + L.V + 6 * b), vin = ld3(ws + L.V + 6 * b + 3);
+  const f3 al = ld3(ws + L.A + 6 * b), aa = ld3(ws + L.A + 6 * b + 3);
+  const bool snapped = ws[L.SN + b] != 0.f;
 
   // spatial inertia of the body about x_b
   const float mb = P0.w;
@@ -464,7 +478,8 @@ HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, c
   }
 }
 
-// Phase 5 for one body: finish the solve, update, velocities, apples, events.
+// Phase 5a for one body (root to leaf, level by level): finish the solve, update, velocities,
+// rupture test.
 HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
                                             const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs,
                                             unsigned, int* frozen) {
@@ -498,33 +513,6 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
   }
   st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vl);
 
-  const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
-  if (acount) {
-    for (int k = 0; k < acount; ++k) {
-      const int ai = afirst + k, ga = v.a0 + ai;
-      const float* at = ws + L.AT + 10 * ai;
-      const bool det = s.detached[ai] != 0;
-      const f3 rh = ld3(at + 6);
-      const f3 vh = det ? mk(0, 0, 0) : vl + cross(w, rh);
-      const f3 vn = ld3(at) + at[3] * vh;
-      // attached: u' = u + dt (v' - v_hang'); detached: x' = x + dt v'
-      const f3 xn = ld3(s.ax + 3 * ai) + dt * (vn - vh);
-      st3(s.av + 3 * ai, vn);
-      st3(s.ax + 3 * ai, xn);
-      bad |= !finite(xn.x) || !finite(xn.y) || !finite(xn.z);
-      if (!det) {
-        const float fdet = m.ap1[ga].z;
-        const int cp = at[5] > fdet ? s.pcnt[ai] + 1 : 0;
-        const int ct = at[4] > a.gamma * fdet ? s.tcnt[ai] + 1 : 0;
-        s.pcnt[ai] = cp;
-        s.tcnt[ai] = ct;
-        if (cp >= a.n_pull || ct >= a.n_tension) {
-          s.detached[ai] = 2;  // becomes a world position at the next step's kinematics
-          s.detach_step[ai] = t_abs;
-        }
-      }
-    }
-  }
   if (nd && !s.broken[b]) {
     const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
     const float mom = P3.z * sqrtf(th2);
@@ -538,6 +526,40 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
   if (bad) {
     atomic_or(s.status, 1u);
     *frozen = 1;  // every lane reads it after the group barrier that ends the sweep
+  }
+}
+
+// Phase 5b for one apple (all apples at once, after the level passes of 5a): the apple update
+// with its body's end-of-step velocity, and the detach tests.
+HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                     float* ws, int ai, int t_abs, int* frozen) {
+  const int ga = v.a0 + ai;
+  const int b = m.apple_body[ga];
+  const f3 w = ld3(ws + L.V + 6 * b), vl = ld3(ws + L.V + 6 * b + 3);
+  const float dt = a.dt;
+  const float* at = ws + L.AT + 10 * ai;
+  const bool det = s.detached[ai] != 0;
+  const f3 rh = ld3(at + 6);
+  const f3 vh = det ? mk(0, 0, 0) : vl + cross(w, rh);
+  const f3 vn = ld3(at) + at[3] * vh;
+  // attached: u' = u + dt (v' - v_hang'); detached: x' = x + dt v'
+  const f3 xn = ld3(s.ax + 3 * ai) + dt * (vn - vh);
+  st3(s.av + 3 * ai, vn);
+  st3(s.ax + 3 * ai, xn);
+  if (!det) {
+    const float fdet = m.ap1[ga].z;
+    const int cp = at[5] > fdet ? s.pcnt[ai] + 1 : 0;
+    const int ct = at[4] > a.gamma * fdet ? s.tcnt[ai] + 1 : 0;
+    s.pcnt[ai] = cp;
+    s.tcnt[ai] = ct;
+    if (cp >= a.n_pull || ct >= a.n_tension) {
+      s.detached[ai] = 2;  // becomes a world position at the next step's kinematics
+      s.detach_step[ai] = t_abs;
+    }
+  }
+  if (!finite(xn.x) || !finite(xn.y) || !finite(xn.z) || !finite(vn.x) || !finite(vn.y) || !finite(vn.z)) {
+    atomic_or(s.status, 1u);
+    *frozen = 1;  // every lane reads it after the group barrier that ends the pass
   }
 }
 
@@ -824,9 +846,11 @@ HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const 
   // 1. root-to-leaf: kinematics, velocities, own forces, apple loads
   for (int l = 0; l < v.nL; ++l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) forward_body(m, s, a, v, L, ws, b, t_abs, gv);
+    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(m, s, v, L, ws, b, gv);
     g.sync();
   }
+  for (int b = g.lane; b < v.nb; b += TPW) forward_force(m, s, a, v, L, ws, b, t_abs, gv);
+  g.sync();
   if (tip_slot >= 0) record_tips(m, a, v, L, ws, tip_slot, g);
   // 2. leaf-to-root: forces and composite inertias, right-hand side
   for (int l = v.nL - 1; l >= 0; --l) {
@@ -864,6 +888,10 @@ HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const 
   for (int l = 0; l < v.nL; ++l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) update_body(m, s, a, v, L, ws, b, t_abs, 0u, g.flag);
+    g.sync();
+  }
+  if (v.na > 0) {
+    for (int ai = g.lane; ai < v.na; ai += TPW) update_apple(m, s, a, v, L, ws, ai, t_abs, g.flag);
     g.sync();
   }
 }
