@@ -208,7 +208,8 @@ ot_status ot_ckpt_bytes(const ot_model* model, int32_t n_steps, int32_t ckpt_eve
 
 /* n_steps steps from absolute step index step0: one persistent launch per size class over a
  * cost-sorted work queue (each group of threads pops a world and runs all its steps),
- * captured once into a CUDA graph per (n_steps, record layout) and replayed. */
+ * captured once into a CUDA graph per (n_steps, record layout, schedules) with the classes as
+ * independent branches (they overlap on the GPU), and replayed on `stream`. */
 ot_status ot_rollout(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
                      const ot_force_schedule* pulls, const ot_record* record, void* stream);
 

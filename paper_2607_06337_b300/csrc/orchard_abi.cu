@@ -413,9 +413,17 @@ struct ot_model {
     int kernels = 0;
   };
   std::vector<GraphEntry> graphs;
+  // one stream per size class: a captured rollout forks the classes onto them so their launches
+  // are independent graph branches that overlap on the GPU
+  std::vector<cudaStream_t> class_streams;
+  std::vector<cudaEvent_t> join_events;
+  cudaEvent_t fork_event = nullptr;
   ~ot_model() {
     for (auto& g : graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaStream_t c : class_streams) cudaStreamDestroy(c);
+    for (cudaEvent_t e : join_events) cudaEventDestroy(e);
+    if (fork_event) cudaEventDestroy(fork_event);
     if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
@@ -893,11 +901,33 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
     ot_status r = class_shape(m, k, &shapes[k]);
     if (r != OT_OK) return r;
   }
+  const int nk = (int)m->P.classes.size();
+  if (!m->fork_event) OT_CUDA(cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming));
+  while ((int)m->class_streams.size() < nk) {
+    cudaStream_t c = nullptr;
+    cudaEvent_t ev = nullptr;
+    OT_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    m->class_streams.push_back(c);
+    OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    m->join_events.push_back(ev);
+  }
   OT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   const long long before = g_launches.load();
   ot_status rst = OT_OK;
-  for (int k = 0; k < (int)m->P.classes.size() && rst == OT_OK; ++k)
-    rst = launch_class_shaped(m, s, k, a, shapes[k], cs);
+  cudaError_t ce = cudaEventRecord(m->fork_event, cs);
+  // largest classes first: they hold the longest-running worlds
+  int forked = 0;
+  for (int k = nk - 1; k >= 0 && ce == cudaSuccess; --k) {
+    cudaStream_t sk = m->class_streams[k];
+    ce = cudaStreamWaitEvent(sk, m->fork_event, 0);
+    if (ce != cudaSuccess) break;
+    ++forked;
+    if (rst == OT_OK) rst = launch_class_shaped(m, s, k, a, shapes[k], sk);
+    ce = cudaEventRecord(m->join_events[k], sk);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cs, m->join_events[k], 0);
+  }
+  (void)forked;
+  if (ce != cudaSuccess && rst == OT_OK) rst = cuda_fail(ce);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(cs, &graph);
   const int kernels = (int)(g_launches.load() - before);
@@ -1119,23 +1149,48 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
   BackArgs ba{dL_dtips, grads->dk, grads->dkd, grads->dq0, grads->dqd0};
   cudaStream_t cs = (cudaStream_t)stream;
   float* work = (float*)workspace;
-  for (int k = 0; k < (int)m->P.classes.size(); ++k) {
+  // the classes run concurrently: each on its own stream, forked from and joined back to `stream`
+  const int nk = (int)m->P.classes.size();
+  if (!m->fork_event) OT_CUDA(cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming));
+  while ((int)m->class_streams.size() < nk) {
+    cudaStream_t c = nullptr;
+    cudaEvent_t ev = nullptr;
+    OT_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    m->class_streams.push_back(c);
+    OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    m->join_events.push_back(ev);
+  }
+  std::vector<float*> works(nk);
+  for (int k = 0; k < nk; ++k) {
+    works[k] = work;
+    const BackPlan p = back_plan(m, m->P.classes[k], rec->ckpt_every);
+    work += p.slots * (size_t)p.sh.global_floats;
+  }
+  OT_CUDA(cudaEventRecord(m->fork_event, cs));
+  ot_status result = OT_OK;
+  for (int k = nk - 1; k >= 0; --k) {
     const ClassInfo& ci = m->P.classes[k];
     const BackPlan p = back_plan(m, ci, rec->ckpt_every);
+    cudaStream_t sk = m->class_streams[k];
+    OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
     int bps = 0;
-    OT_CUDA(backward_attributes(p.tpw, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps));
+    cudaError_t e = backward_attributes(p.tpw, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
     StepArgs b = a;
     b.q_begin = ci.q_begin;
     b.q_end = ci.q_end;
     b.q_counter = s->q_counters + k;
-    OT_CUDA(cudaMemsetAsync(b.q_counter, 0, sizeof(int), cs));
-    if (p.blocks > 0) {
-      launch_backward(p.tpw, p.gpb, p.blocks, cs, m->dev, b, ba, work, p.sh);
-      OT_CUDA(cudaGetLastError());
-      g_launches += 1;
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.q_counter, 0, sizeof(int), sk);
+    if (e == cudaSuccess && p.blocks > 0) {
+      launch_backward(p.tpw, p.gpb, p.blocks, sk, m->dev, b, ba, works[k], p.sh);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) g_launches += 1;
     }
-    work += p.slots * (size_t)p.sh.global_floats;
+    if (e != cudaSuccess && result == OT_OK) result = cuda_fail(e);
+    // always join, so `stream` waits for whatever was enqueued
+    OT_CUDA(cudaEventRecord(m->join_events[k], sk));
+    OT_CUDA(cudaStreamWaitEvent(cs, m->join_events[k], 0));
   }
+  if (result != OT_OK) return result;
   return OT_OK;
 }
 
