@@ -55,8 +55,11 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=24.0)
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adj-workload", default="diff1024", help="diff1024 (default) or stress8192")
+    p.add_argument("--sweep", action="store_true",
+                   help="add a world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
     p.add_argument("--adj-worlds", type=int, default=None)
-    p.add_argument("--adj-steps", type=int, default=200)
+    p.add_argument("--adj-steps", type=int, default=None, help="default: the workload's step count")
     p.add_argument("--adj-ckpt", type=int, default=20)
     return p.parse_args()
 
@@ -228,11 +231,12 @@ def fwd_adjoint(args, dev, rank, ws):
     from paper_2607_06337_b300 import costs
     from paper_2607_06337_b300 import inputs as I
     from paper_2607_06337_b300 import orchard as B
-    name = I.DIFF
+    name = args.adj_workload
     nw = args.adj_worlds or I.WORKLOAD_WORLDS[name]
-    fl = I.Flags()
+    # the stress workload inverts the pivots of twigs under 5 mm in FP64
+    fl = I.Flags(fp64_twig_diam=0.005 if name == I.STRESS else 0.0)
     f = I.make_forest(name, n_worlds=nw, sweep=rank)
-    n, ce = args.adj_steps, args.adj_ckpt
+    n, ce = args.adj_steps or I.WORKLOAD_STEPS[name], args.adj_ckpt
     sim = B.Simulator(f, fl, device=dev)
     stream = torch.cuda.current_stream()
     dev_in = [torch.as_tensor(np.ascontiguousarray(a, np.float32).reshape(-1), device=dev)
@@ -302,9 +306,10 @@ def fwd_adjoint(args, dev, rank, ws):
     fwd_fl = costs.flops_per_step(f) * n
     bwd_fl = costs.adjoint_flops_per_step(f) * n
     g_ok = all(bool(torch.isfinite(g).all()) for g in grads)
+    desc = (f"{nw} trees x 200 segment bodies x 30 apples, {n} steps, fixed 5 N pull" if name == I.DIFF else
+            f"{nw} mixed trees (50/400/2000 bodies), {n} steps, FP64 pivots on twigs under 5 mm")
     return {
-        "workload": f"{nw} trees x 200 segment bodies x 30 apples, {n} steps, fixed 5 N pull, "
-                    f"checkpoints every {ce} steps, tip-tracking loss",
+        "workload": f"{name}: {desc}, checkpoints every {ce} steps, tip-tracking loss",
         "value": ws * bodies * n / (tot_ms / 1e3), "unit": UNIT,
         "ms_per_step": tot_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
         "fwd_only_value": ws * bodies * n / (fwd_ms / 1e3),
@@ -316,6 +321,57 @@ def fwd_adjoint(args, dev, rank, ws):
                              "unit": "TFLOP/s", "frac": fwd_fl / (fwd_ms / 1e3) / 1e12 / peak_tf},
         "l2": "flushed (256 MB write) before every timed step",
     }
+
+
+def world_sweep(args, dev):
+    """Batched (persistent, graph, autotuned) and plain (one launch per world per step) forward
+    body-steps/s at 1024..65536 worlds of the sweep16384 trees (300 bodies, 60 apples). The
+    worlds are the first N of one 65536-world batch (per-world seeds: fresh draws of the same
+    distribution). Batched: 100 steps per timed rollout; plain: 2 steps."""
+    import torch
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+    counts = [1024, 2048, 4096, 8192, 16384, 32768, 65536]
+    fl = I.Flags()
+    big = I.make_forest(I.SWEEP, n_worlds=max(counts))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    out = []
+    for n in counts:
+        f = big.subset(range(n)) if n < big.n_worlds else big
+        sim = B.Simulator(f, fl, device=dev)
+        sim.autotune(n_steps=10)
+        bodies = costs.body_count(f)
+        steps = 100
+        sim.reset()
+        sim.rollout(steps)
+        ms = []
+        for k in range(2):
+            flush.fill_(k)
+            sim.reset()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.rollout(steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        batched = bodies * steps / (min(ms) / 1e3)
+        sim.reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.rollout_plain(2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain = bodies * 2 / (a.elapsed_time(b) / 1e3)
+        out.append({"worlds": n, "batched": batched, "plain": plain, "batched_over_plain": batched / plain})
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    return {"workload": "sweep16384 trees (300 bodies, 60 apples), first N of 65536", "unit": UNIT,
+            "points": out}
 
 
 def run_ours(args):
@@ -441,6 +497,8 @@ def run_ours(args):
            "unit": "GB/s", "bytes_per_launch": hbm_bytes}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
 
+    sweep = world_sweep(args, dev) if args.sweep and ws == 1 else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(forest, fl, args.cpu_seconds, S)
@@ -462,6 +520,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "plain": plain,
             "fwd_adj": adj,
+            "sweep": sweep,
             "clocks": clocks,
             "frozen_worlds": int((status & 1).sum()),
             "wall_s": wall,

@@ -89,6 +89,7 @@ typedef struct ot_tree_desc {
   const int32_t* tip_body;   /* [nt] world-local body of each recorded tip point */
   const double* tip_local;   /* [nt][3] tip point in the body frame */
   const double* gravity;     /* [W][3] */
+  const double* diam;        /* [nb] segment diameter (m); may be NULL unless fp64_twig_diam > 0 */
 } ot_tree_desc;
 
 /* Switchable readings of the model (defaults in parentheses). */
@@ -102,6 +103,8 @@ typedef struct ot_model_flags {
   double clamp_factor;           /* (1.2) reaction clamp = clamp_factor * f_detach */
   double break_ramp_s;           /* (1.5) a broken joint keeps a friction surrogate: a viscous */
   double break_ramp_factor;      /* (5.0) damper ramping from kd to factor * kd over ramp_s (s) */
+  double fp64_twig_diam;         /* (0) joints of segments thinner than this (m) invert their
+                                    factorisation pivot block in FP64; 0: none */
 } ot_model_flags;
 
 /* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */

@@ -530,11 +530,11 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
         if (valid) {
           info = m.bl_info[v.b0 + idx];
           const Pivot P = pivot_of(M, info.y, info.z, info.w);
-          const float yx = y[info.x], yy = info.w == 2 ? y[info.x + 1] : 0.f;
+          const float yx = y[info.x], yy = (info.w & 3) == 2 ? y[info.x + 1] : 0.f;
           zx = P.p00 * yx + P.p01 * yy;  // P^-1 y of this joint
           zy = P.p01 * yx + P.p11 * yy;
         }
-        const bool two = info.w == 2;
+        const bool two = (info.w & 3) == 2;
         const float* rowx = M + info.y;
         const float* rowy = M + (two ? info.z + 1 : info.y);
         const int2* fp = ft + (idx - lo);
@@ -564,7 +564,7 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
     const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
     for (int idx = lo; idx < hi; ++idx) {
       const int4 info = m.bl_info[v.b0 + idx];
-      const bool two = info.w == 2;
+      const bool two = (info.w & 3) == 2;
       const Pivot P = pivot_of(M, info.y, info.z, info.w);
       const float yx = y[info.x], yy = two ? y[info.x + 1] : 0.f;
       const float zx = P.p00 * yx + P.p01 * yy, zy = P.p01 * yx + P.p11 * yy;

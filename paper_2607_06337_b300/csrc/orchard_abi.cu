@@ -113,7 +113,7 @@ ot_schedule default_schedule(long long ws_floats, int max_nb) {
   return s;
 }
 
-ot_status pack(const ot_tree_desc* d, Packed& P) {
+ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   if (!d || d->n_worlds < 0 || !d->body_off || !d->apple_off || !d->tip_off) return OT_EINVAL;
   const int W = d->n_worlds;
   P.W = W;
@@ -130,6 +130,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     return OT_EINVAL;
   if (NT > 0 && (!d->tip_body || !d->tip_local)) return OT_EINVAL;
   if (W > 0 && !d->gravity) return OT_EINVAL;
+  if (!(fp64_twig_diam >= 0) || !std::isfinite(fp64_twig_diam)) return OT_EINVAL;
+  if (fp64_twig_diam > 0 && NB > 0 && !d->diam) return OT_EINVAL;
   // finiteness
   if (NB > 0 && !(finite_all(d->jpos, 3 * (size_t)NB) && finite_all(d->qrel, 4 * (size_t)NB) &&
                   finite_all(d->com, 3 * (size_t)NB) && finite_all(d->mass, NB) &&
@@ -141,6 +143,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     return OT_ENONFINITE;
   if (NT > 0 && !finite_all(d->tip_local, 3 * (size_t)NT)) return OT_ENONFINITE;
   if (W > 0 && !finite_all(d->gravity, 3 * (size_t)W)) return OT_ENONFINITE;
+  if (fp64_twig_diam > 0 && NB > 0 && !finite_all(d->diam, NB)) return OT_ENONFINITE;
   for (int b = 0; b < NB; ++b)
     if (!(d->mass[b] > 0)) return OT_ENONFINITE;
   for (int a = 0; a < NA; ++a)
@@ -246,7 +249,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
     std::vector<int> rowstart(nv);
     for (int i = 0; i < nv; ++i) {
       rowstart[i] = row;
-      P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], 0));
+      const bool f64 = fp64_twig_diam > 0 && d->diam[b0 + dbody[i]] < fp64_twig_diam;
+      P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], f64 ? 1 : 0));
       int j = i;
       for (int c = 0; c <= ddep[i]; ++c) {
         P.anc.push_back((unsigned)j | ((unsigned)dbody[j] << 16));
@@ -285,7 +289,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P) {
         for (int b : pre)
           if (nd[b] > 0 && ddep[dof0[b]] == l) {
             const int i = dof0[b];
-            P.bl_info[b0 + pos] = make_int4(i, rowstart[i], nd[b] == 2 ? rowstart[i + 1] : -1, nd[b]);
+            const bool f64 = fp64_twig_diam > 0 && d->diam[b0 + b] < fp64_twig_diam;
+            P.bl_info[b0 + pos] = make_int4(i, rowstart[i], nd[b] == 2 ? rowstart[i + 1] : -1, nd[b] | (f64 ? 16 : 0));
             first.push_back(i);
             ++pos;
           }
@@ -647,7 +652,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
       !(flags->gamma_tension > 0) || !(flags->break_ramp_s >= 0) || !(flags->break_ramp_factor >= 0))
     return OT_EINVAL;
   ot_model* m = new ot_model();
-  ot_status st = pack(desc, m->P);
+  ot_status st = pack(desc, m->P, flags->fp64_twig_diam);
   if (st != OT_OK) {
     delete m;
     return st;

@@ -27,7 +27,8 @@ struct DevModel {
   const float4* bp2;     // com in the body frame (xyz), Ixx (w)
   const float4* bp3;     // Iyy, Izz, k, kd
   const float4* bp4;     // armature, m_max, -, -
-  const int4* dinfo;     // per DOF: row start (world-local), body, depth d_i, -
+  const int4* dinfo;     // per DOF: row start (world-local), body, depth d_i, 1 if the joint's
+                         // pivot block is inverted in FP64
   const unsigned* anc;   // per row entry c of DOF i: its c-th ancestor DOF j | (body of j) << 16
   const int* bl_off;     // [W+1] start of the world's factorisation level boundaries in bl_bound
   const int* bl_bound;   // world-local level position of each level's first body (+ end). A level
@@ -35,7 +36,7 @@ struct DevModel {
                          // depth-first preorder
   const int4* bl_info;   // per level position (world-local, at the world's body offset): the
                          // body's first DOF, its row start, the second DOF's row start (-1 for a
-                         // one-DOF joint), the DOF count
+                         // one-DOF joint), the DOF count | 16 if the pivot is inverted in FP64
   const int* bl_fbase;   // parallel to bl_bound: each level's first entry in the fac_tgt block
   const int* fac_off;    // [W+1] start of the world's fac_tgt block
   const int2* fac_tgt;   // per level l, ancestor distance c (1..l), position p in the level:

@@ -419,17 +419,25 @@ HD void backward_body(const DevModel& m, const WState& s, const StepArgs& a,
 struct Pivot {
   float p00, p01, p11;  // P^-1 (symmetric)
 };
+// nd: the joint's DOF count, | 16 to invert the block in FP64 (the thinnest twigs).
 HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
   Pivot P;
   const float a = M[rowx];
-  if (nd == 2) {
+  if ((nd & 3) == 2) {
     const float d = M[rowy], b = M[rowy + 1];
-    const float inv = 1.f / (a * d - b * b);
-    P.p00 = d * inv;
-    P.p01 = -b * inv;
-    P.p11 = a * inv;
+    if (nd & 16) {
+      const double inv = 1.0 / ((double)a * d - (double)b * b);
+      P.p00 = (float)(d * inv);
+      P.p01 = (float)(-b * inv);
+      P.p11 = (float)(a * inv);
+    } else {
+      const float inv = 1.f / (a * d - b * b);
+      P.p00 = d * inv;
+      P.p01 = -b * inv;
+      P.p11 = a * inv;
+    }
   } else {
-    P.p00 = 1.f / a;
+    P.p00 = (nd & 16) ? (float)(1.0 / (double)a) : 1.f / a;
     P.p01 = 0.f;
     P.p11 = 0.f;
   }
@@ -440,7 +448,7 @@ HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
 HD void pivot_scale(const float* M, int4 info, float* y) {
   const Pivot P = pivot_of(M, info.y, info.z, info.w);
   const float rx = y[info.x];
-  if (info.w == 2) {
+  if ((info.w & 3) == 2) {
     const float ry = y[info.x + 1];
     y[info.x] = P.p00 * rx + P.p01 * ry;
     y[info.x + 1] = P.p01 * rx + P.p11 * ry;
@@ -468,13 +476,13 @@ HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, c
       sx = fmaf(rowx[c], xa, sx);
       sy = fmaf(rowy[c], xa, sy);
     }
-    const Pivot P = pivot_of(M, dx.x, ry, 2);
+    const Pivot P = pivot_of(M, dx.x, ry, 2 | (dx.w ? 16 : 0));
     y[dof0] -= P.p00 * sx + P.p01 * sy;
     y[dof0 + 1] -= P.p01 * sx + P.p11 * sy;
   } else {
 #pragma unroll 4
     for (int c = 1; c <= dx.z; ++c) sx = fmaf(rowx[c], y[an[c] & 0xffffu], sx);
-    y[dof0] -= sx / rowx[0];
+    y[dof0] -= sx * pivot_of(M, dx.x, -1, 1 | (dx.w ? 16 : 0)).p00;
   }
 }
 
@@ -743,9 +751,9 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         if (valid) {
           P = pivot_of(M, info.y, info.z, info.w);
           rx = r[info.x];
-          if (info.w == 2) ry = r[info.x + 1];
+          if ((info.w & 3) == 2) ry = r[info.x + 1];
         }
-        const bool two = info.w == 2;
+        const bool two = (info.w & 3) == 2;
         const float* rowx = M + info.y;
         const float* rowy = M + (two ? info.z + 1 : info.y);  // rowy[c]: entry of anc_c in the y' row
         const int2* fp = ft + (idx - lo);
@@ -819,7 +827,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
     const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
     for (int idx = lo; idx < hi; ++idx) {
       const int4 info = m.bl_info[v.b0 + idx];
-      const bool two = info.w == 2;
+      const bool two = (info.w & 3) == 2;
       const Pivot P = pivot_of(M, info.y, info.z, info.w);
       const float rx = r[info.x], ry = two ? r[info.x + 1] : 0.f;
       const float* rowx = M + info.y;

@@ -47,14 +47,15 @@ class TreeDesc(C.Structure):
                 ("k", _f64p), ("kd", _f64p), ("armature", _f64p), ("m_max", _f64p),
                 ("apple_body", _i32p), ("hang_local", _f64p), ("apple_mass", _f64p), ("k_s", _f64p),
                 ("c_s", _f64p), ("f_detach", _f64p),
-                ("tip_body", _i32p), ("tip_local", _f64p), ("gravity", _f64p)]
+                ("tip_body", _i32p), ("tip_local", _f64p), ("gravity", _f64p), ("diam", _f64p)]
 
 
 class ModelFlags(C.Structure):
     _fields_ = [("alpha_implicit_spring", C.c_int32), ("tether_implicit", C.c_int32),
                 ("n_break", C.c_int32), ("n_pull", C.c_int32), ("n_tension", C.c_int32),
                 ("gamma_tension", C.c_double), ("clamp_factor", C.c_double),
-                ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double)]
+                ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double),
+                ("fp64_twig_diam", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -175,13 +176,14 @@ def make_desc(forest, keep: _Keep) -> TreeDesc:
         keep.f64(f.mass), keep.f64(f.inertia), keep.f64(f.k), keep.f64(f.kd), keep.f64(f.armature),
         keep.f64(f.m_max), keep.i32(f.apple_body), keep.f64(f.hang_local), keep.f64(f.apple_mass),
         keep.f64(f.k_s), keep.f64(f.c_s), keep.f64(f.f_detach), keep.i32(f.tip_body), keep.f64(f.tip_local),
-        keep.f64(f.gravity))
+        keep.f64(f.gravity), keep.f64(f.diam) if getattr(f, "diam", None) is not None else None)
 
 
 def make_flags(flags) -> ModelFlags:
     return ModelFlags(int(flags.alpha_implicit_spring), int(flags.tether_implicit), int(flags.n_break),
                       int(flags.n_pull), int(flags.n_tension), float(flags.gamma_tension), float(flags.clamp_factor),
-                      float(flags.break_ramp_s), float(flags.break_ramp_factor))
+                      float(flags.break_ramp_s), float(flags.break_ramp_factor),
+                      float(getattr(flags, "fp64_twig_diam", 0.0)))
 
 
 # ------------------------------------------------------------------------------------------

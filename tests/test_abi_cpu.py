@@ -113,6 +113,15 @@ def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
     bad = orch.make_flags(I.Flags(n_break=0))
     assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(bad), C.c_void_p(256), 1 << 20, None,
                                            C.byref(h)) == orch.OT_EINVAL
+    # FP64 twig pivots asked for without diameters, or with a bad threshold
+    twig = orch.make_flags(I.Flags(fp64_twig_diam=0.005))
+    d_nodiam = orch.make_desc(f, keep)
+    d_nodiam.diam = None
+    assert orch.lib().ot_tree_model_upload(C.byref(d_nodiam), C.byref(twig), C.c_void_p(256), 1 << 20, None,
+                                           C.byref(h)) == orch.OT_EINVAL
+    neg = orch.make_flags(I.Flags(fp64_twig_diam=-1.0))
+    assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(neg), C.c_void_p(256), 1 << 20, None,
+                                           C.byref(h)) == orch.OT_EINVAL
     assert h.value is None
 
 

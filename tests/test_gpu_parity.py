@@ -89,15 +89,21 @@ def test_tip_record_matches_oracle():
     assert err < 1e-5, err
 
 
-def test_stress_classes_including_global_workspace():
-    """50 / 400 / 2000-body worlds (the 2000-body class runs with its workspace in global memory)."""
+@pytest.mark.parametrize("twig", [0.0, 0.005])
+def test_stress_classes_including_global_workspace(twig):
+    """50 / 400 / 2000-body worlds (the 2000-body class runs with its workspace in global memory),
+    with FP32 pivots throughout and with FP64 pivots on the joints of twigs under 5 mm (the
+    stress workload's setting); the oracle is FP64 either way."""
     f = I.make_forest(I.STRESS, worlds=[0, 4096, 8000])  # one world per size class
     assert sorted(np.diff(f.body_off)) == [50, 400, 2000]
-    fl = I.Flags()
+    if twig:
+        assert (f.diam < twig).sum() > 100  # the setting reaches many joints
+    fl = I.Flags(fp64_twig_diam=twig)
     g = _run(f, fl, 150)
     st, rec = O.rollout(f, fl, 150, near_eps=PAR.NEAR)
     rep = PAR.compare(f, fl, g, st, rec["near"])
     PAR.assert_parity(rep)
+    print("stress q-error / gate per world:", [round(r["ratio"], 4) for r in rep], "twig", twig)
 
 
 def test_edge_cases_single_body_and_chain():
