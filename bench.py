@@ -182,9 +182,17 @@ def cpu_baseline(forest, flags, seconds, sim_steps):
             break
         n_w = int(min(forest.n_worlds, max(n_w + 1, n_w * 1.1 * seconds / max(dt, 1e-3))))
     bs = costs.body_count(sub) * steps / dt
+    # one thread on a quarter of one thread's share of that sample
+    n1 = max(1, n_w // (4 * cores))
+    sub1 = sample(n1)
+    t = time.perf_counter()
+    O.rollout(sub1, flags, steps, n_threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_w} of {forest.n_worlds} worlds stratified by size x {steps} steps "
-                      f"(FP64, {cores} threads), {dt:.1f} s"}
+                      f"(FP64, {cores} threads), {dt:.1f} s",
+            "value_1core": costs.body_count(sub1) * steps / dt1,
+            "sample_1core": f"{n1} worlds x {steps} steps on one thread, {dt1:.1f} s"}
 
 
 def run_reference(args):

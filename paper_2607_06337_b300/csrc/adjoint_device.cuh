@@ -509,9 +509,10 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
 
 // A solve with the step's factors (see Pivot): L^T sweep leaf to root by factorisation level,
 // the scaling z = P^-1 y, and the L sweep root to leaf by body level; y <- H^-1 y, in place.
+// With lsweep false it stops after the scaling (the caller does the L sweep, joint by joint).
 template <int TPW>
 HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, float* y,
-                       const Group<TPW>& g) {
+                       const Group<TPW>& g, bool lsweep = true) {
   const float* M = ws + L.M;
 #ifdef __CUDA_ARCH__
   constexpr int NW = TPW / 32;
@@ -578,6 +579,7 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
     for (int idx = lo; idx < hi; ++idx) pivot_scale(M, m.bl_info[v.b0 + idx], y);
   }
 #endif
+  if (!lsweep) return;
   // L sweep, root to leaf by body level
   for (int l = 0; l < v.nL; ++l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
@@ -632,6 +634,34 @@ HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, 
 namespace orchard {
 namespace {
 
+// Springs and dampers of one joint (the diagonal terms of r and H): their part of the q and qd
+// cotangents, and the gains' gradients (one writer per joint).
+HD void spring_joint(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba, const WorldView& v,
+                     const AdjLayout& A, float* wa, int b, int t_abs) {
+  const int gb = v.b0 + b;
+  const int4 bi = m.bi[gb];
+  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+  if (nd == 0) return;
+  const float dt = a.dt;
+  const float4 P3 = m.bp3[gb];
+  float k, kd;
+  joint_gains(s, a, b, P3, t_abs, &k, &kd);
+  const float adt = a.alpha ? dt : 0.f;
+  float sk = 0.f, skd = 0.f;
+  for (int j = 0; j < nd; ++j) {
+    const int i = dof0 + j;
+    const float lam = wa[A.lam + i], q1 = wa[A.qd1 + i];
+    wa[A.qb + i] += -dt * k * lam;
+    wa[A.qdb + i] += -dt * (adt * k + kd) * lam;
+    sk += lam * (s.q[i] + adt * q1);
+    skd += lam * q1;
+  }
+  const float kfac = s.broken[b] ? 0.f : 1.f;
+  const float kdfac = P3.w != 0.f ? kd / P3.w : 0.f;
+  if (ba.dk) ba.dk[gb] += -dt * kfac * sk;
+  if (ba.dkd) ba.dkd[gb] += -dt * kdfac * skd;
+}
+
 // Cotangents of one step (t) of one world: the private state holds the step's start state,
 // the forward workspace holds that step's recomputed forward (factors, Delta, apple data), and
 // A.qb1 / qdb1 / ub1 / vb1 hold the cotangents of its end state. Leaves the cotangents of its
@@ -670,39 +700,17 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   hang_load_sweep<TPW>(m, s, v, L, A, ws, wa, wa + A.lam, g);  // qd'-bar += J_h^T vh-bar
   for (int i = g.lane; i < v.nv; i += TPW) wa[A.qdb + i] = wa[A.lam + i];  // qd' = qd + Delta
   g.sync();
-  solve_factored<TPW>(m, v, L, ws, wa + A.lam, g);  // lambda = H^-1 Delta-bar
-  // springs and dampers (diagonal terms of r and H)
-  for (int i = g.lane; i < v.nv; i += TPW) {
-    const int b = m.dinfo[v.d0 + i].y;
-    const int gb = v.b0 + b;
-    const float4 P3 = m.bp3[gb];
-    float k, kd;
-    joint_gains(s, a, b, P3, t_abs, &k, &kd);
-    const float lam = wa[A.lam + i];
-    const float adt = a.alpha ? dt : 0.f;
-    wa[A.qb + i] += -dt * k * lam;
-    wa[A.qdb + i] += -dt * (adt * k + kd) * lam;
-    const float kfac = s.broken[b] ? 0.f : 1.f;
-    const float kdfac = P3.w != 0.f ? kd / P3.w : 0.f;
-    // one writer per joint: the joint's first DOF adds both DOFs' terms
-    const int dof0 = m.bi[gb].y & 0x0fffffff, nd = (unsigned)m.bi[gb].y >> 28;
-    if (i == dof0) {
-      float sk = 0.f, skd = 0.f;
-      for (int j = 0; j < nd; ++j) {
-        const float lj = wa[A.lam + dof0 + j], qj = s.q[dof0 + j], q1j = wa[A.qd1 + dof0 + j];
-        sk += lj * (qj + adt * q1j);
-        skd += lj * q1j;
-      }
-      if (ba.dk) ba.dk[gb] += -dt * kfac * sk;
-      if (ba.dkd) ba.dkd[gb] += -dt * kdfac * skd;
-    }
-  }
-  g.sync();
-  // tape at the step start, then the reverse sweep
+  solve_factored<TPW>(m, v, L, ws, wa + A.lam, g, false);  // lambda = H^-1 Delta-bar, up to the L sweep
+  // root to leaf, joint by joint: the L sweep of lambda, the spring and damper terms, and the
+  // tape at the step start (which needs the joint's final lambda)
   for (int l = 0; l < v.nL; ++l) {
     const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW)
+    for (int b = lo + g.lane; b < hi; b += TPW) {
+      const int4 bi = m.bi[v.b0 + b];
+      lsweep_joint(m, v, L, ws, wa + A.lam, bi.y & 0x0fffffff, (unsigned)bi.y >> 28);
+      spring_joint(m, s, a, ba, v, A, wa, b, t_abs);
       tape_body(m, s, v, A, wa, ws + L.r, 1.f / dt, wa + A.lam, wa + A.qd1, b, gv);
+    }
     g.sync();
   }
   RevArgs ra;

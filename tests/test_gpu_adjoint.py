@@ -233,3 +233,25 @@ def test_full_gradient_against_the_oracle_reverse_mode():
             assert nrm > 0
             assert np.linalg.norm(got - r) <= 1e-3 * nrm, f"world {w} {name}: normwise {np.linalg.norm(got - r) / nrm:.2e}"
             assert np.abs(got - r).max() <= 2e-3 * np.abs(r).max(), f"world {w} {name}"
+
+
+@pytest.mark.parametrize("world,n,per_kind", [(0, 60, 4), (4096, 60, 4), (8000, 30, 2)])
+def test_adjoint_stress_size_classes(world, n, per_kind):
+    """One world per size class of the stress workload (50, 400 and 2000 bodies), with FP64
+    pivots on twigs under 5 mm, against the oracle's complex-step derivative (1 cm target).
+    Per kind of coordinate the error must stay within 2e-3 of the largest sampled entry (the
+    serial FP32 evaluation of the same arithmetic: at most 1.1e-3); the error is printed per
+    size class."""
+    f = I.make_forest(I.STRESS, worlds=[world])
+    fl = I.Flags(fp64_twig_diam=0.005)
+    _, rec0 = O.rollout(f, fl, n, record_tips=True)
+    rng = np.random.default_rng(world + 1)
+    target = rec0["tips"] + rng.normal(0.0, 0.01, rec0["tips"].shape)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    kinds, idx = sample_coords(f, 0, per_kind, rng)
+    g_cs, _ = O.grad(f, fl, 0, n, target, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+    got = pick(f, 0, g, kinds, idx)
+    errs = {["k", "kd", "q0", "qd0"][k]: float(np.abs(got[kinds == k] - g_cs[kinds == k]).max() /
+                                              np.abs(g_cs[kinds == k]).max()) for k in range(4)}
+    print(f"stress adjoint, {int(np.diff(f.body_off)[0])} bodies: relative error per kind {errs}")
+    assert_close_per_kind(got, g_cs, kinds, 2e-3, f"stress world {world}")
