@@ -205,11 +205,12 @@ def run_reference(args):
     nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
     fl = I.Flags()
     cores = os.cpu_count() or 1
-    sample_w = min(max(cores, 8), nw)
+    # every thread gets a few worlds, each bench step a few tenths of a second of host work
+    sample_w = min(4 * cores, nw)
     forest = I.make_forest(args.workload, n_worlds=nw, worlds=np.linspace(0, nw - 1, sample_w).astype(int))
-    steps = 10
+    steps = 100
     for _ in range(args.warmup):
-        O.rollout(forest, fl, 2, n_threads=cores)
+        O.rollout(forest, fl, 5, n_threads=cores)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
