@@ -32,12 +32,41 @@ HD float u2f(unsigned u) {
 #endif
 }
 
+// Fixed-size records (N floats, N a multiple of 4, starting on a 16-byte boundary) moved as
+// float4 on the device.
+template <int N>
+HD void ld_rec(const float* src, float (&d)[N]) {
+#ifdef __CUDA_ARCH__
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int i = 0; i < N / 4; ++i) {
+    const float4 v = s4[i];
+    d[4 * i] = v.x; d[4 * i + 1] = v.y; d[4 * i + 2] = v.z; d[4 * i + 3] = v.w;
+  }
+#else
+  for (int i = 0; i < N; ++i) d[i] = src[i];
+#endif
+}
+template <int N>
+HD void st_rec(float* dst, const float (&v)[N]) {
+#ifdef __CUDA_ARCH__
+  float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int i = 0; i < N / 4; ++i) d4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+#else
+  for (int i = 0; i < N; ++i) dst[i] = v[i];
+#endif
+}
+HD void put3(float* r, int o, f3 v) { r[o] = v.x; r[o + 1] = v.y; r[o + 2] = v.z; }
+HD f3 get3(const float* r, int o) { return mk(r[o], r[o + 1], r[o + 2]); }
+HD m3 getm(const float* r, int o) { return {get3(r, o), get3(r, o + 3), get3(r, o + 6)}; }
+
 // Backward temporaries of one world (floats), at their own base `wa` (shared or global
 // memory), and the snapshots of one checkpoint segment (global memory, `seg`).
 struct AdjLayout {
   int T;          // tape, 36 per body: R, x, w, v, alpha, a, Lw, Lv, Ow, Ov (see tape_body)
-  int C;          // 42 per body: cotangents a body sends to its parent's tape outputs (36),
-                  // plus the hang-velocity channel of Ow, Ov (6; it feeds q, not qd)
+  int C;          // 44 per body: cotangents a body sends to its parent's tape outputs (36),
+                  // the hang-velocity channel of Ow, Ov (6; it feeds q, not qd), 2 of padding
   int AF;         // 6 per body: force sweep accumulator
   int qb, qdb;    // per DOF: cotangents of the step-start q, qd being built
   int qb1, qdb1;  // per DOF: cotangents of the step-end q', qd'
@@ -53,7 +82,7 @@ struct AdjLayout {
     AdjLayout A;
     int o = 0;
     A.T = o; o += 36 * nb;
-    A.C = o; o += 42 * nb;
+    A.C = o; o += 44 * nb;
     A.AF = o; o += 6 * nb;
     A.qb = o; o += nv;
     A.qdb = o; o += nv;
@@ -162,10 +191,11 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
   m3 Rp;
   f3 xp, wp, vp, alp, ap, lwp, lvp, owp, ovp;
   if (p >= 0) {
-    const float* tp = wa + A.T + 36 * p;
-    Rp = ldm(tp);
-    xp = ld3(tp + 9); wp = ld3(tp + 12); vp = ld3(tp + 15); alp = ld3(tp + 18); ap = ld3(tp + 21);
-    lwp = ld3(tp + 24); lvp = ld3(tp + 27); owp = ld3(tp + 30); ovp = ld3(tp + 33);
+    float tp[36];
+    ld_rec(wa + A.T + 36 * p, tp);
+    Rp = getm(tp, 0);
+    xp = get3(tp, 9); wp = get3(tp, 12); vp = get3(tp, 15); alp = get3(tp, 18); ap = get3(tp, 21);
+    lwp = get3(tp, 24); lvp = get3(tp, 27); owp = get3(tp, 30); ovp = get3(tp, 33);
   } else {
     Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
     xp = wp = vp = alp = lwp = lvp = owp = ovp = mk(0, 0, 0);
@@ -194,10 +224,11 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
       R.c0 = c0; R.c2 = c2;
     }
   }
-  float* t = wa + A.T + 36 * b;
-  stm(t, R);
-  st3(t + 9, xb); st3(t + 12, w); st3(t + 15, vin); st3(t + 18, al); st3(t + 21, aa);
-  st3(t + 24, lw); st3(t + 27, lvin); st3(t + 30, ow); st3(t + 33, ovin);
+  float t[36];
+  put3(t, 0, R.c0); put3(t, 3, R.c1); put3(t, 6, R.c2);
+  put3(t, 9, xb); put3(t, 12, w); put3(t, 15, vin); put3(t, 18, al); put3(t, 21, aa);
+  put3(t, 24, lw); put3(t, 27, lvin); put3(t, 30, ow); put3(t, 33, ovin);
+  st_rec(wa + A.T + 36 * b, t);
 }
 
 // Reverse of a 3x3 symmetric-product term: G accumulates d(phi)/d(Io) as a general matrix.
@@ -234,11 +265,13 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
   const float dt = a.dt;
   // cotangents of this body's tape outputs, summed over its children
-  float cb[42];
-  for (int k = 0; k < 42; ++k) cb[k] = 0.f;
+  float cb[44];
+  for (int k = 0; k < 44; ++k) cb[k] = 0.f;
   for (int k = 0; k < ccount; ++k) {
-    const float* c = wa + A.C + 42 * (cfirst + k);
-    for (int j = 0; j < 42; ++j) cb[j] += c[j];
+    float c[44];
+    ld_rec(wa + A.C + 44 * (cfirst + k), c);
+#pragma unroll
+    for (int j = 0; j < 44; ++j) cb[j] += c[j];
   }
   m3 Rb_ = {mk(cb[0], cb[1], cb[2]), mk(cb[3], cb[4], cb[5]), mk(cb[6], cb[7], cb[8])};
   f3 xbb = mk(cb[9], cb[10], cb[11]), wb_ = mk(cb[12], cb[13], cb[14]), vb_ = mk(cb[15], cb[16], cb[17]);
@@ -249,10 +282,11 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   f3 owh = mk(cb[36], cb[37], cb[38]), ovh = mk(cb[39], cb[40], cb[41]);
 
   // own forward values
-  const float* t = wa + A.T + 36 * b;
-  const m3 R = ldm(t);
-  const f3 w = ld3(t + 12), vin = ld3(t + 15), al = ld3(t + 18), aa = ld3(t + 21);
-  const f3 lw = ld3(t + 24), lv = ld3(t + 27), ow = ld3(t + 30), ov = ld3(t + 33);
+  float t[36];
+  ld_rec(wa + A.T + 36 * b, t);
+  const m3 R = getm(t, 0);
+  const f3 w = get3(t, 12), vin = get3(t, 15), al = get3(t, 18), aa = get3(t, 21);
+  const f3 lw = get3(t, 24), lv = get3(t, 27), ow = get3(t, 30), ov = get3(t, 33);
 
   // seeds: virtual work of the body's own Newton-Euler force
   if (ra.dyn) {
@@ -404,9 +438,10 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   m3 Rp;
   f3 wp, alp, lwp, owp;
   if (p >= 0) {
-    const float* tp = wa + A.T + 36 * p;
-    Rp = ldm(tp);
-    wp = ld3(tp + 12); alp = ld3(tp + 18); lwp = ld3(tp + 24); owp = ld3(tp + 30);
+    float tp[36];
+    ld_rec(wa + A.T + 36 * p, tp);
+    Rp = getm(tp, 0);
+    wp = get3(tp, 12); alp = get3(tp, 18); lwp = get3(tp, 24); owp = get3(tp, 30);
   } else {
     Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
     wp = alp = lwp = owp = mk(0, 0, 0);
@@ -500,11 +535,14 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   Rpb.c0 = jb.x * db + (Q.c0.x * Rb_.c0 + Q.c1.x * Rb_.c1 + Q.c2.x * Rb_.c2);
   Rpb.c1 = jb.y * db + (Q.c0.y * Rb_.c0 + Q.c1.y * Rb_.c1 + Q.c2.y * Rb_.c2);
   Rpb.c2 = jb.z * db + (Q.c0.z * Rb_.c0 + Q.c1.z * Rb_.c1 + Q.c2.z * Rb_.c2);
-  float* c = wa + A.C + 42 * b;
-  stm(c, Rpb);
-  st3(c + 9, xpb); st3(c + 12, wpb); st3(c + 15, vpb); st3(c + 18, alpb); st3(c + 21, apb);
-  st3(c + 24, lwpb); st3(c + 27, lvpb); st3(c + 30, owpb); st3(c + 33, ovpb);
-  st3(c + 36, owph); st3(c + 39, ovph);
+  float c[44];
+  put3(c, 0, Rpb.c0); put3(c, 3, Rpb.c1); put3(c, 6, Rpb.c2);
+  put3(c, 9, xpb); put3(c, 12, wpb); put3(c, 15, vpb); put3(c, 18, alpb); put3(c, 21, apb);
+  put3(c, 24, lwpb); put3(c, 27, lvpb); put3(c, 30, owpb); put3(c, 33, ovpb);
+  put3(c, 36, owph); put3(c, 39, ovph);
+  c[42] = 0.f;
+  c[43] = 0.f;
+  st_rec(wa + A.C + 44 * b, c);
 }
 
 // A solve with the step's factors (see Pivot): L^T sweep leaf to root by factorisation level,

@@ -195,7 +195,7 @@ def test_autograd_function_matches_the_direct_call():
     # the loss itself agrees with the oracle's at the unperturbed gains
     lo = sum(O.grad(f, fl, w, n, target[:, f.tip_off[w]:f.tip_off[w + 1]], [2], [0], [1e-20], mode=0)[1]
              for w in range(f.n_worlds))
-    assert float(loss) == pytest.approx(lo, rel=1e-3)
+    assert float(loss.detach()) == pytest.approx(lo, rel=1e-3)
     # a second forward with scaled gains changes the tips; its backward uses its own gains
     k2 = (k.detach() * 1.1).requires_grad_(True)
     tips2 = tip_rollout(sim, k2, kd.detach(), q0.detach(), qd0.detach(), n, ckpt_every=20)
