@@ -57,6 +57,23 @@ HD void st_rec(float* dst, const float (&v)[N]) {
   for (int i = 0; i < N; ++i) dst[i] = v[i];
 #endif
 }
+// Copy n floats (rounded up to whole float4; both ends 16-byte aligned, padding behind both
+// regions) from src to dst, group-parallel.
+template <int TPW>
+HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
+#ifdef __CUDA_ARCH__
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) != 0) {
+    for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];  // not expected: the layouts keep 16-byte alignment
+    return;
+  }
+  const int n4 = (n + 3) >> 2;
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (int i = g.lane; i < n4; i += TPW) d4[i] = s4[i];
+#else
+  for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];
+#endif
+}
 HD void put3(float* r, int o, f3 v) { r[o] = v.x; r[o + 1] = v.y; r[o + 2] = v.z; }
 HD f3 get3(const float* r, int o) { return mk(r[o], r[o + 1], r[o + 2]); }
 HD m3 getm(const float* r, int o) { return {get3(r, o), get3(r, o + 3), get3(r, o + 6)}; }
@@ -79,24 +96,25 @@ struct AdjLayout {
   int total;      // floats at wa
   int snap;       // words per snapshot: the private state, staged in the forward workspace
   HD static AdjLayout make(int nb, int nv, int na) {
+    // every array starts on a 16-byte boundary
     AdjLayout A;
     int o = 0;
     A.T = o; o += 36 * nb;
     A.C = o; o += 44 * nb;
-    A.AF = o; o += 6 * nb;
-    A.qb = o; o += nv;
-    A.qdb = o; o += nv;
-    A.qb1 = o; o += nv;
-    A.qdb1 = o; o += nv;
-    A.lam = o; o += nv;
-    A.qd1 = o; o += nv;
-    A.zero = o; o += nv;
-    A.ub = o; o += 3 * na;
-    A.vb = o; o += 3 * na;
-    A.ub1 = o; o += 3 * na;
-    A.vb1 = o; o += 3 * na;
-    A.vh = o; o += 3 * na;
-    A.snap = WsLayout::state_words(nb, nv, na);
+    A.AF = o; o += WsLayout::r4(6 * nb);
+    A.qb = o; o += WsLayout::r4(nv);
+    A.qdb = o; o += WsLayout::r4(nv);
+    A.qb1 = o; o += WsLayout::r4(nv);
+    A.qdb1 = o; o += WsLayout::r4(nv);
+    A.lam = o; o += WsLayout::r4(nv);
+    A.qd1 = o; o += WsLayout::r4(nv);
+    A.zero = o; o += WsLayout::r4(nv);
+    A.ub = o; o += WsLayout::r4(3 * na);
+    A.vb = o; o += WsLayout::r4(3 * na);
+    A.ub1 = o; o += WsLayout::r4(3 * na);
+    A.vb1 = o; o += WsLayout::r4(3 * na);
+    A.vh = o; o += WsLayout::r4(3 * na);
+    A.snap = WsLayout::r4(WsLayout::state_words(nb, nv, na));
     A.total = o;
     return A;
   }
@@ -105,12 +123,10 @@ struct AdjLayout {
 // Copy the private state (staged at ws + L.S) to or from snapshot `k` of the segment buffer.
 template <int TPW>
 HD void snapshot(float* ws, const WsLayout& L, float* seg, const AdjLayout& A, int k, bool save, const Group<TPW>& g) {
-  float* src = ws + L.S;
-  float* dst = seg + (long long)k * A.snap;
-  for (int i = g.lane; i < A.snap; i += TPW) {
-    if (save) dst[i] = src[i];
-    else src[i] = dst[i];
-  }
+  float* st = ws + L.S;
+  float* sn = seg + (long long)k * A.snap;
+  if (save) copy4<TPW>(sn, st, A.snap, g);
+  else copy4<TPW>(st, sn, A.snap, g);
   g.sync();
 }
 
@@ -118,27 +134,27 @@ HD void snapshot(float* ws, const WsLayout& L, float* seg, const AdjLayout& A, i
 // segment's replay so the step need not run again: joint origins and DOF axes, the solution
 // Delta and the apple data, the snapped flags, the factors, and qd at the step's end.
 HD long long step_record_words(int nb, int nv, int nm, int na) {
-  return 3LL * nb + 3LL * nv + nv + 10LL * na + nb + nm + nv;
+  const WsLayout L = WsLayout::make(nb, nv, nm, na);
+  return (long long)WsLayout::r4(L.E - L.X + 3 * nv) + WsLayout::r4(L.AT - L.r + 10 * na) + WsLayout::r4(nb) +
+         WsLayout::r4(nm) + WsLayout::r4(nv);
 }
 
 template <int TPW>
-HD void record_part(float* rec, long long& o, float* src, int n, bool save, const Group<TPW>& g) {
-  for (int i = g.lane; i < n; i += TPW) {
-    if (save) rec[o + i] = src[i];
-    else src[i] = rec[o + i];
-  }
-  o += n;
+HD void record_part(float* rec, long long& o, float* ws_part, int n, bool save, const Group<TPW>& g) {
+  if (save) copy4<TPW>(rec + o, ws_part, n, g);
+  else copy4<TPW>(ws_part, rec + o, n, g);
+  o += WsLayout::r4(n);
 }
 
 template <int TPW>
 HD void step_record(float* ws, const WsLayout& L, const WState& s, float* wa, const AdjLayout& A,
                     const WorldView& v, float* rec, bool save, const Group<TPW>& g) {
   long long o = 0;
-  record_part<TPW>(rec, o, ws + L.X, 3 * v.nb + 3 * v.nv, save, g);  // X, then E
-  record_part<TPW>(rec, o, ws + L.r, v.nv + 10 * v.na, save, g);     // r, then AT
+  record_part<TPW>(rec, o, ws + L.X, L.E - L.X + 3 * v.nv, save, g);   // X, then E
+  record_part<TPW>(rec, o, ws + L.r, L.AT - L.r + 10 * v.na, save, g);  // r, then AT
   record_part<TPW>(rec, o, ws + L.SN, v.nb, save, g);
   record_part<TPW>(rec, o, ws + L.M, v.nm, save, g);
-  record_part<TPW>(rec, o, save ? s.qd : wa + A.qd1, v.nv, save, g);
+  record_part<TPW>(rec, o, save ? s.qd : wa + A.qd1, v.nv, save, g);    // qd at the step's end
   g.sync();
 }
 

@@ -14,7 +14,7 @@ namespace {
 template <int TPW>
 __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
                                                        BackShape sh) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   __shared__ int frozen[16];
   __shared__ int next[16];
   Group<TPW> g;

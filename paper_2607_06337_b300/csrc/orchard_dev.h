@@ -104,26 +104,28 @@ struct StepArgs {
 // rollout (see staged_view): the step reads and writes it there, not in global memory.
 struct WsLayout {
   int X, E, IC, r, AT, V, SN, S, R, A, F, M, total;
+  // every region starts on a 16-byte boundary, so whole regions move as float4
+  __host__ __device__ static int r4(int n) { return (n + 3) & ~3; }
   __host__ __device__ static int state_words(int nb, int nv, int na) {
-    return 2 * nv + 6 * na + 3 * nb + 4 * na + 1;
+    return 2 * r4(nv) + 6 * na + 3 * nb + 4 * na + 1;  // q and qd each padded to 4 floats
   }
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
-    L.X = 0;                 // joint origins
-    L.E = L.X + 3 * nb;      // DOF axes
-    L.IC = L.E + 3 * nv;     // spatial (then composite) inertias about x_b
-    L.r = L.IC + 10 * nb;    // right-hand side, then the solution
-    L.AT = L.r + nv;         // per apple: velocity with the hang point frozen, beta, tension,
-                             // pull, hang offset r_h (10 floats)
-    L.V = L.AT + 10 * na;    // body velocities (start of step, then end of step)
-    L.SN = L.V + 6 * nb;     // 1 on a snapped sub-tree
-    L.S = L.SN + nb;         // the staged state
-    const int u = L.S + state_words(nb, nv, na);  // shared region
+    L.X = 0;                         // joint origins
+    L.E = L.X + r4(3 * nb);          // DOF axes
+    L.IC = L.E + r4(3 * nv);         // spatial (then composite) inertias about x_b
+    L.r = L.IC + r4(10 * nb);        // right-hand side, then the solution
+    L.AT = L.r + r4(nv);             // per apple: velocity with the hang point frozen, beta,
+                                     // tension, pull, hang offset r_h (10 floats)
+    L.V = L.AT + r4(10 * na);        // body velocities (start of step, then end of step)
+    L.SN = L.V + r4(6 * nb);         // 1 on a snapped sub-tree
+    L.S = L.SN + r4(nb);             // the staged state
+    const int u = L.S + r4(state_words(nb, nv, na));  // shared region
     L.R = u;
-    L.A = L.R + 9 * nb;
-    L.F = L.A + 6 * nb;
+    L.A = L.R + r4(9 * nb);
+    L.F = L.A + r4(6 * nb);
     L.M = u;
-    const int end_sweeps = L.F + 6 * nb, end_m = L.M + nm;
+    const int end_sweeps = L.F + r4(6 * nb), end_m = L.M + r4(nm);
     L.total = end_sweeps > end_m ? end_sweeps : end_m;
     return L;
   }

@@ -185,13 +185,14 @@ HD WState world_state(const DevState& S, const WorldView& v, int w) {
   return s;
 }
 
-// The state staged in a workspace (WsLayout::S): q, qd (nv) and the apples' u-or-x, v (3 na)
-// as floats, then broken, bcnt, break_step (nb), detached, pcnt, tcnt, detach_step (na) and
-// one status word as ints.
+// The state staged in a workspace (WsLayout::S): q, qd (nv, each padded to 4 floats so both
+// start on 16-byte boundaries) and the apples' u-or-x, v (3 na) as floats, then broken, bcnt,
+// break_step (nb), detached, pcnt, tcnt, detach_step (na) and one status word as ints.
 HD WState staged_view(float* base, int nb, int nv, int na) {
   WState s;
-  s.q = base; s.qd = base + nv; s.ax = base + 2 * nv; s.av = base + 2 * nv + 3 * na;
-  int* i = (int*)(base + 2 * nv + 6 * na);
+  const int nv4 = WsLayout::r4(nv);
+  s.q = base; s.qd = base + nv4; s.ax = base + 2 * nv4; s.av = base + 2 * nv4 + 3 * na;
+  int* i = (int*)(base + 2 * nv4 + 6 * na);
   s.broken = i; s.bcnt = i + nb; s.break_step = i + 2 * nb;
   s.detached = i + 3 * nb; s.pcnt = s.detached + na; s.tcnt = s.pcnt + na; s.detach_step = s.tcnt + na;
   s.status = (unsigned*)(s.detach_step + na);

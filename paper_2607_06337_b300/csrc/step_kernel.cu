@@ -8,7 +8,7 @@ namespace {
 
 template <int TPW>
 __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, StepArgs a) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   __shared__ int frozen[16];
   Group<TPW> g;
   g.lane = threadIdx.x % TPW;
