@@ -572,11 +572,11 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
   constexpr int NW = TPW / 32;
   const int warp = g.lane >> 5, lane = g.lane & 31;
   for (int l = v.nBL - 1; l >= 0; --l) {
-    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int lo = v.bb[l], hi = v.bb[l + 1];
     if (lo == hi) continue;  // uniform for the group
     if (l > 0) {
       const int count = hi - lo;
-      const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+      const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
       for (int base = lo; base < hi; base += 32) {
         const int idx = base + lane;
         const bool valid = idx < hi;
@@ -614,9 +614,9 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
   g.sync();
 #else
   for (int l = v.nBL - 1; l >= 0; --l) {
-    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int lo = v.bb[l], hi = v.bb[l + 1];
     const int count = hi - lo;
-    const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+    const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
     for (int idx = lo; idx < hi; ++idx) {
       const int4 info = m.bl_info[v.b0 + idx];
       const bool two = (info.w & 3) == 2;
@@ -636,10 +636,9 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
   if (!lsweep) return;
   // L sweep, root to leaf by body level
   for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
-      const int4 bi = m.bi[v.b0 + b];
-      lsweep_joint(m, v, L, ws, y, bi.y & 0x0fffffff, (unsigned)bi.y >> 28);
+      lsweep_joint(m, v, L, ws, y, m.bi[v.b0 + b].y & 0x0fffffff, m.bj[v.b0 + b]);
     }
     g.sync();
   }
@@ -651,7 +650,7 @@ template <int TPW>
 HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L,
                         const AdjLayout& A, float* ws, float* wa, float* out, const Group<TPW>& g) {
   for (int l = v.nL - 1; l >= 0; --l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
       const int4 bi = m.bi[v.b0 + b];
       const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
@@ -758,10 +757,9 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   // root to leaf, joint by joint: the L sweep of lambda, the spring and damper terms, and the
   // tape at the step start (which needs the joint's final lambda)
   for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
-      const int4 bi = m.bi[v.b0 + b];
-      lsweep_joint(m, v, L, ws, wa + A.lam, bi.y & 0x0fffffff, (unsigned)bi.y >> 28);
+      lsweep_joint(m, v, L, ws, wa + A.lam, m.bi[v.b0 + b].y & 0x0fffffff, m.bj[v.b0 + b]);
       spring_joint(m, s, a, ba, v, A, wa, b, t_abs);
       tape_body(m, s, v, A, wa, ws + L.r, 1.f / dt, wa + A.lam, wa + A.qd1, b, gv);
     }
@@ -775,7 +773,7 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   ra.tipbar = t >= 1 ? ba.dtips + (long long)(t - 1) * a.n_tips_total * 3 : nullptr;
   ra.sphi = -dt;
   for (int l = v.nL - 1; l >= 0; --l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
     g.sync();
   }
@@ -817,7 +815,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     if (sg == nseg - 1) {
       // the last record's tips at the final configuration
       for (int l = 0; l < v.nL; ++l) {
-        const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+        const int lo = v.lv[l], hi = v.lv[l + 1];
         for (int b = lo + g.lane; b < hi; b += TPW)
           tape_body(m, s, v, A, wa, wa + A.zero, 0.f, wa + A.zero, wa + A.zero, b, gv);
         g.sync();
@@ -828,7 +826,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
       ra.sphi = 0.f;
       for (int l = v.nL - 1; l >= 0; --l) {
-        const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+        const int lo = v.lv[l], hi = v.lv[l + 1];
         for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
         g.sync();
       }

@@ -68,7 +68,7 @@ struct Packed {
   std::vector<int> body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl;
   std::vector<int4> bi;
   std::vector<float4> bp0, bp1, bp2, bp3, bp4;
-  std::vector<int4> dinfo;
+  std::vector<int4> bj;               // per body: row starts of its DOFs, first DOF's depth, ndof | fp64
   std::vector<unsigned> anc;
   std::vector<int> bl_off, bl_bound;  // factorisation levels (bodies by first-DOF depth)
   std::vector<int4> bl_info;          // per level position: first DOF, its row, second DOF's row, ndof
@@ -157,8 +157,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.lvl_off.assign(W + 1, 0);
   P.bi.resize(NB);
   P.bp0.resize(NB); P.bp1.resize(NB); P.bp2.resize(NB); P.bp3.resize(NB); P.bp4.resize(NB);
+  P.bj.assign(NB, make_int4(0, -1, 0, 0));
   P.lvl.clear();
-  P.dinfo.clear();
   P.anc.clear();
   P.bl_off.assign(W + 1, 0);
   P.bl_bound.clear();
@@ -170,6 +170,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   std::vector<long long> ws(W);
   std::vector<double> cost(W);
   std::vector<int> wnb(W), wnv(W), wnm(W), wna(W);
+  int n_dofs = 0;
   for (int w = 0; w < W; ++w) {
     const int b0 = d->body_off[w], nb = d->body_off[w + 1] - b0;
     const int a0 = d->apple_off[w], na = d->apple_off[w + 1] - a0;
@@ -243,14 +244,13 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
       }
       last_dof[b] = prev;
     }
-    P.dof_off[w] = (int)P.dinfo.size();
+    P.dof_off[w] = n_dofs;
+    n_dofs += nv;
     P.m_off[w] = (int)P.anc.size();
     int row = 0;
     std::vector<int> rowstart(nv);
     for (int i = 0; i < nv; ++i) {
       rowstart[i] = row;
-      const bool f64 = fp64_twig_diam > 0 && d->diam[b0 + dbody[i]] < fp64_twig_diam;
-      P.dinfo.push_back(make_int4(row, dbody[i], ddep[i], f64 ? 1 : 0));
       int j = i;
       for (int c = 0; c <= ddep[i]; ++c) {
         P.anc.push_back((unsigned)j | ((unsigned)dbody[j] << 16));
@@ -308,6 +308,11 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
     }
     for (int b = 0; b < nb; ++b) {
       const int gb = b0 + b;
+      if (nd[b] > 0) {
+        const int i = dof0[b];
+        const bool f64 = fp64_twig_diam > 0 && d->diam[gb] < fp64_twig_diam;
+        P.bj[gb] = make_int4(rowstart[i], nd[b] == 2 ? rowstart[i + 1] : -1, ddep[i], nd[b] | (f64 ? 16 : 0));
+      }
       if (cfirst[b] < 0) cfirst[b] = 0;
       P.bi[gb] = make_int4(d->parent[gb], dof0[b] | (nd[b] << 28), cfirst[b] | (ccount[b] << 24),
                            afirst[b] | (acount[b] << 24));
@@ -327,7 +332,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
     for (int i = 0; i < nv; ++i) sumsq += (long long)ddep[i] * (ddep[i] + 1) / 2;
     cost[w] = 700.0 * nb + 12.0 * nm + 2.0 * sumsq + 80.0 * na;
   }
-  P.dof_off[W] = (int)P.dinfo.size();
+  P.dof_off[W] = n_dofs;
   P.m_off[W] = (int)P.anc.size();
   P.lvl_off[W] = (int)P.lvl.size();
   P.bl_off[W] = (int)P.bl_bound.size();
@@ -445,7 +450,7 @@ namespace {
 
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
-  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, dinfo, anc, bl_off,
+  size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, bj, anc, bl_off,
       bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue, total;
 };
 
@@ -459,7 +464,7 @@ ModelLayout model_layout(const Packed& P) {
   L.bi = c.take<int4>(P.NB);
   L.bp0 = c.take<float4>(P.NB); L.bp1 = c.take<float4>(P.NB); L.bp2 = c.take<float4>(P.NB);
   L.bp3 = c.take<float4>(P.NB); L.bp4 = c.take<float4>(P.NB);
-  L.dinfo = c.take<int4>(P.NV);
+  L.bj = c.take<int4>(P.NB);
   L.anc = c.take<unsigned>(P.NM);
   L.bl_off = c.take<int>(W1);
   L.bl_bound = c.take<int>(P.bl_bound.size());
@@ -680,7 +685,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.bp0, P.bp0.data(), vbytes(P.bp0)); put(L.bp1, P.bp1.data(), vbytes(P.bp1));
   put(L.bp2, P.bp2.data(), vbytes(P.bp2)); put(L.bp3, P.bp3.data(), vbytes(P.bp3));
   put(L.bp4, P.bp4.data(), vbytes(P.bp4));
-  put(L.dinfo, P.dinfo.data(), vbytes(P.dinfo));
+  put(L.bj, P.bj.data(), vbytes(P.bj));
   put(L.anc, P.anc.data(), vbytes(P.anc));
   put(L.bl_off, P.bl_off.data(), vbytes(P.bl_off));
   put(L.bl_bound, P.bl_bound.data(), vbytes(P.bl_bound));
@@ -716,7 +721,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.bp0 = (const float4*)(base + L.bp0); dm.bp1 = (const float4*)(base + L.bp1);
   dm.bp2 = (const float4*)(base + L.bp2); dm.bp3 = (const float4*)(base + L.bp3);
   dm.bp4 = (const float4*)(base + L.bp4);
-  dm.dinfo = (const int4*)(base + L.dinfo);
+  dm.bj = (const int4*)(base + L.bj);
   dm.anc = (const unsigned*)(base + L.anc);
   dm.bl_off = (const int*)(base + L.bl_off);
   dm.bl_bound = (const int*)(base + L.bl_bound);

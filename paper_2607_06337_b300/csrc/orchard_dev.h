@@ -27,8 +27,9 @@ struct DevModel {
   const float4* bp2;     // com in the body frame (xyz), Ixx (w)
   const float4* bp3;     // Iyy, Izz, k, kd
   const float4* bp4;     // armature, m_max, -, -
-  const int4* dinfo;     // per DOF: row start (world-local), body, depth d_i, 1 if the joint's
-                         // pivot block is inverted in FP64
+  const int4* bj;        // per body: its first DOF's row start, the second DOF's row start (-1 for
+                         // a one-DOF joint), the first DOF's depth, the DOF count | 16 if the
+                         // pivot is inverted in FP64 (zeros, y = -1, for a body without DOFs)
   const unsigned* anc;   // per row entry c of DOF i: its c-th ancestor DOF j | (body of j) << 16
   const int* bl_off;     // [W+1] start of the world's factorisation level boundaries in bl_bound
   const int* bl_bound;   // world-local level position of each level's first body (+ end). A level

@@ -163,6 +163,8 @@ struct Group {
 
 struct WorldView {
   int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, BL0, nBL, f0;
+  // body-level bounds (nL + 1), factorisation-level bounds and fac_tgt bases (nBL + 1 each)
+  const int *lv, *bb, *bf;
 };
 
 // One world's state arrays, indexed world-locally.
@@ -209,6 +211,9 @@ HD WorldView world_view(const DevModel& m, int w) {
   v.L0 = m.lvl_off[w]; v.nL = m.lvl_off[w + 1] - v.L0 - 1;
   v.BL0 = m.bl_off[w]; v.nBL = m.bl_off[w + 1] - v.BL0 - 1;
   v.f0 = m.fac_off[w];
+  v.lv = m.lvl + v.L0;
+  v.bb = m.bl_bound + v.BL0;
+  v.bf = m.bl_fbase + v.BL0;
   return v;
 }
 
@@ -233,15 +238,30 @@ HD void joint_gains(const WState& s, const StepArgs& a, int b, float4 P3, int t_
   *kd = (1.f + a.ramp_gain * ramp) * P3.w;
 }
 
+// The model records a sweep needs of one body, loaded together (independent addresses, so
+// their latencies overlap).
+struct KinRec {
+  int4 bi;
+  float4 P0, P1;
+};
+HD KinRec kin_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bp0[gb], m.bp1[gb]}; }
+struct BwdRec {
+  int4 bi;
+  float4 P3;
+};
+HD BwdRec bwd_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bp3[gb]}; }
+struct UpdRec {
+  int4 bi, bj;
+  float4 P3, P4;
+};
+HD UpdRec upd_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bj[gb], m.bp3[gb], m.bp4[gb]}; }
 // Phase 1a for one body (root to leaf, level by level): kinematics, velocities, bias
 // acceleration, snapped flag.
-HD void forward_kin(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L, float* ws, int b,
-                    f3 g) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
+HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, const KinRec& rec) {
+  const int4 bi = rec.bi;
   const int p = bi.x;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const float4 P0 = m.bp0[gb], P1 = m.bp1[gb];
+  const float4 P0 = rec.P0, P1 = rec.P1;
   m3 Rp;
   f3 xp, wp, vp, alp, ap;
   if (p >= 0) {
@@ -378,10 +398,9 @@ HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, con
 }
 
 // Phase 2 for one body: pull children, bias and right-hand side of its DOFs.
-HD void backward_body(const DevModel& m, const WState& s, const StepArgs& a,
-                                              const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
+HD void backward_body(const WState& s, const StepArgs& a, const WsLayout& L, float* ws, int b, int t_abs,
+                      const BwdRec& rec) {
+  const int4 bi = rec.bi;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
   const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
   f3 n = ld3(ws + L.F + 6 * b), f = ld3(ws + L.F + 6 * b + 3);
@@ -398,9 +417,8 @@ HD void backward_body(const DevModel& m, const WState& s, const StepArgs& a,
   st3(ws + L.F + 6 * b, n); st3(ws + L.F + 6 * b + 3, f);
   st_in(ws + L.IC + 10 * b, I);
   if (nd) {
-    const float4 P3 = m.bp3[gb];
     float k, kd;
-    joint_gains(s, a, b, P3, t_abs, &k, &kd);
+    joint_gains(s, a, b, rec.P3, t_abs, &k, &kd);
     const float dt = a.dt, adt = a.alpha ? dt : 0.f;
     for (int j = 0; j < nd; ++j) {
       const int i = dof0 + j;
@@ -458,42 +476,39 @@ HD void pivot_scale(const float* M, int4 info, float* y) {
   }
 }
 
-// L sweep of one joint (first DOF dof0, nd DOFs): x = z - P^-1 U x_ancestors, in place in y
-// (which holds z for this joint and the final x of every ancestor).
+// L sweep of one joint (first DOF dof0, joint record bj as in DevModel::bj): x = z - P^-1 U
+// x_ancestors, in place in y (which holds z for this joint and the final x of every ancestor).
 HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, const float* ws, float* y, int dof0,
-                     int nd) {
+                     int4 bj) {
+  const int nd = bj.w & 3;
   if (nd == 0) return;
-  const int4 dx = m.dinfo[v.d0 + dof0];
   const float* M = ws + L.M;
-  const float* rowx = M + dx.x;
-  const unsigned* an = m.anc + v.m0 + dx.x;
+  const float* rowx = M + bj.x;
+  const unsigned* an = m.anc + v.m0 + bj.x;
   float sx = 0.f, sy = 0.f;
   if (nd == 2) {
-    const int ry = m.dinfo[v.d0 + dof0 + 1].x;
-    const float* rowy = M + ry + 1;  // rowy[c]: the y' row's entry of the x row's c-th ancestor
+    const float* rowy = M + bj.y + 1;  // rowy[c]: the y' row's entry of the x row's c-th ancestor
 #pragma unroll 4
-    for (int c = 1; c <= dx.z; ++c) {
+    for (int c = 1; c <= bj.z; ++c) {
       const float xa = y[an[c] & 0xffffu];
       sx = fmaf(rowx[c], xa, sx);
       sy = fmaf(rowy[c], xa, sy);
     }
-    const Pivot P = pivot_of(M, dx.x, ry, 2 | (dx.w ? 16 : 0));
+    const Pivot P = pivot_of(M, bj.x, bj.y, bj.w);
     y[dof0] -= P.p00 * sx + P.p01 * sy;
     y[dof0 + 1] -= P.p01 * sx + P.p11 * sy;
   } else {
 #pragma unroll 4
-    for (int c = 1; c <= dx.z; ++c) sx = fmaf(rowx[c], y[an[c] & 0xffffu], sx);
-    y[dof0] -= sx * pivot_of(M, dx.x, -1, 1 | (dx.w ? 16 : 0)).p00;
+    for (int c = 1; c <= bj.z; ++c) sx = fmaf(rowx[c], y[an[c] & 0xffffu], sx);
+    y[dof0] -= sx * pivot_of(M, bj.x, -1, bj.w).p00;
   }
 }
 
 // Phase 5a for one body (root to leaf, level by level): finish the solve, update, velocities,
 // rupture test.
-HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
-                                            const WorldView& v, const WsLayout& L, float* ws, int b, int t_abs,
-                                            unsigned, int* frozen) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
+HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                    float* ws, int b, int t_abs, int* frozen, const UpdRec& rec) {
+  const int4 bi = rec.bi;
   const int p = bi.x;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
   const float dt = a.dt;
@@ -508,7 +523,7 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
   }
   bool bad = false;
   float th2 = 0.f;
-  lsweep_joint(m, v, L, ws, ws + L.r, dof0, nd);
+  lsweep_joint(m, v, L, ws, ws + L.r, dof0, rec.bj);
   for (int j = 0; j < nd; ++j) {
     const int i = dof0 + j;
     const float x = ws[L.r + i];
@@ -523,9 +538,8 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a,
   st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vl);
 
   if (nd && !s.broken[b]) {
-    const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
-    const float mom = P3.z * sqrtf(th2);
-    const int cnt = mom > P4.y ? s.bcnt[b] + 1 : 0;
+    const float mom = rec.P3.z * sqrtf(th2);
+    const int cnt = mom > rec.P4.y ? s.bcnt[b] + 1 : 0;
     s.bcnt[b] = cnt;
     if (cnt >= a.n_break) {
       s.broken[b] = 1;
@@ -572,6 +586,50 @@ HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, cons
   }
 }
 
+// Phase 3 for one body: the mass-matrix rows of its DOFs in ancestor-row storage,
+// M_ij = e_j . (n_i + (x_b(i) - x_b(j)) x f_i) with (n_i; f_i) = I^c_b(i) (e_i; 0), and the
+// implicit diagonal (armature, dt kd', dt^2 k'). The y' row of a two-DOF joint has the x DOF
+// (same body, no lever) as its first ancestor and then the x row's, so both rows share one
+// walk up the ancestors.
+HD void crba_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                  float* ws, int b, int t_abs, const UpdRec& rec) {
+  const int dof0 = rec.bi.y & 0x0fffffff, nd = (unsigned)rec.bi.y >> 28;
+  if (nd == 0) return;
+  const float dt = a.dt;
+  const sinertia I = ld_in(ws + L.IC + 10 * b);
+  const f3 xb = ld3(ws + L.X + 3 * b);
+  float k, kd;
+  joint_gains(s, a, b, rec.P3, t_abs, &k, &kd);
+  const float diag = rec.P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
+  const f3 ex = ld3(ws + L.E + 3 * dof0);
+  const f3 nx = mul(I.I, ex), fx = cross(ex, I.h);
+  float* rx = ws + L.M + rec.bj.x;
+  const unsigned* an = m.anc + v.m0 + rec.bj.x;
+  rx[0] = dot(ex, nx) + diag;
+  if (nd == 2) {
+    const f3 ey = ld3(ws + L.E + 3 * (dof0 + 1));
+    const f3 ny = mul(I.I, ey), fy = cross(ey, I.h);
+    float* ry = ws + L.M + rec.bj.y;
+    ry[0] = dot(ey, ny) + diag;
+    ry[1] = dot(ex, ny);
+#pragma unroll 4
+    for (int c = 1; c <= rec.bj.z; ++c) {
+      const unsigned ab = an[c];
+      const f3 lev = xb - ld3(ws + L.X + 3 * (ab >> 16));
+      const f3 ej = ld3(ws + L.E + 3 * (ab & 0xffffu));
+      rx[c] = dot(ej, nx + cross(lev, fx));
+      ry[c + 1] = dot(ej, ny + cross(lev, fy));
+    }
+  } else {
+#pragma unroll 4
+    for (int c = 1; c <= rec.bj.z; ++c) {
+      const unsigned ab = an[c];
+      const f3 lev = xb - ld3(ws + L.X + 3 * (ab >> 16));
+      rx[c] = dot(ld3(ws + L.E + 3 * (ab & 0xffffu)), nx + cross(lev, fx));
+    }
+  }
+}
+
 template <int TPW>
 HD void write_ckpt(const WState& s, const StepArgs& a, const WorldView& v, int slot, const Group<TPW>& g) {
   unsigned* base = a.ckpt + (long long)slot * a.ckpt_words;
@@ -610,7 +668,7 @@ template <int TPW>
 HD void fk_only(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L, float* ws,
                         const Group<TPW>& g) {
   for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
+    const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
       const int gb = v.b0 + b;
       const int4 bi = m.bi[gb];
@@ -723,11 +781,11 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
   constexpr int NW = TPW / 32;
   const int warp = g.lane >> 5, lane = g.lane & 31;
   for (int l = v.nBL - 1; l >= 0; --l) {
-    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int lo = v.bb[l], hi = v.bb[l + 1];
     if (lo == hi) continue;  // no joint has its first DOF at this depth (uniform for the group)
     if (l > 0) {
       const int count = hi - lo;
-      const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+      const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
       // the first chunk's joint and first target; later chunks' are loaded one chunk ahead
       int4 info_n = make_int4(0, 0, 0, 0);
       int2 tk_n = make_int2(0, -1 - lane);
@@ -823,9 +881,9 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
 #else
   // one serial lane: the same updates, joint by joint in list order
   for (int l = v.nBL - 1; l >= 0; --l) {
-    const int lo = m.bl_bound[v.BL0 + l], hi = m.bl_bound[v.BL0 + l + 1];
+    const int lo = v.bb[l], hi = v.bb[l + 1];
     const int count = hi - lo;
-    const int2* ft = m.fac_tgt + v.f0 + m.bl_fbase[v.BL0 + l];
+    const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
     for (int idx = lo; idx < hi; ++idx) {
       const int4 info = m.bl_info[v.b0 + idx];
       const bool two = (info.w & 3) == 2;
@@ -851,11 +909,10 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
 template <int TPW>
 HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                    float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot) {
-  const float dt = a.dt;
   // 1. root-to-leaf: kinematics, velocities, own forces, apple loads
   for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(m, s, v, L, ws, b, gv);
+    const int lo = v.lv[l], hi = v.lv[l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec(m, v.b0 + b));
     g.sync();
   }
   for (int b = g.lane; b < v.nb; b += TPW) forward_force(m, s, a, v, L, ws, b, t_abs, gv);
@@ -863,40 +920,19 @@ HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const 
   if (tip_slot >= 0) record_tips(m, a, v, L, ws, tip_slot, g);
   // 2. leaf-to-root: forces and composite inertias, right-hand side
   for (int l = v.nL - 1; l >= 0; --l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) backward_body(m, s, a, v, L, ws, b, t_abs);
+    const int lo = v.lv[l], hi = v.lv[l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) backward_body(s, a, L, ws, b, t_abs, bwd_rec(m, v.b0 + b));
     g.sync();
   }
-  // 3. CRBA rows and the implicit diagonal
-  for (int i = g.lane; i < v.nv; i += TPW) {
-    const int4 di = m.dinfo[v.d0 + i];
-    const int b = di.y;
-    const int gb = v.b0 + b;
-    const f3 e = ld3(ws + L.E + 3 * i);
-    const sinertia I = ld_in(ws + L.IC + 10 * b);
-    const f3 n = mul(I.I, e), f = cross(e, I.h);
-    const f3 xb = ld3(ws + L.X + 3 * b);
-    float* row = ws + L.M + di.x;
-    const unsigned* an = m.anc + v.m0 + di.x;
-    const float4 P3 = m.bp3[gb], P4 = m.bp4[gb];
-    float k, kd;
-    joint_gains(s, a, b, P3, t_abs, &k, &kd);
-    row[0] = dot(e, n) + P4.x + dt * kd + (a.alpha ? dt * dt * k : 0.f);
-#pragma unroll 4
-    for (int c = 1; c <= di.z; ++c) {
-      const unsigned ab = an[c];
-      const int j = ab & 0xffffu, bj = ab >> 16;
-      const f3 lev = xb - ld3(ws + L.X + 3 * bj);
-      row[c] = dot(ld3(ws + L.E + 3 * j), n + cross(lev, f));
-    }
-  }
+  // 3. CRBA rows and the implicit diagonal, body by body
+  for (int b = g.lane; b < v.nb; b += TPW) crba_body(m, s, a, v, L, ws, b, t_abs, upd_rec(m, v.b0 + b));
   g.sync();
   // 4. LDL^T by DOF depth, deepest first, with the L^T sweep of the solve
   factor_levels<TPW>(m, v, L, ws, g);
   // 5. root-to-leaf: L sweep, update, velocities, apples, events
   for (int l = 0; l < v.nL; ++l) {
-    const int lo = m.lvl[v.L0 + l], hi = m.lvl[v.L0 + l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) update_body(m, s, a, v, L, ws, b, t_abs, 0u, g.flag);
+    const int lo = v.lv[l], hi = v.lv[l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) update_body(m, s, a, v, L, ws, b, t_abs, g.flag, upd_rec(m, v.b0 + b));
     g.sync();
   }
   if (v.na > 0) {
@@ -939,7 +975,7 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const WState sg = world_state(S, v, w);
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);
-  copy_state<TPW>(s, sg, v, g);
+  copy_state<TPW>(s, sg, v, g);  // ends on a group barrier
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
