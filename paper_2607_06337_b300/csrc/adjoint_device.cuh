@@ -269,33 +269,42 @@ struct RevArgs {
   float sphi;            // scale of the virtual-work term (-dt)
 };
 
-// Reverse of one body's tape (leaf-to-root): consumes the cotangents its children sent (C
-// slots) plus its own seeds, adds the q / qd cotangents of its DOFs, writes its C slot.
-HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v,
-                     const WsLayout& L, const AdjLayout& A, float* ws, float* wa, const RevArgs& ra, int b, f3 g,
-                     int t_abs) {
+// The cotangent of one body's tape outputs, in a C slot's layout: R (9), x_b, w, v, alpha,
+// a, Lw, Lv, Ow, Ov (3 each), then the hang-point channel Ow_h, Ov_h: cotangents of J_h qd'
+// seen by the apple update, whose qd' part is already in Delta-bar (hang_load_sweep), so this
+// channel only reaches q (through the axes and hang offsets).
+struct Cot {
+  m3 R;
+  f3 x, w, v, al, a, lw, lv, ow, ov, owh, ovh;
+};
+HD Cot cot_get(const float* c) {
+  return {{mk(c[0], c[1], c[2]), mk(c[3], c[4], c[5]), mk(c[6], c[7], c[8])},
+          get3(c, 9), get3(c, 12), get3(c, 15), get3(c, 18), get3(c, 21), get3(c, 24), get3(c, 27),
+          get3(c, 30), get3(c, 33), get3(c, 36), get3(c, 39)};
+}
+HD void cot_put(float* c, const Cot& k) {
+  put3(c, 0, k.R.c0); put3(c, 3, k.R.c1); put3(c, 6, k.R.c2);
+  put3(c, 9, k.x); put3(c, 12, k.w); put3(c, 15, k.v); put3(c, 18, k.al); put3(c, 21, k.a);
+  put3(c, 24, k.lw); put3(c, 27, k.lv); put3(c, 30, k.ow); put3(c, 33, k.ov);
+  put3(c, 36, k.owh); put3(c, 39, k.ovh);
+  c[42] = 0.f;
+  c[43] = 0.f;
+}
+
+// The reverse of one body's tape runs in two parts. reverse_seed (all bodies at once): the
+// cotangents its own terms put on its tape outputs (the virtual work of its Newton-Euler
+// force, its apples, its tips), which depend on nothing below it; they are additive, so they
+// go into its C slot before the leaf-to-root sweep. reverse_chain (leaf to root): adds the
+// children's C slots, reverses the body's DOF loop and its shift from the parent, and leaves
+// what goes to the parent in its C slot.
+HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                     const AdjLayout& A, float* ws, float* wa, const RevArgs& ra, int b, f3 g, int t_abs) {
   const int gb = v.b0 + b;
   const int4 bi = m.bi[gb];
-  const int p = bi.x;
-  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-  const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
   const float dt = a.dt;
-  // cotangents of this body's tape outputs, summed over its children
-  float cb[44];
-  for (int k = 0; k < 44; ++k) cb[k] = 0.f;
-  for (int k = 0; k < ccount; ++k) {
-    float c[44];
-    ld_rec(wa + A.C + 44 * (cfirst + k), c);
-#pragma unroll
-    for (int j = 0; j < 44; ++j) cb[j] += c[j];
-  }
-  m3 Rb_ = {mk(cb[0], cb[1], cb[2]), mk(cb[3], cb[4], cb[5]), mk(cb[6], cb[7], cb[8])};
-  f3 xbb = mk(cb[9], cb[10], cb[11]), wb_ = mk(cb[12], cb[13], cb[14]), vb_ = mk(cb[15], cb[16], cb[17]);
-  f3 alb = mk(cb[18], cb[19], cb[20]), ab_ = mk(cb[21], cb[22], cb[23]), lwb = mk(cb[24], cb[25], cb[26]);
-  f3 lvb = mk(cb[27], cb[28], cb[29]), owb = mk(cb[30], cb[31], cb[32]), ovb = mk(cb[33], cb[34], cb[35]);
-  // cotangents of J_h qd' seen by the apple update: their qd' part is already in Delta-bar
-  // (hang_load_sweep), so this channel only reaches q (through the axes and hang offsets)
-  f3 owh = mk(cb[36], cb[37], cb[38]), ovh = mk(cb[39], cb[40], cb[41]);
+  m3 Rb_ = {mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0)};
+  f3 xbb = mk(0, 0, 0), wb_ = xbb, vb_ = xbb, alb = xbb, ab_ = xbb, lwb = xbb, lvb = xbb, owb = xbb, ovb = xbb;
+  f3 owh = xbb, ovh = xbb;
 
   // own forward values
   float t[36];
@@ -450,6 +459,34 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
     }
   }
 
+  float c[44];
+  cot_put(c, {Rb_, xbb, wb_, vb_, alb, ab_, lwb, lvb, owb, ovb, owh, ovh});
+  st_rec(wa + A.C + 44 * b, c);
+}
+
+HD void reverse_chain(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const AdjLayout& A,
+                      float* wa, const RevArgs& ra, int b) {
+  const int gb = v.b0 + b;
+  const int4 bi = m.bi[gb];
+  const int p = bi.x;
+  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+  const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
+  const float dt = a.dt;
+  // the body's own seeds plus what its children sent
+  float cb[44];
+  ld_rec(wa + A.C + 44 * b, cb);
+  for (int k = 0; k < ccount; ++k) {
+    float c[44];
+    ld_rec(wa + A.C + 44 * (cfirst + k), c);
+#pragma unroll
+    for (int j = 0; j < 44; ++j) cb[j] += c[j];
+  }
+  const Cot k0 = cot_get(cb);
+  m3 Rb_ = k0.R;
+  const f3 xbb = k0.x, lvb = k0.lv, ovb = k0.ov, owh = k0.owh, ovh = k0.ovh;
+  f3 wb_ = k0.w, vb_ = k0.v, alb = k0.al, ab_ = k0.a, lwb = k0.lw, owb = k0.ow;
+  const f3 vin = get3(wa + A.T + 36 * b, 15);  // the body's own v at x_b
+
   // reverse of the DOF loop: recompute its intermediates from the parent's tape
   m3 Rp;
   f3 wp, alp, lwp, owp;
@@ -552,12 +589,7 @@ HD void reverse_body(const DevModel& m, const WState& s, const StepArgs& a, cons
   Rpb.c1 = jb.y * db + (Q.c0.y * Rb_.c0 + Q.c1.y * Rb_.c1 + Q.c2.y * Rb_.c2);
   Rpb.c2 = jb.z * db + (Q.c0.z * Rb_.c0 + Q.c1.z * Rb_.c1 + Q.c2.z * Rb_.c2);
   float c[44];
-  put3(c, 0, Rpb.c0); put3(c, 3, Rpb.c1); put3(c, 6, Rpb.c2);
-  put3(c, 9, xpb); put3(c, 12, wpb); put3(c, 15, vpb); put3(c, 18, alpb); put3(c, 21, apb);
-  put3(c, 24, lwpb); put3(c, 27, lvpb); put3(c, 30, owpb); put3(c, 33, ovpb);
-  put3(c, 36, owph); put3(c, 39, ovph);
-  c[42] = 0.f;
-  c[43] = 0.f;
+  cot_put(c, {Rpb, xpb, wpb, vpb, alpb, apb, lwpb, lvpb, owpb, ovpb, owph, ovph});
   st_rec(wa + A.C + 44 * b, c);
 }
 
@@ -772,9 +804,11 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   ra.qd1 = wa + A.qd1;
   ra.tipbar = t >= 1 ? ba.dtips + (long long)(t - 1) * a.n_tips_total * 3 : nullptr;
   ra.sphi = -dt;
+  for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
+  g.sync();
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
+    for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);
     g.sync();
   }
 }
@@ -825,9 +859,11 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       ra.delta = wa + A.zero; ra.lam = wa + A.zero; ra.qd1 = wa + A.zero;
       ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
       ra.sphi = 0.f;
+      for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
+      g.sync();
       for (int l = v.nL - 1; l >= 0; --l) {
         const int lo = v.lv[l], hi = v.lv[l + 1];
-        for (int b = lo + g.lane; b < hi; b += TPW) reverse_body(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
+        for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);
         g.sync();
       }
       for (int i = g.lane; i < v.nv; i += TPW) {
