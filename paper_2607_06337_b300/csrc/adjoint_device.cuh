@@ -79,7 +79,9 @@ HD f3 get3(const float* r, int o) { return mk(r[o], r[o + 1], r[o + 2]); }
 HD m3 getm(const float* r, int o) { return {get3(r, o), get3(r, o + 3), get3(r, o + 6)}; }
 
 // Backward temporaries of one world (floats), at their own base `wa` (shared or global
-// memory), and the snapshots of one checkpoint segment (global memory, `seg`).
+// memory), and the snapshots of one checkpoint segment (global memory, `seg`). The C slots
+// come last: the `head` floats before them may live in shared memory while the C slots stay
+// in global memory (reverse_seed / reverse_chain take their base from RevArgs).
 struct AdjLayout {
   int T;          // tape, 36 per body: R, x, w, v, alpha, a, Lw, Lv, Ow, Ov (see tape_body)
   int C;          // 44 per body: cotangents a body sends to its parent's tape outputs (36),
@@ -93,6 +95,7 @@ struct AdjLayout {
   int ub, vb;     // per apple x3: cotangents of the step-start u (or x), v
   int ub1, vb1;   // per apple x3: of the step-end u', v'
   int vh;         // per apple x3: cotangent of the new hang-point velocity
+  int head;       // floats before C
   int total;      // floats at wa
   int snap;       // words per snapshot: the private state, staged in the forward workspace
   HD static AdjLayout make(int nb, int nv, int na) {
@@ -100,7 +103,6 @@ struct AdjLayout {
     AdjLayout A;
     int o = 0;
     A.T = o; o += 36 * nb;
-    A.C = o; o += 44 * nb;
     A.AF = o; o += WsLayout::r4(6 * nb);
     A.qb = o; o += WsLayout::r4(nv);
     A.qdb = o; o += WsLayout::r4(nv);
@@ -114,6 +116,8 @@ struct AdjLayout {
     A.ub1 = o; o += WsLayout::r4(3 * na);
     A.vb1 = o; o += WsLayout::r4(3 * na);
     A.vh = o; o += WsLayout::r4(3 * na);
+    A.head = o;
+    A.C = o; o += 44 * nb;
     A.snap = WsLayout::r4(WsLayout::state_words(nb, nv, na));
     A.total = o;
     return A;
@@ -267,6 +271,7 @@ struct RevArgs {
   const float* qd1;      // per DOF: qd'
   const float* tipbar;   // [n_tips_total][3] cotangents of this configuration's tips, or null
   float sphi;            // scale of the virtual-work term (-dt)
+  float* cs;             // the C slots, 44 floats per body
 };
 
 // The cotangent of one body's tape outputs, in a C slot's layout: R (9), x_b, w, v, alpha,
@@ -461,7 +466,7 @@ HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, cons
 
   float c[44];
   cot_put(c, {Rb_, xbb, wb_, vb_, alb, ab_, lwb, lvb, owb, ovb, owh, ovh});
-  st_rec(wa + A.C + 44 * b, c);
+  st_rec(ra.cs + 44 * b, c);
 }
 
 HD void reverse_chain(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const AdjLayout& A,
@@ -474,10 +479,10 @@ HD void reverse_chain(const DevModel& m, const WState& s, const StepArgs& a, con
   const float dt = a.dt;
   // the body's own seeds plus what its children sent
   float cb[44];
-  ld_rec(wa + A.C + 44 * b, cb);
+  ld_rec(ra.cs + 44 * b, cb);
   for (int k = 0; k < ccount; ++k) {
     float c[44];
-    ld_rec(wa + A.C + 44 * (cfirst + k), c);
+    ld_rec(ra.cs + 44 * (cfirst + k), c);
 #pragma unroll
     for (int j = 0; j < 44; ++j) cb[j] += c[j];
   }
@@ -590,7 +595,7 @@ HD void reverse_chain(const DevModel& m, const WState& s, const StepArgs& a, con
   Rpb.c2 = jb.z * db + (Q.c0.z * Rb_.c0 + Q.c1.z * Rb_.c1 + Q.c2.z * Rb_.c2);
   float c[44];
   cot_put(c, {Rpb, xpb, wpb, vpb, alpb, apb, lwpb, lvpb, owpb, ovpb, owph, ovph});
-  st_rec(wa + A.C + 44 * b, c);
+  st_rec(ra.cs + 44 * b, c);
 }
 
 // A solve with the step's factors (see Pivot): L^T sweep leaf to root by factorisation level,
@@ -753,7 +758,7 @@ HD void spring_joint(const DevModel& m, const WState& s, const StepArgs& a, cons
 // start state in A.qb / qdb / ub / vb.
 template <int TPW>
 HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
-                     const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa,
+                     const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
                      const Group<TPW>& g, int t, f3 gv) {
   const float dt = a.dt;
   const int t_abs = a.step0 + t;
@@ -804,6 +809,7 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   ra.qd1 = wa + A.qd1;
   ra.tipbar = t >= 1 ? ba.dtips + (long long)(t - 1) * a.n_tips_total * 3 : nullptr;
   ra.sphi = -dt;
+  ra.cs = cs;
   for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
   g.sync();
   for (int l = v.nL - 1; l >= 0; --l) {
@@ -816,14 +822,16 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
 // Backward pass of one world over a recorded rollout.
 template <int TPW>
 // ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
-// seg: ckpt_every snapshots and step records (global memory); ws and wa may be in shared or
-// global memory. Each segment is replayed once, forward, saving every step's start state and
-// its record; then its steps are reversed last to first from those.
+// wc: the C slots when they are not at wa + A.C (null: they are), seg: ckpt_every snapshots
+// and step records (global memory); ws, wa and wc may be in shared or global memory. Each
+// segment is replayed once, forward, saving every step's start state and its record; then its
+// steps are reversed last to first from those.
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
-                       float* seg, const Group<TPW>& g) {
+                       float* wc, float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
+  float* cs = wc ? wc : wa + A.C;
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);  // the world's private state
   // the segment buffer: ckpt_every snapshots, then ckpt_every step records
   const long long recw = step_record_words(v.nb, v.nv, v.nm, v.na);
@@ -859,6 +867,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       ra.delta = wa + A.zero; ra.lam = wa + A.zero; ra.qd1 = wa + A.zero;
       ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
       ra.sphi = 0.f;
+      ra.cs = cs;
       for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
       g.sync();
       for (int l = v.nL - 1; l >= 0; --l) {
@@ -875,7 +884,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     for (int t = t1 - 1; t >= t0; --t) {
       snapshot(ws, L, seg, A, t - t0, false, g);
       step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, false, g);
-      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, g, t, gv);
+      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv);
       for (int i = g.lane; i < v.nv; i += TPW) {
         wa[A.qb1 + i] = wa[A.qb + i];
         wa[A.qdb1 + i] = wa[A.qdb + i];

@@ -5,7 +5,8 @@
 // which temporaries live in the block's shared memory:
 //   0: none (forward and backward temporaries in the global slot),
 //   1: the forward step's temporaries (WsLayout),
-//   2: the forward step's and the backward's (WsLayout, then AdjLayout).
+//   2: the forward step's and the backward's (WsLayout, then AdjLayout),
+//   3: the forward step's and the backward's up to the C slots, which open the global slot.
 #include "adjoint_device.cuh"
 
 namespace orchard {
@@ -24,8 +25,13 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
   const int groups = blockDim.x / TPW;
   float* slot = work + (long long)(blockIdx.x * groups + g.id) * sh.global_floats;
   float* local = smem + (long long)g.id * sh.smem_floats;
-  float *ws, *wa, *seg;
-  if (sh.mode == 2) {
+  float *ws, *wa, *seg, *wc = nullptr;
+  if (sh.mode == 3) {
+    ws = local;
+    wa = local + sh.fwd_floats;
+    wc = slot;
+    seg = slot + sh.c_floats;
+  } else if (sh.mode == 2) {
     ws = local;
     wa = local + sh.fwd_floats;
     seg = slot;
@@ -44,7 +50,7 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
     const int qi = next[g.id];
     g.sync();
     if (qi >= a.q_end - a.q_begin) break;
-    backward_world<TPW>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, seg, g);
+    backward_world<TPW>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
   }
 }
 
@@ -89,6 +95,7 @@ cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes
 }
 
 long long backward_adj_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).total; }
+long long backward_adj_head_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).head; }
 
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every) {
   return (long long)ckpt_every * (AdjLayout::make(nb, nv, na).snap + step_record_words(nb, nv, nm, na));

@@ -1095,18 +1095,33 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
   BackShape& sh = p.sh;
   sh.fwd_floats = round16(ci.ws_floats);
   sh.adj_floats = round16(backward_adj_floats(ci.max_nb, ci.max_nv, ci.max_na));
+  sh.head_floats = round16(backward_adj_head_floats(ci.max_nb, ci.max_nv, ci.max_na));
+  sh.c_floats = round16(44LL * ci.max_nb);
   const long long seg = round16(backward_seg_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na, ce));
   const long long lim = (long long)(kSmemLimit / 4);
-  // measured on B300 (diff1024 trees): the forward step's temporaries alone in shared memory,
-  // with more worlds resident per SM, beat keeping the backward's there too (one world per SM)
-  if (sh.fwd_floats <= lim) {
-    sh.mode = 1;
-    sh.smem_floats = sh.fwd_floats;
-    sh.global_floats = sh.adj_floats + seg;
-  } else {
-    sh.mode = 0;
-    sh.smem_floats = 0;
-    sh.global_floats = sh.fwd_floats + sh.adj_floats + seg;
+  // resident groups per SM the registers allow (the kernel is built for 128 per thread)
+  const long long by_regs = std::min<long long>(std::min<long long>(2048, 65536 / 128) / p.tpw, 16);
+  // The placement with the most groups resident per SM, then the most in shared memory
+  // (measured on B300 with diff1024 trees: more resident worlds beat more shared memory per
+  // world, and at equal residency the backward's temporaries in shared memory beat global).
+  struct Placement {
+    int mode;
+    long long smem, global;
+  };
+  const Placement cand[4] = {{2, sh.fwd_floats + sh.adj_floats, seg},
+                             {3, sh.fwd_floats + sh.head_floats, sh.c_floats + seg},
+                             {1, sh.fwd_floats, sh.adj_floats + seg},
+                             {0, 0, sh.fwd_floats + sh.adj_floats + seg}};
+  long long best = -1;
+  for (const Placement& c : cand) {
+    if (c.smem > lim) continue;
+    const long long per = c.smem > 0 ? std::min(by_regs, lim / c.smem) : by_regs;
+    if (per > best) {
+      best = per;
+      sh.mode = c.mode;
+      sh.smem_floats = c.smem;
+      sh.global_floats = c.global;
+    }
   }
   sh.global_floats = (sh.global_floats + 63) / 64 * 64;
   // groups per block: as many as share one block's shared memory (at most kBackMaxThreads threads)
@@ -1114,8 +1129,8 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
               ? (int)std::max<long long>(1, std::min<long long>(lim / sh.smem_floats, kBackMaxThreads / p.tpw))
               : 1;
   p.gpb = std::min(p.gpb, 16);
-  // resident groups per SM (the kernel is built for 128 registers per thread)
-  long long per_sm = std::min<long long>(std::min<long long>(2048, 65536 / 128) / p.tpw, 16);
+  // resident groups per SM
+  long long per_sm = by_regs;
   if (sh.smem_floats > 0) per_sm = std::min<long long>(per_sm, (long long)(kSmemLimit / 4) / sh.smem_floats);
   per_sm = std::max<long long>(per_sm, 1);
   const size_t worlds = (size_t)(ci.q_end - ci.q_begin);

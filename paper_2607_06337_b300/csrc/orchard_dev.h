@@ -158,11 +158,14 @@ struct BackArgs {
 };
 // Where a backward group keeps its temporaries (see adjoint_kernel.cu): mode 0 all in its
 // global slot, 1 the forward step's in shared memory, 2 the forward's and the backward's in
-// shared memory; the checkpoint segment's snapshots always in the global slot.
+// shared memory, 3 the forward's and the backward's but the C slots in shared memory; the
+// checkpoint segment's snapshots always in the global slot.
 struct BackShape {
   int mode;
   long long fwd_floats;     // forward temporaries of the class's largest world (WsLayout)
   long long adj_floats;     // backward temporaries (AdjLayout)
+  long long head_floats;    // the part of them before the C slots (AdjLayout::head)
+  long long c_floats;       // the C slots (44 per body)
   long long smem_floats;    // per group in shared memory
   long long global_floats;  // per slot of the workspace
 };
@@ -173,6 +176,7 @@ void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st,
                      const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
 cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 long long backward_adj_floats(int nb, int nv, int na);
+long long backward_adj_head_floats(int nb, int nv, int na);
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
