@@ -44,8 +44,8 @@ A_APPLE = 294
 A_ENTRY = 5
 A_TIP = 21
 
-MODEL_BYTES_PER_BODY = 6 * 16   # int4 + 5 float4
-MODEL_BYTES_PER_DOF = 16        # int4
+MODEL_BYTES_PER_BODY = 7 * 16   # 2 int4 (topology, joint rows) + 5 float4
+MODEL_BYTES_PER_DOF = 0         # (the DOFs' rows are found through their body)
 MODEL_BYTES_PER_ENTRY = 2       # uint16 ancestor id
 MODEL_BYTES_PER_APPLE = 36      # 2 float4 + int
 STATE_BYTES_PER_DOF = 8         # q, qd
