@@ -46,7 +46,8 @@ class OFlags(C.Structure):
     _fields_ = [("dt", C.c_double), ("alpha_implicit_spring", C.c_int32), ("tether_implicit", C.c_int32),
                 ("n_break", C.c_int32), ("n_pull", C.c_int32), ("n_tension", C.c_int32),
                 ("gamma_tension", C.c_double), ("clamp_factor", C.c_double), ("dense_limit", C.c_int32),
-                ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double)]
+                ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double),
+                ("lin_damping", C.c_double), ("ang_damping", C.c_double), ("snapped_lin_damping", C.c_double)]
 
 
 class OState(C.Structure):
@@ -119,7 +120,9 @@ def _forest_struct(f, keep: _Keep) -> OForest:
 
 def _flags_struct(fl, dense_limit: int) -> OFlags:
     return OFlags(fl.dt, fl.alpha_implicit_spring, fl.tether_implicit, fl.n_break, fl.n_pull, fl.n_tension,
-                  fl.gamma_tension, fl.clamp_factor, dense_limit, fl.break_ramp_s, fl.break_ramp_factor)
+                  fl.gamma_tension, fl.clamp_factor, dense_limit, fl.break_ramp_s, fl.break_ramp_factor,
+                  getattr(fl, "lin_damping", 0.0), getattr(fl, "ang_damping", 0.0),
+                  getattr(fl, "snapped_lin_damping", 0.1))
 
 
 @dataclass

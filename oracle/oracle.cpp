@@ -19,7 +19,10 @@
 //     attached apple when the tether reaction is taken implicitly), solved densely (LDL^T)
 //     for small trees and by the tree-sparse LTDL factorisation for large ones;
 //   * tether, reaction, clamp and detachment (Sec. IV-C, Eqs. 6-7), rupture with hysteresis
-//     (Sec. IV-B, Eq. 5), semi-implicit update.
+//     (Sec. IV-B, Eq. 5), semi-implicit update;
+//   * velocity-proportional damping of the bodies, force -c_v m v and torque -c_omega I omega
+//     at the centre of mass (Sec. IV-A), with the linear part reduced on a snapped sub-tree
+//     (Sec. IV-B), taken explicitly at the step's start velocities.
 // Every function is templated on the scalar so the same code runs in double and in
 // std::complex<double> (complex-step derivatives for the adjoint checks).
 //
@@ -203,6 +206,9 @@ typedef struct {
   int32_t dense_limit;  // solve densely when n_v <= dense_limit, else by tree LTDL
   double break_ramp_s;      // post-break friction surrogate ramps over this time (s)
   double break_ramp_factor; // ... from kd to this multiple of kd
+  double lin_damping;       // c_v (1/s): force -c_v m v at each body's centre of mass
+  double ang_damping;       // c_omega (1/s): torque -c_omega I omega
+  double snapped_lin_damping;  // factor on c_v for a body on a snapped sub-tree
 } OFlags;
 
 typedef struct {
@@ -465,17 +471,26 @@ void mass_matrix(const World& W, const OFlags& fl, const Kin<T>& K, const AppleL
   }
 }
 
-// c(q, qd) = sum_b J_b^T [m_b (a_c - g); I a + w x I w] - sum_apples J_h^T f_app.
+// c(q, qd) = sum_b J_b^T ([m_b (a_c - g); I a + w x I w] - [F_d; tau_d]) - sum_apples J_h^T f_app,
+// with the damping wrench of body b at its centre of mass (Sec. IV-A): F_d = -c_v s_b m_b v_c,
+// tau_d = -c_omega I_b w_b, where s_b is the snapped factor on a snapped sub-tree (Sec. IV-B:
+// "its linear drag is also reduced") and 1 elsewhere. broken: the joints' flags (null: none).
 template <class T>
-void bias_force(const World& W, const Kin<T>& K, const AppleLoads<T>* A, std::vector<T>& c) {
+void bias_force(const World& W, const OFlags& fl, const Kin<T>& K, const AppleLoads<T>* A, const int32_t* broken,
+                std::vector<T>& c) {
   c.assign(W.nv, T(0));
   V3<T> g = dv<T>(W.g);
+  const std::vector<int> snapped = broken ? snapped_bodies(W, broken) : std::vector<int>(W.nb, 0);
   for (int b = 0; b < W.nb; ++b) {
     V3<T> r = K.c[b] - K.x[b];
     V3<T> ac = K.ax[b] + cross(K.al[b], r) + cross(K.w[b], cross(K.w[b], r));
     M3<T> I = world_inertia(W, K, b);
     V3<T> F = T(W.mass[b]) * (ac - g);
     V3<T> N = mvec(I, K.al[b]) + cross(K.w[b], mvec(I, K.w[b]));
+    const double cv = fl.lin_damping * (snapped[b] ? fl.snapped_lin_damping : 1.0);
+    const V3<T> vc = K.vx[b] + cross(K.w[b], r);
+    F = F + T(cv * W.mass[b]) * vc;                 // minus F_d
+    N = N + T(fl.ang_damping) * mvec(I, K.w[b]);    // minus tau_d
     for (int i : W.chain[b]) c[i] += dot(jac_point(W, K, i, K.c[b]), F) + dot(K.e[i], N);
   }
   if (A) {
@@ -584,7 +599,7 @@ void step_world(const World& W, const OFlags& fl, WState<T>& s, const Gains<T>& 
   apple_loads(W, fl, K, s.ax.data(), s.av.data(), s.detached.data(), s.broken.data(), fext, A);
   std::vector<T> M, c;
   mass_matrix(W, fl, K, &A, s.detached.data(), M);
-  bias_force(W, K, &A, c);
+  bias_force(W, fl, K, &A, s.broken.data(), c);
   int n = W.nv;
   std::vector<T> r(n);
   for (int i = 0; i < n; ++i) {
@@ -793,7 +808,7 @@ int oracle_eval(const OForest* f, const OFlags* fl, int w, const double* q, cons
   apple_loads(W, *fl, K, ax ? ax : zeros.data(), av ? av : zeros.data(), det.data(), nullptr, fext ? fext : zeros.data(), A);
   std::vector<double> M, c;
   mass_matrix(W, *fl, K, ax ? &A : nullptr, det.data(), M);
-  bias_force(W, K, ax ? &A : nullptr, c);
+  bias_force(W, *fl, K, ax ? &A : nullptr, nullptr, c);
   if (M_out) std::copy(M.begin(), M.end(), M_out);
   if (c_out) std::copy(c.begin(), c.end(), c_out);
   for (int b = 0; b < W.nb; ++b) {

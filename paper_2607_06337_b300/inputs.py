@@ -53,6 +53,9 @@ class Flags:
     break_ramp_s: float = 1.5        # post-break friction surrogate: ramp time (s)
     break_ramp_factor: float = 5.0   # ... from kd up to this multiple of kd
     fp64_twig_diam: float = 0.0      # joints thinner than this use float64 pivots (0: none)
+    lin_damping: float = 0.0         # c_v (1/s): force -c_v m v at each body's centre of mass
+    ang_damping: float = 0.0         # c_omega (1/s): torque -c_omega I omega
+    snapped_lin_damping: float = 0.1  # factor on c_v for a body on a snapped sub-tree
 
 
 @dataclass
