@@ -105,6 +105,13 @@ typedef struct ot_model_flags {
   double break_ramp_factor;      /* (5.0) damper ramping from kd to factor * kd over ramp_s (s) */
   double fp64_twig_diam;         /* (0) joints of segments thinner than this (m) invert their
                                     factorisation pivot block in FP64; 0: none */
+  /* Velocity-proportional damping of every segment body (Sec. IV-A), a force -c_v m v_c and a
+     torque -c_omega I_c omega at its centre of mass, taken explicitly at the step's start
+     velocities; on a snapped sub-tree the linear part is scaled by snapped_lin_damping
+     (Sec. IV-B). All >= 0. */
+  double lin_damping;            /* (0) c_v, 1/s */
+  double ang_damping;            /* (0) c_omega, 1/s */
+  double snapped_lin_damping;    /* (0.1) factor on c_v on a snapped sub-tree */
 } ot_model_flags;
 
 /* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */

@@ -371,12 +371,32 @@ HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, cons
     vb_ = vb_ + mb * l2b;
     hb = hb - cross(w, l2b);
     wb_ = wb_ - cross(l2b, h);
+    // body damping: its part of (n, f) is (c_w I_c w + kv r x v_c, kv v_c), I_c = R D R^T,
+    // v_c = vin + w x r, kv = c_v m (c_v reduced on a snapped sub-tree); with
+    // gv = kv (nb x r + fb) its virtual work is c_w nb . I_c w + gv . v_c
+    f3 rdb = mk(0, 0, 0);                               // its cotangent of r
+    g33 Gc = {mk(0, 0, 0), mk(0, 0, 0), mk(0, 0, 0)};  // ... and of I_c
+    if (a.cv != 0.f || a.cw != 0.f) {
+      const float kv = (ws[L.SN + b] != 0.f ? a.cv_snap : a.cv) * mb;
+      const f3 vc = vin + cross(w, r);
+      const f3 wl = mk(dot(R.c0, w), dot(R.c1, w), dot(R.c2, w));
+      const f3 Icw = (Di[0] * wl.x) * R.c0 + (Di[1] * wl.y) * R.c1 + (Di[2] * wl.z) * R.c2;
+      lwb = lwb + sp * (a.cw * Icw + kv * cross(r, vc));
+      lvb = lvb + (sp * kv) * vc;
+      const f3 gv = kv * (cross(nb, r) + fb);
+      const f3 nl = mk(dot(R.c0, nb), dot(R.c1, nb), dot(R.c2, nb));
+      const f3 Icnb = (Di[0] * nl.x) * R.c0 + (Di[1] * nl.y) * R.c1 + (Di[2] * nl.z) * R.c2;
+      vb_ = vb_ + gv;
+      wb_ = wb_ + a.cw * Icnb + cross(r, gv);
+      rdb = kv * cross(vc, nb) + cross(gv, w);
+      g_add_outer(Gc, a.cw * nb, w);
+    }
     // Io = R D R^T + m (|r|^2 1 - r r^T), h = m r, r = R com
     const float trG = G.c0.x + G.c1.y + G.c2.z;
-    const f3 rb = mb * hb + mb * (2.f * trG * r - g_mulT_plus(G, r));
-    Rb_.c0 = Rb_.c0 + com.x * rb + Di[0] * g_mulT_plus(G, R.c0);
-    Rb_.c1 = Rb_.c1 + com.y * rb + Di[1] * g_mulT_plus(G, R.c1);
-    Rb_.c2 = Rb_.c2 + com.z * rb + Di[2] * g_mulT_plus(G, R.c2);
+    const f3 rb = mb * hb + mb * (2.f * trG * r - g_mulT_plus(G, r)) + rdb;
+    Rb_.c0 = Rb_.c0 + com.x * rb + Di[0] * (g_mulT_plus(G, R.c0) + g_mulT_plus(Gc, R.c0));
+    Rb_.c1 = Rb_.c1 + com.y * rb + Di[1] * (g_mulT_plus(G, R.c1) + g_mulT_plus(Gc, R.c1));
+    Rb_.c2 = Rb_.c2 + com.z * rb + Di[2] * (g_mulT_plus(G, R.c2) + g_mulT_plus(Gc, R.c2));
   }
 
   // apples hanging from this body
@@ -747,7 +767,7 @@ HD void spring_joint(const DevModel& m, const WState& s, const StepArgs& a, cons
     skd += lam * q1;
   }
   const float kfac = s.broken[b] ? 0.f : 1.f;
-  const float kdfac = P3.w != 0.f ? kd / P3.w : 0.f;
+  const float kdfac = damper_factor(s, a, b, t_abs);  // d kd' / d kd (also at kd = 0)
   if (ba.dk) ba.dk[gb] += -dt * kfac * sk;
   if (ba.dkd) ba.dkd[gb] += -dt * kdfac * skd;
 }

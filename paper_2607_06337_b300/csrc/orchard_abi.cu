@@ -545,6 +545,9 @@ StepArgs base_args(const ot_model* m, double dt) {
   a.clamp = (float)m->flags.clamp_factor;
   a.ramp_inv = m->flags.break_ramp_s > 0 ? (float)(dt / m->flags.break_ramp_s) : 0.f;
   a.ramp_gain = (float)(m->flags.break_ramp_factor - 1.0);
+  a.cv = (float)m->flags.lin_damping;
+  a.cv_snap = (float)(m->flags.lin_damping * m->flags.snapped_lin_damping);
+  a.cw = (float)m->flags.ang_damping;
   a.single_world = -1;
   a.NB = m->P.NB; a.NV = m->P.NV; a.NA = m->P.NA;
   a.n_tips_total = m->P.NT;
@@ -654,7 +657,10 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   if (flags->n_break < 1 || flags->n_pull < 1 || flags->n_tension < 1 ||
       (flags->alpha_implicit_spring != 0 && flags->alpha_implicit_spring != 1) ||
       (flags->tether_implicit != 0 && flags->tether_implicit != 1) || !(flags->clamp_factor > 0) ||
-      !(flags->gamma_tension > 0) || !(flags->break_ramp_s >= 0) || !(flags->break_ramp_factor >= 0))
+      !(flags->gamma_tension > 0) || !(flags->break_ramp_s >= 0) || !(flags->break_ramp_factor >= 0) ||
+      !(flags->lin_damping >= 0) || !std::isfinite(flags->lin_damping) || !(flags->ang_damping >= 0) ||
+      !std::isfinite(flags->ang_damping) || !(flags->snapped_lin_damping >= 0) ||
+      !std::isfinite(flags->snapped_lin_damping))
     return OT_EINVAL;
   ot_model* m = new ot_model();
   ot_status st = pack(desc, m->P, flags->fp64_twig_diam);

@@ -80,6 +80,8 @@ struct StepArgs {
   float gamma, clamp;
   float ramp_inv;       // 1 / (post-break ramp time in steps), 0: no ramp (full factor at once)
   float ramp_gain;      // post-break damper factor minus one
+  float cv, cv_snap;    // body damping c_v, and c_v on a snapped sub-tree (1/s)
+  float cw;             // body damping c_omega (1/s)
   int step0;            // absolute index of the first step of this launch
   int n_steps;
   const float* pull_force;  // [NA*3] or null

@@ -224,18 +224,20 @@ HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
   return f;
 }
 
-// Joint gains of this step: a broken joint has no spring and keeps the torn-fibre friction,
+// The joint damper's factor on kd this step: 1, or for a broken joint the torn-fibre friction,
 // a damper growing from kd to (1 + ramp_gain) kd over the ramp time (Sec. IV-B).
-HD void joint_gains(const WState& s, const StepArgs& a, int b, float4 P3, int t_abs, float* k, float* kd) {
-  if (!s.broken[b]) {
-    *k = P3.z;
-    *kd = P3.w;
-    return;
-  }
+HD float damper_factor(const WState& s, const StepArgs& a, int b, int t_abs) {
+  if (!s.broken[b]) return 1.f;
   const float since = (float)(t_abs - s.break_step[b]);
   const float ramp = a.ramp_inv > 0.f ? fminf(since * a.ramp_inv, 1.f) : 1.f;
-  *k = 0.f;
-  *kd = (1.f + a.ramp_gain * ramp) * P3.w;
+  return 1.f + a.ramp_gain * ramp;
+}
+
+// Joint gains of this step: a broken joint has no spring and its damper is scaled by
+// damper_factor.
+HD void joint_gains(const WState& s, const StepArgs& a, int b, float4 P3, int t_abs, float* k, float* kd) {
+  *k = s.broken[b] ? 0.f : P3.z;
+  *kd = s.broken[b] ? damper_factor(s, a, b, t_abs) * P3.w : P3.w;
 }
 
 // The model records a sweep needs of one body, loaded together (independent addresses, so
@@ -307,7 +309,7 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
 }
 
 // Phase 1b for one body (all bodies at once, after 1a): spatial inertia, own Newton-Euler
-// force, apple loads.
+// force less the body damping, apple loads.
 HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                       float* ws, int b, int t_abs, f3 g) {
   const int gb = v.b0 + b;
@@ -340,6 +342,16 @@ HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, con
   const f3 n2 = mul(I.I, w) + cross(I.h, vin), f2 = mb * vin - cross(I.h, w);
   f3 n = n1 + cross(w, n2) + cross(vin, f2);
   f3 f = f1 + cross(w, f2);
+  // velocity-proportional damping at the centre of mass (Sec. IV-A), F = -c_v m v_c (c_v
+  // reduced on a snapped sub-tree, Sec. IV-B) and tau = -c_omega I_c w, applied to the body
+  if (a.cv != 0.f || a.cw != 0.f) {
+    const float kv = (snapped ? a.cv_snap : a.cv) * mb;
+    const f3 vc = vin + cross(w, r);
+    const f3 wl = mk(dot(R.c0, w), dot(R.c1, w), dot(R.c2, w));
+    const f3 Icw = (P2.w * wl.x) * R.c0 + (P3.x * wl.y) * R.c1 + (P3.y * wl.z) * R.c2;
+    n = n + a.cw * Icw + kv * cross(r, vc);  // minus (tau + r x F)
+    f = f + kv * vc;                          // minus F
+  }
 
   // apples hanging from this body
   const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;

@@ -55,7 +55,8 @@ class ModelFlags(C.Structure):
                 ("n_break", C.c_int32), ("n_pull", C.c_int32), ("n_tension", C.c_int32),
                 ("gamma_tension", C.c_double), ("clamp_factor", C.c_double),
                 ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double),
-                ("fp64_twig_diam", C.c_double)]
+                ("fp64_twig_diam", C.c_double), ("lin_damping", C.c_double), ("ang_damping", C.c_double),
+                ("snapped_lin_damping", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -183,7 +184,8 @@ def make_flags(flags) -> ModelFlags:
     return ModelFlags(int(flags.alpha_implicit_spring), int(flags.tether_implicit), int(flags.n_break),
                       int(flags.n_pull), int(flags.n_tension), float(flags.gamma_tension), float(flags.clamp_factor),
                       float(flags.break_ramp_s), float(flags.break_ramp_factor),
-                      float(getattr(flags, "fp64_twig_diam", 0.0)))
+                      float(getattr(flags, "fp64_twig_diam", 0.0)), float(getattr(flags, "lin_damping", 0.0)),
+                      float(getattr(flags, "ang_damping", 0.0)), float(getattr(flags, "snapped_lin_damping", 0.1)))
 
 
 # ------------------------------------------------------------------------------------------

@@ -122,6 +122,12 @@ def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
     neg = orch.make_flags(I.Flags(fp64_twig_diam=-1.0))
     assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(neg), C.c_void_p(256), 1 << 20, None,
                                            C.byref(h)) == orch.OT_EINVAL
+    # body damping coefficients must be finite and non-negative
+    for kw in (dict(lin_damping=-1.0), dict(ang_damping=float("nan")), dict(snapped_lin_damping=-0.5),
+               dict(lin_damping=float("inf"))):
+        bad_d = orch.make_flags(I.Flags(**kw))
+        assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(bad_d), C.c_void_p(256), 1 << 20, None,
+                                               C.byref(h)) == orch.OT_EINVAL, kw
     assert h.value is None
 
 

@@ -156,6 +156,46 @@ def test_adjoint_with_breaks_and_detaches_masks_frozen():
         assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, 2e-3, f"world {w} with events")
 
 
+def test_adjoint_with_body_damping_and_events():
+    """Velocity-proportional body damping on (Sec. IV-A), with the linear part reduced on snapped
+    sub-trees (Sec. IV-B), in worlds where branches break and apples detach: the adjoint of the
+    damping wrench against the oracle's complex-step derivative, masks frozen."""
+    f = I.make_forest(I.BATCH, worlds=[23, 79])
+    fl = I.Flags(lin_damping=3.0, ang_damping=2.0, snapped_lin_damping=0.2)
+    n = 200
+    st, rec = O.rollout(f, fl, n, record_tips=True, near_eps=PAR.NEAR)
+    assert st.broken.sum() > 0
+    rng = np.random.default_rng(4)
+    target = rec["tips"] + rng.normal(0.0, 0.02, rec["tips"].shape)
+    g, ev, _ = gpu_gradients(f, fl, n, 25, target)
+    for w in range(f.n_worlds):
+        ref_ev = PAR.events(st.broken, st.break_step, st.detached, st.detach_step, f, w)
+        got_ev = PAR.events(ev["broken"], ev["break_step"], ev["detached"], ev["detach_step"], f, w)
+        assert got_ev == ref_ev, f"world {w}: event sets differ, the gradients are not comparable"
+        kinds, idx = sample_coords(f, w, 4, rng)
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, 2e-3, f"world {w} with damping")
+
+
+def test_damper_gradient_of_a_joint_without_damper():
+    """dL/dkd of a joint whose kd is 0 (the compliant root of a small tree): the step's damper
+    is kd' = kd (times the post-break factor), so the derivative is that of kd', not zero."""
+    from tests import _trees as T
+    f = T.small_random_tree(2, n_b=7, depth=3, ndof=2, root_ndof=2)
+    assert f.kd[0] == 0.0
+    fl = I.Flags()
+    n = 60
+    _, rec = O.rollout(f, fl, n, record_tips=True)
+    target = rec["tips"] + np.random.default_rng(8).normal(0.0, 0.01, rec["tips"].shape)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    kinds = np.array([1] * f.n_bodies)
+    idx = np.arange(f.n_bodies)
+    g_cs, _ = O.grad(f, fl, 0, n, target, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+    assert abs(g_cs[0]) > 1e-3 * np.abs(g_cs).max()
+    assert_close_per_kind(pick(f, 0, g, kinds, idx), g_cs, kinds, TOL_FAR, "kd with a zero damper")
+
+
 def test_checkpoint_interval_does_not_change_the_gradient():
     """Every checkpoint interval, including one that does not divide the step count and one
     longer than the rollout, gives the same gradient: the replayed segments run the forward's

@@ -60,6 +60,20 @@ def test_config0_plain_parity_1000_steps(form):
     assert (g["status"] == 0).all()
 
 
+def test_body_damping_with_pulls_and_events():
+    """Velocity-proportional body damping on (Sec. IV-A), reduced linear drag on snapped
+    sub-trees (Sec. IV-B): uneven trees with random pulls, q gate and identical event sets."""
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 3, 17, 33])
+    fl = I.Flags(lin_damping=3.0, ang_damping=2.0, snapped_lin_damping=0.2)
+    g = _run(f, fl, 1000)
+    st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    assert sum(r["n_events"] for r in rep) > 5  # breaks put bodies on snapped sub-trees
+    st0, _ = O.rollout(f, I.Flags(), 1000)
+    assert np.abs(st.q - st0.q).max() > 1e-3  # the damping does change the motion
+
+
 def test_step_by_step_equals_rollout():
     f = I.make_forest(I.BATCH, worlds=[5, 6, 7])
     fl = I.Flags()
