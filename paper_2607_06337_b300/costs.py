@@ -90,10 +90,11 @@ def flops_per_step(forest) -> float:
 
 
 def adjoint_flops_per_step(forest) -> float:
-    """Flops of one step of the backward pass (two forward recomputations included)."""
+    """Flops of one step of the backward pass: the segment replay's forward step (whose records
+    the reverse reads, so the step runs once more, not twice) plus the reverse terms."""
     nb, nv, na, E, P = world_terms(forest)
     nt = np.diff(forest.tip_off).astype(np.int64)
-    return 2.0 * flops_per_step(forest) + float(np.sum(A_BODY * nb + A_DOF * nv + A_APPLE * na + A_ENTRY * E +
+    return 1.0 * flops_per_step(forest) + float(np.sum(A_BODY * nb + A_DOF * nv + A_APPLE * na + A_ENTRY * E +
                                                         A_TIP * nt))
 
 
