@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=24.0)
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-damped", action="store_true", help="skip the body-damping leg")
     p.add_argument("--adj-workload", default="diff1024", help="diff1024 (default) or stress8192")
     p.add_argument("--sweep", action="store_true",
                    help="add a world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
@@ -332,6 +333,37 @@ def fwd_adjoint(args, dev, rank, ws):
     }
 
 
+def damped_leg(args, dev, forest, S, flush):
+    """The same batch with the body damping of Sec. IV-A on (the reduced linear drag on snapped
+    sub-trees included): its own model upload, autotune, one warm-up and one timed rollout."""
+    import torch
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+    fl = I.Flags(lin_damping=3.0, ang_damping=2.0, snapped_lin_damping=0.2)
+    sim = B.Simulator(forest, fl, device=dev)
+    stream = torch.cuda.current_stream()
+    sim.reset()
+    sim.autotune(n_steps=20)
+    sim.reset()
+    sim.rollout(S)
+    flush.fill_(1)
+    sim.reset()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.rollout(S)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out = {"flags": {"lin_damping": fl.lin_damping, "ang_damping": fl.ang_damping,
+                     "snapped_lin_damping": fl.snapped_lin_damping},
+           "value": costs.body_count(forest) * S / (ms / 1e3), "unit": UNIT, "ms": ms,
+           "frozen_worlds": int((sim.status.cpu().numpy() & 1).sum())}
+    del sim
+    return out
+
+
 def world_sweep(args, dev):
     """Batched (persistent, graph, autotuned) and plain (one launch per world per step) forward
     body-steps/s at 1024..65536 worlds of the sweep16384 trees (300 bodies, 60 apples). The
@@ -470,6 +502,9 @@ def run_ours(args):
     e2e_value = ws * bodies * S / statistics.mean(e2e_times)
 
     adj = None if args.no_adjoint else fwd_adjoint(args, dev, rank, ws)
+    damped = None if args.no_damped or ws > 1 else damped_leg(args, dev, forest, S, flush)
+    if damped:
+        damped["vs_undamped"] = damped["value"] / (value / ws)
 
     # the plain form: one launch per world per step, no graph, no autotune
     plain = None
@@ -529,6 +564,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "plain": plain,
             "fwd_adj": adj,
+            "damped": damped,
             "sweep": sweep,
             "clocks": clocks,
             "frozen_worlds": int((status & 1).sum()),
