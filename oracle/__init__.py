@@ -47,7 +47,8 @@ class OFlags(C.Structure):
                 ("n_break", C.c_int32), ("n_pull", C.c_int32), ("n_tension", C.c_int32),
                 ("gamma_tension", C.c_double), ("clamp_factor", C.c_double), ("dense_limit", C.c_int32),
                 ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double),
-                ("lin_damping", C.c_double), ("ang_damping", C.c_double), ("snapped_lin_damping", C.c_double)]
+                ("lin_damping", C.c_double), ("ang_damping", C.c_double), ("snapped_lin_damping", C.c_double),
+                ("rail_speed", C.c_double), ("rail_fade_speed", C.c_double), ("rail_brake", C.c_double)]
 
 
 class OState(C.Structure):
@@ -122,7 +123,8 @@ def _flags_struct(fl, dense_limit: int) -> OFlags:
     return OFlags(fl.dt, fl.alpha_implicit_spring, fl.tether_implicit, fl.n_break, fl.n_pull, fl.n_tension,
                   fl.gamma_tension, fl.clamp_factor, dense_limit, fl.break_ramp_s, fl.break_ramp_factor,
                   getattr(fl, "lin_damping", 0.0), getattr(fl, "ang_damping", 0.0),
-                  getattr(fl, "snapped_lin_damping", 0.1))
+                  getattr(fl, "snapped_lin_damping", 0.1), getattr(fl, "rail_speed", 0.0),
+                  getattr(fl, "rail_fade_speed", 0.0), getattr(fl, "rail_brake", 0.0))
 
 
 @dataclass

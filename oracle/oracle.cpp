@@ -22,7 +22,9 @@
 //     (Sec. IV-B, Eq. 5), semi-implicit update;
 //   * velocity-proportional damping of the bodies, force -c_v m v and torque -c_omega I omega
 //     at the centre of mass (Sec. IV-A), with the linear part reduced on a snapped sub-tree
-//     (Sec. IV-B), taken explicitly at the step's start velocities.
+//     (Sec. IV-B), taken explicitly at the step's start velocities;
+//   * the three rails on the applied force of an apple (App. B: impulse cap, power fade, speed
+//     brake), at the step's start velocity.
 // Every function is templated on the scalar so the same code runs in double and in
 // std::complex<double> (complex-step derivatives for the adjoint checks).
 //
@@ -209,6 +211,9 @@ typedef struct {
   double lin_damping;       // c_v (1/s): force -c_v m v at each body's centre of mass
   double ang_damping;       // c_omega (1/s): torque -c_omega I omega
   double snapped_lin_damping;  // factor on c_v for a body on a snapped sub-tree
+  double rail_speed;        // v_lim (m/s) of the applied-force rails, 0: rails off
+  double rail_fade_speed;   // v_fade (m/s), 0 <= v_fade < v_lim
+  double rail_brake;        // c_b (1/s) of the speed brake
 } OFlags;
 
 typedef struct {
@@ -388,6 +393,34 @@ std::vector<int> snapped_bodies(const World& W, const int32_t* broken) {
   return s;
 }
 
+// The three rails of App. B on the applied force f of a body of mass m and velocity v (this
+// step's start):
+//   (1) impulse cap: the velocity f alone adds in one step, dt |f| / m, is at most v_lim;
+//   (2) power fade: the component of f along v, when it pushes along v, fades linearly from
+//       full at |v| = v_fade to none at |v| = v_lim;
+//   (3) speed brake: above v_lim, -c_b m (|v| - v_lim) v / |v| is added.
+// Rails off (v_lim = 0) or no applied force: f unchanged. At rest, below the cap, nothing
+// changes ("none of which affects static loading").
+template <class T> V3<T> rails(const OFlags& fl, T m, V3<T> v, V3<T> f) {
+  if (!(fl.rail_speed > 0)) return f;
+  T fn = sqrt(dot(f, f));
+  if (re(fn) == 0.0) return f;
+  const double vl = fl.rail_speed, vf = fl.rail_fade_speed;
+  T cap = m * T(vl / fl.dt);
+  if (re(fn) > re(cap)) f = (cap / fn) * f;
+  T s = sqrt(dot(v, v));
+  if (re(s) > vf) {
+    V3<T> vh = (T(1) / s) * v;
+    T p = dot(f, vh);
+    if (re(p) > 0) {
+      T phi = re(s) >= vl ? T(0) : (T(vl) - s) / T(vl - vf);
+      f = f - ((T(1) - phi) * p) * vh;
+    }
+    if (re(s) > vl) f = f - (T(fl.rail_brake) * m * (s - T(vl))) * vh;
+  }
+  return f;
+}
+
 template <class T>
 void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax, const T* av,
                  const int32_t* detached, const int32_t* broken, const double* fext, AppleLoads<T>& A) {
@@ -407,10 +440,10 @@ void apple_loads(const World& W, const OFlags& fl, const Kin<T>& K, const T* ax,
     V3<T> va = {av[3 * a], av[3 * a + 1], av[3 * a + 2]};
     V3<T> fs = T(-W.ks[a]) * ua;
     A.tension[a] = sqrt(dot(fs, fs));
-    V3<T> fe = dv<T>(fext + 3 * a);
+    T m = T(W.am[a]);
+    const V3<T> fe = rails(fl, m, va, dv<T>(fext + 3 * a));  // the applied force, through the rails
     A.pull[a] = sqrt(dot(fe, fe));
     V3<T> zero = {T(0), T(0), T(0)};
-    T m = T(W.am[a]);
     if (detached[a]) {
       A.fapp[a] = zero;
       A.tension[a] = T(0);

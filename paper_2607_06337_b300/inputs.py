@@ -56,6 +56,9 @@ class Flags:
     lin_damping: float = 0.0         # c_v (1/s): force -c_v m v at each body's centre of mass
     ang_damping: float = 0.0         # c_omega (1/s): torque -c_omega I omega
     snapped_lin_damping: float = 0.1  # factor on c_v for a body on a snapped sub-tree
+    rail_speed: float = 0.0          # v_lim (m/s) of the applied-force rails (App. B), 0: off
+    rail_fade_speed: float = 0.0     # v_fade (m/s): the power fade starts here (< v_lim)
+    rail_brake: float = 0.0          # c_b (1/s): speed brake above v_lim
 
 
 @dataclass
