@@ -112,6 +112,13 @@ typedef struct ot_model_flags {
   double lin_damping;            /* (0) c_v, 1/s */
   double ang_damping;            /* (0) c_omega, 1/s */
   double snapped_lin_damping;    /* (0.1) factor on c_v on a snapped sub-tree */
+  /* Rails on an apple's applied force (App. B), at the step's start velocity v: (1) impulse
+     cap, dt |f| / m <= v_lim; (2) power fade, the component of f pushing along v scaled by
+     (v_lim - |v|) / (v_lim - v_fade) between v_fade and v_lim (0 above); (3) speed brake,
+     -c_b m (|v| - v_lim) v / |v| added above v_lim. Only where an applied force acts. */
+  double rail_speed;             /* (0) v_lim, m/s; 0: rails off */
+  double rail_fade_speed;        /* (0) v_fade, m/s, 0 <= v_fade < v_lim when the rails are on */
+  double rail_brake;             /* (0) c_b, 1/s, >= 0 */
 } ot_model_flags;
 
 /* Launch schedule of a rollout for one size class of worlds (set by the autotuner or by hand). */

@@ -418,13 +418,11 @@ HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, cons
       const bool snapped = ws[L.SN + b] != 0.f;
       if (!snapped) {
         const float ma = A0.w, ks = A1.x, csd = A1.y, fdet = A1.z;
-        const f3 u = ld3(s.ax + 3 * ai), vv = ld3(s.av + 3 * ai);
-        const f3 fe = apple_force(a, ga, t_abs);
+        const f3 u = ld3(s.ax + 3 * ai);
         const float D = ma + dt * csd + dt * dt * ks;
         const float beta = dt * dt * ks / D;
         const f3 fr = ks * u - ma * g;
-        const f3 avec = (1.f / D) * (ma * vv + dt * (fe + ma * g - ks * u));
-        (void)beta;
+        const f3 avec = ld3(ws + L.AT + 10 * ai);  // the step's a, as recorded
         const float nfr = sqrtf(dot(fr, fr)), fc = a.clamp * fdet;
         const bool clamped = nfr > fc;
         const float sc = clamped ? fc / nfr : 1.f;
@@ -443,6 +441,7 @@ HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, cons
           const float psi_core = dot(wv, G) - dt * kap0 * dot(wv, vh1);
           ubar = (dt * sc * kap0) * wv;
           if (clamped) ubar = ubar + (dt * psi_core * (-sc * ks / (nfr * nfr))) * fr;
+          // avec = (ma v + dt (f + ...)) / D; the rails' dependence of f on v is in rails_adjoint
           vbar = (dt * sc * dt * ks * ma / D) * wv;
         } else {
           // psi_a = dt w . (sc fr)
@@ -772,6 +771,47 @@ HD void spring_joint(const DevModel& m, const WState& s, const StepArgs& a, cons
   if (ba.dkd) ba.dkd[gb] += -dt * kdfac * skd;
 }
 
+// The rails' part of the cotangent of each apple's start velocity v (App. B: the rails make the
+// applied force f a function of v). f enters the apple update, a = (m v + dt (f + m g - k_s u))
+// / D when attached and v' = v + dt (g + f / m) when detached, and, through a, the coupled
+// reaction on the tree (its virtual work dt sc w . (dt k_s a), w = Lv + Lw x r_h). Both are
+// linear in f, so they reach v through one product J^T y of the rails' Jacobian (regimes
+// frozen). A pass of its own after the seeds, run only with the rails on, and out of line (its
+// code inlined slowed the backward with the rails off).
+template <int TPW>
+__host__ __device__ __noinline__ void rails_adjoint(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
+                      const AdjLayout& A, float* ws, float* wa, const Group<TPW>& g, int t_abs, f3 gv) {
+  const float dt = a.dt;
+  for (int ai = g.lane; ai < v.na; ai += TPW) {
+    const int ga = v.a0 + ai;
+    const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
+    const float ma = A0.w, ks = A1.x, csd = A1.y, fdet = A1.z;
+    RailTrace rt;
+    apply_rails(a, ma, ld3(s.av + 3 * ai), apple_force(a, ga, t_abs), &rt);
+    if (!rt.fade && !rt.brake) continue;  // the cap alone does not depend on v
+    f3 y = ld3(wa + A.vb1 + 3 * ai) + dt * ld3(wa + A.ub1 + 3 * ai);  // the update's cotangent of v'
+    if (s.detached[ai] == 0) {
+      const float D = ma + dt * csd + dt * dt * ks;
+      y = (dt / D) * y;
+      const int b = m.apple_body[ga];
+      if (a.tether_implicit && ws[L.SN + b] == 0.f) {
+        float t[36];
+        ld_rec(wa + A.T + 36 * b, t);
+        const m3 R = getm(t, 0);
+        const f3 lw = get3(t, 24), lv = get3(t, 27);
+        const f3 rh = mul(R, xyz(A0));
+        const f3 fr = ks * ld3(s.ax + 3 * ai) - ma * gv;
+        const float nfr = sqrtf(dot(fr, fr)), fc = a.clamp * fdet;
+        const float sc = nfr > fc ? fc / nfr : 1.f;
+        y = y + (dt * sc * dt * ks * dt / D) * (lv + cross(lw, rh));
+      }
+    } else {
+      y = (dt / ma) * y;
+    }
+    st3(wa + A.vb + 3 * ai, ld3(wa + A.vb + 3 * ai) + rails_vjp(a, ma, rt, y));
+  }
+}
+
 // Cotangents of one step (t) of one world: the private state holds the step's start state,
 // the forward workspace holds that step's recomputed forward (factors, Delta, apple data), and
 // A.qb1 / qdb1 / ub1 / vb1 hold the cotangents of its end state. Leaves the cotangents of its
@@ -787,15 +827,16 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
     wa[A.lam + i] = wa[A.qdb1 + i] + dt * wa[A.qb1 + i];           // qd'-bar (first part)
   }
   // the apple update: u' = u + dt (v' - v_hang'), v' = a + beta v_hang' (attached), or
-  // x' = x + dt v', v' = v + dt (g + f / m) (detached)
+  // x' = x + dt v', v' = v + dt (g + f / m) (detached); a = (m v + dt (f + m g - k_s u)) / D,
+  // f the applied force through the rails (a function of v)
   for (int ai = g.lane; ai < v.na; ai += TPW) {
     const int ga = v.a0 + ai;
     const f3 u1b = ld3(wa + A.ub1 + 3 * ai), v1b = ld3(wa + A.vb1 + 3 * ai);
     const f3 vtot = v1b + dt * u1b;
     if (s.detached[ai] == 0) {
       const float beta = ws[L.AT + 10 * ai + 3];
-      const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
-      const float ma = A0.w, ks = A1.x, csd = A1.y;
+      const float4 A1 = m.ap1[ga];
+      const float ma = m.ap0[ga].w, ks = A1.x, csd = A1.y;
       const float D = ma + dt * csd + dt * dt * ks;
       st3(wa + A.vh + 3 * ai, beta * vtot - dt * u1b);
       st3(wa + A.ub + 3 * ai, u1b - (dt * ks / D) * vtot);
@@ -832,6 +873,10 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   ra.cs = cs;
   for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, t_abs);
   g.sync();
+  if (a.rail_v > 0.f) {
+    rails_adjoint<TPW>(m, s, a, v, L, A, ws, wa, g, t_abs, gv);
+    g.sync();
+  }
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);

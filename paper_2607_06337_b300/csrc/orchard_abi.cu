@@ -548,6 +548,13 @@ StepArgs base_args(const ot_model* m, double dt) {
   a.cv = (float)m->flags.lin_damping;
   a.cv_snap = (float)(m->flags.lin_damping * m->flags.snapped_lin_damping);
   a.cw = (float)m->flags.ang_damping;
+  if (m->flags.rail_speed > 0) {
+    a.rail_v = (float)m->flags.rail_speed;
+    a.rail_vf = (float)m->flags.rail_fade_speed;
+    a.rail_inv = (float)(1.0 / (m->flags.rail_speed - m->flags.rail_fade_speed));
+    a.rail_cap = (float)(m->flags.rail_speed / dt);
+    a.rail_cb = (float)m->flags.rail_brake;
+  }
   a.single_world = -1;
   a.NB = m->P.NB; a.NV = m->P.NV; a.NA = m->P.NA;
   a.n_tips_total = m->P.NT;
@@ -660,7 +667,9 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
       !(flags->gamma_tension > 0) || !(flags->break_ramp_s >= 0) || !(flags->break_ramp_factor >= 0) ||
       !(flags->lin_damping >= 0) || !std::isfinite(flags->lin_damping) || !(flags->ang_damping >= 0) ||
       !std::isfinite(flags->ang_damping) || !(flags->snapped_lin_damping >= 0) ||
-      !std::isfinite(flags->snapped_lin_damping))
+      !std::isfinite(flags->snapped_lin_damping) || !(flags->rail_speed >= 0) ||
+      !std::isfinite(flags->rail_speed) || !(flags->rail_brake >= 0) || !std::isfinite(flags->rail_brake) ||
+      (flags->rail_speed > 0 && !(flags->rail_fade_speed >= 0 && flags->rail_fade_speed < flags->rail_speed)))
     return OT_EINVAL;
   ot_model* m = new ot_model();
   ot_status st = pack(desc, m->P, flags->fp64_twig_diam);

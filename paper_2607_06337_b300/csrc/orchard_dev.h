@@ -82,6 +82,9 @@ struct StepArgs {
   float ramp_gain;      // post-break damper factor minus one
   float cv, cv_snap;    // body damping c_v, and c_v on a snapped sub-tree (1/s)
   float cw;             // body damping c_omega (1/s)
+  float rail_v;         // applied-force rails: v_lim (0: off), v_fade, 1 / (v_lim - v_fade),
+  float rail_vf;        // v_lim / dt (the impulse cap per unit mass), brake c_b
+  float rail_inv, rail_cap, rail_cb;
   int step0;            // absolute index of the first step of this launch
   int n_steps;
   const float* pull_force;  // [NA*3] or null

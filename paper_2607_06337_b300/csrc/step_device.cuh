@@ -224,6 +224,74 @@ HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
   return f;
 }
 
+// The rails of App. B on the applied force f of an apple of mass m with velocity v at the
+// step's start: (1) impulse cap, the velocity f alone adds in one step is at most v_lim;
+// (2) power fade, f's component pushing along v fades linearly from full at |v| = v_fade to
+// none at v_lim; (3) speed brake, -c_b m (|v| - v_lim) v / |v| added above v_lim. Rails off
+// or no applied force: f unchanged. `tr` (optional) keeps what the adjoint's Jacobian needs.
+struct RailTrace {
+  f3 f1, vh;        // the force after the cap, v / |v|
+  float s, p, phi;  // |v|, f1 . vh, the fade factor
+  float dphi;       // d phi / d|v|
+  bool fade, brake;
+};
+HD f3 apply_rails(const StepArgs& a, float m, f3 v, f3 f, RailTrace* tr) {
+  RailTrace t;
+  t.fade = t.brake = false;
+  if (a.rail_v > 0.f) {
+    const float fn = sqrtf(dot(f, f));
+    if (fn > 0.f) {
+      const float cap = m * a.rail_cap;
+      if (fn > cap) f = (cap / fn) * f;
+      t.f1 = f;
+      t.s = sqrtf(dot(v, v));
+      if (t.s > a.rail_vf) {
+        t.vh = (1.f / t.s) * v;
+        t.p = dot(f, t.vh);
+        if (t.p > 0.f) {
+          t.fade = true;
+          t.phi = t.s >= a.rail_v ? 0.f : (a.rail_v - t.s) * a.rail_inv;
+          t.dphi = t.s >= a.rail_v ? 0.f : -a.rail_inv;
+          f = f - ((1.f - t.phi) * t.p) * t.vh;
+        }
+        if (t.s > a.rail_v) {
+          t.brake = true;
+          f = f - (a.rail_cb * m * (t.s - a.rail_v)) * t.vh;
+        }
+      }
+    }
+  }
+  if (tr) *tr = t;
+  return f;
+}
+// apply_rails out of line, on scalars: keeps the rails' code out of the inlined step, whose
+// size costs the backward kernel (which replays the step) even with the rails off.
+__host__ __device__ __noinline__ f3 rails_force(float rv, float rvf, float rinv, float rcap, float rcb, float m, f3 v,
+                                                f3 f) {
+  StepArgs a{};
+  a.rail_v = rv;
+  a.rail_vf = rvf;
+  a.rail_inv = rinv;
+  a.rail_cap = rcap;
+  a.rail_cb = rcb;
+  return apply_rails(a, m, v, f, nullptr);
+}
+
+// J^T y with J the Jacobian of apply_rails with respect to v (the force given, the regimes of
+// the trace frozen).
+HD f3 rails_vjp(const StepArgs& a, float m, const RailTrace& t, f3 y) {
+  f3 r = mk(0.f, 0.f, 0.f);
+  if (!t.fade && !t.brake) return r;
+  const float vy = dot(t.vh, y);
+  const f3 yp = y - vy * t.vh;  // (1 - vh vh^T) y
+  if (t.fade) {
+    const f3 fp = t.f1 - t.p * t.vh;  // (1 - vh vh^T) f1
+    r = r + (t.dphi * t.p * vy) * t.vh - ((1.f - t.phi) / t.s) * (vy * fp + t.p * yp);
+  }
+  if (t.brake) r = r - (a.rail_cb * m) * (vy * t.vh + ((t.s - a.rail_v) / t.s) * yp);
+  return r;
+}
+
 // The joint damper's factor on kd this step: 1, or for a broken joint the torn-fibre friction,
 // a damper growing from kd to (1 + ramp_gain) kd over the ramp time (Sec. IV-B).
 HD float damper_factor(const WState& s, const StepArgs& a, int b, int t_abs) {
@@ -371,7 +439,8 @@ HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, con
       st3(s.ax + 3 * ai, ua);
       s.detached[ai] = det = 1;
     }
-    const f3 fe = apple_force(a, ga, t_abs);
+    f3 fe = apple_force(a, ga, t_abs);  // through the rails, when they are on
+    if (a.rail_v > 0.f) fe = rails_force(a.rail_v, a.rail_vf, a.rail_inv, a.rail_cap, a.rail_cb, ma, va, fe);
     const f3 fs = det ? mk(0, 0, 0) : (-ks) * ua;
     const float T = sqrtf(dot(fs, fs)), P = sqrtf(dot(fe, fe));
     f3 avec, fapp = mk(0, 0, 0);

@@ -56,7 +56,8 @@ class ModelFlags(C.Structure):
                 ("gamma_tension", C.c_double), ("clamp_factor", C.c_double),
                 ("break_ramp_s", C.c_double), ("break_ramp_factor", C.c_double),
                 ("fp64_twig_diam", C.c_double), ("lin_damping", C.c_double), ("ang_damping", C.c_double),
-                ("snapped_lin_damping", C.c_double)]
+                ("snapped_lin_damping", C.c_double), ("rail_speed", C.c_double), ("rail_fade_speed", C.c_double),
+                ("rail_brake", C.c_double)]
 
 
 class Schedule(C.Structure):
@@ -185,7 +186,9 @@ def make_flags(flags) -> ModelFlags:
                       int(flags.n_pull), int(flags.n_tension), float(flags.gamma_tension), float(flags.clamp_factor),
                       float(flags.break_ramp_s), float(flags.break_ramp_factor),
                       float(getattr(flags, "fp64_twig_diam", 0.0)), float(getattr(flags, "lin_damping", 0.0)),
-                      float(getattr(flags, "ang_damping", 0.0)), float(getattr(flags, "snapped_lin_damping", 0.1)))
+                      float(getattr(flags, "ang_damping", 0.0)), float(getattr(flags, "snapped_lin_damping", 0.1)),
+                      float(getattr(flags, "rail_speed", 0.0)), float(getattr(flags, "rail_fade_speed", 0.0)),
+                      float(getattr(flags, "rail_brake", 0.0)))
 
 
 # ------------------------------------------------------------------------------------------

@@ -124,7 +124,9 @@ def test_upload_rejects_bad_arguments_without_touching_the_device(orch):
                                            C.byref(h)) == orch.OT_EINVAL
     # body damping coefficients must be finite and non-negative
     for kw in (dict(lin_damping=-1.0), dict(ang_damping=float("nan")), dict(snapped_lin_damping=-0.5),
-               dict(lin_damping=float("inf"))):
+               dict(lin_damping=float("inf")), dict(rail_speed=-1.0),
+               dict(rail_speed=2.0, rail_fade_speed=2.0), dict(rail_speed=2.0, rail_fade_speed=-0.1),
+               dict(rail_speed=2.0, rail_fade_speed=1.0, rail_brake=-1.0)):
         bad_d = orch.make_flags(I.Flags(**kw))
         assert orch.lib().ot_tree_model_upload(C.byref(d), C.byref(bad_d), C.c_void_p(256), 1 << 20, None,
                                                C.byref(h)) == orch.OT_EINVAL, kw

@@ -178,6 +178,27 @@ def test_adjoint_with_body_damping_and_events():
         assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, 2e-3, f"world {w} with damping")
 
 
+def test_adjoint_through_the_applied_force_rails():
+    """The rails' Jacobian in the adjoint: a low speed limit (2 cm/s) puts the pulled apple of
+    each differentiation-workload tree in the cap, fade and brake regimes while attached; the
+    gradients against the oracle's complex-step derivative (far target)."""
+    f = I.make_forest(I.DIFF, worlds=[0, 1])
+    fl = I.Flags(rail_speed=0.02, rail_fade_speed=0.005, rail_brake=20.0)
+    n = 100
+    _, rec = O.rollout(f, fl, n, record_tips=True)
+    off, _ = O.rollout(f, I.Flags(), n)
+    on, _ = O.rollout(f, fl, n)
+    assert np.abs(on.av - off.av).max() > 1e-3  # the rails act
+    rng = np.random.default_rng(6)
+    target = rec["tips"] + rng.normal(0.0, 0.01, rec["tips"].shape)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    for w in range(f.n_worlds):
+        kinds, idx = sample_coords(f, w, 5, rng)
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        g_cs, _ = O.grad(f, fl, w, n, tw, kinds, idx, np.full(len(kinds), 1e-20), mode=0)
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_cs, kinds, TOL_FAR, f"world {w} with rails")
+
+
 def test_damper_gradient_of_a_joint_without_damper():
     """dL/dkd of a joint whose kd is 0 (the compliant root of a small tree): the step's damper
     is kd' = kd (times the post-break factor), so the derivative is that of kd', not zero."""

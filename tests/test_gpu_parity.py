@@ -74,6 +74,37 @@ def test_body_damping_with_pulls_and_events():
     assert np.abs(st.q - st0.q).max() > 1e-3  # the damping does change the motion
 
 
+def test_applied_force_rails_with_pulls_and_events():
+    """The rails of App. B on the apples' applied forces (impulse cap, power fade, speed brake)
+    in uneven trees with random pulls up to 60 N: q gate and identical event sets, and the
+    detached apples' speeds against the oracle's (they fly under their pull, so the rails act on
+    them while it lasts)."""
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Simulator
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 3, 17, 33])
+    fl = I.Flags(rail_speed=3.0, rail_fade_speed=1.5, rail_brake=10.0)
+    n = 1000
+    sim = Simulator(f, fl)
+    sim.reset()
+    sim.rollout(n)
+    torch.cuda.synchronize()
+    g = _gpu_state(sim)
+    gv = sim.apple_v.cpu().numpy().astype(np.float64)
+    st, rec = O.rollout(f, fl, n, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    det = (st.detached > 0) & (g["detached"] > 0)
+    assert det.sum() >= 5
+    s_ref = np.linalg.norm(st.av[det], axis=1)
+    s_gpu = np.linalg.norm(gv[det], axis=1)
+    # the rails hold the flying apples near v_lim: gravity is not an applied force, so under a
+    # pull the brake balances it at v_lim + g / c_b at most
+    assert s_ref.max() < 3.0 + 9.81 / 10.0 + 1e-6
+    np.testing.assert_allclose(s_gpu, s_ref, rtol=1e-3, atol=1e-4)
+    off, _ = O.rollout(f, I.Flags(), n)
+    assert np.linalg.norm(off.av[det], axis=1).max() > 10.0  # without the rails they run away
+
+
 def test_step_by_step_equals_rollout():
     f = I.make_forest(I.BATCH, worlds=[5, 6, 7])
     fl = I.Flags()
