@@ -22,6 +22,11 @@ per-apple descriptor values that the step takes as inputs:
   is its elongation x - x_hang; a detached apple's is its world position);
 * the external pull schedule on apples.
 
+Model variants (ModelVariant, the defaults above unless asked for): the pipe exponent beta in
+[2.0, 2.5] (Sec. III, Eq. 2), capsule links (a cylinder of the segment's length with
+hemispherical caps, Sec. IV), the paper's damping law Kd = c_d Kp (Sec. IV-A, Eq. 4), and the
+per-level exponential stiffness k = k_0 gamma^(depth - 1) (Sec. IV-A).
+
 Every value is derived in float64 from a ``numpy.random.Generator(PCG64(seed))`` with
 seed = 1_000_003 * (the workload's position in WORKLOADS) + world, so both sides receive
 bit-identical inputs.
@@ -59,6 +64,16 @@ class Flags:
     rail_speed: float = 0.0          # v_lim (m/s) of the applied-force rails (App. B), 0: off
     rail_fade_speed: float = 0.0     # v_fade (m/s): the power fade starts here (< v_lim)
     rail_brake: float = 0.0          # c_b (1/s): speed brake above v_lim
+
+
+@dataclass
+class ModelVariant:
+    """Switches of the generated model (defaults: the workloads' model)."""
+    pipe_exponent: float = 2.0       # beta of r_parent^beta = sum r_child^beta (Eq. 2), in [2, 2.5]
+    capsule: bool = False            # capsule links (cylinder + hemispherical caps) for mass, inertia
+    damping_cd: float = 0.0          # > 0: Kd = c_d Kp (Eq. 4) with this c_d (s) instead of the zeta law
+    level_k0: float = 0.0            # > 0: per-level stiffness k = level_k0 level_gamma^(depth - 1)
+    level_gamma: float = 0.3
 
 
 @dataclass
@@ -324,7 +339,7 @@ def world_seed(workload: str, w: int, sweep: int = 0) -> int:
 
 
 def make_forest(workload: str, n_worlds: int | None = None, worlds=None, sweep: int = 0,
-                recipe_override: WorldRecipe | None = None) -> Forest:
+                recipe_override: WorldRecipe | None = None, variant: ModelVariant | None = None) -> Forest:
     """Generate a named workload (optionally a subset of its worlds).
 
     ``worlds`` picks world indices of the full workload (the seeds do not change), so a subset
@@ -340,7 +355,7 @@ def make_forest(workload: str, n_worlds: int | None = None, worlds=None, sweep: 
         rng = np.random.Generator(np.random.PCG64(world_seed(workload, w, sweep)))
         rec = recipe_override or world_recipe(workload, w, full, rng)
         per.append(_make_world(rng, rec))
-    forest = _pack(per)
+    forest = _pack(per, variant or ModelVariant())
     forest.meta.update(workload=workload, n_worlds_full=full, worlds=worlds, sweep=sweep)
     return forest
 
@@ -389,7 +404,7 @@ def _make_world(rng: np.random.Generator, rec: WorldRecipe) -> dict:
                 pull_force=pull_force, pull_start=pull_start, pull_end=pull_end, leaves=leaves)
 
 
-def _pack(per: list) -> Forest:
+def _pack(per: list, var: ModelVariant) -> Forest:
     W = len(per)
     nbs = np.array([len(p["par"]) for p in per], np.int64)
     nas = np.array([len(p["abody"]) for p in per], np.int64)
@@ -448,16 +463,24 @@ def _pack(per: list) -> Forest:
         idx = np.nonzero(dep == lvl)[0]
         np.add.at(leaves_in, gpar[idx], leaves_in[idx])
     root_of = body_off[:-1].astype(np.int64)[wid]
-    diam = 0.06 * np.sqrt(leaves_in / leaves_in[root_of])
+    # d ~ leaves^(1 / beta): leaves(p) = sum leaves(c) makes d_p^beta = sum d_c^beta exactly
+    diam = 0.06 * (leaves_in / leaves_in[root_of]) ** (1.0 / var.pipe_exponent)
     r = 0.5 * diam
-    mass = rho * math.pi * diam ** 2 * length / 4.0
-    inertia = np.stack([mass * (3 * r ** 2 + length ** 2) / 12.0,
-                        mass * (3 * r ** 2 + length ** 2) / 12.0,
-                        mass * r ** 2 / 2.0], axis=1)
+    if var.capsule:
+        mass, Ixx, Izz = capsule(diam, length, rho)
+        inertia = np.stack([Ixx, Ixx, Izz], axis=1)
+    else:
+        mass = rho * math.pi * diam ** 2 * length / 4.0
+        inertia = np.stack([mass * (3 * r ** 2 + length ** 2) / 12.0,
+                            mass * (3 * r ** 2 + length ** 2) / 12.0,
+                            mass * r ** 2 / 2.0], axis=1)
     com = np.zeros((NB, 3))
     com[:, 2] = 0.5 * length
     ndof = np.where(nonroot, 2, 0).astype(np.int32)
-    k = np.where(nonroot, math.pi * E * r ** 4 / (4.0 * length), 0.0)
+    if var.level_k0 > 0:
+        k = np.where(nonroot, var.level_k0 * var.level_gamma ** np.maximum(dep - 1, 0), 0.0)
+    else:
+        k = np.where(nonroot, math.pi * E * r ** 4 / (4.0 * length), 0.0)
     m_max = sig * math.pi * r ** 3 / 4.0
 
     # subtree moment of inertia about each joint's rest x and y axes (through the joint)
@@ -477,7 +500,10 @@ def _pack(per: list) -> Forest:
             np.add.at(J[:, a], b, val)
         anc = np.where(ok, gpar[np.maximum(anc, 0)], -1)
     Jm = J.mean(axis=1)
-    kd = np.where(nonroot, 2.0 * zeta * np.sqrt(k * Jm), 0.0)
+    if var.damping_cd > 0:
+        kd = np.where(nonroot, var.damping_cd * k, 0.0)
+    else:
+        kd = np.where(nonroot, 2.0 * zeta * np.sqrt(k * Jm), 0.0)
 
     # apples
     abody = cat("abody").astype(np.int64) if W else np.zeros(0, np.int64)
@@ -564,6 +590,20 @@ def cylinder(diam: float, length: float, rho: float):
     m = rho * math.pi * diam ** 2 * length / 4.0
     return m, (0.0, 0.0, 0.5 * length), (m * (3 * r * r + length * length) / 12.0,
                                           m * (3 * r * r + length * length) / 12.0, m * r * r / 2.0)
+
+
+def capsule(diam, length, rho):
+    """Mass and principal inertia (about the centre; axis, then across) of a capsule link: a
+    cylinder of radius r and length l along +z with a hemisphere of radius r on each end."""
+    r = 0.5 * np.asarray(diam, np.float64)
+    l = np.asarray(length, np.float64)
+    mc = rho * math.pi * r ** 2 * l                 # the cylinder
+    ms = rho * 4.0 / 3.0 * math.pi * r ** 3         # the two caps together
+    Izz = mc * r ** 2 / 2.0 + ms * 2.0 * r ** 2 / 5.0
+    # each cap: 2/5 m r^2 about the sphere's centre, which sits l/2 from the link's centre;
+    # parallel-axis through the cap's own centre of mass, 3 r / 8 beyond the flat face
+    Ixx = mc * (3.0 * r ** 2 + l ** 2) / 12.0 + ms * (2.0 * r ** 2 / 5.0 + l ** 2 / 4.0 + 3.0 * l * r / 8.0)
+    return mc + ms, Ixx, Izz
 
 
 def beam_stiffness(E: float, diam: float, length: float) -> float:

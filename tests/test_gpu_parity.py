@@ -105,6 +105,30 @@ def test_applied_force_rails_with_pulls_and_events():
     assert np.linalg.norm(off.av[det], axis=1).max() > 10.0  # without the rails they run away
 
 
+def test_model_variants_with_pulls_and_events():
+    """Generated-model variants (pipe exponent 2.3, capsule links, the paper's Kd = c_d Kp with
+    c_d = 0.1 s) on uneven trees with random pulls: q gate and identical event sets."""
+    var = I.ModelVariant(pipe_exponent=2.3, capsule=True, damping_cd=0.1)
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 17], variant=var)
+    fl = I.Flags()
+    g = _run(f, fl, 1000)
+    st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+
+
+def test_per_level_stiffness_variant():
+    """The per-level exponential stiffness (k = 2000 N m / rad x 0.3^(depth - 1)) on the plain
+    workload's trees under gravity: q gate."""
+    var = I.ModelVariant(level_k0=2000.0, level_gamma=0.3)
+    f = I.make_forest(I.PLAIN, variant=var)
+    fl = I.Flags()
+    g = _run(f, fl, 500)
+    st, rec = O.rollout(f, fl, 500, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+
+
 def test_step_by_step_equals_rollout():
     f = I.make_forest(I.BATCH, worlds=[5, 6, 7])
     fl = I.Flags()
