@@ -56,6 +56,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=24.0)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-damped", action="store_true", help="skip the body-damping leg")
+    p.add_argument("--no-dr", action="store_true", help="skip the on-device domain-randomisation leg")
     p.add_argument("--adj-workload", default="diff1024", help="diff1024 (default) or stress8192")
     p.add_argument("--sweep", action="store_true",
                    help="add a world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
@@ -364,6 +365,35 @@ def damped_leg(args, dev, forest, S, flush):
     return out
 
 
+def dr_leg(sim, forest, dev):
+    """Domain randomisation of the whole batch (per-world lengths, diameters, materials and c_d)
+    rebuilt on the device (ot_model_randomize), against its host counterpart inputs.randomize.
+    Run last: it changes the benchmark model."""
+    import torch
+    from paper_2607_06337_b300 import inputs as I
+    rng = np.random.default_rng(17)
+    W = forest.n_worlds
+    fac = np.column_stack([rng.uniform(0.85, 1.15, (W, 5)), rng.uniform(0.05, 0.15, W)]).astype(np.float32)
+    fd = torch.as_tensor(fac, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        sim.randomize(fd)
+    ms = []
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.randomize(fd)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = time.perf_counter()
+    I.randomize(forest, fac.astype(np.float64))
+    host_s = time.perf_counter() - t
+    return {"worlds": W, "bodies": forest.n_bodies, "device_ms": statistics.median(ms), "host_s": host_s,
+            "host": "numpy float64 inputs.randomize on one core", "launches_per_build": 1}
+
+
 def world_sweep(args, dev):
     """Batched (persistent, graph, autotuned) and plain (one launch per world per step) forward
     body-steps/s at 1024..65536 worlds of the sweep16384 trees (300 bodies, 60 apples). The
@@ -543,6 +573,8 @@ def run_ours(args):
 
     sweep = world_sweep(args, dev) if args.sweep and ws == 1 else None
 
+    dr = None if args.no_dr or ws > 1 else dr_leg(sim, forest, dev)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(forest, fl, args.cpu_seconds, S)
@@ -565,6 +597,7 @@ def run_ours(args):
             "plain": plain,
             "fwd_adj": adj,
             "damped": damped,
+            "dr_build": dr,
             "sweep": sweep,
             "clocks": clocks,
             "frozen_worlds": int((status & 1).sum()),

@@ -90,6 +90,12 @@ typedef struct ot_tree_desc {
   const double* tip_local;   /* [nt][3] tip point in the body frame */
   const double* gravity;     /* [W][3] */
   const double* diam;        /* [nb] segment diameter (m); may be NULL unless fp64_twig_diam > 0 */
+  /* Per-body geometry and material of generated trees, for ot_model_randomize (all four, with
+     diam, or none: NULL). */
+  const double* length;      /* [nb] segment length (m) */
+  const double* rho;         /* [nb] wood density (kg/m^3) */
+  const double* youngs;      /* [nb] Young's modulus (Pa) */
+  const double* sigma_r;     /* [nb] modulus of rupture (Pa) */
 } ot_tree_desc;
 
 /* Switchable readings of the model (defaults in parentheses). */
@@ -142,6 +148,22 @@ ot_status ot_model_bytes(const ot_tree_desc* desc, size_t* bytes);
 ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* flags, void* dev_buf,
                                size_t dev_bytes, void* stream, ot_model** out);
 void ot_model_release(ot_model* model);
+
+/* ---------------------------------------------------------------------------------------
+ * Domain randomisation on the device (Sec. VI-B: per-world geometry and material, built on the
+ * GPU). factors: device [W][6] floats per world (s_len, s_diam, s_rho, s_E, s_sigma, c_d). Each
+ * world's segment lengths and every body-frame point (joint origins, centres of mass, apple hang
+ * points, tip points) are scaled by s_len, its diameters by s_diam, its wood density, Young's
+ * modulus and modulus of rupture by s_rho, s_E, s_sigma, relative to the uploaded model, and
+ * every derived per-body value is rebuilt: mass and inertia (solid cylinders, or capsule links
+ * when capsule_links = 1), k = E I / l for compliant joints (I = pi r^4 / 4), kd = c_d k
+ * (Sec. IV-A, Eq. 4) and the rupture moment sigma_r pi r^3 / 4 (Sec. IV-B, Eq. 5). Topology,
+ * rest rotations, armature, the apples' own parameters, the size classes, schedules and the
+ * FP64-pivot choice (from the uploaded diameters) are kept. Asynchronous on `stream`; rollouts
+ * and graphs captured before it read the new values. Errors: OT_EINVAL for a null argument or
+ * a model uploaded without length, rho, youngs, sigma_r and diam. Factors are not checked on
+ * the device: non-positive ones give a non-physical model (status bits may then be set). */
+ot_status ot_model_randomize(ot_model* model, const float* factors, int32_t capsule_links, void* stream);
 
 /* Counts of the uploaded forest: worlds, bodies, DOFs, apples, tips, size classes. */
 ot_status ot_model_counts(const ot_model* model, int64_t counts[6]);

@@ -80,6 +80,10 @@ struct Packed {
   std::vector<float4> tip_local, gravity;
   std::vector<int> queue;
   std::vector<ClassInfo> classes;
+  // domain-randomisation base (empty unless the descriptor has the material): per body
+  // {length, diam, rho, E}, {jpos, sigma_r}, {com, armature}; per apple {hang, mass}; per tip
+  // the uploaded point
+  std::vector<float4> dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip;
 };
 
 bool finite_all(const double* p, size_t n) {
@@ -356,6 +360,21 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.gravity.resize(W);
   for (int w = 0; w < W; ++w)
     P.gravity[w] = make_float4((float)d->gravity[3 * w], (float)d->gravity[3 * w + 1], (float)d->gravity[3 * w + 2], 0.f);
+  P.dr_geo.clear(); P.dr_jpos.clear(); P.dr_com.clear(); P.dr_ap0.clear(); P.dr_tip.clear();
+  if (d->length && d->rho && d->youngs && d->sigma_r && d->diam) {
+    if (!finite_all(d->length, NB) || !finite_all(d->rho, NB) || !finite_all(d->youngs, NB) ||
+        !finite_all(d->sigma_r, NB) || !finite_all(d->diam, NB))
+      return OT_ENONFINITE;
+    for (int b = 0; b < NB; ++b) {
+      P.dr_geo.push_back(make_float4((float)d->length[b], (float)d->diam[b], (float)d->rho[b], (float)d->youngs[b]));
+      P.dr_jpos.push_back(make_float4((float)d->jpos[3 * b], (float)d->jpos[3 * b + 1], (float)d->jpos[3 * b + 2],
+                                      (float)d->sigma_r[b]));
+      P.dr_com.push_back(make_float4((float)d->com[3 * b], (float)d->com[3 * b + 1], (float)d->com[3 * b + 2],
+                                     (float)d->armature[b]));
+    }
+    P.dr_ap0 = P.ap0;
+    P.dr_tip = P.tip_local;
+  }
   // size classes by workspace bytes, queue sorted by (class, cost descending)
   const long long bounds[] = {6 * 1024, 14 * 1024, 28 * 1024, 55 * 1024, (long long)kSmemLimit / 4};
   const int n_bounds = 5;
@@ -409,6 +428,50 @@ __global__ void set_gains_kernel(float4* bp3, const float* k, const float* kd, i
   if (kd) v.w = kd[b];
   bp3[b] = v;
 }
+
+// Domain randomisation, one block per world (see ot_model_randomize): the world's factors
+// (s_len, s_diam, s_rho, s_E, s_sigma, c_d) applied to the uploaded geometry and material, and
+// every derived record rebuilt.
+struct DrRecords {
+  float4 *bp0, *bp2, *bp3, *bp4, *ap0, *tip;
+  const float4 *geo, *jpos, *com, *base_ap0, *base_tip;
+};
+__global__ void dr_build_kernel(DevModel m, DrRecords o, const float* factors, int capsule_links) {
+  constexpr float kPi = 3.14159265358979f;
+  const int w = blockIdx.x;
+  const float* F = factors + 6 * (long long)w;
+  const float sl = F[0], sd = F[1], sr = F[2], sE = F[3], ss = F[4], cd = F[5];
+  for (int gb = m.body_off[w] + threadIdx.x; gb < m.body_off[w + 1]; gb += blockDim.x) {
+    const float4 G = o.geo[gb], J = o.jpos[gb], Cm = o.com[gb];
+    const float len = G.x * sl, r = 0.5f * G.y * sd, rho = G.z * sr, E = G.w * sE, sig = J.w * ss;
+    const float r2 = r * r;
+    float mass, Ixx, Izz;
+    if (capsule_links) {  // a cylinder of length len with a hemisphere of radius r on each end
+      const float mc = rho * kPi * r2 * len, ms = rho * (4.f / 3.f) * kPi * r2 * r;
+      mass = mc + ms;
+      Izz = mc * r2 * 0.5f + ms * 0.4f * r2;
+      Ixx = mc * (3.f * r2 + len * len) / 12.f + ms * (0.4f * r2 + 0.25f * len * len + 0.375f * len * r);
+    } else {              // a solid cylinder
+      mass = rho * kPi * r2 * len;
+      Izz = mass * r2 * 0.5f;
+      Ixx = mass * (3.f * r2 + len * len) / 12.f;
+    }
+    const bool compliant = ((unsigned)m.bi[gb].y >> 28) > 0;
+    const float k = compliant ? kPi * E * r2 * r2 / (4.f * len) : 0.f;
+    o.bp0[gb] = make_float4(J.x * sl, J.y * sl, J.z * sl, mass);
+    o.bp2[gb] = make_float4(Cm.x * sl, Cm.y * sl, Cm.z * sl, Ixx);
+    o.bp3[gb] = make_float4(Ixx, Izz, k, cd * k);
+    o.bp4[gb] = make_float4(Cm.w, sig * kPi * r2 * r * 0.25f, 0.f, 0.f);
+  }
+  for (int ga = m.apple_off[w] + threadIdx.x; ga < m.apple_off[w + 1]; ga += blockDim.x) {
+    const float4 H = o.base_ap0[ga];
+    o.ap0[ga] = make_float4(H.x * sl, H.y * sl, H.z * sl, H.w);
+  }
+  for (int gt = m.tip_off[w] + threadIdx.x; gt < m.tip_off[w + 1]; gt += blockDim.x) {
+    const float4 T = o.base_tip[gt];
+    o.tip[gt] = make_float4(T.x * sl, T.y * sl, T.z * sl, T.w);
+  }
+}
 }  // namespace orchard
 
 struct ot_model {
@@ -416,6 +479,10 @@ struct ot_model {
   DevModel dev{};
   ot_model_flags flags{};
   int n_sm = 148;
+  // the records ot_model_randomize rewrites, and its base (null without the material)
+  float4 *w_bp0 = nullptr, *w_bp2 = nullptr, *w_bp3 = nullptr, *w_bp4 = nullptr, *w_ap0 = nullptr,
+         *w_tip = nullptr;
+  const float4 *dr_geo = nullptr, *dr_jpos = nullptr, *dr_com = nullptr, *dr_ap0 = nullptr, *dr_tip = nullptr;
   cudaStream_t capture_stream = nullptr;
   struct GraphEntry {
     std::string key;
@@ -451,7 +518,8 @@ namespace {
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
   size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, bj, anc, bl_off,
-      bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue, total;
+      bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue,
+      dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -479,6 +547,9 @@ ModelLayout model_layout(const Packed& P) {
   L.tip_local = c.take<float4>(P.NT);
   L.gravity = c.take<float4>(P.W);
   L.queue = c.take<int>(P.W);
+  L.dr_geo = c.take<float4>(P.dr_geo.size()); L.dr_jpos = c.take<float4>(P.dr_jpos.size());
+  L.dr_com = c.take<float4>(P.dr_com.size()); L.dr_ap0 = c.take<float4>(P.dr_ap0.size());
+  L.dr_tip = c.take<float4>(P.dr_tip.size());
   L.total = c.off;
   return L;
 }
@@ -715,6 +786,9 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.tip_local, P.tip_local.data(), vbytes(P.tip_local));
   put(L.gravity, P.gravity.data(), vbytes(P.gravity));
   put(L.queue, P.queue.data(), vbytes(P.queue));
+  put(L.dr_geo, P.dr_geo.data(), vbytes(P.dr_geo)); put(L.dr_jpos, P.dr_jpos.data(), vbytes(P.dr_jpos));
+  put(L.dr_com, P.dr_com.data(), vbytes(P.dr_com)); put(L.dr_ap0, P.dr_ap0.data(), vbytes(P.dr_ap0));
+  put(L.dr_tip, P.dr_tip.data(), vbytes(P.dr_tip));
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dev_buf, host.data(), L.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -751,6 +825,13 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.tip_local = (const float4*)(base + L.tip_local);
   dm.gravity = (const float4*)(base + L.gravity);
   dm.queue = (const int*)(base + L.queue);
+  m->w_bp0 = (float4*)(base + L.bp0); m->w_bp2 = (float4*)(base + L.bp2); m->w_bp3 = (float4*)(base + L.bp3);
+  m->w_bp4 = (float4*)(base + L.bp4); m->w_ap0 = (float4*)(base + L.ap0); m->w_tip = (float4*)(base + L.tip_local);
+  if (!P.dr_geo.empty()) {
+    m->dr_geo = (const float4*)(base + L.dr_geo); m->dr_jpos = (const float4*)(base + L.dr_jpos);
+    m->dr_com = (const float4*)(base + L.dr_com); m->dr_ap0 = (const float4*)(base + L.dr_ap0);
+    m->dr_tip = (const float4*)(base + L.dr_tip);
+  }
   *out = m;
   return OT_OK;
 }
@@ -764,6 +845,17 @@ ot_status ot_model_set_gains(ot_model* m, const float* k, const float* kd, void*
   if (nb == 0) return OT_OK;
   const int threads = 256, blocks = (nb + threads - 1) / threads;
   set_gains_kernel<<<blocks, threads, 0, (cudaStream_t)stream>>>(const_cast<float4*>(m->dev.bp3), k, kd, nb);
+  OT_CUDA(cudaGetLastError());
+  g_launches += 1;
+  return OT_OK;
+}
+
+ot_status ot_model_randomize(ot_model* m, const float* factors, int32_t capsule_links, void* stream) {
+  if (!m || !factors || !m->dr_geo) return OT_EINVAL;
+  if (m->P.W == 0) return OT_OK;
+  DrRecords o{m->w_bp0, m->w_bp2, m->w_bp3, m->w_bp4, m->w_ap0, m->w_tip, m->dr_geo, m->dr_jpos, m->dr_com,
+              m->dr_ap0, m->dr_tip};
+  dr_build_kernel<<<m->P.W, 128, 0, (cudaStream_t)stream>>>(m->dev, o, factors, capsule_links ? 1 : 0);
   OT_CUDA(cudaGetLastError());
   g_launches += 1;
   return OT_OK;

@@ -123,6 +123,10 @@ class Forest:
     # rest geometry in world coordinates (for pins and diagnostics)
     rest_x: np.ndarray = None      # (nb,3) joint origins
     rest_R: np.ndarray = None      # (nb,3,3)
+    # per-body material, for domain randomisation (None: not a generated tree)
+    rho: np.ndarray = None         # (nb,) wood density [kg/m^3]
+    youngs: np.ndarray = None      # (nb,) Young's modulus [Pa]
+    sigma_r: np.ndarray = None     # (nb,) modulus of rupture [Pa]
     meta: dict = field(default_factory=dict)
 
     # --------------------------------------------------------------------------------
@@ -182,6 +186,7 @@ class Forest:
             apple_v0=opt(self.apple_v0, asel), pull_force=opt(self.pull_force, asel),
             pull_start=opt(self.pull_start, asel), pull_end=opt(self.pull_end, asel),
             rest_x=opt(self.rest_x, bsel), rest_R=opt(self.rest_R, bsel),
+            rho=opt(self.rho, bsel), youngs=opt(self.youngs, bsel), sigma_r=opt(self.sigma_r, bsel),
             meta=dict(self.meta, subset=worlds),
         )
 
@@ -539,8 +544,9 @@ def _pack(per: list, var: ModelVariant) -> Forest:
         q0=np.zeros(NV), qd0=np.zeros(NV), apple_x0=x0, apple_v0=np.zeros((NA, 3)),
         pull_force=cat("pull_force").reshape(-1, 3) if W else np.zeros((0, 3)),
         pull_start=cat("pull_start").astype(np.int32), pull_end=cat("pull_end").astype(np.int32),
-        rest_x=Xw, rest_R=Rw,
+        rest_x=Xw, rest_R=Rw, rho=rho.copy(), youngs=E.copy(), sigma_r=sig.copy(),
     )
+    f.meta["capsule"] = bool(var.capsule)
     f.meta["E"] = np.array([p["E"] for p in per])
     f.meta["sigma_r"] = np.array([p["sigma_r"] for p in per])
     return f
@@ -590,6 +596,52 @@ def cylinder(diam: float, length: float, rho: float):
     m = rho * math.pi * diam ** 2 * length / 4.0
     return m, (0.0, 0.0, 0.5 * length), (m * (3 * r * r + length * length) / 12.0,
                                           m * (3 * r * r + length * length) / 12.0, m * r * r / 2.0)
+
+
+DR_FACTORS = ("len", "diam", "rho", "E", "sigma", "c_d")
+
+
+def randomize(forest: "Forest", factors: np.ndarray, capsule_links: bool = False) -> "Forest":
+    """Host counterpart of the on-device domain-randomisation build (ot_model_randomize): per
+    world, factors[w] = (s_len, s_diam, s_rho, s_E, s_sigma, c_d) scale the segment lengths (and
+    every body-frame point: joint origins, centres of mass, hang and tip points), diameters,
+    wood density, Young's modulus and modulus of rupture, and every derived value is rebuilt:
+    mass and inertia (solid cylinder, or capsule links), k = E I / l for compliant joints, the
+    rupture moment sigma_r pi r^3 / 4, and kd = c_d k (the paper's law, Eq. 4). Topology, rest
+    rotations, armature and the apples' own parameters are kept."""
+    if forest.rho is None or forest.youngs is None or forest.sigma_r is None:
+        raise ValueError("randomize needs the per-body material of a generated forest")
+    import copy
+    f = copy.deepcopy(forest)
+    fac = np.asarray(factors, np.float64).reshape(forest.n_worlds, len(DR_FACTORS))
+    wid = np.repeat(np.arange(forest.n_worlds), np.diff(forest.body_off))
+    sl, sd, sr, sE, ss, cd = (fac[wid, i] for i in range(6))
+    f.length = forest.length * sl
+    f.diam = forest.diam * sd
+    f.rho = forest.rho * sr
+    f.youngs = forest.youngs * sE
+    f.sigma_r = forest.sigma_r * ss
+    f.jpos = forest.jpos * sl[:, None]
+    f.com = forest.com * sl[:, None]
+    r = 0.5 * f.diam
+    if capsule_links:
+        f.mass, Ixx, Izz = capsule(f.diam, f.length, f.rho)
+        f.inertia = np.stack([Ixx, Ixx, Izz], axis=1)
+    else:
+        f.mass = f.rho * math.pi * f.diam ** 2 * f.length / 4.0
+        f.inertia = np.stack([f.mass * (3 * r ** 2 + f.length ** 2) / 12.0,
+                              f.mass * (3 * r ** 2 + f.length ** 2) / 12.0, f.mass * r ** 2 / 2.0], axis=1)
+    f.k = np.where(forest.ndof > 0, math.pi * f.youngs * r ** 4 / (4.0 * f.length), 0.0)
+    f.kd = cd * f.k
+    f.m_max = f.sigma_r * math.pi * r ** 3 / 4.0
+    awid = np.repeat(np.arange(forest.n_worlds), np.diff(forest.apple_off))
+    twid = np.repeat(np.arange(forest.n_worlds), np.diff(forest.tip_off))
+    f.hang_local = forest.hang_local * fac[awid, 0][:, None]
+    f.attach_local = forest.attach_local * fac[awid, 0][:, None]
+    f.tip_local = forest.tip_local * fac[twid, 0][:, None]
+    f.rest_x = None
+    f.rest_R = None
+    return f
 
 
 def capsule(diam, length, rho):

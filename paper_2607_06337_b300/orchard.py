@@ -47,7 +47,8 @@ class TreeDesc(C.Structure):
                 ("k", _f64p), ("kd", _f64p), ("armature", _f64p), ("m_max", _f64p),
                 ("apple_body", _i32p), ("hang_local", _f64p), ("apple_mass", _f64p), ("k_s", _f64p),
                 ("c_s", _f64p), ("f_detach", _f64p),
-                ("tip_body", _i32p), ("tip_local", _f64p), ("gravity", _f64p), ("diam", _f64p)]
+                ("tip_body", _i32p), ("tip_local", _f64p), ("gravity", _f64p), ("diam", _f64p),
+                ("length", _f64p), ("rho", _f64p), ("youngs", _f64p), ("sigma_r", _f64p)]
 
 
 class ModelFlags(C.Structure):
@@ -96,6 +97,7 @@ _SIGS = {
     "ot_model_release": (None, [C.c_void_p]),
     "ot_model_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "ot_model_set_gains": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ot_model_randomize": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ot_state_bytes": (C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     "ot_world_state_alloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
     "ot_state_release": (None, [C.c_void_p]),
@@ -178,7 +180,9 @@ def make_desc(forest, keep: _Keep) -> TreeDesc:
         keep.f64(f.mass), keep.f64(f.inertia), keep.f64(f.k), keep.f64(f.kd), keep.f64(f.armature),
         keep.f64(f.m_max), keep.i32(f.apple_body), keep.f64(f.hang_local), keep.f64(f.apple_mass),
         keep.f64(f.k_s), keep.f64(f.c_s), keep.f64(f.f_detach), keep.i32(f.tip_body), keep.f64(f.tip_local),
-        keep.f64(f.gravity), keep.f64(f.diam) if getattr(f, "diam", None) is not None else None)
+        keep.f64(f.gravity), keep.f64(f.diam) if getattr(f, "diam", None) is not None else None,
+        *(keep.f64(getattr(f, key)) if getattr(f, key, None) is not None else None
+          for key in ("length", "rho", "youngs", "sigma_r")))
 
 
 def make_flags(flags) -> ModelFlags:
@@ -219,6 +223,16 @@ def model_set_gains(model, k=None, kd=None, stream=None):
         if t is not None and (t.dtype.itemsize != 4 or not t.is_cuda or not t.is_contiguous()):
             raise ValueError("gains must be contiguous float32 CUDA tensors")
     _check(lib().ot_model_set_gains(model, _ptr(k), _ptr(kd), _stream_handle(stream)), "ot_model_set_gains")
+
+
+def model_randomize(model, factors, capsule_links=False, stream=None):
+    """Domain randomisation on the device: factors, a float32 CUDA tensor [worlds, 6] of
+    (s_len, s_diam, s_rho, s_E, s_sigma, c_d) per world (see include/orchard.h)."""
+    if factors.dtype.itemsize != 4 or not factors.is_cuda or not factors.is_contiguous() or factors.dim() != 2 \
+            or factors.shape[1] != 6:
+        raise ValueError("factors must be a contiguous float32 CUDA tensor [worlds, 6]")
+    _check(lib().ot_model_randomize(model, _ptr(factors), int(bool(capsule_links)), _stream_handle(stream)),
+           "ot_model_randomize")
 
 
 def state_bytes(model) -> int:
@@ -382,6 +396,12 @@ class Simulator:
     def set_gains(self, k=None, kd=None, stream=None):
         """Per-body joint stiffness and damping from float32 device tensors [bodies]."""
         model_set_gains(self.model, k, kd, stream)
+
+    def randomize(self, factors, capsule_links=None, stream=None):
+        """Per-world domain randomisation on the device (factors [worlds, 6], float32 CUDA)."""
+        if capsule_links is None:
+            capsule_links = bool(self.forest.meta.get("capsule", False))
+        model_randomize(self.model, factors, capsule_links, stream)
 
     def record_buffers(self, n_steps, ckpt_every, tips=True):
         """Device buffers for a recorded rollout: tips [n_steps, n_tips, 3] and checkpoints."""

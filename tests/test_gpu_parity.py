@@ -129,6 +129,43 @@ def test_per_level_stiffness_variant():
     PAR.assert_parity(rep)
 
 
+def test_device_domain_randomisation_against_the_host_build():
+    """ot_model_randomize (per-world lengths, diameters, density, modulus, rupture strength and
+    c_d; every derived record rebuilt on the GPU) against its host counterpart inputs.randomize:
+    the GPU rollout of the device-randomised model and the oracle's rollout of the host-randomised
+    forest, with the same (float32) factors: q gate and identical event sets."""
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Simulator
+    f = I.make_forest(I.BATCH, worlds=[0, 1, 2, 17])
+    rng = np.random.default_rng(9)
+    fac = np.column_stack([rng.uniform(0.85, 1.15, (f.n_worlds, 5)), rng.uniform(0.05, 0.15, f.n_worlds)])
+    fac = fac.astype(np.float32)
+    fl = I.Flags()
+    n = 600
+    sim = Simulator(f, fl)
+    sim.randomize(torch.as_tensor(fac, device="cuda"))
+    sim.reset()
+    sim.rollout(n)
+    torch.cuda.synchronize()
+    g = _gpu_state(sim)
+    h = I.randomize(f, fac.astype(np.float64))
+    st, rec = O.rollout(h, fl, n, near_eps=PAR.NEAR)
+    rep = PAR.compare(h, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    plain, _ = O.rollout(f, fl, n)
+    assert np.abs(plain.q - st.q).max() > 1e-3  # the randomisation does change the worlds
+
+
+def test_domain_randomisation_needs_the_material():
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Simulator
+    from tests import _trees as T
+    f, _, _ = T.single_hinge()
+    sim = Simulator(f, I.Flags())
+    with pytest.raises(RuntimeError):
+        sim.randomize(torch.ones((1, 6), dtype=torch.float32, device="cuda"))
+
+
 def test_step_by_step_equals_rollout():
     f = I.make_forest(I.BATCH, worlds=[5, 6, 7])
     fl = I.Flags()
