@@ -138,10 +138,22 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def kernel_source_hash():
+def code_tokens(text: str) -> str:
+    """C++ source with // comments, blank lines and indentation removed (the code, not its prose)."""
+    out = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].strip() if '"' not in line.split("//", 1)[0] else line.strip()
+        if code:
+            out.append(code)
+    return "\n".join(out)
+
+
+def kernel_source_hash(read=None):
+    """Hash of the rollout kernel's code (comments excluded), keying the committed DRAM capture."""
+    read = read or (lambda name: open(os.path.join(ROOT, "paper_2607_06337_b300", "csrc", name)).read())
     h = hashlib.sha256()
     for name in ("step_kernel.cu", "step_device.cuh", "orchard_dev.h"):
-        h.update(open(os.path.join(ROOT, "paper_2607_06337_b300", "csrc", name), "rb").read())
+        h.update(code_tokens(read(name)).encode())
     return h.hexdigest()[:16]
 
 

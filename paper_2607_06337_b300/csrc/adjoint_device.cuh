@@ -9,8 +9,10 @@
 //       = -dt sum_i lambda_i [k'_i (q_i + alpha dt qd'_i) + kd'_i qd'_i]
 //         - dt lambda^T ID(q, qd, Delta / dt)
 //         + dt sum_apples [ w_a . P0_a - dt kappa_a w_a . v_hang'_a ],
-// where ID is the inverse dynamics (inertia, velocity products, gravity), w_a = J_h lambda is
-// the virtual velocity of the hang point and P0_a the clamped reaction of the coupled tether.
+// where ID is the inverse dynamics (inertia, velocity products, gravity, less the optional body
+// damping), w_a = J_h lambda is the virtual velocity of the hang point and P0_a the clamped
+// reaction of the coupled tether (with the applied force through the optional rails, whose
+// dependence on the apple's velocity is taken in rails_adjoint).
 // lambda^T ID = sum_b Lambda_b . F_b (virtual work of each body's Newton-Euler force under the
 // virtual velocity Lambda_b of lambda), so the q and qd gradients come from one reverse sweep
 // over a per-body tape of the forward kinematics, velocities, accelerations and the virtual

@@ -3,20 +3,25 @@
 // Spatial algebra is written in world orientation with each body's own joint origin x_b as
 // the reference point (so a hinge's motion subspace is (e_i; 0) and lever arms stay
 // segment-sized, which keeps twig inertias well conditioned in FP32). Per step and world:
-//   1. root-to-leaf level sweep: forward kinematics (Sec. IV Eq. 3, two Cardan DOFs per
-//      joint), body velocities and velocity-product accelerations (RNE forward pass, base
-//      acceleration -g), the body's own Newton-Euler force, apple tether loads (Sec. IV-C
-//      Eqs. 6-7) and the body's spatial inertia (plus the tether coupling point masses);
+//   1a. root-to-leaf level sweep: forward kinematics (Sec. IV Eq. 3, two Cardan DOFs per
+//       joint), body velocities and velocity-product accelerations (RNE forward pass, base
+//       acceleration -g), snapped flags;
+//   1b. all bodies at once: the body's spatial inertia, its own Newton-Euler force less the
+//       optional body damping (Sec. IV-A), and the apple tether loads (Sec. IV-C Eqs. 6-7, the
+//       applied force through the optional rails of App. B), plus the tether coupling point
+//       masses;
 //   2. leaf-to-root level sweep: RNE force accumulation and CRBA composite inertias; bias
 //      c_i = e_i . n_b and the right-hand side r = dt(-K'(q + alpha dt qd) - D' qd - c);
-//   3. CRBA rows in ancestor-row storage M_ij = e_j . (n_i + (x_b(i) - x_b(j)) x f_i) with
-//      (n_i; f_i) = I^c_b(i) (e_i; 0), plus the implicit diagonal (armature, dt kd', dt^2 k');
-//   4. tree-sparse LDL^T: DOFs eliminated from the last to the first (children have larger
-//      indices), each a rank-1 update of its ancestor rows; the L^T sweep of the solve rides
-//      along; rows are kept unscaled (U = D L);
+//   3. CRBA rows in ancestor-row storage, body by body, M_ij = e_j . (n_i + (x_b(i) - x_b(j))
+//      x f_i) with (n_i; f_i) = I^c_b(i) (e_i; 0), plus the implicit diagonal (armature,
+//      dt kd', dt^2 k');
+//   4. tree-sparse LDL^T in joint blocks (a joint's one or two DOFs together, see Pivot),
+//      level by level from the deepest, each joint a rank-2 update of its ancestor rows; the
+//      L^T sweep of the solve rides along; rows are kept unscaled;
 //   5. root-to-leaf level sweep: the L sweep of the solve, qd += Delta, q += dt qd, the new
-//      body velocities, the coupled apple update, and the rupture / detachment tests with
-//      their hysteresis counters (Sec. IV-B Eq. 5, Sec. IV-C).
+//      body velocities and the rupture tests; then all apples at once: the coupled apple
+//      update and the detach tests, with their hysteresis counters (Sec. IV-B Eq. 5,
+//      Sec. IV-C).
 #pragma once
 #include <cuda_runtime.h>
 
