@@ -149,10 +149,11 @@ def code_tokens(text: str) -> str:
 
 
 def kernel_source_hash(read=None):
-    """Hash of the rollout kernel's code (comments excluded), keying the committed DRAM capture."""
+    """Hash of the rollout kernel's code and of the model packing (comments excluded), keying the
+    committed DRAM capture."""
     read = read or (lambda name: open(os.path.join(ROOT, "paper_2607_06337_b300", "csrc", name)).read())
     h = hashlib.sha256()
-    for name in ("step_kernel.cu", "step_device.cuh", "orchard_dev.h"):
+    for name in ("step_kernel.cu", "step_device.cuh", "orchard_dev.h", "orchard_abi.cu"):  # kernel and model layout
         h.update(code_tokens(read(name)).encode())
     return h.hexdigest()[:16]
 

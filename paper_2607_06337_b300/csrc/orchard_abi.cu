@@ -251,24 +251,14 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
     P.dof_off[w] = n_dofs;
     n_dofs += nv;
     P.m_off[w] = (int)P.anc.size();
-    int row = 0;
-    std::vector<int> rowstart(nv);
-    for (int i = 0; i < nv; ++i) {
-      rowstart[i] = row;
-      int j = i;
-      for (int c = 0; c <= ddep[i]; ++c) {
-        P.anc.push_back((unsigned)j | ((unsigned)dbody[j] << 16));
-        j = dpar[j];
-      }
-      row += ddep[i] + 1;
-    }
-    const int nm = row;
-    // Factorisation levels: the bodies with DOFs by the depth of their first DOF, each level in
-    // depth-first preorder (children in index order), so the bodies of one level below any
-    // given DOF are contiguous. Per (level l, ancestor distance c = 1..l, position p): the
-    // c-th ancestor of the p-th body's first DOF, as {its row start - c, it}, level-major.
+    // Ancestor-row storage, laid out by factorisation level (the depth of a joint's first DOF)
+    // and, within a level, in its depth-first order: the level's x rows (length l + 1), then
+    // its y' rows (length l + 2), each at a stride padded to an odd number of floats. The
+    // factorisation reads the rows of 32 consecutive joints of a level at once, one lane each,
+    // and an odd stride puts those 32 reads in 32 different shared-memory banks. Every access
+    // goes through the row starts (bj, bl_info, fac_tgt, anc), so nothing else depends on it.
+    std::vector<int> pre;  // depth-first preorder of the bodies (children in index order)
     {
-      std::vector<int> pre;
       pre.reserve(nb);
       std::vector<int> stack;
       if (nb > 0) stack.push_back(0);
@@ -278,9 +268,39 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
         pre.push_back(b);
         for (int c = ccount[b] - 1; c >= 0; --c) stack.push_back(cfirst[b] + c);
       }
-      int maxd = -1;
-      for (int b = 0; b < nb; ++b)
-        if (nd[b] > 0) maxd = std::max(maxd, ddep[dof0[b]]);
+    }
+    int maxd = -1;
+    for (int b = 0; b < nb; ++b)
+      if (nd[b] > 0) maxd = std::max(maxd, ddep[dof0[b]]);
+    std::vector<int> rowstart(nv, 0);
+    int row = 0;
+    for (int l = 0; l <= maxd; ++l) {
+      const int sx = (l + 1) | 1, sy = (l + 2) | 1;
+      int nx = 0, ny = 0;
+      for (int b : pre)
+        if (nd[b] > 0 && ddep[dof0[b]] == l) rowstart[dof0[b]] = row + sx * nx++;
+      row += sx * nx;
+      for (int b : pre)
+        if (nd[b] == 2 && ddep[dof0[b]] == l) rowstart[dof0[b] + 1] = row + sy * ny++;
+      row += sy * ny;
+    }
+    const int nm = row;
+    {
+      std::vector<unsigned> anc_w(nm, 0u);
+      for (int i = 0; i < nv; ++i) {
+        int j = i;
+        for (int c = 0; c <= ddep[i]; ++c) {
+          anc_w[rowstart[i] + c] = (unsigned)j | ((unsigned)dbody[j] << 16);
+          j = dpar[j];
+        }
+      }
+      P.anc.insert(P.anc.end(), anc_w.begin(), anc_w.end());
+    }
+    // Factorisation levels: the bodies with DOFs by the depth of their first DOF, each level in
+    // depth-first preorder (children in index order), so the bodies of one level below any
+    // given DOF are contiguous. Per (level l, ancestor distance c = 1..l, position p): the
+    // c-th ancestor of the p-th body's first DOF, as {its row start - c, it}, level-major.
+    {
       P.bl_off[w] = (int)P.bl_bound.size();
       P.fac_off[w] = (int)P.fac_tgt.size();
       std::vector<int> first;  // first DOF of each level position
