@@ -246,8 +246,13 @@ def run_reference(args):
 def fwd_adjoint(args, dev, rank, ws):
     """Forward + adjoint body-steps/s on the differentiation workload: 1024 trees of 200
     segment bodies and 30 apples, a 200-step rollout under a fixed 5 N pull on one apple per
-    tree, tip positions recorded, checkpoints every 20 steps; the loss is the squared error of
-    the tips against a target rollout, and the backward gives dL/dk, dL/dkd, dL/dq0, dL/dqd0.
+    tree, tip positions recorded; the loss is the squared error of the tips against a target
+    rollout, and the backward gives dL/dk, dL/dkd, dL/dq0, dL/dqd0.
+
+    Two forms of the record are timed: the forward's full tape (the backward runs no step
+    again; taken when it fits in half the free device memory) and checkpoints every
+    ``--adj-ckpt`` steps (each segment replayed once in the backward). The line's value is the
+    faster one; the other is reported beside it.
 
     The target here is this library's own rollout with every k scaled by U(0.8, 1.2) (the
     timing does not depend on it; the tests take the target from the oracle)."""
@@ -260,7 +265,7 @@ def fwd_adjoint(args, dev, rank, ws):
     # the stress workload inverts the pivots of twigs under 5 mm in FP64
     fl = I.Flags(fp64_twig_diam=0.005 if name == I.STRESS else 0.0)
     f = I.make_forest(name, n_worlds=nw, sweep=rank)
-    n, ce = args.adj_steps or I.WORKLOAD_STEPS[name], args.adj_ckpt
+    n = args.adj_steps or I.WORKLOAD_STEPS[name]
     sim = B.Simulator(f, fl, device=dev)
     stream = torch.cuda.current_stream()
     dev_in = [torch.as_tensor(np.ascontiguousarray(a, np.float32).reshape(-1), device=dev)
@@ -268,11 +273,12 @@ def fwd_adjoint(args, dev, rank, ws):
     k0 = torch.as_tensor(np.asarray(f.k, np.float32), device=dev)
     rng = np.random.default_rng(4321 + rank)
     kp = torch.as_tensor(np.asarray(f.k * rng.uniform(0.8, 1.2, f.n_bodies), np.float32), device=dev)
-    tips, ckpt, rec = sim.record_buffers(n, ce)
+    tips, _, rec = sim.record_buffers(n, args.adj_ckpt)
     sim.set_gains(kp)
     sim.reset_from_device(*dev_in)
     sim.rollout(n, record=rec)
     target = tips.clone()
+    del tips, rec
     sim.set_gains(k0)
     if not args.no_autotune:
         sim.reset_from_device(*dev_in)
@@ -280,60 +286,78 @@ def fwd_adjoint(args, dev, rank, ws):
     counts = np.diff(f.tip_off)
     w_tip = torch.as_tensor(np.repeat(2.0 / (n * np.maximum(counts, 1)), counts).astype(np.float32),
                             device=dev)[None, :, None]
-    work = torch.empty(B.backward_workspace_bytes(sim.model, ce), dtype=torch.uint8, device=dev)
     grads = tuple(torch.zeros(m, dtype=torch.float32, device=dev) for m in (f.n_bodies, f.n_bodies, f.n_dofs,
                                                                            f.n_dofs))
-    dtips = torch.empty_like(tips)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-
-    def one(k, ev=None):
-        flush.fill_(k & 0xff)
-        sim.reset_from_device(*dev_in)
-        if ev:
-            ev[0].record(stream)
-        sim.rollout(n, record=rec)
-        if ev:
-            ev[1].record(stream)
-        torch.sub(tips, target, out=dtips)
-        dtips.mul_(w_tip)
-        grads[0].zero_()
-        grads[1].zero_()
-        if ev:
-            ev[2].record(stream)
-        sim.backward(n, rec, dtips, grads=grads, workspace=work)
-        if ev:
-            ev[3].record(stream)
-
-    for k in range(args.warmup):
-        one(k)
-    torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    B.launch_count(reset=True)
-    for k in range(args.steps):
-        one(k, evs[k])
-    torch.cuda.synchronize()
-    launches = B.launch_count()
-    fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
-    bwd_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
-    tot_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
     bodies = costs.body_count(f)
+
+    def timed(ce):
+        """(fwd_ms, bwd_ms, tot_ms, launches, grads finite, record bytes) with checkpoints every
+        ce steps, or the full tape (ce 0)."""
+        tips, buf, rec = sim.record_buffers(n, ce)
+        work = torch.empty(B.backward_workspace_bytes(sim.model, ce), dtype=torch.uint8, device=dev)
+        dtips = torch.empty_like(tips)
+
+        def one(k, ev=None):
+            flush.fill_(k & 0xff)
+            sim.reset_from_device(*dev_in)
+            if ev:
+                ev[0].record(stream)
+            sim.rollout(n, record=rec)
+            if ev:
+                ev[1].record(stream)
+            torch.sub(tips, target, out=dtips)
+            dtips.mul_(w_tip)
+            grads[0].zero_()
+            grads[1].zero_()
+            if ev:
+                ev[2].record(stream)
+            sim.backward(n, rec, dtips, grads=grads, workspace=work)
+            if ev:
+                ev[3].record(stream)
+
+        for k in range(args.warmup):
+            one(k)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        B.launch_count(reset=True)
+        for k in range(args.steps):
+            one(k, evs[k])
+        torch.cuda.synchronize()
+        launches = B.launch_count()
+        fwd_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+        bwd_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+        tot_ms = statistics.mean(e[0].elapsed_time(e[3]) for e in evs)
+        if ws > 1:
+            t = torch.tensor([tot_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        g_ok = all(bool(torch.isfinite(g).all()) for g in grads)
+        return fwd_ms, bwd_ms, tot_ms, launches, g_ok, buf.numel()
+
+    free, _ = torch.cuda.mem_get_info(dev)
+    tape_fits = B.tape_bytes(sim.model, n) <= free // 2
+    runs = {}
+    if tape_fits:
+        runs["tape"] = timed(0)
+    runs["checkpoints"] = timed(args.adj_ckpt)
+    mode = min(runs, key=lambda k: runs[k][2])
+    fwd_ms, bwd_ms, tot_ms, launches, g_ok, rec_bytes = runs[mode]
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
     peak_tf = fp32_peak_tflops(sm_mhz)
     fwd_fl = costs.flops_per_step(f) * n
-    bwd_fl = costs.adjoint_flops_per_step(f) * n
-    g_ok = all(bool(torch.isfinite(g).all()) for g in grads)
+    bwd_fl = costs.adjoint_flops_per_step(f, replay=(mode == "checkpoints")) * n
     desc = (f"{nw} trees x 200 segment bodies x 30 apples, {n} steps, fixed 5 N pull" if name == I.DIFF else
             f"{nw} mixed trees (50/400/2000 bodies), {n} steps, FP64 pivots on twigs under 5 mm")
-    return {
-        "workload": f"{name}: {desc}, checkpoints every {ce} steps, tip-tracking loss",
+    rec_desc = (f"the forward's full tape ({rec_bytes / 1e9:.2f} GB)" if mode == "tape" else
+                f"checkpoints every {args.adj_ckpt} steps")
+    out = {
+        "workload": f"{name}: {desc}, {rec_desc}, tip-tracking loss",
+        "record": mode,
         "value": ws * bodies * n / (tot_ms / 1e3), "unit": UNIT,
         "ms_per_step": tot_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
         "fwd_only_value": ws * bodies * n / (fwd_ms / 1e3),
@@ -345,6 +369,13 @@ def fwd_adjoint(args, dev, rank, ws):
                              "unit": "TFLOP/s", "frac": fwd_fl / (fwd_ms / 1e3) / 1e12 / peak_tf},
         "l2": "flushed (256 MB write) before every timed step",
     }
+    for other, r in runs.items():
+        if other != mode:
+            out[other] = {"value": ws * bodies * n / (r[2] / 1e3), "fwd_ms": r[0], "bwd_ms": r[1],
+                          "record_bytes": r[5], "grads_finite": r[4]}
+    if not tape_fits:
+        out["tape"] = {"skipped": f"{B.tape_bytes(sim.model, n) / 1e9:.1f} GB tape over half the free memory"}
+    return out
 
 
 def damped_leg(args, dev, forest, S, flush):

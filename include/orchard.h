@@ -236,14 +236,24 @@ ot_status ot_step(ot_model* model, ot_state* state, const float* ext_force, cons
 /* Record of a rollout (device buffers, any may be NULL):
  *   tips: [n_steps][n_tips][3] tip positions after every step;
  *   ckpt: state snapshots taken before steps 0, ckpt_every, 2 ckpt_every, ...
- *         (ot_ckpt_bytes gives the size for n_steps). */
+ *         (ot_ckpt_bytes gives the size for n_steps);
+ *   tape: the adjoint's full tape (ot_tape_bytes gives the size for n_steps; 16-byte aligned):
+ *         every step's start state and what the reverse of the step reads from its forward
+ *         pass (joint origins, DOF axes, the solution, apple data, the snapped flags, the
+ *         factors, the end velocities), so that ot_rollout_backward runs no step again. It
+ *         trades memory for the replay of checkpoint segments: about 40 KB per step of a
+ *         200-body world (8 GB for 1024 such worlds over 200 steps).
+ * A buffer too small (or a misaligned tape) fails with OT_EINVAL before any work is queued. */
 typedef struct ot_record {
   float* tips;
   void* ckpt;
   size_t ckpt_bytes;
   int32_t ckpt_every;
+  float* tape;
+  size_t tape_bytes;
 } ot_record;
 ot_status ot_ckpt_bytes(const ot_model* model, int32_t n_steps, int32_t ckpt_every, size_t* bytes);
+ot_status ot_tape_bytes(const ot_model* model, int32_t n_steps, size_t* bytes);
 
 /* n_steps steps from absolute step index step0: one persistent launch per size class over a
  * cost-sorted work queue (each group of threads pops a world and runs all its steps),
@@ -260,14 +270,19 @@ ot_status ot_rollout_plain(ot_model* model, ot_state* state, int32_t n_steps, in
  * Adjoint of a recorded rollout with the break and detach masks frozen as recorded (an
  * addition: the paper simulates forward only and never differentiates the step).
  * The forward must have been run by ot_rollout with the same model, n_steps, step0, dt and
- * pulls, and a record holding checkpoints (ckpt, ckpt_every). The caller gives the cotangent
+ * pulls, and a record holding a tape or checkpoints (ckpt, ckpt_every); with both, the tape is
+ * used. A world the forward froze on a non-finite state gets NaN gradients (tape) or whatever
+ * its replay gives (checkpoints). The caller gives the cotangent
  * of the recorded tips, dL_dtips [n_steps][n_tips][3] (device); for the tip-tracking loss
  * L = sum_t sum_tips |p_t - p*_t|^2 / (n_steps n_tips_of_world) it is 2 (p - p*) / (...).
  * Gradients (device, any may be NULL): dk, dkd [nb] per joint are ACCUMULATED into; dq0,
- * dqd0 [n_dofs] (the initial state) are written. Each segment between checkpoints is
- * recomputed forward with the forward's step code (equal to the recorded run up to the last
- * bits: it is compiled into another kernel) and then swept in reverse step by step.
- * workspace: device buffer of at least ot_backward_workspace_bytes bytes (256-byte aligned). */
+ * dqd0 [n_dofs] (the initial state) are written. Without a tape, each segment between
+ * checkpoints is recomputed forward with the forward's step code (equal to the recorded run up
+ * to the last bits: it is compiled into another kernel) and then swept in reverse step by step;
+ * with a tape, the steps are swept in reverse straight from it.
+ * workspace: device buffer of at least ot_backward_workspace_bytes bytes (256-byte aligned),
+ * queried with the record's ckpt_every, or 0 for a record with a tape (no segment buffers);
+ * NULL when that size is 0. */
 typedef struct ot_grads {
   float* dk;
   float* dkd;

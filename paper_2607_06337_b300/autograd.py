@@ -3,9 +3,11 @@
 ``tip_rollout(sim, k, kd, q0, qd0, n_steps, ckpt_every)`` runs ``n_steps`` steps of every world
 of ``sim`` from the initial joint state (q0, qd0) with per-body stiffness k and damping kd
 (Sec. IV-A, Eq. 4) and returns the recorded tip positions [n_steps, n_tips, 3]. Its backward
-is the hand-written adjoint kernel: each checkpoint segment is recomputed forward and swept
-in reverse, with the break and detach masks frozen as the forward recorded them (the paper
-simulates forward only; differentiating the step is an addition of this library).
+is the hand-written adjoint kernel, with the break and detach masks frozen as the forward
+recorded them (the paper simulates forward only; differentiating the step is an addition of
+this library): each checkpoint segment is recomputed forward and swept in reverse, or with
+``ckpt_every`` 0 the forward keeps the full tape (ot_tape_bytes of device memory) and the
+backward sweeps it in reverse without recomputing any step.
 
 Apples start from the forest's initial apple state; all four inputs are float32 CUDA tensors.
 The forward overwrites the model's k and kd and the state of ``sim``; the backward writes the

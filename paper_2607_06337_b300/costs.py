@@ -89,13 +89,14 @@ def flops_per_step(forest) -> float:
     return float(np.sum(F_BODY * nb + F_APPLE * na + F_DOF * nv + F_ENTRY * E + F_PAIR * P))
 
 
-def adjoint_flops_per_step(forest) -> float:
-    """Flops of one step of the backward pass: the segment replay's forward step (whose records
-    the reverse reads, so the step runs once more, not twice) plus the reverse terms."""
+def adjoint_flops_per_step(forest, replay=True) -> float:
+    """Flops of one step of the backward pass: the reverse terms, plus with checkpoints the
+    segment replay's forward step (whose records the reverse reads, so the step runs once more,
+    not twice); with the forward's full tape (replay=False) no step runs again."""
     nb, nv, na, E, P = world_terms(forest)
     nt = np.diff(forest.tip_off).astype(np.int64)
-    return 1.0 * flops_per_step(forest) + float(np.sum(A_BODY * nb + A_DOF * nv + A_APPLE * na + A_ENTRY * E +
-                                                        A_TIP * nt))
+    rev = float(np.sum(A_BODY * nb + A_DOF * nv + A_APPLE * na + A_ENTRY * E + A_TIP * nt))
+    return (flops_per_step(forest) if replay else 0.0) + rev
 
 
 def hbm_bytes_per_rollout(forest) -> float:

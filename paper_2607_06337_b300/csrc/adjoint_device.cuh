@@ -59,23 +59,6 @@ HD void st_rec(float* dst, const float (&v)[N]) {
   for (int i = 0; i < N; ++i) dst[i] = v[i];
 #endif
 }
-// Copy n floats (rounded up to whole float4; both ends 16-byte aligned, padding behind both
-// regions) from src to dst, group-parallel.
-template <int TPW>
-HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
-#ifdef __CUDA_ARCH__
-  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) != 0) {
-    for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];  // not expected: the layouts keep 16-byte alignment
-    return;
-  }
-  const int n4 = (n + 3) >> 2;
-  float4* d4 = reinterpret_cast<float4*>(dst);
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int i = g.lane; i < n4; i += TPW) d4[i] = s4[i];
-#else
-  for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];
-#endif
-}
 HD void put3(float* r, int o, f3 v) { r[o] = v.x; r[o + 1] = v.y; r[o + 2] = v.z; }
 HD f3 get3(const float* r, int o) { return mk(r[o], r[o + 1], r[o + 2]); }
 HD m3 getm(const float* r, int o) { return {get3(r, o), get3(r, o + 3), get3(r, o + 6)}; }
@@ -120,7 +103,7 @@ struct AdjLayout {
     A.vh = o; o += WsLayout::r4(3 * na);
     A.head = o;
     A.C = o; o += 44 * nb;
-    A.snap = WsLayout::r4(WsLayout::state_words(nb, nv, na));
+    A.snap = WsLayout::snap_words(nb, nv, na);
     A.total = o;
     return A;
   }
@@ -136,32 +119,13 @@ HD void snapshot(float* ws, const WsLayout& L, float* seg, const AdjLayout& A, i
   g.sync();
 }
 
-// What the reverse of one step reads from that step's forward workspace, saved during the
-// segment's replay so the step need not run again: joint origins and DOF axes, the solution
-// Delta and the apple data, the snapped flags, the factors, and qd at the step's end.
-HD long long step_record_words(int nb, int nv, int nm, int na) {
-  const WsLayout L = WsLayout::make(nb, nv, nm, na);
-  return (long long)WsLayout::r4(L.E - L.X + 3 * nv) + WsLayout::r4(L.AT - L.r + 10 * na) + WsLayout::r4(nb) +
-         WsLayout::r4(nm) + WsLayout::r4(nv);
-}
-
-template <int TPW>
-HD void record_part(float* rec, long long& o, float* ws_part, int n, bool save, const Group<TPW>& g) {
-  if (save) copy4<TPW>(rec + o, ws_part, n, g);
-  else copy4<TPW>(ws_part, rec + o, n, g);
-  o += WsLayout::r4(n);
-}
-
+// One step's record (WsLayout::record_words): saved by the forward rollout into its tape, or
+// by the backward during a checkpoint segment's replay, so that the step's reverse need not
+// run the step again.
 template <int TPW>
 HD void step_record(float* ws, const WsLayout& L, const WState& s, float* wa, const AdjLayout& A,
                     const WorldView& v, float* rec, bool save, const Group<TPW>& g) {
-  long long o = 0;
-  record_part<TPW>(rec, o, ws + L.X, L.E - L.X + 3 * v.nv, save, g);   // X, then E
-  record_part<TPW>(rec, o, ws + L.r, L.AT - L.r + 10 * v.na, save, g);  // r, then AT
-  record_part<TPW>(rec, o, ws + L.SN, v.nb, save, g);
-  record_part<TPW>(rec, o, ws + L.M, v.nm, save, g);
-  record_part<TPW>(rec, o, save ? s.qd : wa + A.qd1, v.nv, save, g);    // qd at the step's end
-  g.sync();
+  record_copy<TPW>(ws, L, save ? s.qd : wa + A.qd1, v, rec, save, g);
 }
 
 // Load checkpoint `slot` of the forward record into the private state (its world's ranges).
@@ -886,13 +850,68 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   }
 }
 
-// Backward pass of one world over a recorded rollout.
+// The seed of the backward pass: the cotangents of the final state from the last record's tips
+// (taken at the final configuration, which the staged state holds).
 template <int TPW>
+HD void reverse_final(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
+                      const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
+                      const Group<TPW>& g, f3 gv) {
+  for (int l = 0; l < v.nL; ++l) {
+    const int lo = v.lv[l], hi = v.lv[l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW)
+      tape_body(m, s, v, A, wa, wa + A.zero, 0.f, wa + A.zero, wa + A.zero, b, gv);
+    g.sync();
+  }
+  RevArgs ra;
+  ra.dyn = 0;
+  ra.delta = wa + A.zero; ra.lam = wa + A.zero; ra.qd1 = wa + A.zero;
+  ra.tipbar = ba.dtips + (long long)(a.n_steps - 1) * a.n_tips_total * 3;
+  ra.sphi = 0.f;
+  ra.cs = cs;
+  for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + a.n_steps);
+  g.sync();
+  for (int l = v.nL - 1; l >= 0; --l) {
+    const int lo = v.lv[l], hi = v.lv[l + 1];
+    for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);
+    g.sync();
+  }
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    wa[A.qb1 + i] = wa[A.qb + i];
+    wa[A.qb + i] = 0.f;
+  }
+  g.sync();
+}
+
+// The reverse of step t from its start state (snapshot `snap`) and its record `rec`: the
+// cotangents of its end state in A.qb1 / qdb1 / ub1 / vb1 become those of its start state.
+template <int TPW>
+HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
+                         const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
+                         const float* snap, const float* rec, const Group<TPW>& g, int t, f3 gv) {
+  copy4<TPW>(ws + L.S, snap, A.snap, g);
+  g.sync();
+  step_record<TPW>(ws, L, s, wa, A, v, const_cast<float*>(rec), false, g);
+  reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv);
+  for (int i = g.lane; i < v.nv; i += TPW) {
+    wa[A.qb1 + i] = wa[A.qb + i];
+    wa[A.qdb1 + i] = wa[A.qdb + i];
+  }
+  for (int i = g.lane; i < 3 * v.na; i += TPW) {
+    wa[A.ub1 + i] = wa[A.ub + i];
+    wa[A.vb1 + i] = wa[A.vb + i];
+  }
+  g.sync();
+}
+
+// Backward pass of one world over a recorded rollout.
 // ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
 // wc: the C slots when they are not at wa + A.C (null: they are), seg: ckpt_every snapshots
-// and step records (global memory); ws, wa and wc may be in shared or global memory. Each
-// segment is replayed once, forward, saving every step's start state and its record; then its
-// steps are reversed last to first from those.
+// and step records (global memory); ws, wa and wc may be in shared or global memory.
+// With the forward's tape (a.tape), every step's start state and record are there: the steps
+// are reversed last to first straight from it. Otherwise each checkpoint segment is replayed
+// once, forward, saving every step's start state and its record into seg; then its steps are
+// reversed last to first from those.
+template <int TPW>
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
                        float* wc, float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
@@ -900,67 +919,55 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
   const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
   float* cs = wc ? wc : wa + A.C;
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);  // the world's private state
-  // the segment buffer: ckpt_every snapshots, then ckpt_every step records
-  const long long recw = step_record_words(v.nb, v.nv, v.nm, v.na);
-  float* recs = seg + (long long)a.ckpt_every * A.snap;
+  const long long recw = WsLayout::record_words(v.nb, v.nv, v.nm, v.na);
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
-  const float dt = a.dt;
-  const int T = a.n_steps, ce = a.ckpt_every;
-  const int nseg = (T + ce - 1) / ce;
+  const int T = a.n_steps;
   for (int i = g.lane; i < v.nv; i += TPW) {
     wa[A.qb1 + i] = 0.f; wa[A.qdb1 + i] = 0.f; wa[A.zero + i] = 0.f; wa[A.qb + i] = 0.f; wa[A.qdb + i] = 0.f;
   }
   for (int i = g.lane; i < 3 * v.na; i += TPW) { wa[A.ub1 + i] = 0.f; wa[A.vb1 + i] = 0.f; }
   g.sync();
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    const int t0 = sg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
-    load_ckpt(a, v, s, sg, g);
-    for (int t = t0; t < t1; ++t) {
-      snapshot(ws, L, seg, A, t - t0, true, g);
-      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
-      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
-    }
-    if (sg == nseg - 1) {
-      // the last record's tips at the final configuration
-      for (int l = 0; l < v.nL; ++l) {
-        const int lo = v.lv[l], hi = v.lv[l + 1];
-        for (int b = lo + g.lane; b < hi; b += TPW)
-          tape_body(m, s, v, A, wa, wa + A.zero, 0.f, wa + A.zero, wa + A.zero, b, gv);
-        g.sync();
-      }
-      RevArgs ra;
-      ra.dyn = 0;
-      ra.delta = wa + A.zero; ra.lam = wa + A.zero; ra.qd1 = wa + A.zero;
-      ra.tipbar = ba.dtips + (long long)(T - 1) * a.n_tips_total * 3;
-      ra.sphi = 0.f;
-      ra.cs = cs;
-      for (int b = g.lane; b < v.nb; b += TPW) reverse_seed(m, s, a, v, L, A, ws, wa, ra, b, gv, a.step0 + T);
-      g.sync();
-      for (int l = v.nL - 1; l >= 0; --l) {
-        const int lo = v.lv[l], hi = v.lv[l + 1];
-        for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);
-        g.sync();
+  if (a.tape) {
+    const float* tape = a.tape + (long long)(T + 1) * m.tape_off[w];
+    const float* trec = tape + (long long)(T + 1) * A.snap;
+    copy4<TPW>(ws + L.S, tape + (long long)T * A.snap, A.snap, g);  // the final state
+    g.sync();
+    if (*s.status & 1u) {
+      // the forward froze this world on a non-finite state: its gradients are NaN
+      const float nan = u2f(0x7fc00000u);
+      for (int i = g.lane; i < v.nb; i += TPW) {
+        if (ba.dk) ba.dk[v.b0 + i] += nan;
+        if (ba.dkd) ba.dkd[v.b0 + i] += nan;
       }
       for (int i = g.lane; i < v.nv; i += TPW) {
-        wa[A.qb1 + i] = wa[A.qb + i];
-        wa[A.qb + i] = 0.f;
+        if (ba.dq0) ba.dq0[v.d0 + i] = nan;
+        if (ba.dqd0) ba.dqd0[v.d0 + i] = nan;
       }
       g.sync();
+      return;
     }
-    for (int t = t1 - 1; t >= t0; --t) {
-      snapshot(ws, L, seg, A, t - t0, false, g);
-      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, false, g);
-      reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv);
-      for (int i = g.lane; i < v.nv; i += TPW) {
-        wa[A.qb1 + i] = wa[A.qb + i];
-        wa[A.qdb1 + i] = wa[A.qdb + i];
+    reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
+    for (int t = T - 1; t >= 0; --t)
+      reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, tape + (long long)t * A.snap, trec + (long long)t * recw,
+                            g, t, gv);
+  } else {
+    // the segment buffer: ckpt_every snapshots, then ckpt_every step records
+    float* recs = seg + (long long)a.ckpt_every * A.snap;
+    const int ce = a.ckpt_every;
+    const int nseg = (T + ce - 1) / ce;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int t0 = sg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
+      load_ckpt(a, v, s, sg, g);
+      for (int t = t0; t < t1; ++t) {
+        snapshot(ws, L, seg, A, t - t0, true, g);
+        step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
+        step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
       }
-      for (int i = g.lane; i < 3 * v.na; i += TPW) {
-        wa[A.ub1 + i] = wa[A.ub + i];
-        wa[A.vb1 + i] = wa[A.vb + i];
-      }
-      g.sync();
+      if (sg == nseg - 1) reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
+      for (int t = t1 - 1; t >= t0; --t)
+        reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, seg + (long long)(t - t0) * A.snap,
+                              recs + (long long)(t - t0) * recw, g, t, gv);
     }
   }
   for (int i = g.lane; i < v.nv; i += TPW) {
@@ -968,7 +975,6 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
     if (ba.dqd0) ba.dqd0[v.d0 + i] = wa[A.qdb1 + i];
   }
   g.sync();
-  (void)dt;
 }
 
 }  // namespace

@@ -98,7 +98,7 @@ long long backward_adj_floats(int nb, int nv, int na) { return AdjLayout::make(n
 long long backward_adj_head_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).head; }
 
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every) {
-  return (long long)ckpt_every * (AdjLayout::make(nb, nv, na).snap + step_record_words(nb, nv, nm, na));
+  return (long long)ckpt_every * WsLayout::tape_unit(nb, nv, nm, na);
 }
 
 }  // namespace orchard

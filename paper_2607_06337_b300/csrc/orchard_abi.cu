@@ -78,6 +78,7 @@ struct Packed {
   std::vector<float4> ap0, ap1;
   std::vector<int> apple_body, tip_body, btip;
   std::vector<float4> tip_local, gravity;
+  std::vector<long long> tape_off;    // [W+1] prefix sums of WsLayout::tape_unit (floats)
   std::vector<int> queue;
   std::vector<ClassInfo> classes;
   // domain-randomisation base (empty unless the descriptor has the material): per body
@@ -169,6 +170,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.bl_info.assign(NB, make_int4(0, 0, -1, 0));
   P.bl_fbase.clear();
   P.fac_off.assign(W + 1, 0);
+  P.tape_off.assign(W + 1, 0);
   P.fac_tgt.clear();
   P.btip.clear();
   std::vector<long long> ws(W);
@@ -352,6 +354,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
     }
     wnb[w] = nb; wnv[w] = nv; wnm[w] = nm; wna[w] = na;
     ws[w] = WsLayout::make(nb, nv, nm, na).total;
+    P.tape_off[w + 1] = P.tape_off[w] + WsLayout::tape_unit(nb, nv, nm, na);
     long long sumsq = 0;
     for (int i = 0; i < nv; ++i) sumsq += (long long)ddep[i] * (ddep[i] + 1) / 2;
     cost[w] = 700.0 * nb + 12.0 * nm + 2.0 * sumsq + 80.0 * na;
@@ -539,7 +542,7 @@ namespace {
 struct ModelLayout {
   size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, bj, anc, bl_off,
       bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue,
-      dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, total;
+      dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, tape_off, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -570,6 +573,7 @@ ModelLayout model_layout(const Packed& P) {
   L.dr_geo = c.take<float4>(P.dr_geo.size()); L.dr_jpos = c.take<float4>(P.dr_jpos.size());
   L.dr_com = c.take<float4>(P.dr_com.size()); L.dr_ap0 = c.take<float4>(P.dr_ap0.size());
   L.dr_tip = c.take<float4>(P.dr_tip.size());
+  L.tape_off = c.take<long long>(W1);
   L.total = c.off;
   return L;
 }
@@ -809,6 +813,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.dr_geo, P.dr_geo.data(), vbytes(P.dr_geo)); put(L.dr_jpos, P.dr_jpos.data(), vbytes(P.dr_jpos));
   put(L.dr_com, P.dr_com.data(), vbytes(P.dr_com)); put(L.dr_ap0, P.dr_ap0.data(), vbytes(P.dr_ap0));
   put(L.dr_tip, P.dr_tip.data(), vbytes(P.dr_tip));
+  put(L.tape_off, P.tape_off.data(), vbytes(P.tape_off));
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dev_buf, host.data(), L.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -845,6 +850,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.tip_local = (const float4*)(base + L.tip_local);
   dm.gravity = (const float4*)(base + L.gravity);
   dm.queue = (const int*)(base + L.queue);
+  dm.tape_off = (const long long*)(base + L.tape_off);
   m->w_bp0 = (float4*)(base + L.bp0); m->w_bp2 = (float4*)(base + L.bp2); m->w_bp3 = (float4*)(base + L.bp3);
   m->w_bp4 = (float4*)(base + L.bp4); m->w_ap0 = (float4*)(base + L.ap0); m->w_tip = (float4*)(base + L.tip_local);
   if (!P.dr_geo.empty()) {
@@ -974,6 +980,12 @@ ot_status ot_ckpt_bytes(const ot_model* m, int32_t n_steps, int32_t ckpt_every, 
   return OT_OK;
 }
 
+ot_status ot_tape_bytes(const ot_model* m, int32_t n_steps, size_t* bytes) {
+  if (!m || !bytes || n_steps < 0) return OT_EINVAL;
+  *bytes = (size_t)((long long)(n_steps + 1) * m->P.tape_off[m->P.W] * 4);
+  return OT_OK;
+}
+
 ot_status ot_step(ot_model* m, ot_state* s, const float* ext_force, const ot_force_schedule* pulls, int32_t step,
                   double dt, void* stream) {
   if (!m || !s || s->model != m || !(dt > 0)) return OT_EINVAL;
@@ -1009,13 +1021,19 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
       a.ckpt = (unsigned*)rec->ckpt;
       a.ckpt_every = rec->ckpt_every;
     }
+    if (rec->tape) {
+      size_t need = 0;
+      ot_tape_bytes(m, n_steps, &need);
+      if (rec->tape_bytes < need || ((uintptr_t)rec->tape) % 16) return OT_EINVAL;
+      a.tape = rec->tape;
+    }
   }
   cudaStream_t user = (cudaStream_t)stream;
   // graph key: everything the captured launches depend on
   char key[512];
-  std::snprintf(key, sizeof(key), "%p|%d|%d|%.17g|%p|%p|%p|%p|%p|%d", (void*)s->base, n_steps, step0, dt,
+  std::snprintf(key, sizeof(key), "%p|%d|%d|%.17g|%p|%p|%p|%p|%p|%d|%p", (void*)s->base, n_steps, step0, dt,
                 (const void*)a.pull_force, (const void*)a.pull_start, (const void*)a.tips, (void*)a.ckpt,
-                (const void*)a.pull_end, a.ckpt_every);
+                (const void*)a.pull_end, a.ckpt_every, (void*)a.tape);
   std::string skey = key;
   std::string sched_sig;
   for (const ClassInfo& ci : m->P.classes) {
@@ -1269,7 +1287,7 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
 }  // namespace
 
 ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, size_t* bytes) {
-  if (!m || !bytes || ckpt_every < 1) return OT_EINVAL;
+  if (!m || !bytes || ckpt_every < 0) return OT_EINVAL;
   size_t total = 0;
   for (const ClassInfo& ci : m->P.classes) {
     const BackPlan p = back_plan(m, ci, ckpt_every);
@@ -1282,22 +1300,33 @@ ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, siz
 ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
                               const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
                               ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
-  if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0) || !rec || !dL_dtips || !grads || !workspace)
-    return OT_EINVAL;
-  if (!rec->ckpt || rec->ckpt_every < 1) return OT_ESTATE;
+  if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0) || !rec || !dL_dtips || !grads) return OT_EINVAL;
+  // the tape when the forward wrote one, else the checkpoints (and segment replays)
+  const bool tape = rec->tape != nullptr;
+  if (!tape && (!rec->ckpt || rec->ckpt_every < 1)) return OT_ESTATE;
   if (((uintptr_t)workspace) % kAlign) return OT_EINVAL;
+  const int ce = tape ? 0 : rec->ckpt_every;
   size_t need = 0;
-  ot_ckpt_bytes(m, n_steps, rec->ckpt_every, &need);
-  if (rec->ckpt_bytes < need) return OT_EINVAL;
-  ot_backward_workspace_bytes(m, rec->ckpt_every, &need);
-  if (workspace_bytes < need) return OT_EINVAL;
+  if (tape) {
+    ot_tape_bytes(m, n_steps, &need);
+    if (rec->tape_bytes < need || ((uintptr_t)rec->tape) % 16) return OT_EINVAL;
+  } else {
+    ot_ckpt_bytes(m, n_steps, ce, &need);
+    if (rec->ckpt_bytes < need) return OT_EINVAL;
+  }
+  ot_backward_workspace_bytes(m, ce, &need);
+  if (workspace_bytes < need || (need > 0 && !workspace)) return OT_EINVAL;  // none needed: may be null
   StepArgs a = base_args(m, dt);
   a.step0 = step0;
   a.n_steps = n_steps;
   ot_status st = fill_pulls(a, pulls);
   if (st != OT_OK) return st;
-  a.ckpt = (unsigned*)rec->ckpt;
-  a.ckpt_every = rec->ckpt_every;
+  if (tape) {
+    a.tape = rec->tape;
+  } else {
+    a.ckpt = (unsigned*)rec->ckpt;
+    a.ckpt_every = ce;
+  }
   BackArgs ba{dL_dtips, grads->dk, grads->dkd, grads->dq0, grads->dqd0};
   cudaStream_t cs = (cudaStream_t)stream;
   float* work = (float*)workspace;
@@ -1315,14 +1344,14 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
   std::vector<float*> works(nk);
   for (int k = 0; k < nk; ++k) {
     works[k] = work;
-    const BackPlan p = back_plan(m, m->P.classes[k], rec->ckpt_every);
+    const BackPlan p = back_plan(m, m->P.classes[k], ce);
     work += p.slots * (size_t)p.sh.global_floats;
   }
   OT_CUDA(cudaEventRecord(m->fork_event, cs));
   ot_status result = OT_OK;
   for (int k = nk - 1; k >= 0; --k) {
     const ClassInfo& ci = m->P.classes[k];
-    const BackPlan p = back_plan(m, ci, rec->ckpt_every);
+    const BackPlan p = back_plan(m, ci, ce);
     cudaStream_t sk = m->class_streams[k];
     OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
     int bps = 0;

@@ -52,6 +52,8 @@ struct DevModel {
   const float4* tip_local;
   const float4* gravity; // per world
   const int* queue;      // world ids sorted by (size class, cost descending)
+  const long long* tape_off;  // [W+1] prefix sums of WsLayout::tape_unit over the worlds: the
+                              // tape of a T-step rollout gives world w floats from (T + 1) tape_off[w]
 };
 
 // State arrays in device memory (views into the caller's state buffer).
@@ -96,6 +98,8 @@ struct StepArgs {
   unsigned* ckpt;           // snapshots or null
   int ckpt_every;
   long long ckpt_words;     // 32-bit words per snapshot
+  float* tape;              // the adjoint's tape of the rollout (written by the forward, read by
+                            // the backward), or null
   int NB, NV, NA;           // totals (snapshot layout)
   int q_begin, q_end;       // queue range of this launch
   int* q_counter;           // next queue entry (relative to q_begin); null: one world per group
@@ -114,6 +118,18 @@ struct WsLayout {
   __host__ __device__ static int r4(int n) { return (n + 3) & ~3; }
   __host__ __device__ static int state_words(int nb, int nv, int na) {
     return 2 * r4(nv) + 6 * na + 3 * nb + 4 * na + 1;  // q and qd each padded to 4 floats
+  }
+  // The adjoint's tape of a T-step rollout, per world: T + 1 snapshots of the staged state (before
+  // every step, then the final state), then T step records, each holding what the reverse of the
+  // step reads from its forward workspace: joint origins and DOF axes, the solution Delta and the
+  // apple data, the snapped flags, the factors, and qd at the step's end.
+  __host__ __device__ static int snap_words(int nb, int nv, int na) { return r4(state_words(nb, nv, na)); }
+  __host__ __device__ static long long record_words(int nb, int nv, int nm, int na) {
+    const WsLayout L = make(nb, nv, nm, na);
+    return (long long)r4(L.E - L.X + 3 * nv) + r4(L.AT - L.r + 10 * na) + r4(nb) + r4(nm) + r4(nv);
+  }
+  __host__ __device__ static long long tape_unit(int nb, int nv, int nm, int na) {
+    return snap_words(nb, nv, na) + record_words(nb, nv, nm, na);
   }
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;

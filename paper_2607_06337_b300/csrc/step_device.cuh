@@ -1053,6 +1053,43 @@ HD void copy_state(const WState& d, const WState& src, const WorldView& v, const
   g.sync();
 }
 
+// Copy n floats (rounded up to whole float4; both ends 16-byte aligned, padding behind both
+// regions) from src to dst, group-parallel.
+template <int TPW>
+HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
+#ifdef __CUDA_ARCH__
+  if (((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) != 0) {
+    for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];  // not expected: the layouts keep 16-byte alignment
+    return;
+  }
+  const int n4 = (n + 3) >> 2;
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  for (int i = g.lane; i < n4; i += TPW) d4[i] = s4[i];
+#else
+  for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];
+#endif
+}
+// Copy one step's record (WsLayout::record_words floats at rec) from the workspace and qd
+// (save) or back into them (restore).
+template <int TPW>
+HD void record_part(float* rec, long long& o, float* ws_part, int n, bool save, const Group<TPW>& g) {
+  if (save) copy4<TPW>(rec + o, ws_part, n, g);
+  else copy4<TPW>(ws_part, rec + o, n, g);
+  o += WsLayout::r4(n);
+}
+template <int TPW>
+HD void record_copy(float* ws, const WsLayout& L, float* qd, const WorldView& v, float* rec, bool save,
+                    const Group<TPW>& g) {
+  long long o = 0;
+  record_part<TPW>(rec, o, ws + L.X, L.E - L.X + 3 * v.nv, save, g);   // X, then E
+  record_part<TPW>(rec, o, ws + L.r, L.AT - L.r + 10 * v.na, save, g);  // r, then AT
+  record_part<TPW>(rec, o, ws + L.SN, v.nb, save, g);
+  record_part<TPW>(rec, o, ws + L.M, v.nm, save, g);
+  record_part<TPW>(rec, o, qd, v.nv, save, g);                          // qd at the step's end
+  g.sync();
+}
+
 // All steps of one world: its state is staged in the workspace for the whole rollout.
 template <int TPW>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
@@ -1066,11 +1103,21 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
   g.sync();
+  // the adjoint's tape (WsLayout::tape_unit): snapshots before every step and at the end, records
+  const int snap = WsLayout::snap_words(v.nb, v.nv, v.na);
+  const long long recw = WsLayout::record_words(v.nb, v.nv, v.nm, v.na);
+  float* tape = a.tape ? a.tape + (long long)(a.n_steps + 1) * m.tape_off[w] : nullptr;
+  float* trec = tape ? tape + (long long)(a.n_steps + 1) * snap : nullptr;
   for (int t = 0; t < a.n_steps; ++t) {
     if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
     if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
+    // the step's first write to the staged state comes after several group barriers
+    if (tape) copy4<TPW>(tape + (long long)t * snap, ws + L.S, snap, g);
     step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1);
+    if (tape) record_copy<TPW>(ws, L, s.qd, v, trec + (long long)t * recw, true, g);  // ends on a barrier
   }
+  // the final state (its status word tells the backward whether the world froze)
+  if (tape) copy4<TPW>(tape + (long long)a.n_steps * snap, ws + L.S, snap, g);
   if (a.tips && a.n_steps > 0) {
     fk_only(m, s, v, L, ws, g);
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);

@@ -82,7 +82,8 @@ class ForceSchedule(C.Structure):
 
 
 class Record(C.Structure):
-    _fields_ = [("tips", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_bytes", C.c_size_t), ("ckpt_every", C.c_int32)]
+    _fields_ = [("tips", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_bytes", C.c_size_t), ("ckpt_every", C.c_int32),
+                ("tape", C.c_void_p), ("tape_bytes", C.c_size_t)]
 
 
 class Grads(C.Structure):
@@ -107,6 +108,7 @@ _SIGS = {
     "ot_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(ForceSchedule), C.c_int32, C.c_double,
                           C.c_void_p]),
     "ot_ckpt_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "ot_tape_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_size_t)]),
     "ot_rollout": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.POINTER(ForceSchedule),
                              C.POINTER(Record), C.c_void_p]),
     "ot_rollout_plain": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
@@ -286,6 +288,12 @@ def ckpt_bytes(model, n_steps, ckpt_every) -> int:
     return n.value
 
 
+def tape_bytes(model, n_steps) -> int:
+    n = C.c_size_t(0)
+    _check(lib().ot_tape_bytes(model, int(n_steps), C.byref(n)), "ot_tape_bytes")
+    return n.value
+
+
 def get_schedule(model, k) -> Schedule:
     s = Schedule()
     _check(lib().ot_get_schedule(model, int(k), C.byref(s)), "ot_get_schedule")
@@ -404,13 +412,19 @@ class Simulator:
         model_randomize(self.model, factors, capsule_links, stream)
 
     def record_buffers(self, n_steps, ckpt_every, tips=True):
-        """Device buffers for a recorded rollout: tips [n_steps, n_tips, 3] and checkpoints."""
+        """Device buffers for a recorded rollout: tips [n_steps, n_tips, 3], and checkpoints every
+        ``ckpt_every`` steps, or with ``ckpt_every`` 0 the adjoint's full tape (ot_tape_bytes:
+        the backward then replays no step). Returns (tips, buffer, record)."""
         import torch
         t = torch.empty((n_steps, self.counts.tips, 3), dtype=torch.float32, device=self.device) if tips else None
+        tp = None if t is None else t.data_ptr()
+        if ckpt_every == 0:
+            nb = tape_bytes(self.model, n_steps)
+            buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            return t, buf, Record(tp, None, 0, 0, buf.data_ptr(), nb)
         nb = ckpt_bytes(self.model, n_steps, ckpt_every)
-        ck = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        rec = Record(None if t is None else t.data_ptr(), ck.data_ptr(), nb, ckpt_every)
-        return t, ck, rec
+        buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        return t, buf, Record(tp, buf.data_ptr(), nb, ckpt_every, None, 0)
 
     def backward(self, n_steps, record, dL_dtips, step0=0, dt=None, grads=None, workspace=None, stream=None):
         """Adjoint of a recorded rollout. Returns (dk, dkd, dq0, dqd0) as float32 device tensors.

@@ -233,6 +233,69 @@ def test_checkpoint_interval_does_not_change_the_gradient():
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("worlds,workload", [([7, 8], I.DIFF), ([23, 79], I.BATCH)])
+def test_tape_gives_the_checkpointed_gradient(worlds, workload):
+    """The forward's full tape (no step run again) against checkpoints every step and every 25
+    steps: the same gradient up to the last bits of each step (the backward's replay is
+    compiled into another kernel and may run at another group size), within 1e-5 of each
+    kind's largest entry; the batching worlds break branches and drop apples on the way."""
+    f = I.make_forest(workload, worlds=worlds)
+    fl = I.Flags()
+    n = 120
+    _, rec0 = O.rollout(f, fl, n, record_tips=True)
+    target = rec0["tips"] + np.random.default_rng(9).normal(0.0, 0.01, rec0["tips"].shape)
+    tape, _, sim = gpu_gradients(f, fl, n, 0, target)
+    for ce in (1, 25):
+        ref, _, _ = gpu_gradients(f, fl, n, ce, target, sim=sim)
+        for a, b in zip(tape, ref):
+            np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
+
+
+def test_tape_of_a_frozen_world_gives_nan_gradients_only_there():
+    """A world whose state is non-finite from the start is frozen by the forward: with the tape
+    its gradients are NaN, and the other world's are those of the checkpointed backward."""
+    torch = _torch()
+    f = I.make_forest(I.PLAIN, worlds=[0, 1])
+    f.q0 = f.q0.copy()
+    f.q0[f.dof_off[1] + 3] = np.nan
+    fl = I.Flags()
+    n = 30
+    _, rec0 = O.rollout(f.subset([0]), fl, n, record_tips=True)
+    target = np.zeros((n, f.n_tips, 3))
+    target[:, :f.tip_off[1]] = rec0["tips"] + 0.01
+    tape, _, sim = gpu_gradients(f, fl, n, 0, target)
+    ref, _, _ = gpu_gradients(f, fl, n, 10, target, sim=sim)
+    b1, d1 = f.body_off[1], f.dof_off[1]
+    for k, (a, b) in enumerate(zip(tape, ref)):
+        cut = b1 if k < 2 else d1
+        assert np.all(np.isnan(a[cut:])), k
+        np.testing.assert_allclose(a[:cut], b[:cut], rtol=0, atol=1e-5 * np.abs(b[:cut]).max())
+
+
+def test_tape_buffer_checks():
+    """A tape one float too small, or not on a 16-byte boundary, is refused (OT_EINVAL) by the
+    rollout and by the backward before any work is queued."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    f = I.make_forest(I.DIFF, worlds=[0])
+    sim = B.Simulator(f, I.Flags())
+    n = 8
+    need = B.tape_bytes(sim.model, n)
+    assert need > 0 and need % 16 == 0
+    buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    tips = torch.empty((n, sim.counts.tips, 3), dtype=torch.float32, device="cuda")
+    for ptr, nbytes in ((buf.data_ptr(), need - 4), (buf.data_ptr() + 4, need)):
+        rec = B.Record(tips.data_ptr(), None, 0, 0, ptr, nbytes)
+        with pytest.raises(B.OrchardError) as e:
+            sim.rollout(n, record=rec)
+        assert e.value.status == B.OT_EINVAL
+        with pytest.raises(B.OrchardError) as e:
+            sim.backward(n, rec, torch.zeros_like(tips))
+        assert e.value.status == B.OT_EINVAL
+    sim.rollout(n, record=B.Record(tips.data_ptr(), None, 0, 0, buf.data_ptr(), need))
+    torch.cuda.synchronize()
+
+
 def test_autograd_function_matches_the_direct_call():
     """tip_rollout + tip_loss + loss.backward() gives the gradients of ot_rollout_backward, and
     the forward returns the tips of a plain recorded rollout."""
@@ -261,14 +324,24 @@ def test_autograd_function_matches_the_direct_call():
     k2 = (k.detach() * 1.1).requires_grad_(True)
     tips2 = tip_rollout(sim, k2, kd.detach(), q0.detach(), qd0.detach(), n, ckpt_every=20)
     assert not torch.equal(tips2, tips)
+    # the full tape (ckpt_every 0): the same tips and gradients
+    grads = [t.grad.clone() for t in (k, kd, q0, qd0)]
+    for t in (k, kd, q0, qd0):
+        t.grad = None
+    tips3 = tip_rollout(sim, k, kd, q0, qd0, n, ckpt_every=0)
+    assert torch.equal(tips3, tips)
+    tip_loss(tips3.double(), torch.as_tensor(target, device=dev), f.tip_off).backward()
+    for t, r in zip((k, kd, q0, qd0), grads):
+        np.testing.assert_allclose(t.grad.cpu().numpy(), r.cpu().numpy(), rtol=0, atol=1e-5 * r.abs().max().item())
 
 
-def test_full_gradient_against_the_oracle_reverse_mode():
+@pytest.mark.parametrize("ckpt_every", [16, 0])
+def test_full_gradient_against_the_oracle_reverse_mode(ckpt_every):
     """Every coordinate of the gradient against the oracle's own FP64 adjoint (its reverse-mode
     tape): six generated 24-body trees with 6 apples each and a 12-body tree in which a joint
-    breaks and an apple detaches (masks frozen as recorded), 150 steps, checkpoints every 16,
-    a target 1 cm away. Per world and kind: |g - g_ref|_2 <= 1e-3 |g_ref|_2, and the largest
-    entry error within 2e-3 of the kind's largest entry."""
+    breaks and an apple detaches (masks frozen as recorded), 150 steps, checkpoints every 16 or
+    the forward's full tape (0), a target 1 cm away. Per world and kind: |g - g_ref|_2 <= 1e-3
+    |g_ref|_2, and the largest entry error within 2e-3 of the kind's largest entry."""
     from tests import _trees as T
     from tests.test_oracle_grad import event_tree
     trees = []
@@ -282,7 +355,7 @@ def test_full_gradient_against_the_oracle_reverse_mode():
     n = 150
     st, rec0 = O.rollout(f, fl, n, record_tips=True)
     target = rec0["tips"] + np.random.default_rng(4).normal(0.0, 0.01, rec0["tips"].shape)
-    g, ev, _ = gpu_gradients(f, fl, n, 16, target)
+    g, ev, _ = gpu_gradients(f, fl, n, ckpt_every, target)
     for w in range(f.n_worlds):
         assert PAR.events(ev["broken"], ev["break_step"], ev["detached"], ev["detach_step"], f, w) == \
             PAR.events(st.broken, st.break_step, st.detached, st.detach_step, f, w)
