@@ -907,11 +907,12 @@ HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, 
 // ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
 // wc: the C slots when they are not at wa + A.C (null: they are), seg: ckpt_every snapshots
 // and step records (global memory); ws, wa and wc may be in shared or global memory.
-// With the forward's tape (a.tape), every step's start state and record are there: the steps
+// TAPE: every step's start state and record are in the forward's tape (a.tape), and the steps
 // are reversed last to first straight from it. Otherwise each checkpoint segment is replayed
 // once, forward, saving every step's start state and its record into seg; then its steps are
-// reversed last to first from those.
-template <int TPW>
+// reversed last to first from those. The two are separate kernels, each compiled for its own
+// path.
+template <int TPW, bool TAPE>
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
                        float* wc, float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
@@ -928,7 +929,7 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
   }
   for (int i = g.lane; i < 3 * v.na; i += TPW) { wa[A.ub1 + i] = 0.f; wa[A.vb1 + i] = 0.f; }
   g.sync();
-  if (a.tape) {
+  if constexpr (TAPE) {
     const float* tape = a.tape + (long long)(T + 1) * m.tape_off[w];
     const float* trec = tape + (long long)(T + 1) * A.snap;
     copy4<TPW>(ws + L.S, tape + (long long)T * A.snap, A.snap, g);  // the final state

@@ -1,8 +1,9 @@
 // Backward (adjoint) kernel of a recorded rollout for sm_103a: a persistent grid whose thread
 // groups pop worlds from the cost-sorted queue and run backward_world (adjoint_device.cuh).
 // Each group owns one slot of the caller's workspace (the snapshots of one checkpoint
-// segment, plus whatever of its temporaries is not in shared memory); BackShape::mode says
-// which temporaries live in the block's shared memory:
+// segment, none when the forward kept its full tape, plus whatever of its temporaries is not
+// in shared memory). The tape and checkpoint forms are separate instantiations. BackShape::mode
+// says which temporaries live in the block's shared memory:
 //   0: none (forward and backward temporaries in the global slot),
 //   1: the forward step's temporaries (WsLayout),
 //   2: the forward step's and the backward's (WsLayout, then AdjLayout),
@@ -12,7 +13,7 @@
 namespace orchard {
 namespace {
 
-template <int TPW>
+template <int TPW, bool TAPE>
 __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
                                                        BackShape sh) {
   extern __shared__ __align__(16) float smem[];
@@ -50,23 +51,30 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
     const int qi = next[g.id];
     g.sync();
     if (qi >= a.q_end - a.q_begin) break;
-    backward_world<TPW>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
+    backward_world<TPW, TAPE>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
   }
 }
 
 template <int TPW>
-const void* backward_fn() {
-  return (const void*)backward_kernel<TPW>;
+const void* backward_fn(bool tape) {
+  return tape ? (const void*)backward_kernel<TPW, true> : (const void*)backward_kernel<TPW, false>;
 }
 
-const void* backward_fn_of(int tpw) {
+const void* backward_fn_of(int tpw, bool tape) {
   switch (tpw) {
-    case 32: return backward_fn<32>();
-    case 64: return backward_fn<64>();
-    case 128: return backward_fn<128>();
-    case 256: return backward_fn<256>();
+    case 32: return backward_fn<32>(tape);
+    case 64: return backward_fn<64>(tape);
+    case 128: return backward_fn<128>(tape);
+    case 256: return backward_fn<256>(tape);
     default: return nullptr;
   }
+}
+
+template <int TPW>
+void launch_of(int blocks, int threads, size_t smem, cudaStream_t st, const DevModel& m, const StepArgs& a,
+               const BackArgs& ba, float* work, const BackShape& sh) {
+  if (a.tape) backward_kernel<TPW, true><<<blocks, threads, smem, st>>>(m, a, ba, work, sh);
+  else backward_kernel<TPW, false><<<blocks, threads, smem, st>>>(m, a, ba, work, sh);
 }
 
 }  // namespace
@@ -76,16 +84,16 @@ void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st,
   const int threads = tpw * groups_per_block;
   const size_t smem = (size_t)sh.smem_floats * 4 * groups_per_block;
   switch (tpw) {
-    case 32: backward_kernel<32><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
-    case 64: backward_kernel<64><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
-    case 128: backward_kernel<128><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
-    case 256: backward_kernel<256><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    case 32: launch_of<32>(blocks, threads, smem, st, m, a, ba, work, sh); break;
+    case 64: launch_of<64>(blocks, threads, smem, st, m, a, ba, work, sh); break;
+    case 128: launch_of<128>(blocks, threads, smem, st, m, a, ba, work, sh); break;
+    case 256: launch_of<256>(blocks, threads, smem, st, m, a, ba, work, sh); break;
     default: break;
   }
 }
 
-cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
-  const void* fn = backward_fn_of(tpw);
+cudaError_t backward_attributes(int tpw, bool tape, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
+  const void* fn = backward_fn_of(tpw, tape);
   if (!fn) return cudaErrorInvalidValue;
   if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
   // the attribute belongs to the instantiation, shared by every class using it: always the limit

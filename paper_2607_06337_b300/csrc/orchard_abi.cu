@@ -1355,7 +1355,7 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
     cudaStream_t sk = m->class_streams[k];
     OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
     int bps = 0;
-    cudaError_t e = backward_attributes(p.tpw, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
+    cudaError_t e = backward_attributes(p.tpw, a.tape != nullptr, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
     StepArgs b = a;
     b.q_begin = ci.q_begin;
     b.q_end = ci.q_end;

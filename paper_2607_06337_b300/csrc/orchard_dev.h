@@ -195,7 +195,7 @@ struct BackShape {
 constexpr int kBackMaxThreads = 256;
 void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
                      const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
-cudaError_t backward_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
+cudaError_t backward_attributes(int tpw, bool tape, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 long long backward_adj_floats(int nb, int nv, int na);
 long long backward_adj_head_floats(int nb, int nv, int na);
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);

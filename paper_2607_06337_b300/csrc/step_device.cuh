@@ -1090,6 +1090,26 @@ HD void record_copy(float* ws, const WsLayout& L, float* qd, const WorldView& v,
   g.sync();
 }
 
+// The forward's writes into the adjoint's tape (WsLayout::tape_unit per world and step):
+// record false, the staged state before step t (t = n_steps: the final state); record true,
+// step t's record. Not inlined, so that the step loop keeps nothing live for it.
+template <int TPW>
+HD __noinline__ void tape_write(float* tape, const long long* tape_off, int n_steps, int w, int t, bool record,
+                                int nb, int nv, int nm, int na, float* ws, Group<TPW> g) {
+  const WsLayout L = WsLayout::make(nb, nv, nm, na);
+  const int snap = WsLayout::snap_words(nb, nv, na);
+  float* base = tape + (long long)(n_steps + 1) * tape_off[w];
+  if (!record) {
+    copy4<TPW>(base + (long long)t * snap, ws + L.S, snap, g);
+    return;
+  }
+  WorldView v{};
+  v.nb = nb; v.nv = nv; v.nm = nm; v.na = na;
+  const WState s = staged_view(ws + L.S, nb, nv, na);
+  float* rec = base + (long long)(n_steps + 1) * snap + (long long)t * WsLayout::record_words(nb, nv, nm, na);
+  record_copy<TPW>(ws, L, s.qd, v, rec, true, g);  // ends on a group barrier
+}
+
 // All steps of one world: its state is staged in the workspace for the whole rollout.
 template <int TPW>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
@@ -1103,21 +1123,16 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
   g.sync();
-  // the adjoint's tape (WsLayout::tape_unit): snapshots before every step and at the end, records
-  const int snap = WsLayout::snap_words(v.nb, v.nv, v.na);
-  const long long recw = WsLayout::record_words(v.nb, v.nv, v.nm, v.na);
-  float* tape = a.tape ? a.tape + (long long)(a.n_steps + 1) * m.tape_off[w] : nullptr;
-  float* trec = tape ? tape + (long long)(a.n_steps + 1) * snap : nullptr;
   for (int t = 0; t < a.n_steps; ++t) {
     if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
     if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
     // the step's first write to the staged state comes after several group barriers
-    if (tape) copy4<TPW>(tape + (long long)t * snap, ws + L.S, snap, g);
+    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
     step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1);
-    if (tape) record_copy<TPW>(ws, L, s.qd, v, trec + (long long)t * recw, true, g);  // ends on a barrier
+    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
   }
   // the final state (its status word tells the backward whether the world froze)
-  if (tape) copy4<TPW>(tape + (long long)a.n_steps * snap, ws + L.S, snap, g);
+  if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, a.n_steps, false, v.nb, v.nv, v.nm, v.na, ws, g);
   if (a.tips && a.n_steps > 0) {
     fk_only(m, s, v, L, ws, g);
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);
