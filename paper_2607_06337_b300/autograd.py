@@ -54,8 +54,16 @@ class TipRollout(torch.autograd.Function):
         return None, dk, dkd, dq0, dqd0, None, None, None
 
 
-def tip_rollout(sim, k, kd, q0, qd0, n_steps: int, ckpt_every: int = 20, step0: int = 0):
-    """Tip positions [n_steps, n_tips, 3] of a rollout, differentiable in k, kd, q0 and qd0."""
+def tip_rollout(sim, k, kd, q0, qd0, n_steps: int, ckpt_every=None, step0: int = 0):
+    """Tip positions [n_steps, n_tips, 3] of a rollout, differentiable in k, kd, q0 and qd0.
+
+    ckpt_every: checkpoint interval of the record, or 0 for the forward's full tape; None takes
+    the tape when it needs at most a quarter of the free device memory, else checkpoints every
+    20 steps."""
+    if ckpt_every is None:
+        from .orchard import tape_bytes
+        free, _ = torch.cuda.mem_get_info(sim.device)
+        ckpt_every = 0 if tape_bytes(sim.model, int(n_steps)) <= free // 4 else 20
     return TipRollout.apply(sim, k, kd, q0, qd0, int(n_steps), int(ckpt_every), int(step0))
 
 

@@ -330,6 +330,7 @@ def test_autograd_function_matches_the_direct_call():
         t.grad = None
     tips3 = tip_rollout(sim, k, kd, q0, qd0, n, ckpt_every=0)
     assert torch.equal(tips3, tips)
+    assert torch.equal(tip_rollout(sim, k.detach(), kd.detach(), q0.detach(), qd0.detach(), n), tips)  # default
     tip_loss(tips3.double(), torch.as_tensor(target, device=dev), f.tip_off).backward()
     for t, r in zip((k, kd, q0, qd0), grads):
         np.testing.assert_allclose(t.grad.cpu().numpy(), r.cpu().numpy(), rtol=0, atol=1e-5 * r.abs().max().item())
