@@ -233,15 +233,17 @@ def test_checkpoint_interval_does_not_change_the_gradient():
             np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
 
 
-@pytest.mark.parametrize("worlds,workload", [([7, 8], I.DIFF), ([23, 79], I.BATCH)])
-def test_tape_gives_the_checkpointed_gradient(worlds, workload):
+@pytest.mark.parametrize("worlds,workload,n", [([7, 8], I.DIFF, 120), ([23, 79], I.BATCH, 120),
+                                                ([0, 4096, 8000], I.STRESS, 30)])
+def test_tape_gives_the_checkpointed_gradient(worlds, workload, n):
     """The forward's full tape (no step run again) against checkpoints every step and every 25
     steps: the same gradient up to the last bits of each step (the backward's replay is
     compiled into another kernel and may run at another group size), within 1e-5 of each
-    kind's largest entry; the batching worlds break branches and drop apples on the way."""
+    kind's largest entry. The batching worlds break branches and drop apples on the way; the
+    stress worlds (50, 400 and 2000 bodies) include one whose step temporaries are in global
+    memory, with FP64 pivots on twigs under 5 mm."""
     f = I.make_forest(workload, worlds=worlds)
-    fl = I.Flags()
-    n = 120
+    fl = I.Flags(fp64_twig_diam=0.005 if workload == I.STRESS else 0.0)
     _, rec0 = O.rollout(f, fl, n, record_tips=True)
     target = rec0["tips"] + np.random.default_rng(9).normal(0.0, 0.01, rec0["tips"].shape)
     tape, _, sim = gpu_gradients(f, fl, n, 0, target)
