@@ -242,8 +242,12 @@ ot_status ot_step(ot_model* model, ot_state* state, const float* ext_force, cons
  *         pass (joint origins, DOF axes, the solution, apple data, the snapped flags, the
  *         factors, the end velocities), so that ot_rollout_backward runs no step again. It
  *         trades memory for the replay of checkpoint segments: about 40 KB per step of a
- *         200-body world (8 GB for 1024 such worlds over 200 steps).
- * A buffer too small (or a misaligned tape) fails with OT_EINVAL before any work is queued. */
+ *         200-body world (8 GB for 1024 such worlds over 200 steps). Its layout is internal:
+ *         the caller owns the buffer, ot_rollout writes it, and ot_rollout_backward reads it
+ *         for the same model and n_steps; keep it unmodified in between.
+ * A buffer too small (or a misaligned tape) fails with OT_EINVAL before any work is queued.
+ * ot_ckpt_bytes / ot_tape_bytes write the byte sizes for n_steps steps (OT_EINVAL for a NULL
+ * model or bytes, n_steps < 0, or ckpt_every < 1). */
 typedef struct ot_record {
   float* tips;
   void* ckpt;
