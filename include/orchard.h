@@ -245,6 +245,11 @@ ot_status ot_step(ot_model* model, ot_state* state, const float* ext_force, cons
  *         200-body world (8 GB for 1024 such worlds over 200 steps). Its layout is internal:
  *         the caller owns the buffer, ot_rollout writes it, and ot_rollout_backward reads it
  *         for the same model and n_steps; keep it unmodified in between.
+ *   tape_steps: how many of the rollout's final steps the tape covers (0: all n_steps). With
+ *         0 < tape_steps < n_steps the record must hold checkpoints too: the backward reverses
+ *         the taped steps straight from the tape and replays only the earlier checkpoint
+ *         segments (a tape sized by ot_tape_bytes(model, tape_steps), for rollouts whose full
+ *         tape does not fit in device memory).
  * A buffer too small (or a misaligned tape) fails with OT_EINVAL before any work is queued.
  * ot_ckpt_bytes / ot_tape_bytes write the byte sizes for n_steps steps (OT_EINVAL for a NULL
  * model or bytes, n_steps < 0, or ckpt_every < 1). */
@@ -255,6 +260,7 @@ typedef struct ot_record {
   int32_t ckpt_every;
   float* tape;
   size_t tape_bytes;
+  int32_t tape_steps;
 } ot_record;
 ot_status ot_ckpt_bytes(const ot_model* model, int32_t n_steps, int32_t ckpt_every, size_t* bytes);
 ot_status ot_tape_bytes(const ot_model* model, int32_t n_steps, size_t* bytes);

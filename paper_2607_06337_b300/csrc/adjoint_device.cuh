@@ -903,16 +903,42 @@ HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, 
   g.sync();
 }
 
+// Checkpoint segments over steps [0, t_end), last to first: each is replayed once, forward,
+// from its checkpoint, saving every step's start state and record into seg (ckpt_every
+// snapshots, then as many records); then its steps are reversed last to first from those.
+// seed: the final-tips seed is taken after the last segment's replay (the rollout's end).
+template <int TPW>
+HD void reverse_segments(const DevModel& m, const StepArgs& a, const BackArgs& ba, const WorldView& v,
+                         const WsLayout& L, const AdjLayout& A, const WState& s, float* ws, float* wa, float* cs,
+                         float* seg, long long recw, int t_end, bool seed, const Group<TPW>& g, f3 gv) {
+  float* recs = seg + (long long)a.ckpt_every * A.snap;
+  const int ce = a.ckpt_every;
+  const int nseg = (t_end + ce - 1) / ce;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int t0 = sg * ce, t1 = (t0 + ce < t_end) ? t0 + ce : t_end;
+    load_ckpt(a, v, s, sg, g);
+    for (int t = t0; t < t1; ++t) {
+      snapshot(ws, L, seg, A, t - t0, true, g);
+      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
+      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
+    }
+    if (seed && sg == nseg - 1) reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
+    for (int t = t1 - 1; t >= t0; --t)
+      reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, seg + (long long)(t - t0) * A.snap,
+                            recs + (long long)(t - t0) * recw, g, t, gv);
+  }
+}
+
 // Backward pass of one world over a recorded rollout.
 // ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
 // wc: the C slots when they are not at wa + A.C (null: they are), seg: ckpt_every snapshots
 // and step records (global memory); ws, wa and wc may be in shared or global memory.
-// TAPE: every step's start state and record are in the forward's tape (a.tape), and the steps
-// are reversed last to first straight from it. Otherwise each checkpoint segment is replayed
-// once, forward, saving every step's start state and its record into seg; then its steps are
-// reversed last to first from those. The two are separate kernels, each compiled for its own
-// path.
-template <int TPW, bool TAPE>
+// MODE 0: checkpoints only (reverse_segments over the whole rollout). MODE 1: every step's
+// start state and record are in the forward's tape, and the steps are reversed last to first
+// straight from it. MODE 2: the tape covers the last a.tape_steps steps, reversed from it
+// first; the earlier steps come from their checkpoint segments. The three are separate
+// kernels, each compiled for its own path.
+template <int TPW, int MODE>
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
                        float* wc, float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
@@ -929,10 +955,13 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
   }
   for (int i = g.lane; i < 3 * v.na; i += TPW) { wa[A.ub1 + i] = 0.f; wa[A.vb1 + i] = 0.f; }
   g.sync();
-  if constexpr (TAPE) {
-    const float* tape = a.tape + (long long)(T + 1) * m.tape_off[w];
-    const float* trec = tape + (long long)(T + 1) * A.snap;
-    copy4<TPW>(ws + L.S, tape + (long long)T * A.snap, A.snap, g);  // the final state
+  if constexpr (MODE == 0) {
+    reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T, true, g, gv);
+  } else {
+    const int K = a.tape_steps, T1 = T - K;  // the tape holds steps T1 .. T - 1
+    const float* tape = a.tape + (long long)(K + 1) * m.tape_off[w];
+    const float* trec = tape + (long long)(K + 1) * A.snap;
+    copy4<TPW>(ws + L.S, tape + (long long)K * A.snap, A.snap, g);  // the final state
     g.sync();
     if (*s.status & 1u) {
       // the forward froze this world on a non-finite state: its gradients are NaN
@@ -949,27 +978,10 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       return;
     }
     reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
-    for (int t = T - 1; t >= 0; --t)
-      reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, tape + (long long)t * A.snap, trec + (long long)t * recw,
-                            g, t, gv);
-  } else {
-    // the segment buffer: ckpt_every snapshots, then ckpt_every step records
-    float* recs = seg + (long long)a.ckpt_every * A.snap;
-    const int ce = a.ckpt_every;
-    const int nseg = (T + ce - 1) / ce;
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int t0 = sg * ce, t1 = (t0 + ce < T) ? t0 + ce : T;
-      load_ckpt(a, v, s, sg, g);
-      for (int t = t0; t < t1; ++t) {
-        snapshot(ws, L, seg, A, t - t0, true, g);
-        step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
-        step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
-      }
-      if (sg == nseg - 1) reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
-      for (int t = t1 - 1; t >= t0; --t)
-        reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, seg + (long long)(t - t0) * A.snap,
-                              recs + (long long)(t - t0) * recw, g, t, gv);
-    }
+    for (int t = T - 1; t >= T1; --t)
+      reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, tape + (long long)(t - T1) * A.snap,
+                            trec + (long long)(t - T1) * recw, g, t, gv);
+    if constexpr (MODE == 2) reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T1, false, g, gv);
   }
   for (int i = g.lane; i < v.nv; i += TPW) {
     if (ba.dq0) ba.dq0[v.d0 + i] = wa[A.qb1 + i];

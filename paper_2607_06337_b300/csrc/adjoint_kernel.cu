@@ -2,8 +2,8 @@
 // groups pop worlds from the cost-sorted queue and run backward_world (adjoint_device.cuh).
 // Each group owns one slot of the caller's workspace (the snapshots of one checkpoint
 // segment, none when the forward kept its full tape, plus whatever of its temporaries is not
-// in shared memory). The tape and checkpoint forms are separate instantiations. BackShape::mode
-// says which temporaries live in the block's shared memory:
+// in shared memory). The checkpoint, tape and hybrid forms (MODE 0, 1, 2) are separate
+// instantiations. BackShape::mode says which temporaries live in the block's shared memory:
 //   0: none (forward and backward temporaries in the global slot),
 //   1: the forward step's temporaries (WsLayout),
 //   2: the forward step's and the backward's (WsLayout, then AdjLayout),
@@ -13,7 +13,7 @@
 namespace orchard {
 namespace {
 
-template <int TPW, bool TAPE>
+template <int TPW, int MODE>
 __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m, StepArgs a, BackArgs ba, float* work,
                                                        BackShape sh) {
   extern __shared__ __align__(16) float smem[];
@@ -51,30 +51,37 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
     const int qi = next[g.id];
     g.sync();
     if (qi >= a.q_end - a.q_begin) break;
-    backward_world<TPW, TAPE>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
+    backward_world<TPW, MODE>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
   }
 }
 
 template <int TPW>
-const void* backward_fn(bool tape) {
-  return tape ? (const void*)backward_kernel<TPW, true> : (const void*)backward_kernel<TPW, false>;
+const void* backward_fn(int mode) {
+  return mode == 1 ? (const void*)backward_kernel<TPW, 1>
+                   : mode == 2 ? (const void*)backward_kernel<TPW, 2> : (const void*)backward_kernel<TPW, 0>;
 }
 
-const void* backward_fn_of(int tpw, bool tape) {
+const void* backward_fn_of(int tpw, int mode) {
   switch (tpw) {
-    case 32: return backward_fn<32>(tape);
-    case 64: return backward_fn<64>(tape);
-    case 128: return backward_fn<128>(tape);
-    case 256: return backward_fn<256>(tape);
+    case 32: return backward_fn<32>(mode);
+    case 64: return backward_fn<64>(mode);
+    case 128: return backward_fn<128>(mode);
+    case 256: return backward_fn<256>(mode);
     default: return nullptr;
   }
 }
 
+// 0: checkpoints, 1: the full tape, 2: the tape for the last steps, checkpoints before
+inline int back_mode(const StepArgs& a) { return !a.tape ? 0 : a.tape_steps < a.n_steps ? 2 : 1; }
+
 template <int TPW>
 void launch_of(int blocks, int threads, size_t smem, cudaStream_t st, const DevModel& m, const StepArgs& a,
                const BackArgs& ba, float* work, const BackShape& sh) {
-  if (a.tape) backward_kernel<TPW, true><<<blocks, threads, smem, st>>>(m, a, ba, work, sh);
-  else backward_kernel<TPW, false><<<blocks, threads, smem, st>>>(m, a, ba, work, sh);
+  switch (back_mode(a)) {
+    case 1: backward_kernel<TPW, 1><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    case 2: backward_kernel<TPW, 2><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+    default: backward_kernel<TPW, 0><<<blocks, threads, smem, st>>>(m, a, ba, work, sh); break;
+  }
 }
 
 }  // namespace
@@ -92,8 +99,8 @@ void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st,
   }
 }
 
-cudaError_t backward_attributes(int tpw, bool tape, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
-  const void* fn = backward_fn_of(tpw, tape);
+cudaError_t backward_attributes(int tpw, int mode, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
+  const void* fn = backward_fn_of(tpw, mode);
   if (!fn) return cudaErrorInvalidValue;
   if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
   // the attribute belongs to the instantiation, shared by every class using it: always the limit

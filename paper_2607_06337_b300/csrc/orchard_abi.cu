@@ -1022,18 +1022,21 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
       a.ckpt_every = rec->ckpt_every;
     }
     if (rec->tape) {
+      const int K = rec->tape_steps > 0 ? rec->tape_steps : n_steps;  // the final steps taped
+      if (K > n_steps || (K < n_steps && !a.ckpt)) return OT_EINVAL;  // the rest need checkpoints
       size_t need = 0;
-      ot_tape_bytes(m, n_steps, &need);
+      ot_tape_bytes(m, K, &need);
       if (rec->tape_bytes < need || ((uintptr_t)rec->tape) % 16) return OT_EINVAL;
       a.tape = rec->tape;
+      a.tape_steps = K;
     }
   }
   cudaStream_t user = (cudaStream_t)stream;
   // graph key: everything the captured launches depend on
   char key[512];
-  std::snprintf(key, sizeof(key), "%p|%d|%d|%.17g|%p|%p|%p|%p|%p|%d|%p", (void*)s->base, n_steps, step0, dt,
+  std::snprintf(key, sizeof(key), "%p|%d|%d|%.17g|%p|%p|%p|%p|%p|%d|%p|%d", (void*)s->base, n_steps, step0, dt,
                 (const void*)a.pull_force, (const void*)a.pull_start, (const void*)a.tips, (void*)a.ckpt,
-                (const void*)a.pull_end, a.ckpt_every, (void*)a.tape);
+                (const void*)a.pull_end, a.ckpt_every, (void*)a.tape, a.tape_steps);
   std::string skey = key;
   std::string sched_sig;
   for (const ClassInfo& ci : m->P.classes) {
@@ -1301,16 +1304,21 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
                               const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
                               ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
   if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0) || !rec || !dL_dtips || !grads) return OT_EINVAL;
-  // the tape when the forward wrote one, else the checkpoints (and segment replays)
+  // the tape when the forward wrote one; checkpoints (and segment replays) for the steps before
+  // a tape of the final steps only, or for all steps without a tape
   const bool tape = rec->tape != nullptr;
-  if (!tape && (!rec->ckpt || rec->ckpt_every < 1)) return OT_ESTATE;
+  const int K = tape ? (rec->tape_steps > 0 ? rec->tape_steps : n_steps) : 0;
+  if (K > n_steps) return OT_EINVAL;
+  const bool need_ckpt = K < n_steps;
+  if (need_ckpt && (!rec->ckpt || rec->ckpt_every < 1)) return OT_ESTATE;
   if (((uintptr_t)workspace) % kAlign) return OT_EINVAL;
-  const int ce = tape ? 0 : rec->ckpt_every;
+  const int ce = need_ckpt ? rec->ckpt_every : 0;
   size_t need = 0;
   if (tape) {
-    ot_tape_bytes(m, n_steps, &need);
+    ot_tape_bytes(m, K, &need);
     if (rec->tape_bytes < need || ((uintptr_t)rec->tape) % 16) return OT_EINVAL;
-  } else {
+  }
+  if (need_ckpt) {
     ot_ckpt_bytes(m, n_steps, ce, &need);
     if (rec->ckpt_bytes < need) return OT_EINVAL;
   }
@@ -1323,7 +1331,9 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
   if (st != OT_OK) return st;
   if (tape) {
     a.tape = rec->tape;
-  } else {
+    a.tape_steps = K;
+  }
+  if (need_ckpt) {
     a.ckpt = (unsigned*)rec->ckpt;
     a.ckpt_every = ce;
   }
@@ -1355,7 +1365,8 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
     cudaStream_t sk = m->class_streams[k];
     OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
     int bps = 0;
-    cudaError_t e = backward_attributes(p.tpw, a.tape != nullptr, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
+    const int mode = !a.tape ? 0 : a.tape_steps < a.n_steps ? 2 : 1;
+    cudaError_t e = backward_attributes(p.tpw, mode, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
     StepArgs b = a;
     b.q_begin = ci.q_begin;
     b.q_end = ci.q_end;

@@ -100,6 +100,8 @@ struct StepArgs {
   long long ckpt_words;     // 32-bit words per snapshot
   float* tape;              // the adjoint's tape of the rollout (written by the forward, read by
                             // the backward), or null
+  int tape_steps;           // the final steps the tape covers (n_steps: all; fewer: the earlier
+                            // ones come from the checkpoints)
   int NB, NV, NA;           // totals (snapshot layout)
   int q_begin, q_end;       // queue range of this launch
   int* q_counter;           // next queue entry (relative to q_begin); null: one world per group
@@ -195,7 +197,7 @@ struct BackShape {
 constexpr int kBackMaxThreads = 256;
 void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st, const DevModel& m,
                      const StepArgs& a, const BackArgs& ba, float* work, const BackShape& sh);
-cudaError_t backward_attributes(int tpw, bool tape, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
+cudaError_t backward_attributes(int tpw, int mode, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 long long backward_adj_floats(int nb, int nv, int na);
 long long backward_adj_head_floats(int nb, int nv, int na);
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);

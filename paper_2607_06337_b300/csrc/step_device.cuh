@@ -1090,23 +1090,27 @@ HD void record_copy(float* ws, const WsLayout& L, float* qd, const WorldView& v,
   g.sync();
 }
 
-// The forward's writes into the adjoint's tape (WsLayout::tape_unit per world and step):
-// record false, the staged state before step t (t = n_steps: the final state); record true,
-// step t's record. Not inlined, so that the step loop keeps nothing live for it.
+// The forward's writes into the adjoint's tape, which covers the last K = tape_steps of the
+// rollout's n_steps steps (WsLayout::tape_unit per world and taped step): record false, the
+// staged state before step t (t = n_steps: the final state); record true, step t's record.
+// Steps before the taped ones write nothing. Not inlined, so that the step loop keeps nothing
+// live for it.
 template <int TPW>
-HD __noinline__ void tape_write(float* tape, const long long* tape_off, int n_steps, int w, int t, bool record,
-                                int nb, int nv, int nm, int na, float* ws, Group<TPW> g) {
+HD __noinline__ void tape_write(float* tape, const long long* tape_off, int n_steps, int tape_steps, int w, int t,
+                                bool record, int nb, int nv, int nm, int na, float* ws, Group<TPW> g) {
+  const int k = t - (n_steps - tape_steps);  // index among the taped steps
+  if (k < 0) return;
   const WsLayout L = WsLayout::make(nb, nv, nm, na);
   const int snap = WsLayout::snap_words(nb, nv, na);
-  float* base = tape + (long long)(n_steps + 1) * tape_off[w];
+  float* base = tape + (long long)(tape_steps + 1) * tape_off[w];
   if (!record) {
-    copy4<TPW>(base + (long long)t * snap, ws + L.S, snap, g);
+    copy4<TPW>(base + (long long)k * snap, ws + L.S, snap, g);
     return;
   }
   WorldView v{};
   v.nb = nb; v.nv = nv; v.nm = nm; v.na = na;
   const WState s = staged_view(ws + L.S, nb, nv, na);
-  float* rec = base + (long long)(n_steps + 1) * snap + (long long)t * WsLayout::record_words(nb, nv, nm, na);
+  float* rec = base + (long long)(tape_steps + 1) * snap + (long long)k * WsLayout::record_words(nb, nv, nm, na);
   record_copy<TPW>(ws, L, s.qd, v, rec, true, g);  // ends on a group barrier
 }
 
@@ -1127,12 +1131,13 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
     if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
     if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
     // the step's first write to the staged state comes after several group barriers
-    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
+    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
     step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1);
-    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
+    if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
   }
   // the final state (its status word tells the backward whether the world froze)
-  if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, w, a.n_steps, false, v.nb, v.nv, v.nm, v.na, ws, g);
+  if (a.tape)
+    tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, a.n_steps, false, v.nb, v.nv, v.nm, v.na, ws, g);
   if (a.tips && a.n_steps > 0) {
     fk_only(m, s, v, L, ws, g);
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);

@@ -83,7 +83,7 @@ class ForceSchedule(C.Structure):
 
 class Record(C.Structure):
     _fields_ = [("tips", C.c_void_p), ("ckpt", C.c_void_p), ("ckpt_bytes", C.c_size_t), ("ckpt_every", C.c_int32),
-                ("tape", C.c_void_p), ("tape_bytes", C.c_size_t)]
+                ("tape", C.c_void_p), ("tape_bytes", C.c_size_t), ("tape_steps", C.c_int32)]
 
 
 class Grads(C.Structure):
@@ -411,20 +411,26 @@ class Simulator:
             capsule_links = bool(self.forest.meta.get("capsule", False))
         model_randomize(self.model, factors, capsule_links, stream)
 
-    def record_buffers(self, n_steps, ckpt_every, tips=True):
+    def record_buffers(self, n_steps, ckpt_every, tips=True, tape_steps=0):
         """Device buffers for a recorded rollout: tips [n_steps, n_tips, 3], and checkpoints every
         ``ckpt_every`` steps, or with ``ckpt_every`` 0 the adjoint's full tape (ot_tape_bytes:
-        the backward then replays no step). Returns (tips, buffer, record)."""
+        the backward then replays no step). With ``ckpt_every`` > 0 and 0 < ``tape_steps`` <
+        ``n_steps``, both: a tape of the final ``tape_steps`` steps and checkpoints for the
+        earlier ones. Returns (tips, buffer, record); buffer is (checkpoints, tape) for both."""
         import torch
         t = torch.empty((n_steps, self.counts.tips, 3), dtype=torch.float32, device=self.device) if tips else None
         tp = None if t is None else t.data_ptr()
         if ckpt_every == 0:
             nb = tape_bytes(self.model, n_steps)
             buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
-            return t, buf, Record(tp, None, 0, 0, buf.data_ptr(), nb)
+            return t, buf, Record(tp, None, 0, 0, buf.data_ptr(), nb, 0)
         nb = ckpt_bytes(self.model, n_steps, ckpt_every)
         buf = torch.empty(nb, dtype=torch.uint8, device=self.device)
-        return t, buf, Record(tp, buf.data_ptr(), nb, ckpt_every, None, 0)
+        if 0 < tape_steps < n_steps:
+            nt = tape_bytes(self.model, tape_steps)
+            tbuf = torch.empty(nt, dtype=torch.uint8, device=self.device)
+            return t, (buf, tbuf), Record(tp, buf.data_ptr(), nb, ckpt_every, tbuf.data_ptr(), nt, tape_steps)
+        return t, buf, Record(tp, buf.data_ptr(), nb, ckpt_every, None, 0, 0)
 
     def backward(self, n_steps, record, dL_dtips, step0=0, dt=None, grads=None, workspace=None, stream=None):
         """Adjoint of a recorded rollout. Returns (dk, dkd, dq0, dqd0) as float32 device tensors.

@@ -56,12 +56,12 @@ def tip_cotangent(f, tips, target):
     return 2.0 * (tips - target) * scale[None, :, None]
 
 
-def gpu_gradients(f, fl, n, ckpt_every, target, sim=None):
+def gpu_gradients(f, fl, n, ckpt_every, target, sim=None, tape_steps=0):
     torch = _torch()
     from paper_2607_06337_b300.orchard import Simulator
     sim = sim or Simulator(f, fl)
     sim.reset()
-    tips, ck, rec = sim.record_buffers(n, ckpt_every)
+    tips, ck, rec = sim.record_buffers(n, ckpt_every, tape_steps=tape_steps)
     sim.rollout(n, record=rec)
     tg = torch.as_tensor(np.asarray(target, np.float32), device="cuda")
     dt = tip_cotangent(f, tips.double(), tg.double()).float()
@@ -236,8 +236,8 @@ def test_checkpoint_interval_does_not_change_the_gradient():
 @pytest.mark.parametrize("worlds,workload,n", [([7, 8], I.DIFF, 120), ([23, 79], I.BATCH, 120),
                                                 ([0, 4096, 8000], I.STRESS, 30)])
 def test_tape_gives_the_checkpointed_gradient(worlds, workload, n):
-    """The forward's full tape (no step run again) against checkpoints every step and every 25
-    steps: the same gradient up to the last bits of each step (the backward's replay is
+    """The forward's full tape (no step run again), and a tape of the final third of the steps
+    with checkpoints before it, against checkpoints every step and every 25 steps: the same gradient up to the last bits of each step (the backward's replay is
     compiled into another kernel and may run at another group size), within 1e-5 of each
     kind's largest entry. The batching worlds break branches and drop apples on the way; the
     stress worlds (50, 400 and 2000 bodies) include one whose step temporaries are in global
@@ -247,10 +247,14 @@ def test_tape_gives_the_checkpointed_gradient(worlds, workload, n):
     _, rec0 = O.rollout(f, fl, n, record_tips=True)
     target = rec0["tips"] + np.random.default_rng(9).normal(0.0, 0.01, rec0["tips"].shape)
     tape, _, sim = gpu_gradients(f, fl, n, 0, target)
+    # the hybrid record: a tape of the final steps (a number that splits a checkpoint segment),
+    # checkpoints every 25 steps before them
+    hybrid, _, _ = gpu_gradients(f, fl, n, 25, target, sim=sim, tape_steps=n // 3 + 1)
     for ce in (1, 25):
         ref, _, _ = gpu_gradients(f, fl, n, ce, target, sim=sim)
-        for a, b in zip(tape, ref):
-            np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
+        for got in (tape, hybrid):
+            for a, b in zip(got, ref):
+                np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
 
 
 def test_tape_of_a_frozen_world_gives_nan_gradients_only_there():
@@ -276,7 +280,8 @@ def test_tape_of_a_frozen_world_gives_nan_gradients_only_there():
 
 def test_tape_buffer_checks():
     """A tape one float too small, or not on a 16-byte boundary, is refused (OT_EINVAL) by the
-    rollout and by the backward before any work is queued."""
+    rollout and by the backward before any work is queued; so is a tape of the final steps
+    without checkpoints, or of more steps than the rollout."""
     torch = _torch()
     from paper_2607_06337_b300 import orchard as B
     f = I.make_forest(I.DIFF, worlds=[0])
@@ -287,14 +292,21 @@ def test_tape_buffer_checks():
     buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
     tips = torch.empty((n, sim.counts.tips, 3), dtype=torch.float32, device="cuda")
     for ptr, nbytes in ((buf.data_ptr(), need - 4), (buf.data_ptr() + 4, need)):
-        rec = B.Record(tips.data_ptr(), None, 0, 0, ptr, nbytes)
+        rec = B.Record(tips.data_ptr(), None, 0, 0, ptr, nbytes, 0)
         with pytest.raises(B.OrchardError) as e:
             sim.rollout(n, record=rec)
         assert e.value.status == B.OT_EINVAL
         with pytest.raises(B.OrchardError) as e:
             sim.backward(n, rec, torch.zeros_like(tips))
         assert e.value.status == B.OT_EINVAL
-    sim.rollout(n, record=B.Record(tips.data_ptr(), None, 0, 0, buf.data_ptr(), need))
+    # a tape of the final steps only needs checkpoints for the others; more steps than the
+    # rollout are refused
+    for steps in (3, n + 1):
+        rec = B.Record(tips.data_ptr(), None, 0, 0, buf.data_ptr(), need, steps)
+        with pytest.raises(B.OrchardError) as e:
+            sim.rollout(n, record=rec)
+        assert e.value.status == B.OT_EINVAL
+    sim.rollout(n, record=B.Record(tips.data_ptr(), None, 0, 0, buf.data_ptr(), need, 0))
     torch.cuda.synchronize()
 
 
