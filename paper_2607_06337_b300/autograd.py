@@ -22,7 +22,7 @@ import torch
 
 class TipRollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, sim, k, kd, q0, qd0, n_steps: int, ckpt_every: int, step0: int = 0):
+    def forward(ctx, sim, k, kd, q0, qd0, n_steps: int, ckpt_every: int, step0: int = 0, tape_steps: int = 0):
         dev = sim.device
         for t in (k, kd, q0, qd0):
             if t.device != dev or t.dtype != torch.float32:
@@ -36,35 +36,43 @@ class TipRollout(torch.autograd.Function):
         av = torch.as_tensor(np.asarray(f.apple_v0, np.float32).reshape(-1, 3), device=dev).contiguous()
         sim.set_gains(k, kd)
         sim.reset_from_device(q0c, qd0c, ax, av)
-        tips, ckpt, rec = sim.record_buffers(n_steps, ckpt_every)
+        tips, buffers, rec = sim.record_buffers(n_steps, ckpt_every, tape_steps=tape_steps)
         sim.rollout(n_steps, step0=step0, record=rec)
         ctx.sim = sim
         ctx.rec = rec
+        ctx.buffers = buffers  # the record's device memory, alive until the backward
         ctx.meta = (n_steps, step0)
-        ctx.save_for_backward(k, kd, ckpt)
+        ctx.save_for_backward(k, kd)
         return tips
 
     @staticmethod
     def backward(ctx, dtips):
-        k, kd, ckpt = ctx.saved_tensors
+        k, kd = ctx.saved_tensors
         sim = ctx.sim
         n_steps, step0 = ctx.meta
         sim.set_gains(k, kd)
         dk, dkd, dq0, dqd0 = sim.backward(n_steps, ctx.rec, dtips.to(torch.float32).contiguous(), step0=step0)
-        return None, dk, dkd, dq0, dqd0, None, None, None
+        return None, dk, dkd, dq0, dqd0, None, None, None, None
 
 
 def tip_rollout(sim, k, kd, q0, qd0, n_steps: int, ckpt_every=None, step0: int = 0):
     """Tip positions [n_steps, n_tips, 3] of a rollout, differentiable in k, kd, q0 and qd0.
 
-    ckpt_every: checkpoint interval of the record, or 0 for the forward's full tape; None takes
-    the tape when it needs at most a quarter of the free device memory, else checkpoints every
-    20 steps."""
+    ckpt_every: checkpoint interval of the record, or 0 for the forward's full tape. None takes
+    the full tape when it needs at most a quarter of the free device memory, else a tape of as
+    many final steps as fit there with checkpoints every 20 steps before them (or checkpoints
+    alone when not even one step fits)."""
+    tape_steps = 0
     if ckpt_every is None:
         from .orchard import tape_bytes
         free, _ = torch.cuda.mem_get_info(sim.device)
-        ckpt_every = 0 if tape_bytes(sim.model, int(n_steps)) <= free // 4 else 20
-    return TipRollout.apply(sim, k, kd, q0, qd0, int(n_steps), int(ckpt_every), int(step0))
+        budget = free // 4
+        if tape_bytes(sim.model, int(n_steps)) <= budget:
+            ckpt_every = 0
+        else:
+            ckpt_every = 20
+            tape_steps = max(0, min(int(n_steps) - 1, budget // tape_bytes(sim.model, 0) - 1))
+    return TipRollout.apply(sim, k, kd, q0, qd0, int(n_steps), int(ckpt_every), int(step0), int(tape_steps))
 
 
 def tip_loss(tips, target, tip_off):

@@ -348,6 +348,16 @@ def test_autograd_function_matches_the_direct_call():
     tip_loss(tips3.double(), torch.as_tensor(target, device=dev), f.tip_off).backward()
     for t, r in zip((k, kd, q0, qd0), grads):
         np.testing.assert_allclose(t.grad.cpu().numpy(), r.cpu().numpy(), rtol=0, atol=1e-5 * r.abs().max().item())
+    # the hybrid record (a tape of the last 25 steps, checkpoints every 20 before them), the
+    # default's choice when the full tape does not fit
+    from paper_2607_06337_b300.autograd import TipRollout
+    for t in (k, kd, q0, qd0):
+        t.grad = None
+    tips4 = TipRollout.apply(sim, k, kd, q0, qd0, n, 20, 0, 25)
+    assert torch.equal(tips4, tips)
+    tip_loss(tips4.double(), torch.as_tensor(target, device=dev), f.tip_off).backward()
+    for t, r in zip((k, kd, q0, qd0), grads):
+        np.testing.assert_allclose(t.grad.cpu().numpy(), r.cpu().numpy(), rtol=0, atol=1e-5 * r.abs().max().item())
 
 
 @pytest.mark.parametrize("ckpt_every", [16, 0])
