@@ -257,6 +257,37 @@ def test_tape_gives_the_checkpointed_gradient(worlds, workload, n):
                 np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
 
 
+@pytest.mark.parametrize("n,step0,tape_steps", [(40, 137, 0), (1, 0, 0), (9, 3, 1)])
+def test_tape_edge_cases_against_checkpoints(n, step0, tape_steps):
+    """The tape's records keep absolute step indices (the pull schedule reads them): a rollout
+    starting at step 137; a one-step rollout; a hybrid with a single taped step. Each against
+    the checkpointed gradient of the same rollout (checkpoints every 4 steps), to 1e-5 of each
+    kind's largest entry."""
+    torch = _torch()
+    from paper_2607_06337_b300.orchard import Simulator
+    f = I.make_forest(I.DIFF, worlds=[3, 4])
+    fl = I.Flags()
+    sim = Simulator(f, fl)
+    _, rec0 = O.rollout(f, fl, n, record_tips=True, step0=step0)
+    target = torch.as_tensor(rec0["tips"] + 0.01, device="cuda")
+
+    def grads(ce, k):
+        sim.reset()
+        tips, buf, rec = sim.record_buffers(n, ce, tape_steps=k)
+        sim.rollout(n, step0=step0, record=rec)
+        dt = tip_cotangent(f, tips.double(), target).float()
+        g = sim.backward(n, rec, dt, step0=step0)
+        torch.cuda.synchronize()
+        return [x.cpu().numpy().astype(np.float64) for x in g], tips.cpu().numpy()
+
+    ref, tips_ref = grads(4, 0)
+    got, tips_got = grads(4 if tape_steps else 0, tape_steps)
+    np.testing.assert_array_equal(tips_got, tips_ref)
+    for a, b in zip(got, ref):
+        assert np.abs(b).max() > 0
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-5 * np.abs(b).max())
+
+
 def test_tape_of_a_frozen_world_gives_nan_gradients_only_there():
     """A world whose state is non-finite from the start is frozen by the forward: with the tape
     its gradients are NaN, and the other world's are those of the checkpointed backward."""
