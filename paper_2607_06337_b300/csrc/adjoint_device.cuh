@@ -666,41 +666,30 @@ HD void solve_factored(const DevModel& m, const WorldView& v, const WsLayout& L,
   }
 }
 
-// Leaf-to-root sweep of point loads at the apples' hang points (cotangents vh of the new
-// hang-point velocities): adds J_h^T vh to out (per DOF).
+// Point loads at the apples' hang points (cotangents vh of the new hang-point velocities):
+// adds J_h^T vh to out (per DOF). The moment about a joint origin x_b of its subtree's loads
+// is the sum over the subtree's attached apples of (p_a - x_b) x vh_a, p_a the hang point; the
+// subtree's apples are one range of apre, so every body sums its own range in a fixed order,
+// all bodies at once.
 template <int TPW>
 HD void hang_load_sweep(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L,
                         const AdjLayout& A, float* ws, float* wa, float* out, const Group<TPW>& g) {
-  for (int l = v.nL - 1; l >= 0; --l) {
-    const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) {
-      const int4 bi = m.bi[v.b0 + b];
-      const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
-      const int cfirst = bi.z & 0x00ffffff, ccount = (unsigned)bi.z >> 24;
-      const int afirst = bi.w & 0x00ffffff, acount = (unsigned)bi.w >> 24;
-      f3 n = mk(0, 0, 0), f = mk(0, 0, 0);
-      const f3 xb = ld3(ws + L.X + 3 * b);
-      for (int k = 0; k < acount; ++k) {
-        const int ai = afirst + k;
-        if (s.detached[ai]) continue;
-        const f3 rh = ld3(ws + L.AT + 10 * ai + 6);
-        const f3 fv = ld3(wa + A.vh + 3 * ai);
-        n = n + cross(rh, fv);
-        f = f + fv;
-      }
-      for (int k = 0; k < ccount; ++k) {
-        const int c = cfirst + k;
-        const f3 sft = ld3(ws + L.X + 3 * c) - xb;
-        const f3 fc = ld3(wa + A.AF + 6 * c + 3);
-        n = n + ld3(wa + A.AF + 6 * c) + cross(sft, fc);
-        f = f + fc;
-      }
-      st3(wa + A.AF + 6 * b, n);
-      st3(wa + A.AF + 6 * b + 3, f);
-      for (int j = 0; j < nd; ++j) out[dof0 + j] += dot(ld3(ws + L.E + 3 * (dof0 + j)), n);
+  for (int b = g.lane; b < v.nb; b += TPW) {
+    const int2 r = m.arange[v.b0 + b];
+    const int4 bi = m.bi[v.b0 + b];
+    const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+    if (r.x == r.y || nd == 0) continue;
+    const f3 xb = ld3(ws + L.X + 3 * b);
+    f3 n = mk(0, 0, 0);
+    for (int k = r.x; k < r.y; ++k) {
+      const int2 ab = m.apre[v.a0 + k];
+      if (s.detached[ab.x]) continue;
+      const f3 p = ld3(ws + L.X + 3 * ab.y) + ld3(ws + L.AT + 10 * ab.x + 6);
+      n = n + cross(p - xb, ld3(wa + A.vh + 3 * ab.x));
     }
-    g.sync();
+    for (int j = 0; j < nd; ++j) out[dof0 + j] += dot(ld3(ws + L.E + 3 * (dof0 + j)), n);
   }
+  g.sync();
 }
 
 }  // namespace

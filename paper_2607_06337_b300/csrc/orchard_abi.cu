@@ -79,6 +79,8 @@ struct Packed {
   std::vector<int> apple_body, tip_body, btip;
   std::vector<float4> tip_local, gravity;
   std::vector<long long> tape_off;    // [W+1] prefix sums of WsLayout::tape_unit (floats)
+  std::vector<int2> apre;             // per apple slot: {apple, its body}, in the bodies' preorder
+  std::vector<int2> arange;           // per body: its subtree's slots [x, y) in apre
   std::vector<int> queue;
   std::vector<ClassInfo> classes;
   // domain-randomisation base (empty unless the descriptor has the material): per body
@@ -171,6 +173,8 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.bl_fbase.clear();
   P.fac_off.assign(W + 1, 0);
   P.tape_off.assign(W + 1, 0);
+  P.apre.assign(NA, make_int2(0, 0));
+  P.arange.assign(NB, make_int2(0, 0));
   P.fac_tgt.clear();
   P.btip.clear();
   std::vector<long long> ws(W);
@@ -269,6 +273,28 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
         stack.pop_back();
         pre.push_back(b);
         for (int c = ccount[b] - 1; c >= 0; --c) stack.push_back(cfirst[b] + c);
+      }
+    }
+    // apples ordered by their body's preorder position (stable), so that every subtree's
+    // apples are one range of slots
+    {
+      std::vector<int> pos(nb), sub(nb, 1);
+      for (int i = 0; i < nb; ++i) pos[pre[i]] = i;
+      for (int i = nb - 1; i > 0; --i) sub[d->parent[b0 + pre[i]]] += sub[pre[i]];
+      std::vector<int> order(na);
+      for (int a = 0; a < na; ++a) order[a] = a;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return pos[d->apple_body[a0 + x]] < pos[d->apple_body[a0 + y]];
+      });
+      std::vector<int> key(na);
+      for (int k = 0; k < na; ++k) {
+        key[k] = pos[d->apple_body[a0 + order[k]]];
+        P.apre[a0 + k] = make_int2(order[k], d->apple_body[a0 + order[k]]);
+      }
+      for (int b = 0; b < nb; ++b) {
+        const int lo = (int)(std::lower_bound(key.begin(), key.end(), pos[b]) - key.begin());
+        const int hi = (int)(std::lower_bound(key.begin(), key.end(), pos[b] + sub[b]) - key.begin());
+        P.arange[b0 + b] = make_int2(lo, hi);
       }
     }
     int maxd = -1;
@@ -542,7 +568,7 @@ namespace {
 struct ModelLayout {
   size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, bj, anc, bl_off,
       bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue,
-      dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, tape_off, total;
+      dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, tape_off, apre, arange, total;
 };
 
 ModelLayout model_layout(const Packed& P) {
@@ -574,6 +600,8 @@ ModelLayout model_layout(const Packed& P) {
   L.dr_com = c.take<float4>(P.dr_com.size()); L.dr_ap0 = c.take<float4>(P.dr_ap0.size());
   L.dr_tip = c.take<float4>(P.dr_tip.size());
   L.tape_off = c.take<long long>(W1);
+  L.apre = c.take<int2>(P.NA);
+  L.arange = c.take<int2>(P.NB);
   L.total = c.off;
   return L;
 }
@@ -814,6 +842,8 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.dr_com, P.dr_com.data(), vbytes(P.dr_com)); put(L.dr_ap0, P.dr_ap0.data(), vbytes(P.dr_ap0));
   put(L.dr_tip, P.dr_tip.data(), vbytes(P.dr_tip));
   put(L.tape_off, P.tape_off.data(), vbytes(P.tape_off));
+  put(L.apre, P.apre.data(), vbytes(P.apre));
+  put(L.arange, P.arange.data(), vbytes(P.arange));
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(dev_buf, host.data(), L.total, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -851,6 +881,8 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.gravity = (const float4*)(base + L.gravity);
   dm.queue = (const int*)(base + L.queue);
   dm.tape_off = (const long long*)(base + L.tape_off);
+  dm.apre = (const int2*)(base + L.apre);
+  dm.arange = (const int2*)(base + L.arange);
   m->w_bp0 = (float4*)(base + L.bp0); m->w_bp2 = (float4*)(base + L.bp2); m->w_bp3 = (float4*)(base + L.bp3);
   m->w_bp4 = (float4*)(base + L.bp4); m->w_ap0 = (float4*)(base + L.ap0); m->w_tip = (float4*)(base + L.tip_local);
   if (!P.dr_geo.empty()) {

@@ -54,6 +54,9 @@ struct DevModel {
   const int* queue;      // world ids sorted by (size class, cost descending)
   const long long* tape_off;  // [W+1] prefix sums of WsLayout::tape_unit over the worlds: the
                               // tape of a T-step rollout gives world w floats from (T + 1) tape_off[w]
+  const int2* apre;      // per apple slot (world-local, at the world's apple offset): {apple,
+                         // its body}, ordered by the body's depth-first preorder position
+  const int2* arange;    // per body: the slots [x, y) in apre of the apples in its subtree
 };
 
 // State arrays in device memory (views into the caller's state buffer).
