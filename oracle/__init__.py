@@ -234,7 +234,8 @@ def solve(H, lam, r, mode: int):
 
 def grad(f, flags, w: int, n_steps: int, target, kinds, idx, steps, mode: int, state: OracleState | None = None,
          step0: int = 0, n_threads: int | None = None, dense_limit: int = 256):
-    """Loss gradient of world w by complex step (mode 0) or central differences (mode 1).
+    """Loss gradient of world w by complex step (mode 0), central differences (mode 1), or
+    complex step with every operation in single precision (mode 2: the FP32 rounding floor).
 
     kinds: 0 = k of body idx, 1 = kd of body idx, 2 = q0[idx], 3 = qd0[idx] (world-local).
     target: (n_steps, n_tips_of_world, 3) tip positions.

@@ -43,9 +43,13 @@
 namespace {
 
 using cplx = std::complex<double>;
+// single-precision complex step: the same derivative with every operation rounded to FP32
+// (the rounding floor of an FP32 evaluation of a gradient, for the adjoint's tolerance)
+using cplxf = std::complex<float>;
 
 inline double re(double x) { return x; }
 inline double re(const cplx& x) { return x.real(); }
+inline double re(const cplxf& x) { return x.real(); }
 
 // Reverse-mode scalar: the oracle's own adjoint. Every operation on an RV appends one node
 // to the current thread's tape (its value's local partial derivatives with respect to at most
@@ -888,6 +892,16 @@ int oracle_grad(const OForest* f, const OFlags* fl, const OState* st, const OPul
       if (kind == 2) s.q[i] += cplx(0, h);
       if (kind == 3) s.qd[i] += cplx(0, h);
       return std::imag(world_loss<cplx>(W, *fl, s, G, pl, a0, step0, n_steps, target)) / h;
+    }
+    if (mode == 2) {
+      const float hf = (float)h;
+      WState<cplxf> s = load_state<cplxf>(f, st, W, w);
+      Gains<cplxf> G = gains_of<cplxf>(W);
+      if (kind == 0) G.k[i] += cplxf(0, hf);
+      if (kind == 1) G.kd[i] += cplxf(0, hf);
+      if (kind == 2) s.q[i] += cplxf(0, hf);
+      if (kind == 3) s.qd[i] += cplxf(0, hf);
+      return (double)std::imag(world_loss<cplxf>(W, *fl, s, G, pl, a0, step0, n_steps, target)) / (double)hf;
     }
     double acc[2];
     for (int sgn = 0; sgn < 2; ++sgn) {
