@@ -7,12 +7,16 @@ class. A bench step is one rollout of the whole hot path over the batch. Under t
 rank simulates its own freshly seeded trees (weak scaling; no collective on the data path).
 
 Beside the headline forward number the line carries: the plain form (one launch per world per
-step) on the same batch, the forward + adjoint leg on the differentiation workload (diff1024:
-1024 trees x 200 bodies x 30 apples, 200 steps, checkpoints every 20), the FP32 roofline
-fractions, and the FP64 oracle timed on the host cores on a bounded sample.
+step) on the same batch; forward + adjoint on the differentiation workload (diff1024: 1024
+trees x 200 bodies x 30 apples, 200 steps) and on the stress workload (stress8192: 8192 mixed
+trees of 50/400/2000 bodies, 500 steps, FP64 twig pivots); the world-count sweep of the
+sweep16384 trees (1024..65536 worlds, batched against plain, with the 16384-world headline);
+the FP32 roofline fractions; the FP64 oracle timed on the host cores on a bounded sample; and
+the error against the oracle of each of those workloads (the q gate and the event sets).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload batch4096|sweep16384|stress8192|plain16] [--worlds W]
+    python bench.py --phase-clocks [--worlds W] [--sim-steps S]   (the profiling build)
 """
 from __future__ import annotations
 
@@ -35,8 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "body-steps/s fwd & fwd+adjoint, batched vs plain on B300; frac of FP32/HBM roofline"
 UNIT = "body-steps/s"
-SM_COUNT = 148
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 sub-partitions x 32)
+ORACLE_WORLDS_PER_CORE = 12      # the oracle's sample: this many worlds per host thread
+REF_STEPS = 200                  # the reference arm: simulation steps per bench step
 
 
 def parse():
@@ -53,13 +58,19 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--plain-steps", type=int, default=2)
-    p.add_argument("--cpu-seconds", type=float, default=24.0)
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-damped", action="store_true", help="skip the body-damping leg")
     p.add_argument("--no-dr", action="store_true", help="skip the on-device domain-randomisation leg")
     p.add_argument("--adj-workload", default="diff1024", help="diff1024 (default) or stress8192")
-    p.add_argument("--sweep", action="store_true",
-                   help="add a world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
+    p.add_argument("--no-stress", action="store_true", help="skip the stress8192 forward + adjoint leg")
+    p.add_argument("--stage", default="auto", choices=["auto", "off"],
+                   help="off: after the autotune, run every class with no model records staged in shared "
+                        "memory (A/B of the staging)")
+    p.add_argument("--phase-clocks", action="store_true",
+                   help="profiling: run the workload once on the phase-clock build and print the cycles per "
+                        "world-step of each phase of the step, per size class")
     p.add_argument("--adj-worlds", type=int, default=None)
     p.add_argument("--adj-steps", type=int, default=None, help="default: the workload's step count")
     p.add_argument("--adj-ckpt", type=int, default=20)
@@ -81,9 +92,14 @@ def peaks():
     return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    # 148 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, n_sm: int) -> float:
+    # SMs x 128 FP32 lanes x 2 flops per FMA x SM clock
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def device_sms(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 class ClockSampler:
@@ -172,45 +188,87 @@ def measured_traffic(workload, n_worlds, sim_steps):
     return d.get("dram_bytes_per_rollout")
 
 
-def cpu_baseline(forest, flags, seconds, sim_steps):
-    """The oracle as it stands on the host cores, on a bounded sample of the same workload:
-    worlds stratified by size, the workload's own step count (capped at 1000), as many worlds
-    as fit in about `seconds` of host time."""
+def oracle_sample(forest, n_w):
+    """World indices of a sample stratified by size: n_w worlds at evenly spaced ranks of the
+    size order, listed largest first (the oracle's threads take worlds in list order, so the
+    largest start first and the load stays balanced)."""
+    sizes = np.diff(forest.body_off) + np.diff(forest.apple_off)
+    order = np.argsort(sizes, kind="stable")
+    n_w = min(n_w, forest.n_worlds)
+    pick = np.unique(order[np.linspace(0, len(order) - 1, n_w).round().astype(np.int64)])
+    return pick[np.argsort(-sizes[pick], kind="stable")]
+
+
+def gather_state(forest, sim, pick):
+    """The GPU state of worlds `pick`, laid out as forest.subset(pick) lays out its worlds."""
+    q = sim.q.cpu().numpy().astype(np.float64)
+    arrays = {"broken": sim.broken, "break_step": sim.break_step, "detached": sim.detached,
+              "detach_step": sim.detach_step}
+    arrays = {k: v.cpu().numpy() for k, v in arrays.items()}
+    do, bo, ao = forest.dof_off, forest.body_off, forest.apple_off
+
+    def cat(a, off):
+        return np.concatenate([a[off[w]:off[w + 1]] for w in pick] + [a[:0]])
+
+    return {"q": cat(q, do), "broken": cat(arrays["broken"], bo), "break_step": cat(arrays["break_step"], bo),
+            "detached": cat(arrays["detached"], ao), "detach_step": cat(arrays["detach_step"], ao)}
+
+
+def oracle_accuracy(forest, flags, pick, gpu, steps, cores):
+    """The oracle's run of `steps` steps on worlds `pick` against the GPU's state after the
+    same steps: the q gate and the event-set gate, summarised (not timed)."""
     import oracle as O
+    from oracle import parity as PAR
+    sub = forest.subset(pick)
+    st, rec = O.rollout(sub, flags, steps, n_threads=cores, near_eps=PAR.NEAR)
+    out = PAR.summary(PAR.compare(sub, flags, gpu, st, rec["near"]))
+    out["steps"] = steps
+    return out
+
+
+GATE = ("per world: max|q_gpu - q_oracle| <= 1e-4 max|q_oracle| + 1e-7 rad (ratio = error / that bound); "
+        "event sets of (joint, break step) and (apple, detach step) identical unless the oracle logged "
+        "the test within 1e-5 of its threshold")
+
+
+def cpu_baseline(forest, flags, sim_steps, gpu=None):
+    """The oracle as it stands on the host cores, on a bounded sample of the same workload:
+    ORACLE_WORLDS_PER_CORE worlds per host thread, stratified by size (oracle_sample), the
+    workload's own step count (capped at 1000). With the GPU's state after the same steps on
+    those worlds (gpu), the oracle's result doubles as the accuracy check of the timed run."""
+    import oracle as O
+    from oracle import parity as PAR
     from paper_2607_06337_b300 import costs
     cores = os.cpu_count() or 1
-    sizes = np.diff(forest.body_off)
-    order = np.argsort(sizes)
-
-    def sample(n_w):
-        pick = np.sort(order[np.linspace(0, len(order) - 1, n_w).astype(int)])
-        return forest.subset(pick)
-
+    pick = oracle_sample(forest, ORACLE_WORLDS_PER_CORE * cores)
+    sub = forest.subset(pick)
     steps = min(sim_steps, 1000)
-    n_w = min(cores, forest.n_worlds)
-    while True:  # grow the sample until it takes at least half of `seconds`
-        sub = sample(n_w)
-        t = time.perf_counter()
-        O.rollout(sub, flags, steps, n_threads=cores)
-        dt = time.perf_counter() - t
-        if dt >= seconds / 2 or n_w >= forest.n_worlds:
-            break
-        n_w = int(min(forest.n_worlds, max(n_w + 1, n_w * 1.1 * seconds / max(dt, 1e-3))))
+    t = time.perf_counter()
+    st, rec = O.rollout(sub, flags, steps, n_threads=cores, near_eps=PAR.NEAR)
+    dt = time.perf_counter() - t
     bs = costs.body_count(sub) * steps / dt
     # one thread on a quarter of one thread's share of that sample
-    n1 = max(1, n_w // (4 * cores))
-    sub1 = sample(n1)
+    n1 = max(1, len(pick) // (4 * cores))
+    sub1 = forest.subset(oracle_sample(forest, n1))
     t = time.perf_counter()
     O.rollout(sub1, flags, steps, n_threads=1)
     dt1 = time.perf_counter() - t
-    return {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{n_w} of {forest.n_worlds} worlds stratified by size x {steps} steps "
+    line = {"value": bs, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(pick)} of {forest.n_worlds} worlds stratified by size x {steps} steps "
                       f"(FP64, {cores} threads), {dt:.1f} s",
             "value_1core": costs.body_count(sub1) * steps / dt1,
             "sample_1core": f"{n1} worlds x {steps} steps on one thread, {dt1:.1f} s"}
+    acc = None
+    if gpu is not None:
+        acc = PAR.summary(PAR.compare(sub, flags, gpu, st, rec["near"]))
+        acc["steps"] = steps
+    return line, acc, pick
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, on the same stratified sample as
+    the main arm's cpu_baseline (ORACLE_WORLDS_PER_CORE worlds per thread), REF_STEPS steps per
+    bench step, so that the two oracle rates of a run describe one measurement."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
@@ -220,52 +278,64 @@ def run_reference(args):
     nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
     fl = I.Flags()
     cores = os.cpu_count() or 1
-    # every thread gets a few worlds, each bench step a few tenths of a second of host work
-    sample_w = min(4 * cores, nw)
-    forest = I.make_forest(args.workload, n_worlds=nw, worlds=np.linspace(0, nw - 1, sample_w).astype(int))
-    steps = 100
+    forest = I.make_forest(args.workload, n_worlds=nw, processes=min(16, cores))
+    pick = oracle_sample(forest, ORACLE_WORLDS_PER_CORE * cores)
+    sub = forest.subset(pick)
+    steps = min(REF_STEPS, args.sim_steps or I.WORKLOAD_STEPS[args.workload])
     for _ in range(args.warmup):
-        O.rollout(forest, fl, 5, n_threads=cores)
+        O.rollout(sub, fl, 5, n_threads=cores)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
-        O.rollout(forest, fl, steps, n_threads=cores)
+        O.rollout(sub, fl, steps, n_threads=cores)
         times.append(time.perf_counter() - t)
     per = statistics.mean(times)
-    value = costs.body_count(forest) * steps / per
+    value = costs.body_count(sub) * steps / per
+    desc = f"{len(pick)} of {nw} worlds stratified by size x {steps} steps per bench step (FP64, {cores} threads)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload} sample: {sample_w} of {nw} worlds x {steps} steps"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{sample_w} worlds x {steps} steps per bench step"},
+            "config": {"workload": f"{args.workload} sample: {desc}"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def fwd_adjoint(args, dev, rank, ws):
-    """Forward + adjoint body-steps/s on the differentiation workload: 1024 trees of 200
-    segment bodies and 30 apples, a 200-step rollout under a fixed 5 N pull on one apple per
-    tree, tip positions recorded; the loss is the squared error of the tips against a target
-    rollout, and the backward gives dL/dk, dL/dkd, dL/dq0, dL/dqd0.
+def accuracy_pick(forest, per_size):
+    """Worlds for the accuracy check: per_size evenly spaced worlds of every tree size."""
+    sizes = np.diff(forest.body_off)
+    out = {}
+    for sz in np.unique(sizes):
+        idx = np.nonzero(sizes == sz)[0]
+        out[int(sz)] = idx[np.linspace(0, len(idx) - 1, min(per_size, len(idx))).round().astype(np.int64)]
+    return out
 
-    Two forms of the record are timed: checkpoints every ``--adj-ckpt`` steps (each segment
-    replayed once in the backward), and the forward's full tape (the backward runs no step
-    again) when it fits in half the free device memory, else a tape of the last steps that fit
-    with checkpoints before them (the hybrid). The line's value is the faster form; the other
-    is reported beside it.
+
+def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, acc_per_size=0):
+    """Forward + adjoint body-steps/s on a recorded rollout (tip positions recorded; the loss is
+    the squared error of the tips against a target rollout, and the backward gives dL/dk,
+    dL/dkd, dL/dq0, dL/dqd0). diff1024: 1024 trees of 200 segment bodies and 30 apples, 200
+    steps under a fixed 5 N pull on one apple per tree. stress8192: 8192 trees of 50, 400 and
+    2000 bodies, 500 steps, FP64 pivots for twigs under 5 mm.
+
+    Record forms: the forward's full tape (the backward runs no step again) when it fits in half
+    the free device memory, else a tape of the last steps that fit with checkpoints every
+    ``--adj-ckpt`` steps before them (the hybrid); and, with checkpoint_form, checkpoints only
+    (each segment replayed once in the backward). The line's value is the faster form; the
+    other is reported beside it. ``warmup`` and ``steps`` are this leg's own repeat counts.
 
     The target here is this library's own rollout with every k scaled by U(0.8, 1.2) (the
-    timing does not depend on it; the tests take the target from the oracle)."""
+    timing does not depend on it; the tests take the target from the oracle). With
+    acc_per_size > 0 the GPU state after a plain forward of the same steps is kept for the
+    accuracy check against the oracle (acc_per_size worlds of every tree size)."""
     import torch
     from paper_2607_06337_b300 import costs
     from paper_2607_06337_b300 import inputs as I
     from paper_2607_06337_b300 import orchard as B
-    name = args.adj_workload
     nw = args.adj_worlds or I.WORKLOAD_WORLDS[name]
     # the stress workload inverts the pivots of twigs under 5 mm in FP64
     fl = I.Flags(fp64_twig_diam=0.005 if name == I.STRESS else 0.0)
-    f = I.make_forest(name, n_worlds=nw, sweep=rank)
+    f = I.make_forest(name, n_worlds=nw, sweep=rank, processes=min(16, os.cpu_count() or 1))
     n = args.adj_steps or I.WORKLOAD_STEPS[name]
     sim = B.Simulator(f, fl, device=dev)
     stream = torch.cuda.current_stream()
@@ -317,15 +387,15 @@ def fwd_adjoint(args, dev, rank, ws):
             if ev:
                 ev[3].record(stream)
 
-        for k in range(args.warmup):
+        for k in range(warmup):
             one(k)
         torch.cuda.synchronize()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
         B.launch_count(reset=True)
-        for k in range(args.steps):
+        for k in range(steps):
             one(k, evs[k])
         torch.cuda.synchronize()
         launches = B.launch_count()
@@ -350,12 +420,13 @@ def fwd_adjoint(args, dev, rank, ws):
         runs["tape"] = timed(0)
     elif k_hyb > 0:
         runs["hybrid"] = timed(args.adj_ckpt, k_hyb)
-    runs["checkpoints"] = timed(args.adj_ckpt)
+    if checkpoint_form or not runs:
+        runs["checkpoints"] = timed(args.adj_ckpt)
     mode = min(runs, key=lambda k: runs[k][2])
     fwd_ms, bwd_ms, tot_ms, launches, g_ok, rec_bytes = runs[mode]
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
-    peak_tf = fp32_peak_tflops(sm_mhz)
+    peak_tf = fp32_peak_tflops(sm_mhz, device_sms(dev))
     fwd_fl = costs.flops_per_step(f) * n
     replayed = {"tape": 0, "hybrid": n - k_hyb, "checkpoints": n}[mode]  # steps run again
     bwd_fl = costs.adjoint_flops_per_step(f, replay=False) * n + costs.flops_per_step(f) * replayed
@@ -387,7 +458,19 @@ def fwd_adjoint(args, dev, rank, ws):
         out["tape"] = {"skipped": f"{B.tape_bytes(sim.model, n) / 1e9:.1f} GB tape over half the free memory"}
         if "hybrid" in runs:
             out["tape_steps"] = k_hyb
-    return out
+    out["repeats"] = {"warmup": warmup, "timed": steps}
+    out["schedules"] = sim.class_infos()
+    acc = None
+    if acc_per_size > 0:
+        sim.reset_from_device(*dev_in)
+        sim.rollout(n)
+        torch.cuda.synchronize()
+        acc = {sz: (pick, gather_state(f, sim, pick)) for sz, pick in accuracy_pick(f, acc_per_size).items()}
+        acc = {"forest": f, "flags": fl, "steps": n, "sizes": acc}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out, acc
 
 
 def damped_leg(args, dev, forest, S, flush):
@@ -452,53 +535,176 @@ def dr_leg(sim, forest, dev):
 
 def world_sweep(args, dev):
     """Batched (persistent, graph, autotuned) and plain (one launch per world per step) forward
-    body-steps/s at 1024..65536 worlds of the sweep16384 trees (300 bodies, 60 apples). The
-    worlds are the first N of one 65536-world batch (per-world seeds: fresh draws of the same
-    distribution). Batched: 100 steps per timed rollout; plain: 2 steps."""
+    body-steps/s at 1024, 4096, 16384 and 65536 worlds of the sweep16384 trees (300 bodies, 60
+    apples): the first N of one 65536-world batch, whose first 16384 worlds are the sweep16384
+    workload itself. Batched: 100 steps per timed rollout, one warm-up and two timed; plain: 2
+    steps (1 from 16384 worlds on, where one step is already 16384+ launches). The 16384-world
+    point also runs the workload's full 1000 steps once, timed (the sweep16384 headline), and
+    keeps the GPU state of a sample of its worlds for the accuracy check."""
     import torch
     from paper_2607_06337_b300 import costs
     from paper_2607_06337_b300 import inputs as I
     from paper_2607_06337_b300 import orchard as B
-    counts = [1024, 2048, 4096, 8192, 16384, 32768, 65536]
+    counts = [1024, 4096, 16384, 65536]
     fl = I.Flags()
-    big = I.make_forest(I.SWEEP, n_worlds=max(counts))
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    big = I.make_forest(I.SWEEP, n_worlds=max(counts), processes=min(16, cores))
+    gen_s = time.perf_counter() - t
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    out = []
-    for n in counts:
-        f = big.subset(range(n)) if n < big.n_worlds else big
-        sim = B.Simulator(f, fl, device=dev)
-        sim.autotune(n_steps=10)
-        bodies = costs.body_count(f)
-        steps = 100
-        sim.reset()
-        sim.rollout(steps)
-        ms = []
-        for k in range(2):
-            flush.fill_(k)
-            sim.reset()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            sim.rollout(steps)
-            b.record(stream)
-            torch.cuda.synchronize()
-            ms.append(a.elapsed_time(b))
-        batched = bodies * steps / (min(ms) / 1e3)
+
+    def timed_rollout(sim, steps, k):
+        flush.fill_(k & 0xff)
         sim.reset()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        sim.rollout_plain(2)
+        sim.rollout(steps)
         b.record(stream)
         torch.cuda.synchronize()
-        plain = bodies * 2 / (a.elapsed_time(b) / 1e3)
-        out.append({"worlds": n, "batched": batched, "plain": plain, "batched_over_plain": batched / plain})
+        return a.elapsed_time(b)
+
+    out, headline, acc = [], None, None
+    sched = None
+    for n in counts:
+        f = big if n == big.n_worlds else big.subset(range(n))
+        sim = B.Simulator(f, fl, device=dev)
+        # one tree size: the schedules tuned on the smallest batch serve every batch with the
+        # same size classes
+        if sched is not None and len(sched) == sim.counts.classes:
+            for k, sc in enumerate(sched):
+                B.set_schedule(sim.model, k, sc)
+        else:
+            sim.autotune(n_steps=10)
+            sched = sim.schedules()
+        bodies = costs.body_count(f)
+        steps = 100
+        sim.reset()
+        sim.rollout(steps)
+        ms = min(timed_rollout(sim, steps, k) for k in range(2))
+        batched = bodies * steps / (ms / 1e3)
+        ps = 2 if n <= 4096 else 1
+        sim.reset()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.rollout_plain(ps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        plain = bodies * ps / (a.elapsed_time(b) / 1e3)
+        out.append({"worlds": n, "batched": batched, "plain": plain, "plain_steps": ps,
+                    "batched_over_plain": batched / plain})
+        if n == 16384:
+            scheds = sim.class_infos()
+            S = I.WORKLOAD_STEPS[I.SWEEP]
+            ms = timed_rollout(sim, S, 7)
+            headline = {"worlds": n, "sim_steps": S, "value": bodies * S / (ms / 1e3), "unit": UNIT, "ms": ms,
+                        "batched_over_plain": bodies * S / (ms / 1e3) / plain,
+                        "frozen_worlds": int((sim.status.cpu().numpy() & 1).sum())}
+            pick = oracle_sample(f, 32)
+            acc = {"forest": f, "flags": fl, "steps": S, "sizes": {300: (pick, gather_state(f, sim, pick))}}
         sim.close()
         del sim
         torch.cuda.empty_cache()
     return {"workload": "sweep16384 trees (300 bodies, 60 apples), first N of 65536", "unit": UNIT,
-            "points": out}
+            "points": out, "headline_16384": headline, "schedules": scheds,
+            "host_generation_s": gen_s}, acc
+
+
+def unstage(sim):
+    """Every class keeps its schedule but stages no model records in shared memory."""
+    from paper_2607_06337_b300 import orchard as B
+    for k, sc in enumerate(sim.schedules()):
+        sc.stage = 0
+        B.set_schedule(sim.model, k, sc)
+
+
+def phase_clock_run(args):
+    """Profiling: the workload once on the phase-clock build (ORCHARD_LIB_VARIANT=phase), after
+    the usual autotune and a warm-up rollout; prints the SM cycles per world-step of each phase
+    of the step, per size class. The timing of this build is perturbed by the clock reads, so
+    the line is no benchmark value."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+    assert B.LIB_PATH.endswith("liborchard_phase.so"), B.LIB_PATH
+    nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
+    forest = I.make_forest(args.workload, n_worlds=nw, processes=min(16, os.cpu_count() or 1))
+    S = args.sim_steps or I.WORKLOAD_STEPS[args.workload]
+    fl = I.Flags(fp64_twig_diam=0.005 if args.workload == I.STRESS else 0.0)
+    sim = B.Simulator(forest, fl, device=dev)
+    if not args.no_autotune:
+        sim.autotune(n_steps=20)
+    if args.stage == "off":
+        unstage(sim)
+    sim.reset()
+    sim.rollout(S)
+    torch.cuda.synchronize()
+    B.phase_clocks(sim.model, sim.counts.classes, reset=True)
+    sim.reset()
+    sim.rollout(S)
+    torch.cuda.synchronize()
+    rows = B.phase_clocks(sim.model, sim.counts.classes, reset=True)
+    sizes = np.diff(forest.body_off)
+    out = []
+    for k, (row, ci) in enumerate(zip(rows, sim.class_infos())):
+        total = sum(row[p] for p in B.PHASES)
+        out.append({"class": k, **ci, "world_steps": int(row["world_steps"]),
+                    "cycles_per_world_step": total,
+                    "phases": {p: round(row[p], 1) for p in B.PHASES},
+                    "share": {p: round(row[p] / total, 4) if total else 0.0 for p in B.PHASES}})
+    line = {"phase_clocks": out, "instrumented": True, "workload": args.workload, "worlds": nw,
+            "sim_steps": S, "bodies_min": int(sizes.min()), "bodies_max": int(sizes.max())}
+    sim.close()
+    del sim
+    if not args.no_adjoint:
+        line["backward_phase_clocks"] = backward_phase_run(args, dev)
+    print(json.dumps(line), flush=True)
+
+
+def backward_phase_run(args, dev):
+    """The backward's phase clocks on the differentiation workload (--adj-workload), for each
+    record form: the forward's tape (when it fits in half the free memory) and checkpoints every
+    --adj-ckpt steps; one warm-up backward, then one counted."""
+    import torch
+    from paper_2607_06337_b300 import inputs as I
+    from paper_2607_06337_b300 import orchard as B
+    name = args.adj_workload
+    f = I.make_forest(name, n_worlds=args.adj_worlds or I.WORKLOAD_WORLDS[name],
+                      processes=min(16, os.cpu_count() or 1))
+    n = args.adj_steps or I.WORKLOAD_STEPS[name]
+    fl = I.Flags(fp64_twig_diam=0.005 if name == I.STRESS else 0.0)
+    sim = B.Simulator(f, fl, device=dev)
+    if not args.no_autotune:
+        sim.autotune(n_steps=20)
+    free, _ = torch.cuda.mem_get_info(dev)
+    forms = ([("tape", 0)] if B.tape_bytes(sim.model, n) <= free // 2 else []) + [("checkpoints", args.adj_ckpt)]
+    out = {}
+    for form, ce in forms:
+        tips, buf, rec = sim.record_buffers(n, ce)
+        sim.reset()
+        sim.rollout(n, record=rec)
+        dt = torch.full_like(tips, 1e-3)
+        for k in range(2):
+            if k == 1:
+                torch.cuda.synchronize()
+                B.phase_clocks(sim.model, sim.counts.classes, reset=True, backward=True)
+            sim.backward(n, rec, dt)
+        torch.cuda.synchronize()
+        rows = B.phase_clocks(sim.model, sim.counts.classes, reset=True, backward=True)
+        per = []
+        for k, row in enumerate(rows):
+            total = sum(row[p] for p in B.BACK_PHASES)
+            per.append({"class": k, "world_steps": int(row["world_steps"]), "cycles_per_world_step": total,
+                        "phases": {p: round(row[p], 1) for p in B.BACK_PHASES}})
+        out[form] = per
+        del tips, buf, rec
+        torch.cuda.empty_cache()
+    sim.close()
+    return {"workload": name, "sim_steps": n, "forms": out}
 
 
 def run_ours(args):
@@ -515,7 +721,8 @@ def run_ours(args):
 
     nw = args.worlds or I.WORKLOAD_WORLDS[args.workload]
     fl = I.Flags()
-    forest = I.make_forest(args.workload, n_worlds=nw, sweep=rank)
+    cores = os.cpu_count() or 1
+    forest = I.make_forest(args.workload, n_worlds=nw, sweep=rank, processes=min(16, cores))
     S = args.sim_steps or I.WORKLOAD_STEPS[args.workload]
     sim = B.Simulator(forest, fl, device=dev)
     stream = torch.cuda.current_stream()
@@ -530,8 +737,9 @@ def run_ours(args):
     if not args.no_autotune:
         reset()
         sim.autotune(n_steps=20)
-    scheds = [dict(threads_per_world=s.threads_per_world, worlds_per_block=s.worlds_per_block,
-                   global_workspace=s.global_workspace) for s in sim.schedules()]
+    if args.stage == "off":
+        unstage(sim)
+    scheds = sim.class_infos()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     for _ in range(args.warmup):
@@ -586,8 +794,14 @@ def run_ours(args):
     h2d = sum(h.numel() * 4 for h in host_in)
     d2h = host_q.numel() * 4 + host_st.numel() * 4
     e2e_value = ws * bodies * S / statistics.mean(e2e_times)
+    # the GPU state after S steps of the workload, for the accuracy check against the oracle
+    acc_pick = oracle_sample(forest, ORACLE_WORLDS_PER_CORE * cores)
+    gpu_acc = gather_state(forest, sim, acc_pick) if rank == 0 and ws == 1 and S <= 1000 else None
 
-    adj = None if args.no_adjoint else fwd_adjoint(args, dev, rank, ws)
+    adj, acc_diff = (None, None) if args.no_adjoint else fwd_adjoint(
+        args, dev, rank, ws, args.adj_workload, args.warmup, args.steps, acc_per_size=16 if ws == 1 else 0)
+    stress, acc_stress = (None, None) if args.no_stress or args.no_adjoint else fwd_adjoint(
+        args, dev, rank, ws, I.STRESS, 1, 2, checkpoint_form=False, acc_per_size=4 if ws == 1 else 0)
     damped = None if args.no_damped or ws > 1 else damped_leg(args, dev, forest, S, flush)
     if damped:
         damped["vs_undamped"] = damped["value"] / (value / ws)
@@ -613,27 +827,43 @@ def run_ours(args):
     pk, src = peaks()
     clocks = clk.summary()
     sm_mhz = float(pk.get("sm_max_mhz", 2032.0))
-    peak_tf = fp32_peak_tflops(sm_mhz)
+    n_sm = device_sms(dev)
+    peak_tf = fp32_peak_tflops(sm_mhz, n_sm)
     achieved_tf = flops / (ms_mean / 1e3) / 1e12
-    hbm_bytes = costs.hbm_bytes_per_rollout(forest)
+    hbm_model = costs.hbm_bytes_per_rollout(forest)
     traffic = measured_traffic(args.workload, nw, S)
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf,
                 "traffic": traffic,
-                "peak_source": f"derived: 148 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
-                               f"(sm_max_mhz from MEASURED_PEAKS.json, {src})",
+                "peak_source": f"derived: {n_sm} SMs (from the device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x "
+                               f"{sm_mhz:.0f} MHz (sm_max_mhz from MEASURED_PEAKS.json, {src})",
                 "flops_per_launch": flops}
+    # HBM: the measured DRAM bytes of the timed rollout when the committed capture matches this
+    # kernel and workload, else the algorithmic model (one read of the model, state in and out)
+    hbm_bytes = traffic if traffic else hbm_model
     hbm = {"achieved": hbm_bytes / (ms_mean / 1e3) / 1e9, "peak": float(pk.get("hbm_gbs", 6400.0)),
-           "unit": "GB/s", "bytes_per_launch": hbm_bytes}
+           "unit": "GB/s", "bytes_per_launch": hbm_bytes,
+           "bytes_source": "measured (ncu DRAM bytes of this kernel and workload)" if traffic else
+           "model (algorithmic: one read of the model, one read and write of the state)",
+           "algorithmic_bytes": hbm_model}
     hbm["frac"] = hbm["achieved"] / hbm["peak"]
 
-    sweep = world_sweep(args, dev) if args.sweep and ws == 1 else None
+    sweep, acc_sweep = world_sweep(args, dev) if not args.no_sweep and ws == 1 else (None, None)
 
     dr = None if args.no_dr or ws > 1 else dr_leg(sim, forest, dev)
 
-    cpu = None
+    cpu, accuracy = None, None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = cpu_baseline(forest, fl, args.cpu_seconds, S)
+        cpu, acc_main, _ = cpu_baseline(forest, fl, S, gpu=gpu_acc)
+        accuracy = {"gate": GATE, args.workload: acc_main}
+        for leg in (acc_diff, acc_stress, acc_sweep):
+            if leg is None:
+                continue
+            name = leg["forest"].meta.get("workload")
+            per = {}
+            for sz, (pick, gpu) in leg["sizes"].items():
+                per[f"{sz} bodies"] = oracle_accuracy(leg["forest"], leg["flags"], pick, gpu, leg["steps"], cores)
+            accuracy[name] = per if len(per) > 1 else next(iter(per.values()))
 
     if rank == 0:
         line = {
@@ -652,6 +882,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "plain": plain,
             "fwd_adj": adj,
+            "fwd_adj_stress": stress,
+            "accuracy": accuracy,
             "damped": damped,
             "dr_build": dr,
             "sweep": sweep,
@@ -667,7 +899,10 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.phase_clocks:
+        os.environ["ORCHARD_LIB_VARIANT"] = "phase"  # before the binding is imported
+        phase_clock_run(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -133,7 +133,21 @@ typedef struct ot_schedule {
   int32_t worlds_per_block;    /* groups of threads_per_world threads in one block */
   int32_t blocks;              /* persistent grid size (0: enough for one wave) */
   int32_t global_workspace;    /* 1: per-step temporaries in the state's scratch area */
+  int32_t stage;               /* model records copied into shared memory per world, for all its
+                                  steps (classes in shared memory only): -1 automatic, each of
+                                  the parts (1 sweep topology and frames, 8 ancestor rows,
+                                  4 joint rows, 2 stiffness, 64 force and apple records,
+                                  16 factorisation records, 32 factorisation targets), in that
+                                  order, that fits at the class's resident blocks per SM;
+                                  0 none; > 0 this mask (OT_ECAPACITY at launch when it does
+                                  not fit in shared memory) */
 } ot_schedule;
+
+/* What a size class resolves to under its current schedule: out[0] worlds, [1] largest world's
+ * bodies, [2] per-world step temporaries (bytes), [3] the staged parts (mask), [4] their bytes
+ * per world, [5] dynamic shared memory per block (bytes), [6] resident blocks per SM, [7] the
+ * persistent grid's blocks. Sets the kernel's attributes (not inside a stream capture). */
+ot_status ot_class_info(ot_model* model, int32_t size_class, int64_t out[8]);
 
 /* ---------------------------------------------------------------------------------------
  * Model upload.
@@ -325,7 +339,10 @@ ot_status ot_autotune(ot_model* model, ot_state* state, int32_t n_steps, double 
  * passes the model, the state, the forces and the stream.
  *   - Size: OT_STATIC_SCRATCH_BYTES per GPU, held from library load until process exit. A
  *     world whose temporaries exceed it (minus 256 bytes of counters) is rejected with
- *     OT_ECAPACITY before any work is queued.
+ *     OT_ECAPACITY, and a state of another model or a pull schedule without its start and
+ *     end arrays with OT_EINVAL; every check runs before any work is queued, so a rejected
+ *     call changes nothing. A class whose schedule asks for more worlds per block than the
+ *     array has slots for runs with fewer worlds per block.
  *   - The array's device address is looked up with cudaGetSymbolAddress on the first call on
  *     each device (with that device current); make that first call outside any stream capture.
  *   - Every call uses the same array and leaves its contents behind; the call clears what must
@@ -343,6 +360,18 @@ int32_t ot_last_cuda_error(void);
 /* Number of kernel launches the library issued since the last reset (graph replays count
  * each kernel node once). */
 int64_t ot_launch_count(int32_t reset);
+/* Phase clocks, for profiling only: available in the instrumented build of the library
+ * (compiled with ORCHARD_PHASE_CLOCKS), OT_EINVAL in the product build. Copies max_classes
+ * (at most 64) rows of 10 counters into out (host, [row][10]). Row k < 32: size class k's
+ * rollouts, the SM cycles summed over all world-steps since the last reset for each phase of
+ * the step (forward kinematics sweep, forces and apple loads, tip record, bias sweep,
+ * mass-matrix rows, LDL^T, update sweep, apple update, the rest of the rollout), then the
+ * world-step count. Row 32 + k: class k's backward passes (apple update reverse and hang-point
+ * loads, the solve with the step's factors, the L sweep with springs and tape, the seeds, the
+ * leaf-to-root chain, restoring a step's start state and record, segment replays, the final
+ * seed, the rest), then the world-steps reversed. Synchronises the device; reset != 0 zeroes
+ * the counters afterwards. */
+ot_status ot_phase_clocks(const ot_model* model, uint64_t* out, int32_t max_classes, int32_t reset);
 
 #ifdef __cplusplus
 }

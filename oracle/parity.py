@@ -1,5 +1,7 @@
 """Comparison of a GPU run with the oracle: the joint-position gate and the event-set gate.
 
+Test infrastructure, beside the oracle: the tests and the benchmark's CPU leg use it.
+
 q gate (per world): max |q_gpu - q_ref| <= 1e-4 * max |q_ref| + 1e-7 rad.
 Event gate: the sets of (joint, break step) and (apple, detach step) are identical, except that
 a mismatch is excused when the oracle logged that test within 1e-5 relative of its threshold at
@@ -52,3 +54,16 @@ def assert_parity(rep):
     bad = [r for r in rep if r["unexcused"] or (r["q_gated"] and r["ratio"] > 1.0)]
     assert not bad, "parity failures: " + "; ".join(
         f"w{r['world']} ratio={r['ratio']:.3g} unexcused={r['unexcused'][:4]}" for r in bad[:8])
+
+
+def summary(rep) -> dict:
+    """The gates of a comparison in a few numbers (for a benchmark record)."""
+    gated = [r["ratio"] for r in rep if r["q_gated"]]
+    return {"worlds": len(rep), "q_gate_ratio_max": float(max(gated)) if gated else None,
+            "q_gate_ratio_p50": float(np.median(gated)) if gated else None,
+            "q_err_max_rad": float(max(r["dq"] for r in rep)) if rep else None,
+            "events": int(sum(r["n_events"] for r in rep)),
+            "event_sets_identical": not any(r["unexcused"] or r["excused"] for r in rep),
+            "excused": int(sum(len(r["excused"]) for r in rep)),
+            "unexcused": int(sum(len(r["unexcused"]) for r in rep)),
+            "pass": not any(r["unexcused"] or (r["q_gated"] and r["ratio"] > 1.0) for r in rep)}

@@ -14,15 +14,16 @@ of DOF ancestors of DOF i):
 
   flops = 589 n_b + 182 n_a + 48 n_v + 24 E + 3 P.
 
-Adjoint, per world and step of the backward pass (n_t tips): the segment replay and the
-recompute that supplies the step's factors run the forward step twice, then
+Adjoint, per world and step of the backward pass (n_t tips): with checkpoints the segment
+replay runs the forward step once more and saves its records (factors included), so the
+reverse recomputes nothing; with the forward's tape no step runs again. Then
 
   tape            138 / body + 75 / DOF   (kinematics, accelerations, virtual velocities)
   reverse sweep   978 / body + 189 / DOF + 246 / apple + 21 / tip
   apple update, springs, hang-load sweep and the solve with the step's factors:
                    21 / body + 30 / DOF + 48 / apple + 5 / ancestor entry
 
-  flops = 2 * forward + 1137 n_b + 294 n_v + 294 n_a + 5 E + 21 n_t.
+  flops = [1 x forward with checkpoints] + 1137 n_b + 294 n_v + 294 n_a + 5 E + 21 n_t.
 
 Bytes: the persistent rollout keeps a world's temporaries on chip and re-reads its model from
 L2, so the unavoidable HBM traffic per rollout is one read of the model and one read and write

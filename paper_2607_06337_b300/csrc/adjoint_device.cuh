@@ -771,10 +771,13 @@ __host__ __device__ __noinline__ void rails_adjoint(const DevModel& m, const WSt
 // the forward workspace holds that step's recomputed forward (factors, Delta, apple data), and
 // A.qb1 / qdb1 / ub1 / vb1 hold the cotangents of its end state. Leaves the cotangents of its
 // start state in A.qb / qdb / ub / vb.
+// Phases of the backward for the instrumented build (PhaseClock slots).
+enum BackPhase { kBpApples = 0, kBpSolve, kBpLsweep, kBpSeed, kBpChain, kBpRestore, kBpReplay, kBpFinal, kBpOther };
+
 template <int TPW>
 HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
                      const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
-                     const Group<TPW>& g, int t, f3 gv) {
+                     const Group<TPW>& g, int t, f3 gv, PhaseClock* pc = nullptr) {
   const float dt = a.dt;
   const int t_abs = a.step0 + t;
   for (int i = g.lane; i < v.nv; i += TPW) {
@@ -806,7 +809,9 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   hang_load_sweep<TPW>(m, s, v, L, A, ws, wa, wa + A.lam, g);  // qd'-bar += J_h^T vh-bar
   for (int i = g.lane; i < v.nv; i += TPW) wa[A.qdb + i] = wa[A.lam + i];  // qd' = qd + Delta
   g.sync();
+  if (pc) pc->mark(kBpApples);
   solve_factored<TPW>(m, v, L, ws, wa + A.lam, g, false);  // lambda = H^-1 Delta-bar, up to the L sweep
+  if (pc) pc->mark(kBpSolve);
   // root to leaf, joint by joint: the L sweep of lambda, the spring and damper terms, and the
   // tape at the step start (which needs the joint's final lambda)
   for (int l = 0; l < v.nL; ++l) {
@@ -818,6 +823,7 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
     }
     g.sync();
   }
+  if (pc) pc->mark(kBpLsweep);
   RevArgs ra;
   ra.dyn = 1;
   ra.delta = ws + L.r;
@@ -832,11 +838,13 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
     rails_adjoint<TPW>(m, s, a, v, L, A, ws, wa, g, t_abs, gv);
     g.sync();
   }
+  if (pc) pc->mark(kBpSeed);
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) reverse_chain(m, s, a, v, A, wa, ra, b);
     g.sync();
   }
+  if (pc) pc->mark(kBpChain);
 }
 
 // The seed of the backward pass: the cotangents of the final state from the last record's tips
@@ -876,11 +884,14 @@ HD void reverse_final(const DevModel& m, const WState& s, const StepArgs& a, con
 template <int TPW>
 HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
                          const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
-                         const float* snap, const float* rec, const Group<TPW>& g, int t, f3 gv) {
+                         const float* snap, const float* rec, const Group<TPW>& g, int t, f3 gv,
+                         PhaseClock* pc = nullptr) {
+  if (pc) pc->start();
   copy4<TPW>(ws + L.S, snap, A.snap, g);
   g.sync();
   step_record<TPW>(ws, L, s, wa, A, v, const_cast<float*>(rec), false, g);
-  reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv);
+  if (pc) pc->mark(kBpRestore);
+  reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv, pc);
   for (int i = g.lane; i < v.nv; i += TPW) {
     wa[A.qb1 + i] = wa[A.qb + i];
     wa[A.qdb1 + i] = wa[A.qdb + i];
@@ -899,22 +910,26 @@ HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, 
 template <int TPW>
 HD void reverse_segments(const DevModel& m, const StepArgs& a, const BackArgs& ba, const WorldView& v,
                          const WsLayout& L, const AdjLayout& A, const WState& s, float* ws, float* wa, float* cs,
-                         float* seg, long long recw, int t_end, bool seed, const Group<TPW>& g, f3 gv) {
+                         float* seg, long long recw, int t_end, bool seed, const Group<TPW>& g, f3 gv,
+                         PhaseClock* pc = nullptr) {
   float* recs = seg + (long long)a.ckpt_every * A.snap;
   const int ce = a.ckpt_every;
   const int nseg = (t_end + ce - 1) / ce;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int t0 = sg * ce, t1 = (t0 + ce < t_end) ? t0 + ce : t_end;
+    if (pc) pc->start();
     load_ckpt(a, v, s, sg, g);
     for (int t = t0; t < t1; ++t) {
       snapshot(ws, L, seg, A, t - t0, true, g);
       step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
       step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
     }
+    if (pc) pc->mark(kBpReplay);
     if (seed && sg == nseg - 1) reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
+    if (pc) pc->mark(kBpFinal);
     for (int t = t1 - 1; t >= t0; --t)
       reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, seg + (long long)(t - t0) * A.snap,
-                            recs + (long long)(t - t0) * recw, g, t, gv);
+                            recs + (long long)(t - t0) * recw, g, t, gv, pc);
   }
 }
 
@@ -944,8 +959,14 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
   }
   for (int i = g.lane; i < 3 * v.na; i += TPW) { wa[A.ub1 + i] = 0.f; wa[A.vb1 + i] = 0.f; }
   g.sync();
+  PhaseClock* pc = nullptr;
+#ifdef ORCHARD_PHASE_CLOCKS
+  PhaseClock pcl;
+  for (int i = 0; i < kPhaseSlots; ++i) pcl.acc[i] = 0;
+  if (a.phase_clk && g.lane == 0) pc = &pcl;
+#endif
   if constexpr (MODE == 0) {
-    reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T, true, g, gv);
+    reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T, true, g, gv, pc);
   } else {
     const int K = a.tape_steps, T1 = T - K;  // the tape holds steps T1 .. T - 1
     const float* tape = a.tape + (long long)(K + 1) * m.tape_off[w];
@@ -966,12 +987,23 @@ HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba,
       g.sync();
       return;
     }
+    if (pc) pc->start();
     reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
+    if (pc) pc->mark(kBpFinal);
     for (int t = T - 1; t >= T1; --t)
       reverse_recorded<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, tape + (long long)(t - T1) * A.snap,
-                            trec + (long long)(t - T1) * recw, g, t, gv);
-    if constexpr (MODE == 2) reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T1, false, g, gv);
+                            trec + (long long)(t - T1) * recw, g, t, gv, pc);
+    if constexpr (MODE == 2)
+      reverse_segments<TPW>(m, a, ba, v, L, A, s, ws, wa, cs, seg, recw, T1, false, g, gv, pc);
   }
+#ifdef ORCHARD_PHASE_CLOCKS
+#ifdef __CUDA_ARCH__
+  if (pc) {
+    for (int i = 0; i < kPhases; ++i) atomicAdd(a.phase_clk + i, (unsigned long long)pcl.acc[i]);
+    atomicAdd(a.phase_clk + kPhases, (unsigned long long)T);  // world-steps reversed
+  }
+#endif
+#endif
   for (int i = g.lane; i < v.nv; i += TPW) {
     if (ba.dq0) ba.dq0[v.d0 + i] = wa[A.qb1 + i];
     if (ba.dqd0) ba.dqd0[v.d0 + i] = wa[A.qdb1 + i];

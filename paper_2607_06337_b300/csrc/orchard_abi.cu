@@ -75,6 +75,9 @@ struct Packed {
   std::vector<int> bl_fbase;          // parallel to bl_bound: each level's start in fac_tgt
   std::vector<int> fac_off;           // [W+1] start of each world's fac_tgt block
   std::vector<int2> fac_tgt;          // per (level, c, position): {row start of the c-th ancestor - c, it}
+  std::vector<int> bl_ibase;          // parallel to bl_bound: each level's first work item (world-local)
+  std::vector<int> fit_off;           // [W+1] start of each world's work items
+  std::vector<int4> fitem;            // factorisation work items {c, first, end position, cost}
   std::vector<float4> ap0, ap1;
   std::vector<int> apple_body, tip_body, btip;
   std::vector<float4> tip_local, gravity;
@@ -117,6 +120,7 @@ ot_schedule default_schedule(long long ws_floats, int max_nb) {
     s.global_workspace = 0;
   }
   s.blocks = 0;
+  s.stage = -1;
   return s;
 }
 
@@ -172,6 +176,9 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.bl_info.assign(NB, make_int4(0, 0, -1, 0));
   P.bl_fbase.clear();
   P.fac_off.assign(W + 1, 0);
+  P.fit_off.assign(W + 1, 0);
+  P.bl_ibase.clear();
+  P.fitem.clear();
   P.tape_off.assign(W + 1, 0);
   P.apre.assign(NA, make_int2(0, 0));
   P.arange.assign(NB, make_int2(0, 0));
@@ -328,15 +335,22 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
     // depth-first preorder (children in index order), so the bodies of one level below any
     // given DOF are contiguous. Per (level l, ancestor distance c = 1..l, position p): the
     // c-th ancestor of the p-th body's first DOF, as {its row start - c, it}, level-major.
+    // The factorisation's work items of a level: for each c, the level's positions split into
+    // runs of at most 32 (one warp's chunk) at the boundaries of the groups that share their
+    // c-th ancestor (a group larger than 32 stays whole, its chunks in one item), so no two
+    // items write the same target row; each level's items sorted by their scan count
+    // (chunks x (1 + (l - c + 1) / 8)), largest first, for the warps to take in snake order.
     {
       P.bl_off[w] = (int)P.bl_bound.size();
       P.fac_off[w] = (int)P.fac_tgt.size();
+      P.fit_off[w] = (int)P.fitem.size();
       std::vector<int> first;  // first DOF of each level position
       first.reserve(nb);
-      int pos = 0, fbase = 0;
+      int pos = 0, fbase = 0, ibase = 0;
       for (int l = 0; l <= maxd; ++l) {
         P.bl_bound.push_back(pos);
         P.bl_fbase.push_back(fbase);
+        P.bl_ibase.push_back(ibase);
         const int lo = pos;
         for (int b : pre)
           if (nd[b] > 0 && ddep[dof0[b]] == l) {
@@ -347,16 +361,39 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
             ++pos;
           }
         const int count = pos - lo;
-        for (int c = 1; c <= l; ++c)
+        std::vector<int4> items;
+        std::vector<int> key(count);
+        for (int c = 1; c <= l; ++c) {
           for (int p = 0; p < count; ++p) {
             int j = first[lo + p];
             for (int s2 = 0; s2 < c; ++s2) j = dpar[j];
             P.fac_tgt.push_back(make_int2(rowstart[j] - c, j));
+            key[p] = j;
           }
+          const int scans = 1 + (l - c + 1) / 8;
+          int start = 0, seg = 0;
+          for (int p = 1; p <= count; ++p) {
+            if (p < count && key[p] == key[p - 1]) continue;  // [seg, p) is one group
+            if (p - start > 32 && seg > start) {              // close the run before this group
+              items.push_back(make_int4(c, start, seg, ((seg - start + 31) / 32) * scans));
+              start = seg;
+            }
+            if (p - start >= 32) {
+              items.push_back(make_int4(c, start, p, ((p - start + 31) / 32) * scans));
+              start = p;
+            }
+            seg = p;
+          }
+          if (start < count) items.push_back(make_int4(c, start, count, ((count - start + 31) / 32) * scans));
+        }
+        std::stable_sort(items.begin(), items.end(), [](const int4& a, const int4& b) { return a.w > b.w; });
+        P.fitem.insert(P.fitem.end(), items.begin(), items.end());
         fbase += count * l;
+        ibase += (int)items.size();
       }
       P.bl_bound.push_back(pos);
       P.bl_fbase.push_back(fbase);
+      P.bl_ibase.push_back(ibase);
     }
     for (int b = 0; b < nb; ++b) {
       const int gb = b0 + b;
@@ -390,6 +427,7 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   P.lvl_off[W] = (int)P.lvl.size();
   P.bl_off[W] = (int)P.bl_bound.size();
   P.fac_off[W] = (int)P.fac_tgt.size();
+  P.fit_off[W] = (int)P.fitem.size();
   P.NB = NB; P.NA = NA; P.NT = NT; P.NV = P.dof_off[W]; P.NM = P.m_off[W];
   if (P.NM > 0x7fffffffLL) return OT_ECAPACITY;
   // apples, tips, gravity
@@ -532,6 +570,7 @@ struct ot_model {
   float4 *w_bp0 = nullptr, *w_bp2 = nullptr, *w_bp3 = nullptr, *w_bp4 = nullptr, *w_ap0 = nullptr,
          *w_tip = nullptr;
   const float4 *dr_geo = nullptr, *dr_jpos = nullptr, *dr_com = nullptr, *dr_ap0 = nullptr, *dr_tip = nullptr;
+  unsigned long long* phase_clk = nullptr;  // instrumented builds only: the phase accumulators
   cudaStream_t capture_stream = nullptr;
   struct GraphEntry {
     std::string key;
@@ -567,7 +606,8 @@ namespace {
 // Layout of the packed model in the device buffer.
 struct ModelLayout {
   size_t body_off, dof_off, apple_off, tip_off, m_off, lvl_off, lvl, bi, bp0, bp1, bp2, bp3, bp4, bj, anc, bl_off,
-      bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, ap0, ap1, apple_body, tip_body, btip, tip_local, gravity, queue,
+      bl_bound, bl_info, bl_fbase, fac_off, fac_tgt, bl_ibase, fit_off, fitem, ap0, ap1, apple_body, tip_body, btip,
+      tip_local, gravity, queue,
       dr_geo, dr_jpos, dr_com, dr_ap0, dr_tip, tape_off, apre, arange, total;
 };
 
@@ -589,6 +629,9 @@ ModelLayout model_layout(const Packed& P) {
   L.bl_fbase = c.take<int>(P.bl_fbase.size());
   L.fac_off = c.take<int>(W1);
   L.fac_tgt = c.take<int2>(P.fac_tgt.size());
+  L.bl_ibase = c.take<int>(P.bl_ibase.size());
+  L.fit_off = c.take<int>(W1);
+  L.fitem = c.take<int4>(P.fitem.size());
   L.ap0 = c.take<float4>(P.NA); L.ap1 = c.take<float4>(P.NA);
   L.apple_body = c.take<int>(P.NA);
   L.tip_body = c.take<int>(P.NT);
@@ -691,15 +734,60 @@ struct Shape {
   size_t smem;
   int blocks;
   size_t scratch_off;
+  int stage_mask;
+  long long stage_floats;
+  int bps;
 };
+
+// Shared-memory floats the staged parts `mask` take for the class's largest world.
+long long class_stage_floats(const ot_model* m, const ClassInfo& ci, int mask) {
+  const Packed& P = m->P;
+  long long mx = 0;
+  for (int i = ci.q_begin; i < ci.q_end; ++i) {
+    const int w = P.queue[i];
+    const StageLayout S = StageLayout::make(mask, P.body_off[w + 1] - P.body_off[w], P.m_off[w + 1] - P.m_off[w],
+                                            P.apple_off[w + 1] - P.apple_off[w], P.fac_off[w + 1] - P.fac_off[w],
+                                            P.fit_off[w + 1] - P.fit_off[w]);
+    mx = std::max<long long>(mx, S.total);
+  }
+  return mx;
+}
 
 ot_status class_shape(ot_model* m, int k, Shape* out) {
   ClassInfo& ci = m->P.classes[k];
   const ot_schedule& sc = ci.sched;
-  const size_t smem = sc.global_workspace ? 0 : (size_t)ci.ws_floats * 4 * sc.worlds_per_block;
+  const size_t ws_block = sc.global_workspace ? 0 : (size_t)ci.ws_floats * 4 * sc.worlds_per_block;
   int bps = 0;
-  OT_CUDA(kernel_attributes(sc.threads_per_world, sc.worlds_per_block, std::max<size_t>(smem, 1), &bps));
+  OT_CUDA(kernel_attributes(sc.threads_per_world, false, sc.worlds_per_block, std::max<size_t>(ws_block, 1), &bps));
   if (bps < 1) return OT_ECAPACITY;
+  // staged model parts: each part, in kStageOrder, that keeps the blocks per SM of the bare
+  // workspace
+  int mask = 0;
+  long long st = 0;
+  if (!sc.global_workspace && sc.stage != 0) {
+    if (sc.stage > 0) {
+      mask = sc.stage;
+      st = class_stage_floats(m, ci, mask);
+      if (ws_block + (size_t)st * 4 * sc.worlds_per_block > kSmemLimit) return OT_ECAPACITY;
+    } else {
+      for (int part : kStageOrder) {  // each part that still fits at the same blocks per SM
+        const long long st2 = class_stage_floats(m, ci, mask | part);
+        const size_t smem2 = ws_block + (size_t)st2 * 4 * sc.worlds_per_block;
+        if (smem2 > kSmemLimit) continue;
+        int bps2 = 0;
+        OT_CUDA(kernel_attributes(sc.threads_per_world, true, sc.worlds_per_block, smem2, &bps2));
+        if (bps2 < bps) continue;
+        mask |= part;
+        st = st2;
+      }
+    }
+  }
+  const size_t smem = ws_block + (size_t)st * 4 * sc.worlds_per_block;
+  if (mask) OT_CUDA(kernel_attributes(sc.threads_per_world, true, sc.worlds_per_block, smem, &bps));
+  if (bps < 1) return OT_ECAPACITY;
+  out->stage_mask = mask;
+  out->stage_floats = st;
+  out->bps = bps;
   int slots = 0;
   out->scratch_off = class_scratch_offset(m, k, &slots);
   int blocks = sc.blocks > 0 ? sc.blocks : bps * m->n_sm;
@@ -719,8 +807,11 @@ ot_status launch_class_shaped(ot_model* m, ot_state* s, int k, StepArgs a, const
   a.q_begin = ci.q_begin;
   a.q_end = ci.q_end;
   a.q_counter = s->q_counters + k;
+  a.phase_clk = m->phase_clk && k < kBackPhaseRow ? m->phase_clk + (size_t)k * kPhaseSlots : nullptr;
   a.ws_floats = ci.ws_floats;
   a.global_ws = sc.global_workspace;
+  a.stage_mask = sh.stage_mask;
+  a.stage_floats = sh.stage_floats;
   DevState ds = s->dev;
   ds.scratch = s->dev.scratch + sh.scratch_off;
   OT_CUDA(cudaMemsetAsync(a.q_counter, 0, sizeof(int), st));
@@ -771,6 +862,33 @@ int64_t ot_launch_count(int32_t reset) {
   return g_launches.load();
 }
 
+ot_status ot_class_info(ot_model* m, int32_t k, int64_t out[8]) {
+  if (!m || !out || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  const ClassInfo& ci = m->P.classes[k];
+  Shape sh{};
+  const ot_status r = class_shape(m, k, &sh);
+  if (r != OT_OK) return r;
+  out[0] = ci.q_end - ci.q_begin;
+  out[1] = ci.max_nb;
+  out[2] = ci.ws_floats * 4;
+  out[3] = sh.stage_mask;
+  out[4] = sh.stage_floats * 4;
+  out[5] = (int64_t)sh.smem;
+  out[6] = sh.bps;
+  out[7] = sh.blocks;
+  return OT_OK;
+}
+
+ot_status ot_phase_clocks(const ot_model* m, uint64_t* out, int32_t max_classes, int32_t reset) {
+  if (!m || !out || max_classes < 1) return OT_EINVAL;
+  if (!m->phase_clk) return OT_EINVAL;  // the product build has no phase clocks
+  const int nk = std::min<int>(max_classes, kPhaseClasses);
+  OT_CUDA(cudaDeviceSynchronize());
+  OT_CUDA(cudaMemcpy(out, m->phase_clk, sizeof(uint64_t) * kPhaseSlots * nk, cudaMemcpyDeviceToHost));
+  if (reset) OT_CUDA(cudaMemset(m->phase_clk, 0, sizeof(uint64_t) * kPhaseSlots * kPhaseClasses));
+  return OT_OK;
+}
+
 ot_status ot_model_bytes(const ot_tree_desc* desc, size_t* bytes) {
   if (!bytes) return OT_EINVAL;
   Packed P;
@@ -808,6 +926,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   }
   m->flags = *flags;
   m->n_sm = num_sms();
+  m->phase_clk = phase_clock_buffer();
   std::vector<char> host(L.total, 0);
   auto put = [&](size_t off, const void* src, size_t n) {
     if (n) std::memcpy(host.data() + off, src, n);
@@ -831,6 +950,9 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   put(L.bl_fbase, P.bl_fbase.data(), vbytes(P.bl_fbase));
   put(L.fac_off, P.fac_off.data(), vbytes(P.fac_off));
   put(L.fac_tgt, P.fac_tgt.data(), vbytes(P.fac_tgt));
+  put(L.bl_ibase, P.bl_ibase.data(), vbytes(P.bl_ibase));
+  put(L.fit_off, P.fit_off.data(), vbytes(P.fit_off));
+  put(L.fitem, P.fitem.data(), vbytes(P.fitem));
   put(L.ap0, P.ap0.data(), vbytes(P.ap0)); put(L.ap1, P.ap1.data(), vbytes(P.ap1));
   put(L.apple_body, P.apple_body.data(), vbytes(P.apple_body));
   put(L.tip_body, P.tip_body.data(), vbytes(P.tip_body));
@@ -873,6 +995,9 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
   dm.bl_fbase = (const int*)(base + L.bl_fbase);
   dm.fac_off = (const int*)(base + L.fac_off);
   dm.fac_tgt = (const int2*)(base + L.fac_tgt);
+  dm.bl_ibase = (const int*)(base + L.bl_ibase);
+  dm.fit_off = (const int*)(base + L.fit_off);
+  dm.fitem = (const int4*)(base + L.fitem);
   dm.ap0 = (const float4*)(base + L.ap0); dm.ap1 = (const float4*)(base + L.ap1);
   dm.apple_body = (const int*)(base + L.apple_body);
   dm.tip_body = (const int*)(base + L.tip_body);
@@ -1073,8 +1198,8 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
   std::string sched_sig;
   for (const ClassInfo& ci : m->P.classes) {
     char b[96];
-    std::snprintf(b, sizeof(b), "/%d,%d,%d,%d", ci.sched.threads_per_world, ci.sched.worlds_per_block,
-                  ci.sched.blocks, ci.sched.global_workspace);
+    std::snprintf(b, sizeof(b), "/%d,%d,%d,%d,%d", ci.sched.threads_per_world, ci.sched.worlds_per_block,
+                  ci.sched.blocks, ci.sched.global_workspace, ci.sched.stage);
     sched_sig += b;
   }
   skey += sched_sig;
@@ -1160,7 +1285,7 @@ ot_status ot_rollout_plain(ot_model* m, ot_state* s, int32_t n_steps, int32_t st
   for (const ClassInfo& ci : P.classes)
     if ((size_t)ci.ws_floats * 4 <= kSmemLimit) smem_max = std::max(smem_max, (size_t)ci.ws_floats * 4);
   int bps = 0;
-  OT_CUDA(kernel_attributes(64, 1, smem_max, &bps));
+  OT_CUDA(kernel_attributes(64, false, 1, smem_max, &bps));
   for (int t = 0; t < n_steps; ++t) {
     a.step0 = step0 + t;
     for (int w = 0; w < P.W; ++w) {
@@ -1202,6 +1327,7 @@ ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
   if (!sc->global_workspace && (size_t)ci.ws_floats * 4 * sc->worlds_per_block > kSmemLimit) return OT_EINVAL;
   if (sc->global_workspace && (size_t)sc->worlds_per_block * std::max(sc->blocks, 1) > scratch_slots(m, ci))
     return OT_EINVAL;
+  if (sc->stage < -1 || sc->stage > 127) return OT_EINVAL;
   m->P.classes[k].sched = *sc;
   return OT_OK;
 }
@@ -1220,18 +1346,23 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
     const ot_schedule keep = ci.sched;
     std::vector<ot_schedule> cands;
     for (int t : {32, 64, 128, 256, 512})
-      for (int g : {1, 2, 3, 4, 6, 8, 12, 16}) {
-        ot_schedule c{t, g, 0, keep.global_workspace};
-        if (t * g > 512) continue;
-        if (t > 32 && g > 15) continue;
-        if (!c.global_workspace && (size_t)ci.ws_floats * 4 * g > kSmemLimit) continue;
-        if (c.global_workspace && g > 1) continue;
-        cands.push_back(c);
-      }
+      for (int g : {1, 2, 3, 4, 6, 8, 12, 16})
+        for (int stage : {0, -1}) {  // model records read from global memory, or staged
+          ot_schedule c{t, g, 0, keep.global_workspace, stage};
+          if (t * g > 512) continue;
+          if (t > 32 && g > 15) continue;
+          if (!c.global_workspace && (size_t)ci.ws_floats * 4 * g > kSmemLimit) continue;
+          if (c.global_workspace && (g > 1 || stage != 0)) continue;
+          cands.push_back(c);
+        }
     float best = 1e30f;
     ot_schedule best_s = keep;
     for (const ot_schedule& c : cands) {
       ci.sched = c;
+      if (c.stage == -1) {  // automatic staging that stages nothing repeats the stage-0 candidate
+        Shape sh{};
+        if (class_shape(m, k, &sh) != OT_OK || sh.stage_mask == 0) continue;
+      }
       float ms = 0;
       ot_status r = launch_class(m, s, k, a, st);  // warm-up and attribute set-up
       if (r != OT_OK) continue;
@@ -1403,6 +1534,9 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
     b.q_begin = ci.q_begin;
     b.q_end = ci.q_end;
     b.q_counter = s->q_counters + k;
+    // instrumented builds: the backward's phase clocks of class k sit in row kBackPhaseRow + k
+    b.phase_clk = m->phase_clk && k < kPhaseClasses - kBackPhaseRow
+                      ? m->phase_clk + (size_t)(kBackPhaseRow + k) * kPhaseSlots : nullptr;
     if (e == cudaSuccess) e = cudaMemsetAsync(b.q_counter, 0, sizeof(int), sk);
     if (e == cudaSuccess && p.blocks > 0) {
       launch_backward(p.tpw, p.gpb, p.blocks, sk, m->dev, b, ba, works[k], p.sh);
@@ -1426,43 +1560,57 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
 // ------------------------------------------------------------------------------------------
 namespace orchard {
 
-ot_status static_step_plan(const ot_model* m, int* n_classes, size_t* max_ws_floats) {
-  if (!m || !n_classes || !max_ws_floats) return OT_EINVAL;
-  *n_classes = (int)m->P.classes.size();
-  *max_ws_floats = 0;
-  for (const ClassInfo& ci : m->P.classes) *max_ws_floats = std::max(*max_ws_floats, (size_t)ci.ws_floats);
+ot_status static_step_plan(ot_model* m, const ot_state* s, const ot_force_schedule* pulls, size_t scratch_floats,
+                           int max_classes, int* n_classes, StaticShape* shapes) {
+  if (!m || !s || s->model != m || !n_classes || !shapes) return OT_EINVAL;
+  StepArgs probe{};
+  if (fill_pulls(probe, pulls) != OT_OK) return OT_EINVAL;
+  const int nk = (int)m->P.classes.size();
+  if (nk > max_classes) return OT_ECAPACITY;
+  for (int k = 0; k < nk; ++k) {
+    const ClassInfo& ci = m->P.classes[k];
+    if ((size_t)ci.ws_floats > scratch_floats) return OT_ECAPACITY;  // one world does not fit
+  }
+  for (int k = 0; k < nk; ++k) {
+    const ClassInfo& ci = m->P.classes[k];
+    const ot_schedule& sc = ci.sched;
+    // every group needs a slot of its own: a block never holds more groups than the array
+    // has slots (the class's own schedule may ask for more worlds per block)
+    const long long slots = (long long)(scratch_floats / (size_t)ci.ws_floats);
+    const int wpb = (int)std::min<long long>(sc.worlds_per_block, slots);
+    int bps = 0;
+    OT_CUDA(kernel_attributes(sc.threads_per_world, false, wpb, 1, &bps));
+    if (bps < 1) return OT_ECAPACITY;
+    const int worlds = ci.q_end - ci.q_begin;
+    long long blocks = std::min<long long>((long long)bps * m->n_sm, (worlds + wpb - 1) / wpb);
+    blocks = std::min<long long>(blocks, slots / wpb);
+    if (blocks < 1 && worlds > 0) return OT_ECAPACITY;
+    shapes[k].worlds_per_block = wpb;
+    shapes[k].blocks = (int)blocks;
+  }
+  *n_classes = nk;
   return OT_OK;
 }
 
-ot_status static_step_class(ot_model* m, ot_state* s, int k, const float* ext_force, const ot_force_schedule* pulls,
-                            int32_t step, double dt, float* scratch, size_t scratch_floats, int* counter,
+ot_status static_step_class(ot_model* m, ot_state* s, int k, const StaticShape& sh, const float* ext_force,
+                            const ot_force_schedule* pulls, int32_t step, double dt, float* scratch, int* counter,
                             void* stream) {
-  if (!m || !s || s->model != m || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
   const ClassInfo& ci = m->P.classes[k];
-  const ot_schedule& sc = ci.sched;
-  if ((size_t)ci.ws_floats > scratch_floats) return OT_ECAPACITY;  // one world does not fit
-  const long long slots = (long long)(scratch_floats / (size_t)ci.ws_floats);
+  if (sh.blocks < 1) return OT_OK;
   StepArgs a = base_args(m, dt);
   a.step0 = step;
   a.n_steps = 1;
   a.ext_force = ext_force;
-  ot_status st = fill_pulls(a, pulls);
-  if (st != OT_OK) return st;
+  fill_pulls(a, pulls);  // validated by the plan
   a.q_begin = ci.q_begin;
   a.q_end = ci.q_end;
   a.q_counter = counter;
   a.ws_floats = ci.ws_floats;
   a.global_ws = 1;
-  int bps = 0;
-  OT_CUDA(kernel_attributes(sc.threads_per_world, sc.worlds_per_block, 1, &bps));
-  if (bps < 1) return OT_ECAPACITY;
-  const int worlds = ci.q_end - ci.q_begin;
-  long long blocks = std::min<long long>((long long)bps * m->n_sm, (worlds + sc.worlds_per_block - 1) / sc.worlds_per_block);
-  blocks = std::min<long long>(blocks, slots / sc.worlds_per_block);
-  if (blocks < 1) return OT_ECAPACITY;
   DevState ds = s->dev;
   ds.scratch = scratch;
-  launch_rollout(sc.threads_per_world, sc.worlds_per_block, (int)blocks, 0, (cudaStream_t)stream, m->dev, ds, a);
+  launch_rollout(ci.sched.threads_per_world, sh.worlds_per_block, sh.blocks, 0, (cudaStream_t)stream, m->dev, ds,
+                 a);
   OT_CUDA(cudaGetLastError());
   g_launches += 1;
   return OT_OK;

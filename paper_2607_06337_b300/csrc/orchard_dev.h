@@ -44,6 +44,12 @@ struct DevModel {
                          // entry (c - 1) * count_l + p = {row start of the c-th ancestor of the
                          // p-th body's first DOF minus c (the factorisation's target base), that
                          // ancestor}
+  const int* bl_ibase;   // parallel to bl_bound: each level's first factorisation work item
+  const int* fit_off;    // [W+1] start of the world's work items in fitem
+  const int4* fitem;     // per level, its work items {c, first position, end position, scan
+                         // count}: the positions [first, end) of ancestor distance c, cut only
+                         // between groups of positions that share their c-th ancestor, largest
+                         // first
   const float4* ap0;     // hang point in the body frame (xyz), apple mass (w)
   const float4* ap1;     // k_s, c_s, f_detach, -
   const int* apple_body; // world-local body of each apple
@@ -111,12 +117,81 @@ struct StepArgs {
   int single_world;         // >= 0: the plain form, this world only
   long long ws_floats;      // workspace floats per group
   int global_ws;            // 1: workspace in DevState::scratch, slot = global group index
+  unsigned long long* phase_clk;  // instrumented builds only (ORCHARD_PHASE_CLOCKS): this
+                                  // launch's kPhaseSlots accumulators, or null
+  int stage_mask;           // StageLayout parts copied into shared memory per world (0: none)
+  long long stage_floats;   // shared-memory floats per group for them (the class's largest world)
 };
+
+// Parts of a world's model that a rollout can stage in shared memory (after the workspace),
+// copied once when a group takes the world and read from there for all its steps.
+enum StagePart {
+  kStageKin = 1,     // bi, bp0, bp1: kinematics sweep (and the topology of every pass)
+  kStageBias = 2,    // bp3: bias sweep (stiffness, damping)
+  kStageUpd = 4,     // bj, bp4: update sweep, mass matrix (joint rows, armature, rupture moment)
+  kStageAnc = 8,     // anc: ancestor ids of the mass-matrix rows (L sweep, mass matrix)
+  kStageInfo = 16,   // bl_info, fitem: factorisation level records and work items
+  kStageFac = 32,    // fac_tgt: factorisation targets
+  kStageForce = 64,  // bp2, ap0, ap1, apple_body: forces and apples
+};
+// The order in which the automatic choice takes the parts, each one that still fits (measured
+// on B300: the ancestor walks of the L sweep and the mass matrix gain most, the factorisation's
+// tables least, since its loads are issued one step ahead).
+constexpr int kStageOrder[7] = {kStageKin, kStageAnc, kStageUpd, kStageBias, kStageForce, kStageInfo, kStageFac};
+
+// Float offsets of the staged parts of one world (each on a 16-byte boundary); -1: not staged.
+struct StageLayout {
+  int bi, bp0, bp1, bp3, bj, bp4, anc, info, items, fac, bp2, ap0, ap1, abody, total;
+  __host__ __device__ static int r4(int n) { return (n + 3) & ~3; }
+  __host__ __device__ static StageLayout make(int mask, int nb, int nm, int na, int nfac, int nitem) {
+    StageLayout S;
+    int o = 0;
+    auto take = [&](int part, int floats) {
+      if (!(mask & part)) return -1;
+      const int at = o;
+      o += r4(floats);
+      return at;
+    };
+    S.bi = take(kStageKin, 4 * nb);
+    S.bp0 = take(kStageKin, 4 * nb);
+    S.bp1 = take(kStageKin, 4 * nb);
+    S.bp3 = take(kStageBias, 4 * nb);
+    S.bj = take(kStageUpd, 4 * nb);
+    S.bp4 = take(kStageUpd, 4 * nb);
+    S.anc = take(kStageAnc, nm);
+    S.info = take(kStageInfo, 4 * nb);
+    S.items = take(kStageInfo, 4 * nitem);
+    S.fac = take(kStageFac, 2 * nfac);
+    S.bp2 = take(kStageForce, 4 * nb);
+    S.ap0 = take(kStageForce, 4 * na);
+    S.ap1 = take(kStageForce, 4 * na);
+    S.abody = take(kStageForce, na);
+    S.total = o;
+    return S;
+  }
+};
+
+// Phase clocks of the instrumented build (ORCHARD_PHASE_CLOCKS): per size class, SM cycles
+// summed over every world-step of each phase of the step, then the world-step count.
+// Phases: forward kinematics sweep, forces and apple loads, tip record, bias and composite
+// inertia sweep, mass-matrix rows, LDL^T with the L^T sweep, L sweep and update sweep, apple
+// update and detach tests, and the rest of the rollout (state staging, checkpoints, tape).
+constexpr int kPhases = 9;
+constexpr int kPhaseSlots = kPhases + 1;
+constexpr int kPhaseClasses = 64;
+constexpr int kBackPhaseRow = 32;  // rows kBackPhaseRow + k: the backward of class k
+// Device address of the accumulators ([kPhaseClasses][kPhaseSlots]), null in the product build.
+unsigned long long* phase_clock_buffer();
 
 // Workspace layout of one world (floats), a function of its sizes only. Rotations, bias
 // accelerations and forces (live in the two sweeps) share space with the mass-matrix rows
-// (live from the mass matrix to the end of the step). S holds the world's state for the whole
-// rollout (see staged_view): the step reads and writes it there, not in global memory.
+// (live from the mass matrix to the end of the step). Each body's velocity (w, v: live from the
+// kinematics sweep to the force pass, and from the update sweep to the next step's kinematics)
+// shares its 10-float slot with its spatial, then composite, inertia (live from the force pass
+// to the mass matrix): the force pass reads a body's velocity before it writes the body's
+// inertia, and no pass reads another body's velocity there. S holds the world's state for the
+// whole rollout (see staged_view): the step reads and writes it there, not in global memory.
+constexpr int kVel = 10;  // float stride of the body velocities (the inertia slots)
 struct WsLayout {
   int X, E, IC, r, AT, V, SN, S, R, A, F, M, total;
   // every region starts on a 16-byte boundary, so whole regions move as float4
@@ -144,8 +219,9 @@ struct WsLayout {
     L.r = L.IC + r4(10 * nb);        // right-hand side, then the solution
     L.AT = L.r + r4(nv);             // per apple: velocity with the hang point frozen, beta,
                                      // tension, pull, hang offset r_h (10 floats)
-    L.V = L.AT + r4(10 * na);        // body velocities (start of step, then end of step)
-    L.SN = L.V + r4(6 * nb);         // 1 on a snapped sub-tree
+    L.V = L.IC;                      // body velocities (start of step, then end of step), in
+                                     // the first 6 floats of each inertia slot (kVel)
+    L.SN = L.AT + r4(10 * na);       // 1 on a snapped sub-tree
     L.S = L.SN + r4(nb);             // the staged state
     const int u = L.S + r4(state_words(nb, nv, na));  // shared region
     L.R = u;
@@ -169,10 +245,19 @@ struct ot_force_schedule;
 
 namespace orchard {
 
-// One step of size class k with its workspace in `scratch` (used by the static-scratch entry).
-int static_step_plan(const ot_model* m, int* n_classes, size_t* max_ws_floats);
-int static_step_class(ot_model* m, ot_state* s, int k, const float* ext_force, const ot_force_schedule* pulls,
-                      int step, double dt, float* scratch, size_t scratch_floats, int* counter, void* stream);
+// The static-scratch entry's one-step launches, the workspace in a caller-held area of
+// scratch_floats floats. static_step_plan validates everything a launch could reject (the
+// state's model, the pull schedule, a world too large for the area, the kernel attributes) and
+// fills every class's shape before anything is queued; static_step_class then launches class
+// k with its shape.
+struct StaticShape {
+  int worlds_per_block;  // the class's schedule, capped at the area's slot count
+  int blocks;
+};
+int static_step_plan(ot_model* m, const ot_state* s, const ot_force_schedule* pulls, size_t scratch_floats,
+                     int max_classes, int* n_classes, StaticShape* shapes);
+int static_step_class(ot_model* m, ot_state* s, int k, const StaticShape& sh, const float* ext_force,
+                      const ot_force_schedule* pulls, int step, double dt, float* scratch, int* counter, void* stream);
 
 // Outputs and inputs of a backward pass beyond the forward's StepArgs.
 struct BackArgs {
@@ -207,6 +292,7 @@ long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);
-cudaError_t kernel_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
+// Occupancy of the rollout kernel for tpw threads per world, the staged instantiation or not.
+cudaError_t kernel_attributes(int tpw, bool staged, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 
 }  // namespace orchard

@@ -14,9 +14,11 @@
 // array and are cleared on every call; the rest is fully written before it is read.
 //
 // Limits: OT_STATIC_SCRATCH_BYTES in total (every GPU that loads the library holds it until
-// the process exits). A world whose temporaries do not fit in it is rejected with
-// OT_ECAPACITY before anything runs. All calls share the array, so calls that overlap on the
-// GPU (on different streams, or from different threads) race with each other: serialise them.
+// the process exits). A world whose temporaries do not fit in it, or any other argument a
+// launch would reject, is reported before anything is queued (OT_ECAPACITY, OT_EINVAL). A
+// block holds at most as many worlds as the array has slots, whatever the class's schedule.
+// All calls share the array, so calls that overlap on the GPU (on different streams, or from
+// different threads) race with each other: serialise them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,20 +60,20 @@ cudaError_t scratch_address(float** out) {
 extern "C" ot_status ot_step_static_scratch(ot_model* model, ot_state* state, const float* ext_force,
                                             const ot_force_schedule* pulls, int32_t step, double dt, void* stream) {
   if (!model || !state || !(dt > 0)) return OT_EINVAL;
+  // validate and shape every class before queuing anything: a rejection leaves no work behind
   int n_classes = 0;
-  size_t max_ws = 0;
-  ot_status st = orchard::static_step_plan(model, &n_classes, &max_ws);
+  orchard::StaticShape shapes[kCounterFloats];
+  ot_status st = orchard::static_step_plan(model, state, pulls, kFloats - kCounterFloats, (int)kCounterFloats,
+                                           &n_classes, shapes);
   if (st != OT_OK) return st;
-  // reject before queuing anything: every world's temporaries must fit in the array
-  if (n_classes > (int)kCounterFloats || max_ws > kFloats - kCounterFloats) return OT_ECAPACITY;
   float* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return OT_ECUDA;
   int* counters = (int*)base;
   if (cudaMemsetAsync(counters, 0, kCounterFloats * sizeof(float), (cudaStream_t)stream) != cudaSuccess)
     return OT_ECUDA;
   for (int k = 0; k < n_classes; ++k) {
-    st = orchard::static_step_class(model, state, k, ext_force, pulls, step, dt, base + kCounterFloats,
-                                   kFloats - kCounterFloats, counters + k, stream);
+    st = orchard::static_step_class(model, state, k, shapes[k], ext_force, pulls, step, dt, base + kCounterFloats,
+                                    counters + k, stream);
     if (st != OT_OK) return st;
   }
   return OT_OK;

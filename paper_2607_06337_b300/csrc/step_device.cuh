@@ -167,9 +167,19 @@ struct Group {
 };
 
 struct WorldView {
-  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, BL0, nBL, f0;
-  // body-level bounds (nL + 1), factorisation-level bounds and fac_tgt bases (nBL + 1 each)
-  const int *lv, *bb, *bf;
+  int b0, nb, d0, nv, a0, na, t0, nt, m0, nm, L0, nL, BL0, nBL, f0, nfac, it0, nitem;
+  // body-level bounds (nL + 1), factorisation-level bounds, fac_tgt bases and first work
+  // items (nBL + 1 each)
+  const int *lv, *bb, *bf, *ib;
+  // the world's model records, indexed world-locally, for the staged instantiation of the
+  // step (ST): the model in global memory, or the copies stage_world makes in shared memory.
+  // The other instantiation reads the model directly (rec_* below), so these stay unused
+  const int4 *bi, *bj, *info;
+  const float4 *bp0, *bp1, *bp2, *bp3, *bp4, *ap0, *ap1;
+  const unsigned* anc;
+  const int2* fac;
+  const int4* items;
+  const int* abody;
 };
 
 // One world's state arrays, indexed world-locally.
@@ -216,11 +226,44 @@ HD WorldView world_view(const DevModel& m, int w) {
   v.L0 = m.lvl_off[w]; v.nL = m.lvl_off[w + 1] - v.L0 - 1;
   v.BL0 = m.bl_off[w]; v.nBL = m.bl_off[w + 1] - v.BL0 - 1;
   v.f0 = m.fac_off[w];
+  v.nfac = m.fac_off[w + 1] - v.f0;
+  v.it0 = m.fit_off[w];
+  v.nitem = m.fit_off[w + 1] - v.it0;
   v.lv = m.lvl + v.L0;
   v.bb = m.bl_bound + v.BL0;
   v.bf = m.bl_fbase + v.BL0;
+  v.ib = m.bl_ibase + v.BL0;
+  v.bi = m.bi + v.b0; v.bj = m.bj + v.b0; v.info = m.bl_info + v.b0;
+  v.bp0 = m.bp0 + v.b0; v.bp1 = m.bp1 + v.b0; v.bp2 = m.bp2 + v.b0; v.bp3 = m.bp3 + v.b0; v.bp4 = m.bp4 + v.b0;
+  v.ap0 = m.ap0 + v.a0; v.ap1 = m.ap1 + v.a0; v.abody = m.apple_body + v.a0;
+  v.anc = m.anc + v.m0;
+  v.fac = m.fac_tgt + v.f0;
+  v.items = m.fitem + v.it0;
   return v;
 }
+
+// A world's model records, world-locally indexed: from the staged view (ST), else straight from
+// the model (whose pointers are kernel parameters, so they cost no registers).
+template <bool ST> HD int4 rec_bi(const DevModel& m, const WorldView& v, int b) { return ST ? v.bi[b] : m.bi[v.b0 + b]; }
+template <bool ST> HD int4 rec_bj(const DevModel& m, const WorldView& v, int b) { return ST ? v.bj[b] : m.bj[v.b0 + b]; }
+template <bool ST> HD float4 rec_p0(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp0[b] : m.bp0[v.b0 + b]; }
+template <bool ST> HD float4 rec_p1(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp1[b] : m.bp1[v.b0 + b]; }
+template <bool ST> HD float4 rec_p2(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp2[b] : m.bp2[v.b0 + b]; }
+template <bool ST> HD float4 rec_p3(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp3[b] : m.bp3[v.b0 + b]; }
+template <bool ST> HD float4 rec_p4(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp4[b] : m.bp4[v.b0 + b]; }
+template <bool ST> HD float4 rec_a0(const DevModel& m, const WorldView& v, int a) { return ST ? v.ap0[a] : m.ap0[v.a0 + a]; }
+template <bool ST> HD float4 rec_a1(const DevModel& m, const WorldView& v, int a) { return ST ? v.ap1[a] : m.ap1[v.a0 + a]; }
+template <bool ST> HD int rec_abody(const DevModel& m, const WorldView& v, int a) {
+  return ST ? v.abody[a] : m.apple_body[v.a0 + a];
+}
+template <bool ST> HD int4 rec_info(const DevModel& m, const WorldView& v, int i) {
+  return ST ? v.info[i] : m.bl_info[v.b0 + i];
+}
+template <bool ST> HD int4 rec_item(const DevModel& m, const WorldView& v, int i) {
+  return ST ? v.items[i] : m.fitem[v.it0 + i];
+}
+template <bool ST> HD const unsigned* rec_anc(const DevModel& m, const WorldView& v) { return ST ? v.anc : m.anc + v.m0; }
+template <bool ST> HD const int2* rec_fac(const DevModel& m, const WorldView& v) { return ST ? v.fac : m.fac_tgt + v.f0; }
 
 HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
   f3 f = mk(0.f, 0.f, 0.f);
@@ -319,17 +362,24 @@ struct KinRec {
   int4 bi;
   float4 P0, P1;
 };
-HD KinRec kin_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bp0[gb], m.bp1[gb]}; }
+template <bool ST>
+HD KinRec kin_rec(const DevModel& m, const WorldView& v, int b) {
+  return {rec_bi<ST>(m, v, b), rec_p0<ST>(m, v, b), rec_p1<ST>(m, v, b)};
+}
 struct BwdRec {
   int4 bi;
   float4 P3;
 };
-HD BwdRec bwd_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bp3[gb]}; }
+template <bool ST>
+HD BwdRec bwd_rec(const DevModel& m, const WorldView& v, int b) { return {rec_bi<ST>(m, v, b), rec_p3<ST>(m, v, b)}; }
 struct UpdRec {
   int4 bi, bj;
   float4 P3, P4;
 };
-HD UpdRec upd_rec(const DevModel& m, int gb) { return {m.bi[gb], m.bj[gb], m.bp3[gb], m.bp4[gb]}; }
+template <bool ST>
+HD UpdRec upd_rec(const DevModel& m, const WorldView& v, int b) {
+  return {rec_bi<ST>(m, v, b), rec_bj<ST>(m, v, b), rec_p3<ST>(m, v, b), rec_p4<ST>(m, v, b)};
+}
 // Phase 1a for one body (root to leaf, level by level): kinematics, velocities, bias
 // acceleration, snapped flag.
 HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, const KinRec& rec) {
@@ -342,7 +392,7 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
   if (p >= 0) {
     Rp = ldm(ws + L.R + 9 * p);
     xp = ld3(ws + L.X + 3 * p);
-    wp = ld3(ws + L.V + 6 * p); vp = ld3(ws + L.V + 6 * p + 3);
+    wp = ld3(ws + L.V + kVel * p); vp = ld3(ws + L.V + kVel * p + 3);
     alp = ld3(ws + L.A + 6 * p); ap = ld3(ws + L.A + 6 * p + 3);
   } else {
     Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
@@ -377,20 +427,20 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
   // on a snapped sub-tree (this joint or one above broken): applied forces disabled (App. B)
   const bool snapped = s.broken[b] || (p >= 0 && ws[L.SN + p] != 0.f);
   ws[L.SN + b] = snapped ? 1.f : 0.f;
-  st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vin);
+  st3(ws + L.V + kVel * b, w); st3(ws + L.V + kVel * b + 3, vin);
   st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
 }
 
 // Phase 1b for one body (all bodies at once, after 1a): spatial inertia, own Newton-Euler
 // force less the body damping, apple loads.
+template <bool ST = false>
 HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                       float* ws, int b, int t_abs, f3 g) {
-  const int gb = v.b0 + b;
-  const int4 bi = m.bi[gb];
-  const float4 P0 = m.bp0[gb], P2 = m.bp2[gb], P3 = m.bp3[gb];
+  const int4 bi = rec_bi<ST>(m, v, b);
+  const float4 P0 = rec_p0<ST>(m, v, b), P2 = rec_p2<ST>(m, v, b), P3 = rec_p3<ST>(m, v, b);
   const m3 R = ldm(ws + L.R + 9 * b);
   const f3 xb = ld3(ws + L.X + 3 * b);
-  const f3 w = ld3(ws + L.V + 6 * b), vin = ld3(ws + L.V + 6 * b + 3);
+  const f3 w = ld3(ws + L.V + kVel * b), vin = ld3(ws + L.V + kVel * b + 3);
   const f3 al = ld3(ws + L.A + 6 * b), aa = ld3(ws + L.A + 6 * b + 3);
   const bool snapped = ws[L.SN + b] != 0.f;
 
@@ -431,7 +481,7 @@ HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, con
   const float dt = a.dt;
   for (int k = 0; k < acount; ++k) {
     const int ai = afirst + k, ga = v.a0 + ai;
-    const float4 A0 = m.ap0[ga], A1 = m.ap1[ga];
+    const float4 A0 = rec_a0<ST>(m, v, ai), A1 = rec_a1<ST>(m, v, ai);
     const float ma = A0.w, ks = A1.x, csd = A1.y, fdet = A1.z;
     const f3 rh = mul(R, xyz(A0));
     const f3 xh = xb + rh;
@@ -564,13 +614,14 @@ HD void pivot_scale(const float* M, int4 info, float* y) {
 
 // L sweep of one joint (first DOF dof0, joint record bj as in DevModel::bj): x = z - P^-1 U
 // x_ancestors, in place in y (which holds z for this joint and the final x of every ancestor).
+template <bool ST = false>
 HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, const float* ws, float* y, int dof0,
                      int4 bj) {
   const int nd = bj.w & 3;
   if (nd == 0) return;
   const float* M = ws + L.M;
   const float* rowx = M + bj.x;
-  const unsigned* an = m.anc + v.m0 + bj.x;
+  const unsigned* an = rec_anc<ST>(m, v) + bj.x;
   float sx = 0.f, sy = 0.f;
   if (nd == 2) {
     const float* rowy = M + bj.y + 1;  // rowy[c]: the y' row's entry of the x row's c-th ancestor
@@ -592,6 +643,7 @@ HD void lsweep_joint(const DevModel& m, const WorldView& v, const WsLayout& L, c
 
 // Phase 5a for one body (root to leaf, level by level): finish the solve, update, velocities,
 // rupture test.
+template <bool ST = false>
 HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                     float* ws, int b, int t_abs, int* frozen, const UpdRec& rec) {
   const int4 bi = rec.bi;
@@ -601,7 +653,7 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const
   const f3 xb = ld3(ws + L.X + 3 * b);
   f3 w, vl;
   if (p >= 0) {
-    const f3 wp = ld3(ws + L.V + 6 * p), vp = ld3(ws + L.V + 6 * p + 3);
+    const f3 wp = ld3(ws + L.V + kVel * p), vp = ld3(ws + L.V + kVel * p + 3);
     w = wp;
     vl = vp + cross(wp, xb - ld3(ws + L.X + 3 * p));
   } else {
@@ -609,7 +661,7 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const
   }
   bool bad = false;
   float th2 = 0.f;
-  lsweep_joint(m, v, L, ws, ws + L.r, dof0, rec.bj);
+  lsweep_joint<ST>(m, v, L, ws, ws + L.r, dof0, rec.bj);
   for (int j = 0; j < nd; ++j) {
     const int i = dof0 + j;
     const float x = ws[L.r + i];
@@ -621,7 +673,7 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const
     th2 = fmaf(q, q, th2);
     w = w + qd * ld3(ws + L.E + 3 * i);
   }
-  st3(ws + L.V + 6 * b, w); st3(ws + L.V + 6 * b + 3, vl);
+  st3(ws + L.V + kVel * b, w); st3(ws + L.V + kVel * b + 3, vl);
 
   if (nd && !s.broken[b]) {
     const float mom = rec.P3.z * sqrtf(th2);
@@ -640,11 +692,11 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const
 
 // Phase 5b for one apple (all apples at once, after the level passes of 5a): the apple update
 // with its body's end-of-step velocity, and the detach tests.
+template <bool ST = false>
 HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                      float* ws, int ai, int t_abs, int* frozen) {
-  const int ga = v.a0 + ai;
-  const int b = m.apple_body[ga];
-  const f3 w = ld3(ws + L.V + 6 * b), vl = ld3(ws + L.V + 6 * b + 3);
+  const int b = rec_abody<ST>(m, v, ai);
+  const f3 w = ld3(ws + L.V + kVel * b), vl = ld3(ws + L.V + kVel * b + 3);
   const float dt = a.dt;
   const float* at = ws + L.AT + 10 * ai;
   const bool det = s.detached[ai] != 0;
@@ -656,7 +708,7 @@ HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, cons
   st3(s.av + 3 * ai, vn);
   st3(s.ax + 3 * ai, xn);
   if (!det) {
-    const float fdet = m.ap1[ga].z;
+    const float fdet = rec_a1<ST>(m, v, ai).z;
     const int cp = at[5] > fdet ? s.pcnt[ai] + 1 : 0;
     const int ct = at[4] > a.gamma * fdet ? s.tcnt[ai] + 1 : 0;
     s.pcnt[ai] = cp;
@@ -677,6 +729,7 @@ HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, cons
 // implicit diagonal (armature, dt kd', dt^2 k'). The y' row of a two-DOF joint has the x DOF
 // (same body, no lever) as its first ancestor and then the x row's, so both rows share one
 // walk up the ancestors.
+template <bool ST = false>
 HD void crba_body(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                   float* ws, int b, int t_abs, const UpdRec& rec) {
   const int dof0 = rec.bi.y & 0x0fffffff, nd = (unsigned)rec.bi.y >> 28;
@@ -690,7 +743,7 @@ HD void crba_body(const DevModel& m, const WState& s, const StepArgs& a, const W
   const f3 ex = ld3(ws + L.E + 3 * dof0);
   const f3 nx = mul(I.I, ex), fx = cross(ex, I.h);
   float* rx = ws + L.M + rec.bj.x;
-  const unsigned* an = m.anc + v.m0 + rec.bj.x;
+  const unsigned* an = rec_anc<ST>(m, v) + rec.bj.x;
   rx[0] = dot(ex, nx) + diag;
   if (nd == 2) {
     const f3 ey = ld3(ws + L.E + 3 * (dof0 + 1));
@@ -750,14 +803,13 @@ HD void write_ckpt(const WState& s, const StepArgs& a, const WorldView& v, int s
 }
 
 // Forward kinematics only (positions), for the tip record after the last step.
-template <int TPW>
+template <int TPW, bool ST = false>
 HD void fk_only(const DevModel& m, const WState& s, const WorldView& v, const WsLayout& L, float* ws,
                         const Group<TPW>& g) {
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
-      const int gb = v.b0 + b;
-      const int4 bi = m.bi[gb];
+      const int4 bi = rec_bi<ST>(m, v, b);
       const int p = bi.x;
       const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
       m3 Rp;
@@ -769,8 +821,8 @@ HD void fk_only(const DevModel& m, const WState& s, const WorldView& v, const Ws
         Rp = {mk(1, 0, 0), mk(0, 1, 0), mk(0, 0, 1)};
         xp = mk(0, 0, 0);
       }
-      m3 R = mul(Rp, quat_mat(m.bp1[gb]));
-      const f3 xb = xp + mul(Rp, xyz(m.bp0[gb]));
+      m3 R = mul(Rp, quat_mat(rec_p1<ST>(m, v, b)));
+      const f3 xb = xp + mul(Rp, xyz(rec_p0<ST>(m, v, b)));
       for (int j = 0; j < nd; ++j) {
         float sn, cs;
         sin_cos(s.q[dof0 + j], &sn, &cs);
@@ -856,10 +908,13 @@ __device__ __forceinline__ void seg_scan4(float& a, float& b, float& c, float& d
 // for 1 <= c <= c2 <= l, with anc_c the c-th ancestor of k's first DOF and (a_c, b_c) =
 // (U_k,x[c], U_k,y[c]) P_k^-1. Listed in depth-first order, the joints of one level that share
 // their c-th ancestor are contiguous, so each target's contributions are a segmented sum over
-// consecutive lanes: shuffle scans, deterministic, no atomics. The c values are split over the
-// group's warps (different c means different target rows). z = P^-1 r is stored once the level
-// is done.
-template <int TPW>
+// consecutive lanes: shuffle scans, deterministic, no atomics. Different c means different
+// target rows. A 16-warp group works through the level's list of items (c, a run of positions)
+// built at upload: a run is cut only between groups that share their c-th ancestor, so no two
+// items write the same target, and the warps take the items largest first, in snake order.
+// Smaller groups split the c values over their warps, each warp walking all the level's chunks.
+// z = P^-1 r is stored once the level is done.
+template <int TPW, bool ST = false>
 HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, float* ws, const Group<TPW>& g) {
   float* M = ws + L.M;
   float* r = ws + L.r;
@@ -869,14 +924,119 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
   for (int l = v.nBL - 1; l >= 0; --l) {
     const int lo = v.bb[l], hi = v.bb[l + 1];
     if (lo == hi) continue;  // no joint has its first DOF at this depth (uniform for the group)
-    if (l > 0) {
+    // Groups of 16 warps take the level's work items (balanced over the warps); smaller groups
+    // keep the ancestor distances c split over the warps, each warp walking the level's chunks
+    // with its pivots computed once per chunk (measured faster with 4 and 8 warps).
+    if (TPW >= 512 && l > 0) {
       const int count = hi - lo;
-      const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
+      const int2* ft = rec_fac<ST>(m, v) + v.bf[l];
+      // the level's work items (largest first) dealt to the warps in snake order (round r
+      // gives warp w item r NW + w, or r NW + NW - 1 - w when r is odd); each step is one chunk
+      // of (up to) 32 positions of an item, and the next step's records are loaded before this
+      // one runs
+      const int i0 = v.ib[l], i1 = v.ib[l + 1];
+      int round = 0;
+      int it = i0 + warp;
+      int4 item = it < i1 ? rec_item<ST>(m, v, it) : make_int4(1, 0, 0, 0);
+      int base = lo + item.y;
+      int4 info_n = make_int4(0, 0, 0, 0);
+      int2 tk_n = make_int2(0, -1 - lane);
+      if (it < i1 && base + lane < lo + item.z) {
+        info_n = rec_info<ST>(m, v, base + lane);
+        tk_n = ft[(item.x - 1) * count + base + lane - lo];
+      }
+      while (it < i1) {  // warp-uniform
+        const int c = item.x, end = lo + item.z, idx = base + lane;
+        const bool valid = idx < end;
+        const int4 info = info_n;
+        const int2 tk = tk_n;
+        // the next step: the item's next chunk, or the warp's next item
+        base += 32;
+        if (base >= end) {
+          ++round;
+          it = i0 + round * NW + ((round & 1) ? NW - 1 - warp : warp);
+          if (it < i1) {
+            item = rec_item<ST>(m, v, it);
+            base = lo + item.y;
+          }
+        }
+        info_n = make_int4(0, 0, 0, 0);
+        tk_n = make_int2(0, -1 - lane);
+        if (it < i1 && base + lane < lo + item.z) {
+          info_n = rec_info<ST>(m, v, base + lane);
+          tk_n = ft[(item.x - 1) * count + base + lane - lo];
+        }
+        Pivot P{0.f, 0.f, 0.f};
+        float rx = 0.f, ry = 0.f;
+        if (valid) {
+          P = pivot_of(M, info.y, info.z, info.w);
+          rx = r[info.x];
+          if ((info.w & 3) == 2) ry = r[info.x + 1];
+        }
+        const bool two = (info.w & 3) == 2;
+        const float* rowx = M + info.y;
+        const float* rowy = M + (two ? info.z + 1 : info.y);  // rowy[c]: entry of anc_c in the y' row
+        const int key = tk.y;
+        const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const int next = __shfl_down_sync(0xffffffffu, key, 1);
+        const bool head = lane == 0 || prev != key;
+        const bool tail = lane == 31 || next != key;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int first = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const int span = __reduce_max_sync(0xffffffffu, (unsigned)(lane - first + 1));
+        const float ux = valid ? rowx[c] : 0.f, uy = two ? rowy[c] : 0.f;
+        const float ac = ux * P.p00 + uy * P.p01, bc = ux * P.p01 + uy * P.p11;
+        float* tgt = M + tk.x;  // entry (anc_c, c2 - c) is tgt[c2]
+        int c2 = c;
+        for (; c2 + 8 <= l + 1; c2 += 8) {
+          float sv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) sv[j] = valid ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
+          seg_scan8(sv, lane, first, span);
+          if (valid && tail) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) tgt[c2 + j] -= sv[j];
+          }
+        }
+        // the last up-to-seven entries of the row together with the right-hand side
+        const int rem = l + 1 - c2;  // the same for the whole warp
+        const float sr = fmaf(ac, rx, bc * ry);
+        if (rem <= 3) {
+          float s0 = valid && rem > 0 ? fmaf(ac, rowx[c2], two ? bc * rowy[c2] : 0.f) : 0.f;
+          float s1 = valid && rem > 1 ? fmaf(ac, rowx[c2 + 1], two ? bc * rowy[c2 + 1] : 0.f) : 0.f;
+          float s2 = valid && rem > 2 ? fmaf(ac, rowx[c2 + 2], two ? bc * rowy[c2 + 2] : 0.f) : 0.f;
+          float sy = sr;
+          seg_scan4(s0, s1, s2, sy, lane, first, span);
+          if (valid && tail) {
+            if (rem > 0) tgt[c2] -= s0;
+            if (rem > 1) tgt[c2 + 1] -= s1;
+            if (rem > 2) tgt[c2 + 2] -= s2;
+            r[key] -= sy;
+          }
+        } else {
+          float sv[8];
+#pragma unroll
+          for (int j = 0; j < 7; ++j)
+            sv[j] = valid && rem > j ? fmaf(ac, rowx[c2 + j], two ? bc * rowy[c2 + j] : 0.f) : 0.f;
+          sv[7] = sr;
+          seg_scan8(sv, lane, first, span);
+          if (valid && tail) {
+#pragma unroll
+            for (int j = 0; j < 7; ++j)
+              if (rem > j) tgt[c2 + j] -= sv[j];
+            r[key] -= sv[7];
+          }
+        }
+      }
+    }
+    if (TPW < 512 && l > 0) {
+      const int count = hi - lo;
+      const int2* ft = rec_fac<ST>(m, v) + v.bf[l];
       // the first chunk's joint and first target; later chunks' are loaded one chunk ahead
       int4 info_n = make_int4(0, 0, 0, 0);
       int2 tk_n = make_int2(0, -1 - lane);
       if (lo + lane < hi) {
-        info_n = m.bl_info[v.b0 + lo + lane];
+        info_n = rec_info<ST>(m, v, lo + lane);
         if (1 + warp <= l) tk_n = ft[warp * count + lane];
       }
       for (int base = lo; base < hi; base += 32) {
@@ -885,7 +1045,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         const int4 info = info_n;
         int2 tk_next = tk_n;
         if (base + 32 + lane < hi) {
-          info_n = m.bl_info[v.b0 + base + 32 + lane];
+          info_n = rec_info<ST>(m, v, base + 32 + lane);
           if (1 + warp <= l) tk_n = ft[warp * count + base + 32 + lane - lo];
         } else {
           info_n = make_int4(0, 0, 0, 0);
@@ -961,7 +1121,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
       }
     }
     g.sync();
-    for (int idx = lo + g.lane; idx < hi; idx += TPW) pivot_scale(M, m.bl_info[v.b0 + idx], r);
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) pivot_scale(M, rec_info<ST>(m, v, idx), r);
   }
   g.sync();
 #else
@@ -969,9 +1129,9 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
   for (int l = v.nBL - 1; l >= 0; --l) {
     const int lo = v.bb[l], hi = v.bb[l + 1];
     const int count = hi - lo;
-    const int2* ft = m.fac_tgt + v.f0 + v.bf[l];
+    const int2* ft = rec_fac<ST>(m, v) + v.bf[l];
     for (int idx = lo; idx < hi; ++idx) {
-      const int4 info = m.bl_info[v.b0 + idx];
+      const int4 info = rec_info<ST>(m, v, idx);
       const bool two = (info.w & 3) == 2;
       const Pivot P = pivot_of(M, info.y, info.z, info.w);
       const float rx = r[info.x], ry = two ? r[info.x + 1] : 0.f;
@@ -985,46 +1145,78 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         r[tk.y] -= fmaf(ac, rx, bc * ry);
       }
     }
-    for (int idx = lo; idx < hi; ++idx) pivot_scale(M, m.bl_info[v.b0 + idx], r);
+    for (int idx = lo; idx < hi; ++idx) pivot_scale(M, rec_info<ST>(m, v, idx), r);
   }
 #endif
 }
 
 // One step of one world: phases 1-5 of the header comment, ending on a group barrier. When
 // tip_slot >= 0 the tips of the state at the start of the step are recorded in that slot.
-template <int TPW>
+// Phase clocks of the instrumented build: lane 0 of the group reads the SM clock after each
+// phase's closing barrier and adds the elapsed cycles to that phase's counter.
+struct PhaseClock {
+#ifdef ORCHARD_PHASE_CLOCKS
+  long long acc[kPhaseSlots];
+  long long t;
+  HD void start() {
+#ifdef __CUDA_ARCH__
+    t = clock64();
+#endif
+  }
+  HD void mark(int i) {
+#ifdef __CUDA_ARCH__
+    const long long n = clock64();
+    acc[i] += n - t;
+    t = n;
+#endif
+  }
+#else
+  HD void start() {}
+  HD void mark(int) {}
+#endif
+};
+
+template <int TPW, bool ST = false>
 HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
-                   float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot) {
+                   float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot, PhaseClock* pc = nullptr) {
   // 1. root-to-leaf: kinematics, velocities, own forces, apple loads
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec(m, v.b0 + b));
+    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec<ST>(m, v, b));
     g.sync();
   }
-  for (int b = g.lane; b < v.nb; b += TPW) forward_force(m, s, a, v, L, ws, b, t_abs, gv);
+  if (pc) pc->mark(0);
+  for (int b = g.lane; b < v.nb; b += TPW) forward_force<ST>(m, s, a, v, L, ws, b, t_abs, gv);
   g.sync();
+  if (pc) pc->mark(1);
   if (tip_slot >= 0) record_tips(m, a, v, L, ws, tip_slot, g);
+  if (pc) pc->mark(2);
   // 2. leaf-to-root: forces and composite inertias, right-hand side
   for (int l = v.nL - 1; l >= 0; --l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) backward_body(s, a, L, ws, b, t_abs, bwd_rec(m, v.b0 + b));
+    for (int b = lo + g.lane; b < hi; b += TPW) backward_body(s, a, L, ws, b, t_abs, bwd_rec<ST>(m, v, b));
     g.sync();
   }
+  if (pc) pc->mark(3);
   // 3. CRBA rows and the implicit diagonal, body by body
-  for (int b = g.lane; b < v.nb; b += TPW) crba_body(m, s, a, v, L, ws, b, t_abs, upd_rec(m, v.b0 + b));
+  for (int b = g.lane; b < v.nb; b += TPW) crba_body<ST>(m, s, a, v, L, ws, b, t_abs, upd_rec<ST>(m, v, b));
   g.sync();
+  if (pc) pc->mark(4);
   // 4. LDL^T by DOF depth, deepest first, with the L^T sweep of the solve
-  factor_levels<TPW>(m, v, L, ws, g);
+  factor_levels<TPW, ST>(m, v, L, ws, g);
+  if (pc) pc->mark(5);
   // 5. root-to-leaf: L sweep, update, velocities, apples, events
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) update_body(m, s, a, v, L, ws, b, t_abs, g.flag, upd_rec(m, v.b0 + b));
+    for (int b = lo + g.lane; b < hi; b += TPW) update_body<ST>(m, s, a, v, L, ws, b, t_abs, g.flag, upd_rec<ST>(m, v, b));
     g.sync();
   }
+  if (pc) pc->mark(6);
   if (v.na > 0) {
-    for (int ai = g.lane; ai < v.na; ai += TPW) update_apple(m, s, a, v, L, ws, ai, t_abs, g.flag);
+    for (int ai = g.lane; ai < v.na; ai += TPW) update_apple<ST>(m, s, a, v, L, ws, ai, t_abs, g.flag);
     g.sync();
   }
+  if (pc) pc->mark(7);
 }
 
 // Copy one world's state between two views (group-parallel), status word included.
@@ -1070,6 +1262,50 @@ HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
   for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];
 #endif
 }
+// Copy the parts of the world's model named by `mask` (StagePart) into shared memory at dst
+// (StageLayout offsets) and point the view at the copies. Group-parallel, no closing barrier:
+// the caller's next group barrier publishes the copies.
+template <int TPW>
+HD void stage_world(WorldView& v, int mask, float* dst, const Group<TPW>& g) {
+  const StageLayout S = StageLayout::make(mask, v.nb, v.nm, v.na, v.nfac, v.nitem);
+  auto rec4 = [&](int off, const void* src, int count) -> const void* {
+    copy4<TPW>(dst + off, (const float*)src, 4 * count, g);
+    return dst + off;
+  };
+  if (S.bi >= 0) {
+    v.bi = (const int4*)rec4(S.bi, v.bi, v.nb);
+    v.bp0 = (const float4*)rec4(S.bp0, v.bp0, v.nb);
+    v.bp1 = (const float4*)rec4(S.bp1, v.bp1, v.nb);
+  }
+  if (S.bp3 >= 0) v.bp3 = (const float4*)rec4(S.bp3, v.bp3, v.nb);
+  if (S.bj >= 0) {
+    v.bj = (const int4*)rec4(S.bj, v.bj, v.nb);
+    v.bp4 = (const float4*)rec4(S.bp4, v.bp4, v.nb);
+  }
+  if (S.anc >= 0) {
+    unsigned* d = (unsigned*)(dst + S.anc);
+    for (int i = g.lane; i < v.nm; i += TPW) d[i] = v.anc[i];
+    v.anc = d;
+  }
+  if (S.info >= 0) {
+    v.info = (const int4*)rec4(S.info, v.info, v.nb);
+    v.items = (const int4*)rec4(S.items, v.items, v.nitem);
+  }
+  if (S.fac >= 0) {
+    int2* d = (int2*)(dst + S.fac);
+    for (int i = g.lane; i < v.nfac; i += TPW) d[i] = v.fac[i];
+    v.fac = d;
+  }
+  if (S.bp2 >= 0) {
+    v.bp2 = (const float4*)rec4(S.bp2, v.bp2, v.nb);
+    v.ap0 = (const float4*)rec4(S.ap0, v.ap0, v.na);
+    v.ap1 = (const float4*)rec4(S.ap1, v.ap1, v.na);
+    int* d = (int*)(dst + S.abody);
+    for (int i = g.lane; i < v.na; i += TPW) d[i] = v.abody[i];
+    v.abody = d;
+  }
+}
+
 // Copy one step's record (WsLayout::record_words floats at rec) from the workspace and qd
 // (save) or back into them (restore).
 template <int TPW>
@@ -1115,31 +1351,53 @@ HD __noinline__ void tape_write(float* tape, const long long* tape_off, int n_st
 }
 
 // All steps of one world: its state is staged in the workspace for the whole rollout.
-template <int TPW>
+template <int TPW, bool ST = false>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
                   const Group<TPW>& g) {
-  const WorldView v = world_view(m, w);
+  WorldView v = world_view(m, w);
   const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const WState sg = world_state(S, v, w);
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);
+  // the model records this class stages sit after the workspace, for all the world's steps
+  if (ST && a.stage_mask && !a.global_ws) stage_world<TPW>(v, a.stage_mask, ws + a.ws_floats, g);
   copy_state<TPW>(s, sg, v, g);  // ends on a group barrier
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
   g.sync();
+  PhaseClock* pcp = nullptr;
+#ifdef ORCHARD_PHASE_CLOCKS
+  PhaseClock pc;
+  for (int i = 0; i < kPhaseSlots; ++i) pc.acc[i] = 0;
+  if (a.phase_clk && g.lane == 0) pcp = &pc;
+#endif
+  int steps_run = 0;
   for (int t = 0; t < a.n_steps; ++t) {
+    if (pcp) pcp->start();
     if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
     if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
     // the step's first write to the staged state comes after several group barriers
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
-    step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1);
+    if (pcp) pcp->mark(8);
+    step_world<TPW, ST>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1, pcp);
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
+    if (pcp) pcp->mark(8);
+    ++steps_run;
   }
+#ifdef ORCHARD_PHASE_CLOCKS
+#ifdef __CUDA_ARCH__
+  if (pcp) {
+    for (int i = 0; i < kPhases; ++i) atomicAdd(a.phase_clk + i, (unsigned long long)pc.acc[i]);
+    atomicAdd(a.phase_clk + kPhases, (unsigned long long)steps_run);
+  }
+#endif
+#endif
+  (void)steps_run;
   // the final state (its status word tells the backward whether the world froze)
   if (a.tape)
     tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, a.n_steps, false, v.nb, v.nv, v.nm, v.na, ws, g);
   if (a.tips && a.n_steps > 0) {
-    fk_only(m, s, v, L, ws, g);
+    fk_only<TPW, ST>(m, s, v, L, ws, g);
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);
     g.sync();
   }

@@ -6,7 +6,9 @@
 namespace orchard {
 namespace {
 
-template <int TPW>
+// ST: the instantiation that reads the model records a class stages in shared memory (the
+// other one reads them from the model in global memory and holds no pointers for them).
+template <int TPW, bool ST>
 __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, StepArgs a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int frozen[16];
@@ -16,9 +18,9 @@ __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, St
   g.flag = &frozen[g.id];
   const int groups = blockDim.x / TPW;
   float* ws = a.global_ws ? s.scratch + (long long)(blockIdx.x * groups + g.id) * a.ws_floats
-                          : smem + (long long)g.id * a.ws_floats;
+                          : smem + (long long)g.id * (a.ws_floats + a.stage_floats);
   if (a.single_world >= 0) {
-    run_world<TPW>(m, s, a, a.single_world, ws, g);
+    run_world<TPW, ST>(m, s, a, a.single_world, ws, g);
     return;
   }
   __shared__ int next[16];
@@ -33,36 +35,62 @@ __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, St
       qi = blockIdx.x * groups + g.id;
     }
     if (qi >= a.q_end - a.q_begin) break;
-    run_world<TPW>(m, s, a, m.queue[a.q_begin + qi], ws, g);
+    run_world<TPW, ST>(m, s, a, m.queue[a.q_begin + qi], ws, g);
     if (!a.q_counter) break;
   }
 }
 
+#ifdef ORCHARD_PHASE_CLOCKS
+__device__ unsigned long long g_phase_clk[kPhaseClasses * kPhaseSlots];
+#endif
+
 }  // namespace
 
-void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t st,
-                    const DevModel& m, const DevState& s, const StepArgs& a) {
-  const int threads = tpw * groups_per_block;
+unsigned long long* phase_clock_buffer() {
+#ifdef ORCHARD_PHASE_CLOCKS
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_phase_clk) != cudaSuccess) return nullptr;
+  return (unsigned long long*)p;
+#else
+  return nullptr;
+#endif
+}
+
+template <bool ST>
+const void* rollout_fn(int tpw) {
   switch (tpw) {
-    case 32: rollout_kernel<32><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 64: rollout_kernel<64><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 128: rollout_kernel<128><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 256: rollout_kernel<256><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 512: rollout_kernel<512><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 32: return (const void*)rollout_kernel<32, ST>;
+    case 64: return (const void*)rollout_kernel<64, ST>;
+    case 128: return (const void*)rollout_kernel<128, ST>;
+    case 256: return (const void*)rollout_kernel<256, ST>;
+    case 512: return (const void*)rollout_kernel<512, ST>;
+    default: return nullptr;
+  }
+}
+
+template <bool ST>
+void launch_rollout_t(int tpw, int threads, int blocks, size_t smem_bytes, cudaStream_t st, const DevModel& m,
+                      const DevState& s, const StepArgs& a) {
+  switch (tpw) {
+    case 32: rollout_kernel<32, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 64: rollout_kernel<64, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 128: rollout_kernel<128, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 256: rollout_kernel<256, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 512: rollout_kernel<512, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
     default: break;
   }
 }
 
-cudaError_t kernel_attributes(int tpw, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
-  const void* fn = nullptr;
-  switch (tpw) {
-    case 32: fn = (const void*)rollout_kernel<32>; break;
-    case 64: fn = (const void*)rollout_kernel<64>; break;
-    case 128: fn = (const void*)rollout_kernel<128>; break;
-    case 256: fn = (const void*)rollout_kernel<256>; break;
-    case 512: fn = (const void*)rollout_kernel<512>; break;
-    default: return cudaErrorInvalidValue;
-  }
+void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t st,
+                    const DevModel& m, const DevState& s, const StepArgs& a) {
+  const int threads = tpw * groups_per_block;
+  if (a.stage_mask) launch_rollout_t<true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+  else launch_rollout_t<false>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+}
+
+cudaError_t kernel_attributes(int tpw, bool staged, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
+  const void* fn = staged ? rollout_fn<true>(tpw) : rollout_fn<false>(tpw);
+  if (!fn) return cudaErrorInvalidValue;
   if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
   // the attribute belongs to the instantiation, shared by every class using it: always the limit
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimitBytes);

@@ -190,6 +190,29 @@ class Forest:
             meta=dict(self.meta, subset=worlds),
         )
 
+    @staticmethod
+    def concat(forests: list) -> "Forest":
+        """One forest holding the worlds of several, in order."""
+        import dataclasses
+        offs = ("body_off", "apple_off", "tip_off")
+        kw = {"n_worlds": sum(f.n_worlds for f in forests)}
+        for name in offs:
+            out = [0]
+            for f in forests:
+                out.extend((out[-1] + np.asarray(getattr(f, name))[1:]).tolist())
+            kw[name] = np.array(out, np.int32)
+        for fld in dataclasses.fields(Forest):
+            if fld.name in kw or fld.name == "meta":
+                continue
+            parts = [getattr(f, fld.name) for f in forests]
+            kw[fld.name] = None if any(p is None for p in parts) else np.concatenate(parts)
+        meta = dict(forests[0].meta) if forests else {}
+        for key in ("E", "sigma_r"):
+            if forests and all(key in f.meta for f in forests):
+                meta[key] = np.concatenate([f.meta[key] for f in forests])
+        kw["meta"] = meta
+        return Forest(**kw)
+
     def forces_at(self, step: int) -> np.ndarray:
         """External pull on every apple during simulation step ``step`` (na,3)."""
         on = (step >= self.pull_start) & (step < self.pull_end)
@@ -343,24 +366,45 @@ def world_seed(workload: str, w: int, sweep: int = 0) -> int:
     return 1_000_003 * WORKLOADS.index(workload) + w + 10_000_019 * sweep
 
 
-def make_forest(workload: str, n_worlds: int | None = None, worlds=None, sweep: int = 0,
-                recipe_override: WorldRecipe | None = None, variant: ModelVariant | None = None) -> Forest:
-    """Generate a named workload (optionally a subset of its worlds).
-
-    ``worlds`` picks world indices of the full workload (the seeds do not change), so a subset
-    holds exactly the same trees as the full batch. ``sweep`` > 0 draws fresh seeds of the
-    same distribution (the world-count sweep, and one batch per rank).
-    """
-    if workload not in WORKLOADS:
-        raise ValueError(f"unknown workload {workload!r}; one of {WORKLOADS}")
-    full = WORKLOAD_WORLDS[workload] if n_worlds is None else n_worlds
-    worlds = list(range(full)) if worlds is None else [int(w) for w in worlds]
+def _make_worlds(workload: str, worlds: list, full: int, sweep: int, recipe_override) -> list:
     per = []
     for w in worlds:
         rng = np.random.Generator(np.random.PCG64(world_seed(workload, w, sweep)))
         rec = recipe_override or world_recipe(workload, w, full, rng)
         per.append(_make_world(rng, rec))
-    forest = _pack(per, variant or ModelVariant())
+    return per
+
+
+def _make_packed(workload: str, worlds: list, full: int, sweep: int, recipe_override, var) -> "Forest":
+    return _pack(_make_worlds(workload, worlds, full, sweep, recipe_override), var)
+
+
+def make_forest(workload: str, n_worlds: int | None = None, worlds=None, sweep: int = 0,
+                recipe_override: WorldRecipe | None = None, variant: ModelVariant | None = None,
+                processes: int = 1) -> Forest:
+    """Generate a named workload (optionally a subset of its worlds).
+
+    ``worlds`` picks world indices of the full workload (the seeds do not change), so a subset
+    holds exactly the same trees as the full batch. ``sweep`` > 0 draws fresh seeds of the
+    same distribution (the world-count sweep, and one batch per rank). ``processes`` > 1
+    grows the trees in that many spawned worker processes (each world has its own seed, so
+    the forest is the same).
+    """
+    if workload not in WORKLOADS:
+        raise ValueError(f"unknown workload {workload!r}; one of {WORKLOADS}")
+    full = WORKLOAD_WORLDS[workload] if n_worlds is None else n_worlds
+    worlds = list(range(full)) if worlds is None else [int(w) for w in worlds]
+    var = variant or ModelVariant()
+    if processes > 1 and len(worlds) >= 512:
+        # each worker grows and packs a chunk of worlds; packing is per world, so the chunks
+        # concatenate to the same forest
+        import multiprocessing as mp
+        chunks = [c.tolist() for c in np.array_split(np.array(worlds, np.int64), 2 * processes)]
+        with mp.get_context("spawn").Pool(processes) as pool:
+            parts = pool.starmap(_make_packed, [(workload, c, full, sweep, recipe_override, var) for c in chunks])
+        forest = Forest.concat(parts)
+    else:
+        forest = _pack(_make_worlds(workload, worlds, full, sweep, recipe_override), var)
     forest.meta.update(workload=workload, n_worlds_full=full, worlds=worlds, sweep=sweep)
     return forest
 

@@ -16,6 +16,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "liborchard.so")
+# ORCHARD_LIB_VARIANT=phase loads the profiling build with the step's phase clocks instead
+if os.environ.get("ORCHARD_LIB_VARIANT", "") == "phase":
+    LIB_PATH = os.path.join(HERE, "_lib", "liborchard_phase.so")
 
 OT_OK = 0
 OT_EINVAL = -1
@@ -63,7 +66,7 @@ class ModelFlags(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("threads_per_world", C.c_int32), ("worlds_per_block", C.c_int32), ("blocks", C.c_int32),
-                ("global_workspace", C.c_int32)]
+                ("global_workspace", C.c_int32), ("stage", C.c_int32)]
 
 
 class StateInit(C.Structure):
@@ -125,6 +128,8 @@ _SIGS = {
     "ot_status_string": (C.c_char_p, [C.c_int]),
     "ot_last_cuda_error": (C.c_int32, []),
     "ot_launch_count": (C.c_int64, [C.c_int32]),
+    "ot_phase_clocks": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64), C.c_int32, C.c_int32]),
+    "ot_class_info": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -134,7 +139,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError(f"liborchard.so not built ({LIB_PATH}); run paper_2607_06337_b300/build.py")
+            raise ImportError(f"{os.path.basename(LIB_PATH)} not built ({LIB_PATH}); run paper_2607_06337_b300/build.py")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             fn = getattr(L, name)
@@ -304,12 +309,47 @@ def set_schedule(model, k, sched: Schedule):
     _check(lib().ot_set_schedule(model, int(k), C.byref(sched)), "ot_set_schedule")
 
 
+CLASS_INFO = ("worlds", "max_bodies", "workspace_bytes", "stage_mask", "stage_bytes", "smem_per_block",
+              "blocks_per_sm", "blocks")
+
+
+def class_info(model, k) -> dict:
+    """What size class k resolves to under its schedule (ot_class_info)."""
+    out = (C.c_int64 * 8)()
+    _check(lib().ot_class_info(model, int(k), out), "ot_class_info")
+    return dict(zip(CLASS_INFO, (int(x) for x in out)))
+
+
 def autotune(model, state, n_steps, dt=2e-3, stream=None):
     _check(lib().ot_autotune(model, state, int(n_steps), float(dt), _stream_handle(stream)), "ot_autotune")
 
 
 def launch_count(reset=False) -> int:
     return int(lib().ot_launch_count(1 if reset else 0))
+
+
+PHASES = ("kinematics", "forces", "tips", "bias_sweep", "mass_matrix", "ldlt", "update_sweep", "apples", "other")
+BACK_PHASES = ("apples_hang", "solve", "lsweep_springs_tape", "seeds", "chain", "restore", "replay", "final",
+               "other")
+BACK_ROW = 32
+
+
+def phase_clocks(model, n_classes, reset=True, backward=False):
+    """Per size class, SM cycles per world-step of each phase (the profiling build only):
+    a list of dicts {phase: cycles, "world_steps": n}; backward=True: the backward passes'."""
+    n = len(PHASES) + 1
+    rows = BACK_ROW + n_classes if backward else n_classes
+    buf = (C.c_uint64 * (n * rows))()
+    _check(lib().ot_phase_clocks(model, buf, int(rows), 1 if reset else 0), "ot_phase_clocks")
+    names = BACK_PHASES if backward else PHASES
+    out = []
+    for k in range(BACK_ROW if backward else 0, rows):
+        row = list(buf[k * n:(k + 1) * n])
+        steps = row[-1]
+        d = {p: (row[i] / steps if steps else 0.0) for i, p in enumerate(names)}
+        d["world_steps"] = steps
+        out.append(d)
+    return out
 
 
 # ------------------------------------------------------------------------------------------
@@ -451,6 +491,16 @@ class Simulator:
 
     def schedules(self):
         return [get_schedule(self.model, k) for k in range(self.counts.classes)]
+
+    def class_infos(self):
+        """Per size class: its schedule and what it resolves to (class_info)."""
+        out = []
+        for k, sc in enumerate(self.schedules()):
+            d = dict(threads_per_world=sc.threads_per_world, worlds_per_block=sc.worlds_per_block,
+                     global_workspace=sc.global_workspace, stage=sc.stage)
+            d.update(class_info(self.model, k))
+            out.append(d)
+        return out
 
     def autotune(self, n_steps=20, dt=None, stream=None):
         """Pick every class's fastest schedule; the state is scratch meanwhile, so it is reset

@@ -142,3 +142,26 @@ def test_flop_count_scales_with_the_terms():
     assert E[0] == depth.sum() and P[0] == (depth * (depth + 1) // 2).sum()
     per_body = costs.flops_per_step(f) / costs.body_count(f)
     assert 500 < per_body < 5000  # of the order of a few kflop per body-step
+
+
+def test_flop_model_against_the_executed_fp32_instructions():
+    """The algorithmic flop count behind the roofline fraction (paper_2607_06337_b300/costs.py,
+    a tally of the step's arithmetic: FMA 2, add, multiply, divide, square root, sine and cosine
+    1) against the hardware's own count: the FP32 instructions the rollout kernel executed over
+    a recorded rollout (ncu, 2 FFMA + FADD + FMUL with the predicate on, all size classes;
+    profiles/rollout_fp32_ops_batch4096_600w.json). The executed count bounds the algorithmic
+    one from above: the kernel also executes the redundant adds of its segmented scans, pivot
+    inverses computed once per warp, and the division and square-root sequences. A model that
+    overcounts, or misses a quarter of the work, fails."""
+    import json
+    import os
+
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rec = json.load(open(os.path.join(root, "profiles", "rollout_fp32_ops_batch4096_600w.json")))
+    f = I.make_forest(rec["workload"], n_worlds=rec["worlds"])
+    algo = costs.flops_per_step(f) * rec["sim_steps"]
+    ratio = algo / rec["fp32_flops_executed"]
+    assert 0.75 <= ratio <= 1.0, ratio
+    assert rec["fp64_flops_executed"] == 0  # no FP64 pivots in this workload

@@ -111,6 +111,26 @@ def test_adjoint_differentiation_workload_against_oracle():
             assert_close_per_kind(got, g_fd, kinds, 1.5 * tol, f"world {w} vs central differences")
 
 
+def test_adjoint_eight_worlds_64_coordinates_against_central_differences():
+    """The differentiation workload's gradient check at its stated size: 8 worlds x 64 random
+    coordinates (16 each of k, kd, q0, qd0), against FP64 central differences of the oracle
+    (1e-3 relative steps), on the workload's own +-20% stiffness target and with checkpoints
+    every 20 steps. Tolerance 1.5e-2 per kind: the 1e-2 rounding floor of this gradient (see the
+    module docstring) plus the differences' own O(h^2) error."""
+    f = I.make_forest(I.DIFF, worlds=[0, 1, 2, 3, 200, 401, 702, 1023])
+    fl = I.Flags()
+    n = 200
+    target = perturbed_target(f, fl, n)
+    g, _, _ = gpu_gradients(f, fl, n, 20, target)
+    rng = np.random.default_rng(64)
+    for w in range(f.n_worlds):
+        tw = target[:, f.tip_off[w]:f.tip_off[w + 1]]
+        kinds, idx = sample_coords(f, w, 16, rng)
+        assert len(kinds) == 64
+        g_fd, _ = O.grad(f, fl, w, n, tw, kinds, idx, fd_steps(f, w, kinds, idx), mode=1)
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_fd, kinds, 1.5e-2, f"world {w} vs central differences")
+
+
 def test_adjoint_far_target_bounds_the_adjoint_rounding():
     """The same worlds against a target 1 cm away (noise on the oracle's own tips): the loss is
     well resolved in FP32, so the adjoint must match the complex-step derivative to 1e-3."""

@@ -186,6 +186,53 @@ def test_config1_subset_with_pulls_and_events():
     assert sum(r["n_events"] for r in rep) > 10  # the workload does exercise breaks and detaches
 
 
+def _stratified(f, n):
+    """n worlds at evenly spaced ranks of the size order (bodies plus apples)."""
+    sizes = np.diff(f.body_off) + np.diff(f.apple_off)
+    order = np.argsort(sizes, kind="stable")
+    return np.unique(order[np.linspace(0, len(order) - 1, n).round().astype(np.int64)])
+
+
+def test_config1_stratified_64_worlds_1000_steps():
+    """The batching workload's parity sample: 64 of its 4096 trees stratified by size (100-600
+    bodies, with their random pulls), 1000 steps, through the autotuned batched rollout; q gate
+    and identical event sets on every world."""
+    from paper_2607_06337_b300.orchard import Simulator
+    torch = _torch()
+    full = I.make_forest(I.BATCH, processes=8)
+    f = full.subset(_stratified(full, 64))
+    fl = I.Flags()
+    sim = Simulator(f, fl)
+    sim.autotune(n_steps=10)
+    sim.reset()
+    sim.rollout(1000)
+    torch.cuda.synchronize()
+    g = _gpu_state(sim)
+    st, rec = O.rollout(f, fl, 1000, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    assert len(rep) == 64 and sum(r["n_events"] for r in rep) > 100
+    print("batch4096 stratified 64: max q-error / gate", round(max(r["ratio"] for r in rep), 4))
+
+
+def test_config4_stress_four_worlds_per_class_500_steps():
+    """The stress workload's parity sample: four worlds of each size class (50, 400 and 2000
+    bodies, the last with its temporaries in global memory) over the workload's full 500 steps,
+    FP64 pivots on twigs under 5 mm as the workload runs them; the error against the oracle
+    per size class."""
+    f = I.make_forest(I.STRESS, worlds=[0, 1365, 2730, 4095, 4096, 5461, 6826, 8191 - 820, 7373, 7782, 8000, 8191])
+    sizes = np.diff(f.body_off)
+    assert sorted(np.unique(sizes).tolist()) == [50, 400, 2000] and all((sizes == s).sum() == 4 for s in (50, 400, 2000))
+    fl = I.Flags(fp64_twig_diam=0.005)
+    g = _run(f, fl, 500)
+    st, rec = O.rollout(f, fl, 500, near_eps=PAR.NEAR)
+    rep = PAR.compare(f, fl, g, st, rec["near"])
+    PAR.assert_parity(rep)
+    for s in (50, 400, 2000):
+        print(f"stress {s} bodies: max q-error / gate",
+              round(max(r["ratio"] for r, n in zip(rep, sizes) if n == s), 4))
+
+
 def test_tip_record_matches_oracle():
     f = I.make_forest(I.DIFF, worlds=[0, 1, 2])
     fl = I.Flags()
