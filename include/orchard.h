@@ -164,7 +164,7 @@ ot_status ot_tree_model_upload(const ot_tree_desc* desc, const ot_model_flags* f
 void ot_model_release(ot_model* model);
 
 /* ---------------------------------------------------------------------------------------
- * Domain randomisation on the device (Sec. VI-B: per-world geometry and material, built on the
+ * Domain randomisation on the device (Sec. IV-D and VII-A: per-world geometry and material, built on the
  * GPU). factors: device [W][6] floats per world (s_len, s_diam, s_rho, s_E, s_sigma, c_d). Each
  * world's segment lengths and every body-frame point (joint origins, centres of mass, apple hang
  * points, tip points) are scaled by s_len, its diameters by s_diam, its wood density, Young's

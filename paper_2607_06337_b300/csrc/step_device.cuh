@@ -574,8 +574,11 @@ HD void backward_body(const WState& s, const StepArgs& a, const WsLayout& L, flo
 struct Pivot {
   float p00, p01, p11;  // P^-1 (symmetric)
 };
+// Once a level is eliminated the factorisation stores each of its joints' P^-1 in place of the
+// block: p00 takes H_xx's place, p11 H_yy's and p01 H_yx's (the y' row's entry of x). The
+// later uses (the L sweep, the adjoint's solves) read P^-1 there (pivot_of).
 // nd: the joint's DOF count, | 16 to invert the block in FP64 (the thinnest twigs).
-HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
+HD Pivot invert_block(const float* M, int rowx, int rowy, int nd) {
   Pivot P;
   const float a = M[rowx];
   if ((nd & 3) == 2) {
@@ -593,6 +596,35 @@ HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
     }
   } else {
     P.p00 = (nd & 16) ? (float)(1.0 / (double)a) : 1.f / a;
+    P.p01 = 0.f;
+    P.p11 = 0.f;
+  }
+  return P;
+}
+// z = P^-1 r for one joint of a finished level, in place in y, and P^-1 stored in place of the
+// joint's block.
+HD void scale_and_store(float* M, int4 info, float* y) {
+  const Pivot P = invert_block(M, info.y, info.z, info.w);
+  const float rx = y[info.x];
+  M[info.y] = P.p00;
+  if ((info.w & 3) == 2) {
+    const float ry = y[info.x + 1];
+    y[info.x] = P.p00 * rx + P.p01 * ry;
+    y[info.x + 1] = P.p01 * rx + P.p11 * ry;
+    M[info.z] = P.p11;
+    M[info.z + 1] = P.p01;
+  } else {
+    y[info.x] = P.p00 * rx;
+  }
+}
+// P^-1 of a joint whose block the factorisation has inverted in place.
+HD Pivot pivot_of(const float* M, int rowx, int rowy, int nd) {
+  Pivot P;
+  P.p00 = M[rowx];
+  if ((nd & 3) == 2) {
+    P.p11 = M[rowy];
+    P.p01 = M[rowy + 1];
+  } else {
     P.p01 = 0.f;
     P.p11 = 0.f;
   }
@@ -969,7 +1001,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         Pivot P{0.f, 0.f, 0.f};
         float rx = 0.f, ry = 0.f;
         if (valid) {
-          P = pivot_of(M, info.y, info.z, info.w);
+          P = invert_block(M, info.y, info.z, info.w);
           rx = r[info.x];
           if ((info.w & 3) == 2) ry = r[info.x + 1];
         }
@@ -1054,7 +1086,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         Pivot P{0.f, 0.f, 0.f};
         float rx = 0.f, ry = 0.f;
         if (valid) {
-          P = pivot_of(M, info.y, info.z, info.w);
+          P = invert_block(M, info.y, info.z, info.w);
           rx = r[info.x];
           if ((info.w & 3) == 2) ry = r[info.x + 1];
         }
@@ -1121,7 +1153,8 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
       }
     }
     g.sync();
-    for (int idx = lo + g.lane; idx < hi; idx += TPW) pivot_scale(M, rec_info<ST>(m, v, idx), r);
+    // z = P^-1 r for this level, and P^-1 stored in place of its block for the later uses
+    for (int idx = lo + g.lane; idx < hi; idx += TPW) scale_and_store(M, rec_info<ST>(m, v, idx), r);
   }
   g.sync();
 #else
@@ -1133,7 +1166,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
     for (int idx = lo; idx < hi; ++idx) {
       const int4 info = rec_info<ST>(m, v, idx);
       const bool two = (info.w & 3) == 2;
-      const Pivot P = pivot_of(M, info.y, info.z, info.w);
+      const Pivot P = invert_block(M, info.y, info.z, info.w);
       const float rx = r[info.x], ry = two ? r[info.x + 1] : 0.f;
       const float* rowx = M + info.y;
       const float* rowy = M + (two ? info.z + 1 : info.y);
@@ -1145,7 +1178,7 @@ HD void factor_levels(const DevModel& m, const WorldView& v, const WsLayout& L, 
         r[tk.y] -= fmaf(ac, rx, bc * ry);
       }
     }
-    for (int idx = lo; idx < hi; ++idx) pivot_scale(M, rec_info<ST>(m, v, idx), r);
+    for (int idx = lo; idx < hi; ++idx) scale_and_store(M, rec_info<ST>(m, v, idx), r);
   }
 #endif
 }

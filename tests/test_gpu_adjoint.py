@@ -73,12 +73,18 @@ def pick(f, w, g, kinds, idx):
     return np.array([g[k][(b0 if k < 2 else d0) + i] for k, i in zip(kinds, idx)])
 
 
-def assert_close_per_kind(got, ref, kinds, tol, what):
+def assert_close_per_kind(got, ref, kinds, tol, what, dt=0.0):
+    """Per kind of coordinate, the error against its largest sampled magnitude. With dt > 0 the
+    scale of the qd0 kind is at least dt times the q0 kind's: a velocity at step 0 is, to first
+    order, a displacement dt later, so dL/dqd0 holds dt dL/dq0 and inherits dt times q0's
+    rounding floor (on the +-20% target the qd0 gradients are about that size)."""
     for kind in range(4):
         s = kinds == kind
         if not s.any():
             continue
         scale = np.abs(ref[s]).max()
+        if kind == 3 and dt > 0 and (kinds == 2).any():
+            scale = max(scale, dt * np.abs(ref[kinds == 2]).max())
         err = np.abs(got[s] - ref[s]).max()
         assert err <= tol * scale + 1e-30, (
             f"{what}: {['k', 'kd', 'q0', 'qd0'][kind]} max err {err:.3e} vs scale {scale:.3e}\n"
@@ -111,16 +117,24 @@ def test_adjoint_differentiation_workload_against_oracle():
             assert_close_per_kind(got, g_fd, kinds, 1.5 * tol, f"world {w} vs central differences")
 
 
-def test_adjoint_eight_worlds_64_coordinates_against_central_differences():
+@pytest.mark.parametrize("target_kind", ["far", "perturbed"])
+def test_adjoint_eight_worlds_64_coordinates_against_central_differences(target_kind):
     """The differentiation workload's gradient check at its stated size: 8 worlds x 64 random
     coordinates (16 each of k, kd, q0, qd0), against FP64 central differences of the oracle
-    (1e-3 relative steps), on the workload's own +-20% stiffness target and with checkpoints
-    every 20 steps. Tolerance 1.5e-2 per kind: the 1e-2 rounding floor of this gradient (see the
-    module docstring) plus the differences' own O(h^2) error."""
+    (1e-3 relative steps), with checkpoints every 20 steps. Far target (tips + 1 cm noise):
+    1e-3 per kind, the sharp check. The workload's own +-20% stiffness target: 1.5e-2 per kind,
+    the 1e-2 rounding floor of that gradient (module docstring) plus the differences' own
+    O(h^2) error. qd0 is scaled as in assert_close_per_kind (dt times q0's floor)."""
     f = I.make_forest(I.DIFF, worlds=[0, 1, 2, 3, 200, 401, 702, 1023])
     fl = I.Flags()
     n = 200
-    target = perturbed_target(f, fl, n)
+    if target_kind == "far":
+        _, rec0 = O.rollout(f, fl, n, record_tips=True)
+        target = rec0["tips"] + np.random.default_rng(31).normal(0.0, 0.01, rec0["tips"].shape)
+        tol = TOL_FAR
+    else:
+        target = perturbed_target(f, fl, n)
+        tol = 1.5e-2
     g, _, _ = gpu_gradients(f, fl, n, 20, target)
     rng = np.random.default_rng(64)
     for w in range(f.n_worlds):
@@ -128,7 +142,8 @@ def test_adjoint_eight_worlds_64_coordinates_against_central_differences():
         kinds, idx = sample_coords(f, w, 16, rng)
         assert len(kinds) == 64
         g_fd, _ = O.grad(f, fl, w, n, tw, kinds, idx, fd_steps(f, w, kinds, idx), mode=1)
-        assert_close_per_kind(pick(f, w, g, kinds, idx), g_fd, kinds, 1.5e-2, f"world {w} vs central differences")
+        assert_close_per_kind(pick(f, w, g, kinds, idx), g_fd, kinds, tol, f"world {w} vs central differences",
+                              dt=fl.dt)
 
 
 def test_adjoint_far_target_bounds_the_adjoint_rounding():

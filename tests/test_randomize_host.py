@@ -1,5 +1,5 @@
 """Pins of inputs.randomize, the host counterpart of the on-device domain-randomisation build
-(Sec. VI-B: per-world geometric and material transforms of a fixed tree graph), CPU only.
+(Sec. IV-D and VII-A: per-world geometric and material transforms of a fixed tree graph), CPU only.
 
 The device build is checked against this function on the GPU, so a mistake shared by the two
 would pass there; these tests tie it to what the transforms must do: unit factors give back the
