@@ -368,6 +368,13 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
         tips, buf, rec = sim.record_buffers(n, ce, tape_steps=tape_steps)
         work = torch.empty(B.backward_workspace_bytes(sim.model, ce), dtype=torch.uint8, device=dev)
         dtips = torch.empty_like(tips)
+        if not args.no_autotune:
+            # the backward's threads per world per size class, tuned on this record form
+            sim.reset_from_device(*dev_in)
+            sim.rollout(n, record=rec)
+            torch.sub(tips, target, out=dtips)
+            dtips.mul_(w_tip)
+            sim.autotune_backward(n, rec, dtips, workspace=work)
 
         def one(k, ev=None):
             flush.fill_(k & 0xff)
@@ -408,8 +415,10 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
             tot_ms = float(t.item())
         g_ok = all(bool(torch.isfinite(g).all()) for g in grads)
         nbytes = sum(b.numel() for b in buf) if isinstance(buf, tuple) else buf.numel()
+        back_sched[ce if tape_steps == 0 else -1] = sim.backward_schedules()
         return fwd_ms, bwd_ms, tot_ms, launches, g_ok, nbytes
 
+    back_sched = {}
     free, _ = torch.cuda.mem_get_info(dev)
     tape_fits = B.tape_bytes(sim.model, n) <= free // 2
     # the hybrid's tape: as many final steps as fit in half the free memory (one step's share
@@ -459,6 +468,8 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
         if "hybrid" in runs:
             out["tape_steps"] = k_hyb
     out["repeats"] = {"warmup": warmup, "timed": steps}
+    out["backward_threads_per_world"] = {{0: "tape", -1: "hybrid"}.get(k, "checkpoints"): v
+                                         for k, v in back_sched.items()}
     out["schedules"] = sim.class_infos()
     acc = None
     if acc_per_size > 0:

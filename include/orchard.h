@@ -314,6 +314,18 @@ typedef struct ot_grads {
   float* dqd0;
 } ot_grads;
 ot_status ot_backward_workspace_bytes(const ot_model* model, int32_t ckpt_every, size_t* bytes);
+/* Backward schedules: the backward kernel's threads per world for size class c (64, 128 or 256;
+ * 0 restores the default by tree size: 64 up to 96 bodies, else 256). ot_autotune_backward
+ * takes ot_rollout_backward's arguments (a recorded rollout), times each candidate of each
+ * class on it with CUDA events on `stream`, one class at a time, and keeps the fastest. The
+ * grads then hold meaningless values (they serve as scratch, as the state does for
+ * ot_autotune); run ot_rollout_backward again for the gradients. The workspace size
+ * (ot_backward_workspace_bytes) fits every candidate, so it does not change with the choice. */
+ot_status ot_get_backward_schedule(const ot_model* model, int32_t size_class, int32_t* threads_per_world);
+ot_status ot_set_backward_schedule(ot_model* model, int32_t size_class, int32_t threads_per_world);
+ot_status ot_autotune_backward(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
+                               const ot_force_schedule* pulls, const ot_record* record, const float* dL_dtips,
+                               ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream);
 ot_status ot_rollout_backward(ot_model* model, ot_state* state, int32_t n_steps, int32_t step0, double dt,
                               const ot_force_schedule* pulls, const ot_record* record, const float* dL_dtips,
                               ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream);

@@ -59,6 +59,7 @@ struct ClassInfo {
   ot_schedule sched;
   size_t scratch_off;  // byte offset of this class's scratch in the state buffer (global workspace)
   int scratch_slots;
+  int back_tpw = 0;    // the backward's threads per world (0: by tree size, see back_plan)
 };
 
 // Host-side packed forest (FP32 device layout) plus bookkeeping.
@@ -1399,10 +1400,13 @@ struct BackPlan {
 };
 inline long long round16(long long f) { return (f + 15) / 16 * 16; }
 
-BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
+constexpr int kBackTpw[3] = {64, 128, 256};  // the backward's candidate threads per world
+
+BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce, int tpw = 0) {
   BackPlan p{};
-  // threads per world by tree size (measured on B300 with 200-body trees: 256 beat 128)
-  p.tpw = ci.max_nb <= 96 ? 64 : 256;
+  // threads per world: as given, as the class's backward schedule says, or by tree size
+  // (measured on B300 with 200-body trees: 256 beat 128)
+  p.tpw = tpw > 0 ? tpw : ci.back_tpw > 0 ? ci.back_tpw : (ci.max_nb <= 96 ? 64 : 256);
   BackShape& sh = p.sh;
   sh.fwd_floats = round16(ci.ws_floats);
   sh.adj_floats = round16(backward_adj_floats(ci.max_nb, ci.max_nv, ci.max_na));
@@ -1450,22 +1454,21 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce) {
   p.blocks = (int)(p.slots / p.gpb);
   return p;
 }
-}  // namespace
-
-ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, size_t* bytes) {
-  if (!m || !bytes || ckpt_every < 0) return OT_EINVAL;
-  size_t total = 0;
-  for (const ClassInfo& ci : m->P.classes) {
-    const BackPlan p = back_plan(m, ci, ckpt_every);
-    total += p.slots * (size_t)p.sh.global_floats * 4;
+// A class's share of the backward workspace (floats): enough for any of the candidate threads
+// per world, so that the layout does not depend on the class's backward schedule.
+size_t back_class_floats(const ot_model* m, const ClassInfo& ci, int ce) {
+  size_t mx = 0;
+  for (int t : kBackTpw) {
+    const BackPlan p = back_plan(m, ci, ce, t);
+    mx = std::max(mx, p.slots * (size_t)p.sh.global_floats);
   }
-  *bytes = total;
-  return OT_OK;
+  return mx;
 }
 
-ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
-                              const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
-                              ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
+// The backward's arguments from ot_rollout_backward's (validated; see orchard.h).
+ot_status backward_args(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                        const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips, ot_grads* grads,
+                        void* workspace, size_t workspace_bytes, StepArgs* out, BackArgs* ba, int* ce_out) {
   if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0) || !rec || !dL_dtips || !grads) return OT_EINVAL;
   // the tape when the forward wrote one; checkpoints (and segment replays) for the steps before
   // a tape of the final steps only, or for all steps without a tape
@@ -1500,7 +1503,123 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
     a.ckpt = (unsigned*)rec->ckpt;
     a.ckpt_every = ce;
   }
-  BackArgs ba{dL_dtips, grads->dk, grads->dkd, grads->dq0, grads->dqd0};
+  *out = a;
+  *ba = BackArgs{dL_dtips, grads->dk, grads->dkd, grads->dq0, grads->dqd0};
+  *ce_out = ce;
+  return OT_OK;
+}
+
+// The start of class k's share of the backward workspace.
+float* back_work(const ot_model* m, float* work, int k, int ce) {
+  for (int i = 0; i < k; ++i) work += back_class_floats(m, m->P.classes[i], ce);
+  return work;
+}
+
+// Launch class k's backward on stream sk with its current plan.
+cudaError_t launch_back_class(ot_model* m, ot_state* s, int k, const StepArgs& a, const BackArgs& ba, float* work,
+                              int ce, cudaStream_t sk) {
+  const ClassInfo& ci = m->P.classes[k];
+  const BackPlan p = back_plan(m, ci, ce);
+  int bps = 0;
+  const int mode = !a.tape ? 0 : a.tape_steps < a.n_steps ? 2 : 1;
+  cudaError_t e = backward_attributes(p.tpw, mode, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
+  if (e == cudaSuccess && bps < 1) e = cudaErrorInvalidConfiguration;
+  StepArgs b = a;
+  b.q_begin = ci.q_begin;
+  b.q_end = ci.q_end;
+  b.q_counter = s->q_counters + k;
+  // instrumented builds: the backward's phase clocks of class k sit in row kBackPhaseRow + k
+  b.phase_clk = m->phase_clk && k < kPhaseClasses - kBackPhaseRow
+                    ? m->phase_clk + (size_t)(kBackPhaseRow + k) * kPhaseSlots : nullptr;
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.q_counter, 0, sizeof(int), sk);
+  if (e == cudaSuccess && p.blocks > 0) {
+    launch_backward(p.tpw, p.gpb, p.blocks, sk, m->dev, b, ba, work, p.sh);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) g_launches += 1;
+  }
+  return e;
+}
+}  // namespace
+
+ot_status ot_backward_workspace_bytes(const ot_model* m, int32_t ckpt_every, size_t* bytes) {
+  if (!m || !bytes || ckpt_every < 0) return OT_EINVAL;
+  size_t total = 0;
+  for (const ClassInfo& ci : m->P.classes) total += back_class_floats(m, ci, ckpt_every) * 4;
+  *bytes = total;
+  return OT_OK;
+}
+
+ot_status ot_get_backward_schedule(const ot_model* m, int32_t k, int32_t* threads_per_world) {
+  if (!m || !threads_per_world || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  *threads_per_world = back_plan(m, m->P.classes[k], 0).tpw;
+  return OT_OK;
+}
+
+ot_status ot_set_backward_schedule(ot_model* m, int32_t k, int32_t threads_per_world) {
+  if (!m || k < 0 || k >= (int)m->P.classes.size()) return OT_EINVAL;
+  const int t = threads_per_world;
+  if (t != 0 && t != 64 && t != 128 && t != 256) return OT_EINVAL;
+  m->P.classes[k].back_tpw = t;
+  return OT_OK;
+}
+
+ot_status ot_autotune_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                               const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
+                               ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
+  StepArgs a{};
+  BackArgs ba{};
+  int ce = 0;
+  ot_status st = backward_args(m, s, n_steps, step0, dt, pulls, rec, dL_dtips, grads, workspace, workspace_bytes,
+                               &a, &ba, &ce);
+  if (st != OT_OK) return st;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  OT_CUDA(cudaEventCreate(&e0));
+  OT_CUDA(cudaEventCreate(&e1));
+  ot_status result = OT_OK;
+  for (int k = 0; k < (int)m->P.classes.size() && result == OT_OK; ++k) {
+    ClassInfo& ci = m->P.classes[k];
+    float* work = back_work(m, (float*)workspace, k, ce);
+    const int keep = ci.back_tpw;
+    float best = 1e30f;
+    int best_t = keep;
+    for (int t : kBackTpw) {
+      ci.back_tpw = t;
+      if (launch_back_class(m, s, k, a, ba, work, ce, cs) != cudaSuccess) continue;  // warm-up
+      cudaEventRecord(e0, cs);
+      const cudaError_t e = launch_back_class(m, s, k, a, ba, work, ce, cs);
+      cudaEventRecord(e1, cs);
+      if (e != cudaSuccess) continue;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        result = cuda_fail(cudaGetLastError());
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_t = t;
+      }
+    }
+    ci.back_tpw = best_t;
+  }
+  cudaGetLastError();  // a candidate that could not launch leaves no error behind
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, double dt,
+                              const ot_force_schedule* pulls, const ot_record* rec, const float* dL_dtips,
+                              ot_grads* grads, void* workspace, size_t workspace_bytes, void* stream) {
+  StepArgs a{};
+  BackArgs ba{};
+  int ce = 0;
+  {
+    const ot_status st = backward_args(m, s, n_steps, step0, dt, pulls, rec, dL_dtips, grads, workspace,
+                                       workspace_bytes, &a, &ba, &ce);
+    if (st != OT_OK) return st;
+  }
   cudaStream_t cs = (cudaStream_t)stream;
   float* work = (float*)workspace;
   // the classes run concurrently: each on its own stream, forked from and joined back to `stream`
@@ -1514,35 +1633,12 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
     OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     m->join_events.push_back(ev);
   }
-  std::vector<float*> works(nk);
-  for (int k = 0; k < nk; ++k) {
-    works[k] = work;
-    const BackPlan p = back_plan(m, m->P.classes[k], ce);
-    work += p.slots * (size_t)p.sh.global_floats;
-  }
   OT_CUDA(cudaEventRecord(m->fork_event, cs));
   ot_status result = OT_OK;
   for (int k = nk - 1; k >= 0; --k) {
-    const ClassInfo& ci = m->P.classes[k];
-    const BackPlan p = back_plan(m, ci, ce);
     cudaStream_t sk = m->class_streams[k];
     OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
-    int bps = 0;
-    const int mode = !a.tape ? 0 : a.tape_steps < a.n_steps ? 2 : 1;
-    cudaError_t e = backward_attributes(p.tpw, mode, p.gpb, (size_t)p.sh.smem_floats * 4 * p.gpb, &bps);
-    StepArgs b = a;
-    b.q_begin = ci.q_begin;
-    b.q_end = ci.q_end;
-    b.q_counter = s->q_counters + k;
-    // instrumented builds: the backward's phase clocks of class k sit in row kBackPhaseRow + k
-    b.phase_clk = m->phase_clk && k < kPhaseClasses - kBackPhaseRow
-                      ? m->phase_clk + (size_t)(kBackPhaseRow + k) * kPhaseSlots : nullptr;
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.q_counter, 0, sizeof(int), sk);
-    if (e == cudaSuccess && p.blocks > 0) {
-      launch_backward(p.tpw, p.gpb, p.blocks, sk, m->dev, b, ba, works[k], p.sh);
-      e = cudaGetLastError();
-      if (e == cudaSuccess) g_launches += 1;
-    }
+    const cudaError_t e = launch_back_class(m, s, k, a, ba, back_work(m, work, k, ce), ce, sk);
     if (e != cudaSuccess && result == OT_OK) result = cuda_fail(e);
     // always join, so `stream` waits for whatever was enqueued
     OT_CUDA(cudaEventRecord(m->join_events[k], sk));

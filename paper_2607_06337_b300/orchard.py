@@ -120,6 +120,11 @@ _SIGS = {
     "ot_rollout_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
                                       C.POINTER(ForceSchedule), C.POINTER(Record), C.c_void_p, C.POINTER(Grads),
                                       C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ot_autotune_backward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_double,
+                                       C.POINTER(ForceSchedule), C.POINTER(Record), C.c_void_p, C.POINTER(Grads),
+                                       C.c_void_p, C.c_size_t, C.c_void_p]),
+    "ot_get_backward_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "ot_set_backward_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "ot_get_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Schedule)]),
     "ot_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p]),
@@ -285,6 +290,24 @@ def rollout_backward(model, state, n_steps, step0, dt, pulls, record, dL_dtips, 
                                      C.byref(record), _ptr(dL_dtips), C.byref(grads), _ptr(workspace),
                                      workspace.numel() * workspace.element_size(), _stream_handle(stream)),
            "ot_rollout_backward")
+
+
+def autotune_backward(model, state, n_steps, step0, dt, pulls, record, dL_dtips, grads, workspace, stream=None):
+    fs = pulls if pulls is not None else ForceSchedule(None, None, None)
+    _check(lib().ot_autotune_backward(model, state, int(n_steps), int(step0), float(dt), C.byref(fs),
+                                      C.byref(record), _ptr(dL_dtips), C.byref(grads), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), _stream_handle(stream)),
+           "ot_autotune_backward")
+
+
+def get_backward_schedule(model, k) -> int:
+    t = C.c_int32(0)
+    _check(lib().ot_get_backward_schedule(model, int(k), C.byref(t)), "ot_get_backward_schedule")
+    return int(t.value)
+
+
+def set_backward_schedule(model, k, threads_per_world):
+    _check(lib().ot_set_backward_schedule(model, int(k), int(threads_per_world)), "ot_set_backward_schedule")
 
 
 def ckpt_bytes(model, n_steps, ckpt_every) -> int:
@@ -491,6 +514,24 @@ class Simulator:
 
     def schedules(self):
         return [get_schedule(self.model, k) for k in range(self.counts.classes)]
+
+    def backward_schedules(self):
+        """The backward's threads per world of each size class."""
+        return [get_backward_schedule(self.model, k) for k in range(self.counts.classes)]
+
+    def autotune_backward(self, n_steps, record, dL_dtips, step0=0, dt=None, workspace=None, stream=None):
+        """Pick every class's fastest backward threads per world on a recorded rollout (the
+        gradients it produces meanwhile are discarded)."""
+        import torch
+        c = self.counts
+        grads = tuple(torch.zeros(n, dtype=torch.float32, device=self.device)
+                      for n in (c.bodies, c.bodies, c.dofs, c.dofs))
+        if workspace is None:
+            workspace = torch.empty(backward_workspace_bytes(self.model, record.ckpt_every), dtype=torch.uint8,
+                                    device=self.device)
+        g = Grads(*[t.data_ptr() if t.numel() else None for t in grads])
+        autotune_backward(self.model, self.state, n_steps, step0, self.flags.dt if dt is None else dt, self.pulls,
+                          record, dL_dtips.contiguous(), g, workspace, stream)
 
     def class_infos(self):
         """Per size class: its schedule and what it resolves to (class_info)."""

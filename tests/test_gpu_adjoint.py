@@ -474,3 +474,36 @@ def test_adjoint_stress_size_classes(world, n, per_kind):
                                               np.abs(g_cs[kinds == k]).max()) for k in range(4)}
     print(f"stress adjoint, {int(np.diff(f.body_off)[0])} bodies: relative error per kind {errs}")
     assert_close_per_kind(got, g_cs, kinds, 2e-3, f"stress world {world}")
+
+
+@pytest.mark.parametrize("ckpt_every", [0, 10])
+def test_backward_schedules_give_the_same_gradients(ckpt_every):
+    """Two size classes (50- and 400-body stress trees), 40 steps, the forward's tape or
+    checkpoints: every backward threads-per-world candidate, and the one the backward autotuner
+    picks, give the default plan's gradients (the work of each joint and each scan does not
+    depend on which warp takes it)."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    f = I.make_forest(I.STRESS, worlds=[0, 1, 4096, 4097])
+    fl = I.Flags(fp64_twig_diam=0.005)
+    n = 40
+    sim = B.Simulator(f, fl)
+    assert sim.counts.classes >= 2
+    sim.reset()
+    tips, _, rec = sim.record_buffers(n, ckpt_every)
+    sim.rollout(n, record=rec)
+    dtips = (1e-3 * torch.sin(torch.arange(tips.numel(), device="cuda", dtype=torch.float32))).view_as(tips)
+    ref = [g.cpu().numpy() for g in sim.backward(n, rec, dtips)]
+
+    def same(got, what):
+        for a, b, name in zip(got, ref, ("dk", "dkd", "dq0", "dqd0")):
+            np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6 * np.abs(b).max(), err_msg=f"{what} {name}")
+
+    for t in (64, 128, 256):
+        for k in range(sim.counts.classes):
+            B.set_backward_schedule(sim.model, k, t)
+        assert sim.backward_schedules() == [t] * sim.counts.classes
+        same([g.cpu().numpy() for g in sim.backward(n, rec, dtips)], f"{t} threads per world")
+    sim.autotune_backward(n, rec, dtips)
+    assert all(t in (64, 128, 256) for t in sim.backward_schedules())
+    same([g.cpu().numpy() for g in sim.backward(n, rec, dtips)], "autotuned")

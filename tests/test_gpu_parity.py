@@ -233,6 +233,39 @@ def test_config4_stress_four_worlds_per_class_500_steps():
               round(max(r["ratio"] for r, n in zip(rep, sizes) if n == s), 4))
 
 
+@pytest.mark.parametrize("workload,worlds,stage", [(I.BATCH, list(range(0, 60, 3)), -1),
+                                                   (I.PLAIN, list(range(16)), 127)])
+def test_staged_model_records_give_the_same_states(workload, worlds, stage):
+    """The staged instantiation (model records copied into shared memory per world: stage -1
+    takes every part that fits, 127 all of them) reads the same values as the unstaged one, so
+    every class's states after a rollout are bit-identical: uneven batch trees with pulls, breaks
+    and detaches (automatic staging), and the plain-form trees with every part staged."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    f = I.make_forest(workload, worlds=worlds)
+    fl = I.Flags()
+    out = []
+    for st in (0, stage):
+        sim = B.Simulator(f, fl)
+        for k, sc in enumerate(sim.schedules()):
+            # one world per block at 64 threads: room for the records of most of these trees
+            B.set_schedule(sim.model, k, B.Schedule(64, 1, 0, sc.global_workspace, st))
+        infos = sim.class_infos()
+        if st == -1:
+            assert any(ci["stage_mask"] for ci in infos)
+        if st == 127:
+            assert all(ci["stage_mask"] == 127 for ci in infos)
+        sim.reset()
+        sim.rollout(300)
+        torch.cuda.synchronize()
+        out.append(_gpu_state(sim))
+        sim.close()
+    for key in ("q", "qd", "ax", "broken", "break_step", "detached", "detach_step", "status"):
+        np.testing.assert_array_equal(out[1][key], out[0][key], err_msg=key)
+    if workload == I.BATCH:
+        assert out[0]["broken"].sum() + out[0]["detached"].sum() > 0
+
+
 def test_tip_record_matches_oracle():
     f = I.make_forest(I.DIFF, worlds=[0, 1, 2])
     fl = I.Flags()
