@@ -165,3 +165,22 @@ def test_flop_model_against_the_executed_fp32_instructions():
     ratio = algo / rec["fp32_flops_executed"]
     assert 0.75 <= ratio <= 1.0, ratio
     assert rec["fp64_flops_executed"] == 0  # no FP64 pivots in this workload
+
+
+def test_adjoint_flop_model_against_the_executed_fp32_instructions():
+    """The backward's flop tally (costs.adjoint_flops_per_step without the replayed forward step,
+    as in the tape form) against the FP32 instructions one tape-form backward launch executed
+    over a 20-step recorded rollout of 256 diff1024 trees (ncu, 2 FFMA + FADD + FMUL;
+    profiles/backward_fp32_ops_diff1024_256w.json). The executed count bounds it from above (the
+    scans' redundant adds, divisions and square roots expanded); within a quarter below."""
+    import json
+    import os
+
+    from paper_2607_06337_b300 import costs
+    from paper_2607_06337_b300 import inputs as I
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rec = json.load(open(os.path.join(root, "profiles", "backward_fp32_ops_diff1024_256w.json")))
+    f = I.make_forest(rec["workload"], n_worlds=rec["worlds"])
+    algo = costs.adjoint_flops_per_step(f, replay=False) * rec["sim_steps"]
+    ratio = algo / rec["fp32_flops_executed"]
+    assert 0.75 <= ratio <= 1.0, ratio
