@@ -65,9 +65,9 @@ def parse():
     p.add_argument("--no-sweep", action="store_true",
                    help="skip the world-count sweep (1024..65536 sweep16384 trees, batched and plain form)")
     p.add_argument("--no-stress", action="store_true", help="skip the stress8192 forward + adjoint leg")
-    p.add_argument("--stage", default="auto", choices=["auto", "off"],
+    p.add_argument("--stage", default="auto", choices=["auto", "off", "on"],
                    help="off: after the autotune, run every class with no model records staged in shared "
-                        "memory (A/B of the staging)")
+                        "memory; on: with every part that keeps its blocks per SM staged (A/B of the staging)")
     p.add_argument("--phase-clocks", action="store_true",
                    help="profiling: run the workload once on the phase-clock build and print the cycles per "
                         "world-step of each phase of the step, per size class")
@@ -318,8 +318,9 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
     steps under a fixed 5 N pull on one apple per tree. stress8192: 8192 trees of 50, 400 and
     2000 bodies, 500 steps, FP64 pivots for twigs under 5 mm.
 
-    Record forms: the forward's full tape (the backward runs no step again) when it fits in half
-    the free device memory, else a tape of the last steps that fit with checkpoints every
+    Record forms: the forward's full tape (the backward runs no step again) when it fits in 80%
+    of the free device memory (less the other buffers), else a tape of the last steps that fit
+    with checkpoints every
     ``--adj-ckpt`` steps before them (the hybrid); and, with checkpoint_form, checkpoints only
     (each segment replayed once in the backward). The line's value is the faster form; the
     other is reported beside it. ``warmup`` and ``steps`` are this leg's own repeat counts.
@@ -420,10 +421,14 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
 
     back_sched = {}
     free, _ = torch.cuda.mem_get_info(dev)
-    tape_fits = B.tape_bytes(sim.model, n) <= free // 2
-    # the hybrid's tape: as many final steps as fit in half the free memory (one step's share
-    # of the tape is tape_bytes(model, 0); the final state takes one more)
-    k_hyb = 0 if tape_fits else min(n - 1, (free // 2) // B.tape_bytes(sim.model, 0) - 1)
+    # the tape's budget: 80% of the free device memory less the checkpoints, the backward's
+    # workspace and a 4 GB margin
+    budget = int(0.8 * free) - B.ckpt_bytes(sim.model, n, args.adj_ckpt) - \
+        B.backward_workspace_bytes(sim.model, args.adj_ckpt) - (4 << 30)
+    tape_fits = B.tape_bytes(sim.model, n) <= budget
+    # the hybrid's tape: as many final steps as fit in the budget (one step's share of the tape
+    # is tape_bytes(model, 0); the final state takes one more)
+    k_hyb = 0 if tape_fits else min(n - 1, max(0, budget // B.tape_bytes(sim.model, 0) - 1))
     runs = {}
     if tape_fits:
         runs["tape"] = timed(0)
@@ -464,7 +469,8 @@ def fwd_adjoint(args, dev, rank, ws, name, warmup, steps, checkpoint_form=True, 
             out[other] = {"value": ws * bodies * n / (r[2] / 1e3), "fwd_ms": r[0], "bwd_ms": r[1],
                           "record_bytes": r[5], "grads_finite": r[4]}
     if not tape_fits:
-        out["tape"] = {"skipped": f"{B.tape_bytes(sim.model, n) / 1e9:.1f} GB tape over half the free memory"}
+        out["tape"] = {"skipped": f"{B.tape_bytes(sim.model, n) / 1e9:.1f} GB tape over the {budget / 1e9:.0f} GB "
+                                  f"budget (80% of the free device memory less the other buffers)"}
         if "hybrid" in runs:
             out["tape_steps"] = k_hyb
     out["repeats"] = {"warmup": warmup, "timed": steps}
@@ -623,11 +629,12 @@ def world_sweep(args, dev):
             "host_generation_s": gen_s}, acc
 
 
-def unstage(sim):
-    """Every class keeps its schedule but stages no model records in shared memory."""
+def set_staging(sim, stage):
+    """Every class keeps its schedule but stages `stage` (0: no model records in shared memory;
+    -1: each part that keeps the class's blocks per SM)."""
     from paper_2607_06337_b300 import orchard as B
     for k, sc in enumerate(sim.schedules()):
-        sc.stage = 0
+        sc.stage = stage
         B.set_schedule(sim.model, k, sc)
 
 
@@ -649,8 +656,8 @@ def phase_clock_run(args):
     sim = B.Simulator(forest, fl, device=dev)
     if not args.no_autotune:
         sim.autotune(n_steps=20)
-    if args.stage == "off":
-        unstage(sim)
+    if args.stage != "auto":
+        set_staging(sim, 0 if args.stage == "off" else -1)
     sim.reset()
     sim.rollout(S)
     torch.cuda.synchronize()
@@ -678,7 +685,7 @@ def phase_clock_run(args):
 
 def backward_phase_run(args, dev):
     """The backward's phase clocks on the differentiation workload (--adj-workload), for each
-    record form: the forward's tape (when it fits in half the free memory) and checkpoints every
+    record form: the forward's tape (when it fits in half the free memory here) and checkpoints every
     --adj-ckpt steps; one warm-up backward, then one counted."""
     import torch
     from paper_2607_06337_b300 import inputs as I
@@ -748,8 +755,8 @@ def run_ours(args):
     if not args.no_autotune:
         reset()
         sim.autotune(n_steps=20)
-    if args.stage == "off":
-        unstage(sim)
+    if args.stage != "auto":
+        set_staging(sim, 0 if args.stage == "off" else -1)
     scheds = sim.class_infos()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 

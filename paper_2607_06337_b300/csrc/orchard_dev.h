@@ -139,13 +139,24 @@ enum StagePart {
 // tables least, since its loads are issued one step ahead).
 constexpr int kStageOrder[7] = {kStageKin, kStageAnc, kStageUpd, kStageBias, kStageForce, kStageInfo, kStageFac};
 
-// Float offsets of the staged parts of one world (each on a 16-byte boundary); -1: not staged.
+// The staged area of a world opens with a table of one pointer per model record array (kTab*):
+// to the array's copy in shared memory when its part is staged, else to the world's records in
+// global memory. The step reads a record through the table, so no pointer stays in a register.
+enum StageTab {
+  kTabBi, kTabBj, kTabInfo, kTabP0, kTabP1, kTabP2, kTabP3, kTabP4, kTabA0, kTabA1, kTabAnc, kTabFac,
+  kTabItems, kTabAbody, kTabEntries
+};
+constexpr int kStageTableFloats = 32;  // kTabEntries 8-byte pointers, rounded up to 16 bytes
+static_assert(2 * kTabEntries <= kStageTableFloats, "stage table");
+
+// Float offsets of the staged parts of one world (each on a 16-byte boundary, after the table);
+// -1: not staged. total: the whole staged area, 0 when nothing is staged.
 struct StageLayout {
   int bi, bp0, bp1, bp3, bj, bp4, anc, info, items, fac, bp2, ap0, ap1, abody, total;
   __host__ __device__ static int r4(int n) { return (n + 3) & ~3; }
   __host__ __device__ static StageLayout make(int mask, int nb, int nm, int na, int nfac, int nitem) {
     StageLayout S;
-    int o = 0;
+    int o = mask ? kStageTableFloats : 0;
     auto take = [&](int part, int floats) {
       if (!(mask & part)) return -1;
       const int at = o;

@@ -171,15 +171,9 @@ struct WorldView {
   // body-level bounds (nL + 1), factorisation-level bounds, fac_tgt bases and first work
   // items (nBL + 1 each)
   const int *lv, *bb, *bf, *ib;
-  // the world's model records, indexed world-locally, for the staged instantiation of the
-  // step (ST): the model in global memory, or the copies stage_world makes in shared memory.
-  // The other instantiation reads the model directly (rec_* below), so these stay unused
-  const int4 *bi, *bj, *info;
-  const float4 *bp0, *bp1, *bp2, *bp3, *bp4, *ap0, *ap1;
-  const unsigned* anc;
-  const int2* fac;
-  const int4* items;
-  const int* abody;
+  // the staged instantiation of the step (ST): the world's table of record pointers (StageTab),
+  // written by stage_world. The other instantiation reads the model directly (rec_* below).
+  const void* const* tab;
 };
 
 // One world's state arrays, indexed world-locally.
@@ -233,37 +227,56 @@ HD WorldView world_view(const DevModel& m, int w) {
   v.bb = m.bl_bound + v.BL0;
   v.bf = m.bl_fbase + v.BL0;
   v.ib = m.bl_ibase + v.BL0;
-  v.bi = m.bi + v.b0; v.bj = m.bj + v.b0; v.info = m.bl_info + v.b0;
-  v.bp0 = m.bp0 + v.b0; v.bp1 = m.bp1 + v.b0; v.bp2 = m.bp2 + v.b0; v.bp3 = m.bp3 + v.b0; v.bp4 = m.bp4 + v.b0;
-  v.ap0 = m.ap0 + v.a0; v.ap1 = m.ap1 + v.a0; v.abody = m.apple_body + v.a0;
-  v.anc = m.anc + v.m0;
-  v.fac = m.fac_tgt + v.f0;
-  v.items = m.fitem + v.it0;
+  v.tab = nullptr;
   return v;
 }
 
-// A world's model records, world-locally indexed: from the staged view (ST), else straight from
-// the model (whose pointers are kernel parameters, so they cost no registers).
-template <bool ST> HD int4 rec_bi(const DevModel& m, const WorldView& v, int b) { return ST ? v.bi[b] : m.bi[v.b0 + b]; }
-template <bool ST> HD int4 rec_bj(const DevModel& m, const WorldView& v, int b) { return ST ? v.bj[b] : m.bj[v.b0 + b]; }
-template <bool ST> HD float4 rec_p0(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp0[b] : m.bp0[v.b0 + b]; }
-template <bool ST> HD float4 rec_p1(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp1[b] : m.bp1[v.b0 + b]; }
-template <bool ST> HD float4 rec_p2(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp2[b] : m.bp2[v.b0 + b]; }
-template <bool ST> HD float4 rec_p3(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp3[b] : m.bp3[v.b0 + b]; }
-template <bool ST> HD float4 rec_p4(const DevModel& m, const WorldView& v, int b) { return ST ? v.bp4[b] : m.bp4[v.b0 + b]; }
-template <bool ST> HD float4 rec_a0(const DevModel& m, const WorldView& v, int a) { return ST ? v.ap0[a] : m.ap0[v.a0 + a]; }
-template <bool ST> HD float4 rec_a1(const DevModel& m, const WorldView& v, int a) { return ST ? v.ap1[a] : m.ap1[v.a0 + a]; }
+// A world's model records, world-locally indexed: through the world's table of record pointers
+// (ST), else straight from the model (whose pointers are kernel parameters, so they cost no
+// registers). The table sits in shared memory: a read costs one shared load and holds nothing.
+template <class T> HD const T* tab_ptr(const WorldView& v, int e) { return (const T*)v.tab[e]; }
+template <bool ST> HD int4 rec_bi(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<int4>(v, kTabBi)[b] : m.bi[v.b0 + b];
+}
+template <bool ST> HD int4 rec_bj(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<int4>(v, kTabBj)[b] : m.bj[v.b0 + b];
+}
+template <bool ST> HD float4 rec_p0(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<float4>(v, kTabP0)[b] : m.bp0[v.b0 + b];
+}
+template <bool ST> HD float4 rec_p1(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<float4>(v, kTabP1)[b] : m.bp1[v.b0 + b];
+}
+template <bool ST> HD float4 rec_p2(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<float4>(v, kTabP2)[b] : m.bp2[v.b0 + b];
+}
+template <bool ST> HD float4 rec_p3(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<float4>(v, kTabP3)[b] : m.bp3[v.b0 + b];
+}
+template <bool ST> HD float4 rec_p4(const DevModel& m, const WorldView& v, int b) {
+  return ST ? tab_ptr<float4>(v, kTabP4)[b] : m.bp4[v.b0 + b];
+}
+template <bool ST> HD float4 rec_a0(const DevModel& m, const WorldView& v, int a) {
+  return ST ? tab_ptr<float4>(v, kTabA0)[a] : m.ap0[v.a0 + a];
+}
+template <bool ST> HD float4 rec_a1(const DevModel& m, const WorldView& v, int a) {
+  return ST ? tab_ptr<float4>(v, kTabA1)[a] : m.ap1[v.a0 + a];
+}
 template <bool ST> HD int rec_abody(const DevModel& m, const WorldView& v, int a) {
-  return ST ? v.abody[a] : m.apple_body[v.a0 + a];
+  return ST ? tab_ptr<int>(v, kTabAbody)[a] : m.apple_body[v.a0 + a];
 }
 template <bool ST> HD int4 rec_info(const DevModel& m, const WorldView& v, int i) {
-  return ST ? v.info[i] : m.bl_info[v.b0 + i];
+  return ST ? tab_ptr<int4>(v, kTabInfo)[i] : m.bl_info[v.b0 + i];
 }
 template <bool ST> HD int4 rec_item(const DevModel& m, const WorldView& v, int i) {
-  return ST ? v.items[i] : m.fitem[v.it0 + i];
+  return ST ? tab_ptr<int4>(v, kTabItems)[i] : m.fitem[v.it0 + i];
 }
-template <bool ST> HD const unsigned* rec_anc(const DevModel& m, const WorldView& v) { return ST ? v.anc : m.anc + v.m0; }
-template <bool ST> HD const int2* rec_fac(const DevModel& m, const WorldView& v) { return ST ? v.fac : m.fac_tgt + v.f0; }
+template <bool ST> HD const unsigned* rec_anc(const DevModel& m, const WorldView& v) {
+  return ST ? tab_ptr<unsigned>(v, kTabAnc) : m.anc + v.m0;
+}
+template <bool ST> HD const int2* rec_fac(const DevModel& m, const WorldView& v) {
+  return ST ? tab_ptr<int2>(v, kTabFac) : m.fac_tgt + v.f0;
+}
 
 HD f3 apple_force(const StepArgs& a, int ga, int t_abs) {
   f3 f = mk(0.f, 0.f, 0.f);
@@ -1296,46 +1309,57 @@ HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
 #endif
 }
 // Copy the parts of the world's model named by `mask` (StagePart) into shared memory at dst
-// (StageLayout offsets) and point the view at the copies. Group-parallel, no closing barrier:
-// the caller's next group barrier publishes the copies.
+// (StageLayout offsets, after the table) and write the world's table of record pointers at dst:
+// each to its copy, or to the model in global memory for a part not staged. Group-parallel, no
+// closing barrier: the caller's next group barrier publishes the copies and the table.
 template <int TPW>
-HD void stage_world(WorldView& v, int mask, float* dst, const Group<TPW>& g) {
+HD void stage_world(const DevModel& m, WorldView& v, int mask, float* dst, const Group<TPW>& g) {
   const StageLayout S = StageLayout::make(mask, v.nb, v.nm, v.na, v.nfac, v.nitem);
-  auto rec4 = [&](int off, const void* src, int count) -> const void* {
-    copy4<TPW>(dst + off, (const float*)src, 4 * count, g);
-    return dst + off;
+  const void** tab = (const void**)dst;
+  // lane e of the group writes entry e (the group has at least kTabEntries lanes)
+  auto entry = [&](int e, int off, const void* global) {
+    if (g.lane == e) tab[e] = off >= 0 ? (const void*)(dst + off) : global;
   };
-  if (S.bi >= 0) {
-    v.bi = (const int4*)rec4(S.bi, v.bi, v.nb);
-    v.bp0 = (const float4*)rec4(S.bp0, v.bp0, v.nb);
-    v.bp1 = (const float4*)rec4(S.bp1, v.bp1, v.nb);
-  }
-  if (S.bp3 >= 0) v.bp3 = (const float4*)rec4(S.bp3, v.bp3, v.nb);
-  if (S.bj >= 0) {
-    v.bj = (const int4*)rec4(S.bj, v.bj, v.nb);
-    v.bp4 = (const float4*)rec4(S.bp4, v.bp4, v.nb);
-  }
+  entry(kTabBi, S.bi, m.bi + v.b0);
+  entry(kTabBj, S.bj, m.bj + v.b0);
+  entry(kTabInfo, S.info, m.bl_info + v.b0);
+  entry(kTabP0, S.bp0, m.bp0 + v.b0);
+  entry(kTabP1, S.bp1, m.bp1 + v.b0);
+  entry(kTabP2, S.bp2, m.bp2 + v.b0);
+  entry(kTabP3, S.bp3, m.bp3 + v.b0);
+  entry(kTabP4, S.bp4, m.bp4 + v.b0);
+  entry(kTabA0, S.ap0, m.ap0 + v.a0);
+  entry(kTabA1, S.ap1, m.ap1 + v.a0);
+  entry(kTabAnc, S.anc, m.anc + v.m0);
+  entry(kTabFac, S.fac, m.fac_tgt + v.f0);
+  entry(kTabItems, S.items, m.fitem + v.it0);
+  entry(kTabAbody, S.abody, m.apple_body + v.a0);
+  v.tab = tab;
+  auto rec4 = [&](int off, const void* src, int count) {
+    if (off >= 0) copy4<TPW>(dst + off, (const float*)src, 4 * count, g);
+  };
+  rec4(S.bi, m.bi + v.b0, v.nb);
+  rec4(S.bp0, m.bp0 + v.b0, v.nb);
+  rec4(S.bp1, m.bp1 + v.b0, v.nb);
+  rec4(S.bp3, m.bp3 + v.b0, v.nb);
+  rec4(S.bj, m.bj + v.b0, v.nb);
+  rec4(S.bp4, m.bp4 + v.b0, v.nb);
+  rec4(S.info, m.bl_info + v.b0, v.nb);
+  rec4(S.items, m.fitem + v.it0, v.nitem);
+  rec4(S.bp2, m.bp2 + v.b0, v.nb);
+  rec4(S.ap0, m.ap0 + v.a0, v.na);
+  rec4(S.ap1, m.ap1 + v.a0, v.na);
   if (S.anc >= 0) {
     unsigned* d = (unsigned*)(dst + S.anc);
-    for (int i = g.lane; i < v.nm; i += TPW) d[i] = v.anc[i];
-    v.anc = d;
-  }
-  if (S.info >= 0) {
-    v.info = (const int4*)rec4(S.info, v.info, v.nb);
-    v.items = (const int4*)rec4(S.items, v.items, v.nitem);
+    for (int i = g.lane; i < v.nm; i += TPW) d[i] = m.anc[v.m0 + i];
   }
   if (S.fac >= 0) {
     int2* d = (int2*)(dst + S.fac);
-    for (int i = g.lane; i < v.nfac; i += TPW) d[i] = v.fac[i];
-    v.fac = d;
+    for (int i = g.lane; i < v.nfac; i += TPW) d[i] = m.fac_tgt[v.f0 + i];
   }
-  if (S.bp2 >= 0) {
-    v.bp2 = (const float4*)rec4(S.bp2, v.bp2, v.nb);
-    v.ap0 = (const float4*)rec4(S.ap0, v.ap0, v.na);
-    v.ap1 = (const float4*)rec4(S.ap1, v.ap1, v.na);
+  if (S.abody >= 0) {
     int* d = (int*)(dst + S.abody);
-    for (int i = g.lane; i < v.na; i += TPW) d[i] = v.abody[i];
-    v.abody = d;
+    for (int i = g.lane; i < v.na; i += TPW) d[i] = m.apple_body[v.a0 + i];
   }
 }
 
@@ -1392,7 +1416,7 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
   const WState sg = world_state(S, v, w);
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);
   // the model records this class stages sit after the workspace, for all the world's steps
-  if (ST && a.stage_mask && !a.global_ws) stage_world<TPW>(v, a.stage_mask, ws + a.ws_floats, g);
+  if (ST) stage_world<TPW>(m, v, a.stage_mask, ws + a.ws_floats, g);  // launched with a shared workspace
   copy_state<TPW>(s, sg, v, g);  // ends on a group barrier
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);

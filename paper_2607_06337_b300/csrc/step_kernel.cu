@@ -84,7 +84,8 @@ void launch_rollout_t(int tpw, int threads, int blocks, size_t smem_bytes, cudaS
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t st,
                     const DevModel& m, const DevState& s, const StepArgs& a) {
   const int threads = tpw * groups_per_block;
-  if (a.stage_mask) launch_rollout_t<true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+  // the staged instantiation keeps the world's records and their table after its workspace
+  if (a.stage_mask && !a.global_ws) launch_rollout_t<true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
   else launch_rollout_t<false>(tpw, threads, blocks, smem_bytes, st, m, s, a);
 }
 
