@@ -829,6 +829,45 @@ ot_status launch_class(ot_model* m, ot_state* s, int k, StepArgs a, cudaStream_t
   return launch_class_shaped(m, s, k, a, sh, st);
 }
 
+// One stream and one join event per size class, and the fork event (created once per model):
+// the classes of a rollout, a backward or an autotune run concurrently on them.
+ot_status ensure_class_streams(ot_model* m) {
+  const int nk = (int)m->P.classes.size();
+  if (!m->fork_event) OT_CUDA(cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming));
+  while ((int)m->class_streams.size() < nk) {
+    cudaStream_t c = nullptr;
+    cudaEvent_t ev = nullptr;
+    OT_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
+    m->class_streams.push_back(c);
+    OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    m->join_events.push_back(ev);
+  }
+  return OT_OK;
+}
+
+// Time one launch of every class at its current schedule, the classes concurrent as a rollout
+// runs them: each on its own stream, forked from and joined back to st, largest first.
+ot_status time_classes_together(ot_model* m, ot_state* s, const StepArgs& a, cudaStream_t st, cudaEvent_t e0,
+                                cudaEvent_t e1, float* ms) {
+  const int nk = (int)m->P.classes.size();
+  OT_CUDA(cudaEventRecord(e0, st));
+  OT_CUDA(cudaEventRecord(m->fork_event, st));
+  ot_status result = OT_OK;
+  for (int k = nk - 1; k >= 0; --k) {
+    cudaStream_t sk = m->class_streams[k];
+    OT_CUDA(cudaStreamWaitEvent(sk, m->fork_event, 0));
+    if (result == OT_OK) result = launch_class(m, s, k, a, sk);
+    // always join, so st waits for whatever was enqueued
+    OT_CUDA(cudaEventRecord(m->join_events[k], sk));
+    OT_CUDA(cudaStreamWaitEvent(st, m->join_events[k], 0));
+  }
+  OT_CUDA(cudaEventRecord(e1, st));
+  if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (result != OT_OK) return result;
+  OT_CUDA(cudaEventElapsedTime(ms, e0, e1));
+  return OT_OK;
+}
+
 ot_status fill_pulls(StepArgs& a, const ot_force_schedule* pulls) {
   if (pulls && pulls->force) {
     if (!pulls->start || !pulls->end) return OT_EINVAL;
@@ -1218,14 +1257,9 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
     if (r != OT_OK) return r;
   }
   const int nk = (int)m->P.classes.size();
-  if (!m->fork_event) OT_CUDA(cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming));
-  while ((int)m->class_streams.size() < nk) {
-    cudaStream_t c = nullptr;
-    cudaEvent_t ev = nullptr;
-    OT_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
-    m->class_streams.push_back(c);
-    OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    m->join_events.push_back(ev);
+  {
+    const ot_status r = ensure_class_streams(m);
+    if (r != OT_OK) return r;
   }
   OT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   const long long before = g_launches.load();
@@ -1336,13 +1370,21 @@ ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
 ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void* stream) {
   if (!m || !s || s->model != m || n_steps < 1 || !(dt > 0)) return OT_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const ot_status r = ensure_class_streams(m);
+    if (r != OT_OK) return r;
+  }
   cudaEvent_t e0, e1;
   OT_CUDA(cudaEventCreate(&e0));
   OT_CUDA(cudaEventCreate(&e1));
   StepArgs a = base_args(m, dt);
   a.n_steps = n_steps;
   ot_status result = OT_OK;
-  for (int k = 0; k < (int)m->P.classes.size() && result == OT_OK; ++k) {
+  const int nk = (int)m->P.classes.size();
+  // Pass 1, each class alone: every candidate timed once after a warm-up; the fastest few kept.
+  constexpr int kKeep = 3;
+  std::vector<std::vector<ot_schedule>> kept(nk);
+  for (int k = 0; k < nk && result == OT_OK; ++k) {
     ClassInfo& ci = m->P.classes[k];
     const ot_schedule keep = ci.sched;
     std::vector<ot_schedule> cands;
@@ -1356,9 +1398,9 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
           if (c.global_workspace && (g > 1 || stage != 0)) continue;
           cands.push_back(c);
         }
-    float best = 1e30f;
-    ot_schedule best_s = keep;
-    for (const ot_schedule& c : cands) {
+    std::vector<std::pair<float, int>> timed;
+    for (int i = 0; i < (int)cands.size(); ++i) {
+      const ot_schedule& c = cands[i];
       ci.sched = c;
       if (c.stage == -1) {  // automatic staging that stages nothing repeats the stage-0 candidate
         Shape sh{};
@@ -1376,6 +1418,31 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
         break;
       }
       cudaEventElapsedTime(&ms, e0, e1);
+      timed.push_back({ms, i});
+    }
+    std::sort(timed.begin(), timed.end());
+    for (int j = 0; j < (int)timed.size() && j < kKeep; ++j) kept[k].push_back(cands[timed[j].second]);
+    ci.sched = kept[k].empty() ? keep : kept[k][0];
+  }
+  // Pass 2, the classes together as a rollout runs them (concurrently, one stream each): a
+  // schedule that is fastest alone can lose once the other classes share the SMs. Largest class
+  // first, each kept candidate is timed with the others at their current choice (best of two
+  // timings after a warm-up), and the one with the shortest whole-batch time stays.
+  for (int k = nk - 1; k >= 0 && result == OT_OK && nk > 1; --k) {
+    ClassInfo& ci = m->P.classes[k];
+    if (kept[k].size() < 2) continue;
+    float best = 1e30f;
+    ot_schedule best_s = ci.sched;
+    for (const ot_schedule& c : kept[k]) {
+      ci.sched = c;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3 && result == OT_OK; ++rep) {
+        float t = 0;
+        const ot_status r = time_classes_together(m, s, a, st, e0, e1, &t);
+        if (r == OT_ECUDA) result = r;
+        if (r != OT_OK) break;
+        if (rep > 0) ms = std::min(ms, t);  // the first launch is the warm-up
+      }
       if (ms < best) {
         best = ms;
         best_s = c;
@@ -1624,14 +1691,9 @@ ot_status ot_rollout_backward(ot_model* m, ot_state* s, int32_t n_steps, int32_t
   float* work = (float*)workspace;
   // the classes run concurrently: each on its own stream, forked from and joined back to `stream`
   const int nk = (int)m->P.classes.size();
-  if (!m->fork_event) OT_CUDA(cudaEventCreateWithFlags(&m->fork_event, cudaEventDisableTiming));
-  while ((int)m->class_streams.size() < nk) {
-    cudaStream_t c = nullptr;
-    cudaEvent_t ev = nullptr;
-    OT_CUDA(cudaStreamCreateWithFlags(&c, cudaStreamNonBlocking));
-    m->class_streams.push_back(c);
-    OT_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    m->join_events.push_back(ev);
+  {
+    const ot_status r = ensure_class_streams(m);
+    if (r != OT_OK) return r;
   }
   OT_CUDA(cudaEventRecord(m->fork_event, cs));
   ot_status result = OT_OK;
