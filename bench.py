@@ -686,7 +686,8 @@ def phase_clock_run(args):
 def backward_phase_run(args, dev):
     """The backward's phase clocks on the differentiation workload (--adj-workload), for each
     record form: the forward's tape (when it fits in half the free memory here) and checkpoints every
-    --adj-ckpt steps; one warm-up backward, then one counted."""
+    --adj-ckpt steps; the backward autotuned per form as the bench's, one warm-up backward, then
+    one counted."""
     import torch
     from paper_2607_06337_b300 import inputs as I
     from paper_2607_06337_b300 import orchard as B
@@ -706,6 +707,8 @@ def backward_phase_run(args, dev):
         sim.reset()
         sim.rollout(n, record=rec)
         dt = torch.full_like(tips, 1e-3)
+        if not args.no_autotune:
+            sim.autotune_backward(n, rec, dt)
         for k in range(2):
             if k == 1:
                 torch.cuda.synchronize()
@@ -716,7 +719,8 @@ def backward_phase_run(args, dev):
         per = []
         for k, row in enumerate(rows):
             total = sum(row[p] for p in B.BACK_PHASES)
-            per.append({"class": k, "world_steps": int(row["world_steps"]), "cycles_per_world_step": total,
+            per.append({"class": k, "threads_per_world": sim.backward_schedules()[k],
+                        "world_steps": int(row["world_steps"]), "cycles_per_world_step": total,
                         "phases": {p: round(row[p], 1) for p in B.BACK_PHASES}})
         out[form] = per
         del tips, buf, rec

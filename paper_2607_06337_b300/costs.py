@@ -15,15 +15,16 @@ of DOF ancestors of DOF i):
   flops = 589 n_b + 182 n_a + 48 n_v + 24 E + 3 P.
 
 Adjoint, per world and step of the backward pass (n_t tips): with checkpoints the segment
-replay runs the forward step once more and saves its records (factors included), so the
-reverse recomputes nothing; with the forward's tape no step runs again. Then
+replay runs the forward step once more and saves its records (factors and kinematics
+included), so the reverse recomputes nothing; with the forward's tape no step runs again. Then
 
-  tape            138 / body + 75 / DOF   (kinematics, accelerations, virtual velocities)
+  tape             51 / body + 19 / DOF   (the joint-acceleration and virtual-velocity parts; the
+                                           kinematics come from the step's record)
   reverse sweep   978 / body + 189 / DOF + 246 / apple + 21 / tip
   apple update, springs, hang-load sweep and the solve with the step's factors:
                    21 / body + 30 / DOF + 48 / apple + 5 / ancestor entry
 
-  flops = [1 x forward with checkpoints] + 1137 n_b + 294 n_v + 294 n_a + 5 E + 21 n_t.
+  flops = [1 x forward with checkpoints] + 1050 n_b + 238 n_v + 294 n_a + 5 E + 21 n_t.
 
 Bytes: the persistent rollout keeps a world's temporaries on chip and re-reads its model from
 L2, so the unavoidable HBM traffic per rollout is one read of the model and one read and write
@@ -39,8 +40,8 @@ F_DOF = 48
 F_ENTRY = 24
 F_PAIR = 3
 
-A_BODY = 1137
-A_DOF = 294
+A_BODY = 1050
+A_DOF = 238
 A_APPLE = 294
 A_ENTRY = 5
 A_TIP = 21

@@ -64,9 +64,11 @@ HD f3 get3(const float* r, int o) { return mk(r[o], r[o + 1], r[o + 2]); }
 HD m3 getm(const float* r, int o) { return {get3(r, o), get3(r, o + 3), get3(r, o + 6)}; }
 
 // Backward temporaries of one world (floats), at their own base `wa` (shared or global
-// memory), and the snapshots of one checkpoint segment (global memory, `seg`). The C slots
-// come last: the `head` floats before them may live in shared memory while the C slots stay
-// in global memory (reverse_seed / reverse_chain take their base from RevArgs).
+// memory), and the snapshots of one checkpoint segment (global memory, `seg`). The per-DOF and
+// per-apple arrays come first (`small` floats), then the tape T, then the C slots: the arrays
+// before T, or before C (`head`), may live in shared memory while the rest stays in global
+// memory. T is reached through `tb` (set by backward_world: wa + T, or its own base), C through
+// RevArgs::cs.
 struct AdjLayout {
   int T;          // tape, 36 per body: R, x, w, v, alpha, a, Lw, Lv, Ow, Ov (see tape_body)
   int C;          // 44 per body: cotangents a body sends to its parent's tape outputs (36),
@@ -80,14 +82,15 @@ struct AdjLayout {
   int ub, vb;     // per apple x3: cotangents of the step-start u (or x), v
   int ub1, vb1;   // per apple x3: of the step-end u', v'
   int vh;         // per apple x3: cotangent of the new hang-point velocity
+  int small;      // floats before T
   int head;       // floats before C
   int total;      // floats at wa
   int snap;       // words per snapshot: the private state, staged in the forward workspace
+  float* tb;      // the tape T of the world being reversed
   HD static AdjLayout make(int nb, int nv, int na) {
     // every array starts on a 16-byte boundary
     AdjLayout A;
     int o = 0;
-    A.T = o; o += 36 * nb;
     A.AF = o; o += WsLayout::r4(6 * nb);
     A.qb = o; o += WsLayout::r4(nv);
     A.qdb = o; o += WsLayout::r4(nv);
@@ -101,10 +104,13 @@ struct AdjLayout {
     A.ub1 = o; o += WsLayout::r4(3 * na);
     A.vb1 = o; o += WsLayout::r4(3 * na);
     A.vh = o; o += WsLayout::r4(3 * na);
+    A.small = o;
+    A.T = o; o += 36 * nb;
     A.head = o;
     A.C = o; o += 44 * nb;
     A.snap = WsLayout::snap_words(nb, nv, na);
     A.total = o;
+    A.tb = nullptr;
     return A;
   }
 };
@@ -178,7 +184,7 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
   f3 xp, wp, vp, alp, ap, lwp, lvp, owp, ovp;
   if (p >= 0) {
     float tp[36];
-    ld_rec(wa + A.T + 36 * p, tp);
+    ld_rec(A.tb + 36 * p, tp);
     Rp = getm(tp, 0);
     xp = get3(tp, 9); wp = get3(tp, 12); vp = get3(tp, 15); alp = get3(tp, 18); ap = get3(tp, 21);
     lwp = get3(tp, 24); lvp = get3(tp, 27); owp = get3(tp, 30); ovp = get3(tp, 33);
@@ -214,7 +220,53 @@ HD void tape_body(const DevModel& m, const WState& s, const WorldView& v, const 
   put3(t, 0, R.c0); put3(t, 3, R.c1); put3(t, 6, R.c2);
   put3(t, 9, xb); put3(t, 12, w); put3(t, 15, vin); put3(t, 18, al); put3(t, 21, aa);
   put3(t, 24, lw); put3(t, 27, lvin); put3(t, 30, ow); put3(t, 33, ovin);
-  st_rec(wa + A.T + 36 * b, t);
+  st_rec(A.tb + 36 * b, t);
+}
+
+// tape_body for a step with a record: the kinematics come from the record's kinematic part
+// (kin: R, x_b, w, v at x_b and the velocity-product accelerations, as the forward's kinematics
+// sweep found them), so only the parts linear in Delta, lambda and qd' are swept here. The joint
+// accelerations qdd = Delta / dt add alpha_D = alpha_D,p + sum_j qdd_j e_j and a_D = a_D,p +
+// alpha_D,p x d on top of the record's accelerations; the parent's parts come back as its tape's
+// accelerations less its record's. The DOF axes e are the step's (restored at L.E).
+HD void tape_body_recorded(const DevModel& m, const WorldView& v, const WsLayout& L, const AdjLayout& A,
+                           const float* ws, float* wa, const float* delta, float inv_dt, const float* lam,
+                           const float* qd1, int b, const float* kin) {
+  const int4 bi = m.bi[v.b0 + b];
+  const int p = bi.x;
+  const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
+  float k[WsLayout::kKin];
+  ld_rec(kin + WsLayout::kKin * b, k);
+  const f3 xb = get3(k, 9);
+  f3 xp, ald, aad, lw, lvp, ow, ovp;
+  if (p >= 0) {
+    float tp[36];
+    ld_rec(A.tb + 36 * p, tp);
+    const float4* kp = reinterpret_cast<const float4*>(kin + WsLayout::kKin * p);
+    const float4 k4 = kp[4], k5 = kp[5];  // the parent's record: al (k4.z, k4.w, k5.x), a (k5.yzw)
+    xp = get3(tp, 9);
+    ald = get3(tp, 18) - mk(k4.z, k4.w, k5.x);
+    aad = get3(tp, 21) - mk(k5.y, k5.z, k5.w);
+    lw = get3(tp, 24); lvp = get3(tp, 27); ow = get3(tp, 30); ovp = get3(tp, 33);
+  } else {
+    xp = ald = aad = lw = lvp = ow = ovp = mk(0, 0, 0);
+  }
+  const f3 d = xb - xp;
+  const f3 lvin = lvp + cross(lw, d), ovin = ovp + cross(ow, d);
+  aad = aad + cross(ald, d);
+  for (int j = 0; j < nd; ++j) {
+    const int i = dof0 + j;
+    const f3 e = ld3(ws + L.E + 3 * i);
+    ald = ald + (delta[i] * inv_dt) * e;
+    lw = lw + lam[i] * e;
+    ow = ow + qd1[i] * e;
+  }
+  float t[36];
+#pragma unroll
+  for (int j = 0; j < 18; ++j) t[j] = k[j];  // R, x_b, w, v at x_b
+  put3(t, 18, get3(k, 18) + ald); put3(t, 21, get3(k, 21) + aad);
+  put3(t, 24, lw); put3(t, 27, lvin); put3(t, 30, ow); put3(t, 33, ovin);
+  st_rec(A.tb + 36 * b, t);
 }
 
 // Reverse of a 3x3 symmetric-product term: G accumulates d(phi)/d(Io) as a general matrix.
@@ -279,7 +331,7 @@ HD void reverse_seed(const DevModel& m, const WState& s, const StepArgs& a, cons
 
   // own forward values
   float t[36];
-  ld_rec(wa + A.T + 36 * b, t);
+  ld_rec(A.tb + 36 * b, t);
   const m3 R = getm(t, 0);
   const f3 w = get3(t, 12), vin = get3(t, 15), al = get3(t, 18), aa = get3(t, 21);
   const f3 lw = get3(t, 24), lv = get3(t, 27), ow = get3(t, 30), ov = get3(t, 33);
@@ -475,14 +527,14 @@ HD void reverse_chain(const DevModel& m, const WState& s, const StepArgs& a, con
   m3 Rb_ = k0.R;
   const f3 xbb = k0.x, lvb = k0.lv, ovb = k0.ov, owh = k0.owh, ovh = k0.ovh;
   f3 wb_ = k0.w, vb_ = k0.v, alb = k0.al, ab_ = k0.a, lwb = k0.lw, owb = k0.ow;
-  const f3 vin = get3(wa + A.T + 36 * b, 15);  // the body's own v at x_b
+  const f3 vin = get3(A.tb + 36 * b, 15);  // the body's own v at x_b
 
   // reverse of the DOF loop: recompute its intermediates from the parent's tape
   m3 Rp;
   f3 wp, alp, lwp, owp;
   if (p >= 0) {
     float tp[36];
-    ld_rec(wa + A.T + 36 * p, tp);
+    ld_rec(A.tb + 36 * p, tp);
     Rp = getm(tp, 0);
     wp = get3(tp, 12); alp = get3(tp, 18); lwp = get3(tp, 24); owp = get3(tp, 30);
   } else {
@@ -751,7 +803,7 @@ __host__ __device__ __noinline__ void rails_adjoint(const DevModel& m, const WSt
       const int b = m.apple_body[ga];
       if (a.tether_implicit && ws[L.SN + b] == 0.f) {
         float t[36];
-        ld_rec(wa + A.T + 36 * b, t);
+        ld_rec(A.tb + 36 * b, t);
         const m3 R = getm(t, 0);
         const f3 lw = get3(t, 24), lv = get3(t, 27);
         const f3 rh = mul(R, xyz(A0));
@@ -777,7 +829,7 @@ enum BackPhase { kBpApples = 0, kBpSolve, kBpLsweep, kBpSeed, kBpChain, kBpResto
 template <int TPW>
 HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, const BackArgs& ba,
                      const WorldView& v, const WsLayout& L, const AdjLayout& A, float* ws, float* wa, float* cs,
-                     const Group<TPW>& g, int t, f3 gv, PhaseClock* pc = nullptr) {
+                     const float* kin, const Group<TPW>& g, int t, f3 gv, PhaseClock* pc = nullptr) {
   const float dt = a.dt;
   const int t_abs = a.step0 + t;
   for (int i = g.lane; i < v.nv; i += TPW) {
@@ -813,13 +865,13 @@ HD void reverse_step(const DevModel& m, const WState& s, const StepArgs& a, cons
   solve_factored<TPW>(m, v, L, ws, wa + A.lam, g, false);  // lambda = H^-1 Delta-bar, up to the L sweep
   if (pc) pc->mark(kBpSolve);
   // root to leaf, joint by joint: the L sweep of lambda, the spring and damper terms, and the
-  // tape at the step start (which needs the joint's final lambda)
+  // tape at the step start (which needs the joint's final lambda; kinematics from the record)
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
     for (int b = lo + g.lane; b < hi; b += TPW) {
       lsweep_joint(m, v, L, ws, wa + A.lam, m.bi[v.b0 + b].y & 0x0fffffff, m.bj[v.b0 + b]);
       spring_joint(m, s, a, ba, v, A, wa, b, t_abs);
-      tape_body(m, s, v, A, wa, ws + L.r, 1.f / dt, wa + A.lam, wa + A.qd1, b, gv);
+      tape_body_recorded(m, v, L, A, ws, wa, ws + L.r, 1.f / dt, wa + A.lam, wa + A.qd1, b, kin);
     }
     g.sync();
   }
@@ -888,10 +940,17 @@ HD void reverse_recorded(const DevModel& m, const WState& s, const StepArgs& a, 
                          PhaseClock* pc = nullptr) {
   if (pc) pc->start();
   copy4<TPW>(ws + L.S, snap, A.snap, g);
+  const float* kin = rec + WsLayout::kin_offset(v.nb, v.nv, v.nm, v.na);
+#ifdef __CUDA_ARCH__
+  // the record's kinematics are read level by level in the root-to-leaf sweep: bring them into
+  // L2 now, while the rest of the record is copied
+  for (int i = g.lane; i < (WsLayout::kKin * v.nb + 31) / 32; i += TPW)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(kin + 32 * i));
+#endif
   g.sync();
   step_record<TPW>(ws, L, s, wa, A, v, const_cast<float*>(rec), false, g);
   if (pc) pc->mark(kBpRestore);
-  reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, t, gv, pc);
+  reverse_step<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, kin, g, t, gv, pc);
   for (int i = g.lane; i < v.nv; i += TPW) {
     wa[A.qb1 + i] = wa[A.qb + i];
     wa[A.qdb1 + i] = wa[A.qdb + i];
@@ -921,8 +980,10 @@ HD void reverse_segments(const DevModel& m, const StepArgs& a, const BackArgs& b
     load_ckpt(a, v, s, sg, g);
     for (int t = t0; t < t1; ++t) {
       snapshot(ws, L, seg, A, t - t0, true, g);
-      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1);
-      step_record<TPW>(ws, L, s, wa, A, v, recs + (long long)(t - t0) * recw, true, g);
+      float* rec = recs + (long long)(t - t0) * recw;
+      step_world<TPW>(m, s, a, v, L, ws, g, a.step0 + t, gv, -1, nullptr,
+                      rec + WsLayout::kin_offset(v.nb, v.nv, v.nm, v.na));
+      step_record<TPW>(ws, L, s, wa, A, v, rec, true, g);
     }
     if (pc) pc->mark(kBpReplay);
     if (seed && sg == nseg - 1) reverse_final<TPW>(m, s, a, ba, v, L, A, ws, wa, cs, g, gv);
@@ -934,9 +995,10 @@ HD void reverse_segments(const DevModel& m, const StepArgs& a, const BackArgs& b
 }
 
 // Backward pass of one world over a recorded rollout.
-// ws: the forward step's temporaries (WsLayout), wa: the backward temporaries (AdjLayout),
-// wc: the C slots when they are not at wa + A.C (null: they are), seg: ckpt_every snapshots
-// and step records (global memory); ws, wa and wc may be in shared or global memory.
+// ws: the forward step's temporaries (WsLayout; without a step to replay, MODE 1, the compact
+// WsLayout::make_reverse), wa: the backward temporaries (AdjLayout), wt / wc: the tape T / the
+// C slots when they are not at wa + A.T / wa + A.C (null: they are), seg: ckpt_every snapshots
+// and step records (global memory); ws, wa, wt and wc may be in shared or global memory.
 // MODE 0: checkpoints only (reverse_segments over the whole rollout). MODE 1: every step's
 // start state and record are in the forward's tape, and the steps are reversed last to first
 // straight from it. MODE 2: the tape covers the last a.tape_steps steps, reversed from it
@@ -944,10 +1006,11 @@ HD void reverse_segments(const DevModel& m, const StepArgs& a, const BackArgs& b
 // kernels, each compiled for its own path.
 template <int TPW, int MODE>
 HD void backward_world(const DevModel& m, const StepArgs& a, const BackArgs& ba, int w, float* ws, float* wa,
-                       float* wc, float* seg, const Group<TPW>& g) {
+                       float* wt, float* wc, float* seg, const Group<TPW>& g) {
   const WorldView v = world_view(m, w);
-  const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
-  const AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
+  const WsLayout L = MODE == 1 ? WsLayout::make_reverse(v.nb, v.nv, v.nm, v.na) : WsLayout::make(v.nb, v.nv, v.nm, v.na);
+  AdjLayout A = AdjLayout::make(v.nb, v.nv, v.na);
+  A.tb = wt ? wt : wa + A.T;
   float* cs = wc ? wc : wa + A.C;
   const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);  // the world's private state
   const long long recw = WsLayout::record_words(v.nb, v.nv, v.nm, v.na);

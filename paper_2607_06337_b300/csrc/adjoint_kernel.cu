@@ -7,7 +7,9 @@
 //   0: none (forward and backward temporaries in the global slot),
 //   1: the forward step's temporaries (WsLayout),
 //   2: the forward step's and the backward's (WsLayout, then AdjLayout),
-//   3: the forward step's and the backward's up to the C slots, which open the global slot.
+//   3: the forward step's and the backward's up to the C slots, which open the global slot,
+//   4: the forward step's and the backward's up to the tape T; T, then the C slots, open the
+//      global slot.
 #include "adjoint_device.cuh"
 
 namespace orchard {
@@ -26,8 +28,14 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
   const int groups = blockDim.x / TPW;
   float* slot = work + (long long)(blockIdx.x * groups + g.id) * sh.global_floats;
   float* local = smem + (long long)g.id * sh.smem_floats;
-  float *ws, *wa, *seg, *wc = nullptr;
-  if (sh.mode == 3) {
+  float *ws, *wa, *seg, *wt = nullptr, *wc = nullptr;
+  if (sh.mode == 4) {
+    ws = local;
+    wa = local + sh.fwd_floats;
+    wt = slot;
+    wc = slot + sh.t_floats;
+    seg = wc + sh.c_floats;
+  } else if (sh.mode == 3) {
     ws = local;
     wa = local + sh.fwd_floats;
     wc = slot;
@@ -51,7 +59,7 @@ __global__ void __launch_bounds__(kBackMaxThreads, 2) backward_kernel(DevModel m
     const int qi = next[g.id];
     g.sync();
     if (qi >= a.q_end - a.q_begin) break;
-    backward_world<TPW, MODE>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wc, seg, g);
+    backward_world<TPW, MODE>(m, a, ba, m.queue[a.q_begin + qi], ws, wa, wt, wc, seg, g);
   }
 }
 
@@ -111,6 +119,10 @@ cudaError_t backward_attributes(int tpw, int mode, int groups_per_block, size_t 
 
 long long backward_adj_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).total; }
 long long backward_adj_head_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).head; }
+long long backward_adj_small_floats(int nb, int nv, int na) { return AdjLayout::make(nb, nv, na).small; }
+long long backward_reverse_ws_floats(int nb, int nv, int nm, int na) {
+  return WsLayout::make_reverse(nb, nv, nm, na).total;
+}
 
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every) {
   return (long long)ckpt_every * WsLayout::tape_unit(nb, nv, nm, na);

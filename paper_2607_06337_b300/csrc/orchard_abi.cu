@@ -1475,9 +1475,13 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce, int tpw = 0) 
   // (measured on B300 with 200-body trees: 256 beat 128)
   p.tpw = tpw > 0 ? tpw : ci.back_tpw > 0 ? ci.back_tpw : (ci.max_nb <= 96 ? 64 : 256);
   BackShape& sh = p.sh;
-  sh.fwd_floats = round16(ci.ws_floats);
+  // without checkpoints no step is replayed: the reverse needs only the compact forward layout
+  sh.fwd_floats = round16(ce == 0 ? backward_reverse_ws_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na)
+                                  : ci.ws_floats);
   sh.adj_floats = round16(backward_adj_floats(ci.max_nb, ci.max_nv, ci.max_na));
+  sh.small_floats = round16(backward_adj_small_floats(ci.max_nb, ci.max_nv, ci.max_na));
   sh.head_floats = round16(backward_adj_head_floats(ci.max_nb, ci.max_nv, ci.max_na));
+  sh.t_floats = round16(36LL * ci.max_nb);
   sh.c_floats = round16(44LL * ci.max_nb);
   const long long seg = round16(backward_seg_floats(ci.max_nb, ci.max_nv, ci.max_nm, ci.max_na, ce));
   const long long lim = (long long)(kSmemLimit / 4);
@@ -1490,8 +1494,9 @@ BackPlan back_plan(const ot_model* m, const ClassInfo& ci, int ce, int tpw = 0) 
     int mode;
     long long smem, global;
   };
-  const Placement cand[4] = {{2, sh.fwd_floats + sh.adj_floats, seg},
+  const Placement cand[5] = {{2, sh.fwd_floats + sh.adj_floats, seg},
                              {3, sh.fwd_floats + sh.head_floats, sh.c_floats + seg},
+                             {4, sh.fwd_floats + sh.small_floats, sh.t_floats + sh.c_floats + seg},
                              {1, sh.fwd_floats, sh.adj_floats + seg},
                              {0, 0, sh.fwd_floats + sh.adj_floats + seg}};
   long long best = -1;

@@ -213,14 +213,37 @@ struct WsLayout {
   // The adjoint's tape of a T-step rollout, per world: T + 1 snapshots of the staged state (before
   // every step, then the final state), then T step records, each holding what the reverse of the
   // step reads from its forward workspace: joint origins and DOF axes, the solution Delta and the
-  // apple data, the snapped flags, the factors, and qd at the step's end.
+  // apple data, the snapped flags, the factors, and qd at the step's end; then (kin_offset) the
+  // step's kinematics as its kinematics sweep found them, kKin floats per body: R (3 columns),
+  // x_b, w, v at x_b, and the velocity-product accelerations alpha, a (gravity as a base
+  // acceleration, no joint acceleration).
+  static constexpr int kKin = 24;
   __host__ __device__ static int snap_words(int nb, int nv, int na) { return r4(state_words(nb, nv, na)); }
-  __host__ __device__ static long long record_words(int nb, int nv, int nm, int na) {
+  __host__ __device__ static long long kin_offset(int nb, int nv, int nm, int na) {
     const WsLayout L = make(nb, nv, nm, na);
     return (long long)r4(L.E - L.X + 3 * nv) + r4(L.AT - L.r + 10 * na) + r4(nb) + r4(nm) + r4(nv);
   }
+  __host__ __device__ static long long record_words(int nb, int nv, int nm, int na) {
+    return kin_offset(nb, nv, nm, na) + (long long)kKin * nb;
+  }
   __host__ __device__ static long long tape_unit(int nb, int nv, int nm, int na) {
     return snap_words(nb, nv, na) + record_words(nb, nv, nm, na);
+  }
+  // The regions a step's reverse reads, packed (the adjoint without a step to replay): joint
+  // origins and DOF axes, the solution and the apple data, the snapped flags, the staged state
+  // and the factors. The sweep temporaries and the inertias (IC, V, R, A, F) are absent (-1).
+  __host__ __device__ static WsLayout make_reverse(int nb, int nv, int nm, int na) {
+    WsLayout L;
+    L.X = 0;
+    L.E = L.X + r4(3 * nb);
+    L.r = L.E + r4(3 * nv);
+    L.AT = L.r + r4(nv);
+    L.SN = L.AT + r4(10 * na);
+    L.S = L.SN + r4(nb);
+    L.M = L.S + r4(state_words(nb, nv, na));
+    L.total = L.M + r4(nm);
+    L.IC = L.V = L.R = L.A = L.F = -1;
+    return L;
   }
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
@@ -284,9 +307,12 @@ struct BackArgs {
 // checkpoint segment's snapshots always in the global slot.
 struct BackShape {
   int mode;
-  long long fwd_floats;     // forward temporaries of the class's largest world (WsLayout)
+  long long fwd_floats;     // forward temporaries of the class's largest world (WsLayout, or
+                            // WsLayout::make_reverse for the tape-only backward)
   long long adj_floats;     // backward temporaries (AdjLayout)
+  long long small_floats;   // the part of them before the tape T (AdjLayout::small)
   long long head_floats;    // the part of them before the C slots (AdjLayout::head)
+  long long t_floats;       // the tape T (36 per body)
   long long c_floats;       // the C slots (44 per body)
   long long smem_floats;    // per group in shared memory
   long long global_floats;  // per slot of the workspace
@@ -299,6 +325,8 @@ void launch_backward(int tpw, int groups_per_block, int blocks, cudaStream_t st,
 cudaError_t backward_attributes(int tpw, int mode, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
 long long backward_adj_floats(int nb, int nv, int na);
 long long backward_adj_head_floats(int nb, int nv, int na);
+long long backward_adj_small_floats(int nb, int nv, int na);
+long long backward_reverse_ws_floats(int nb, int nv, int nm, int na);
 long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,

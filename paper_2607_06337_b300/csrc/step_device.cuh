@@ -395,7 +395,7 @@ HD UpdRec upd_rec(const DevModel& m, const WorldView& v, int b) {
 }
 // Phase 1a for one body (root to leaf, level by level): kinematics, velocities, bias
 // acceleration, snapped flag.
-HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, const KinRec& rec) {
+HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, const KinRec& rec, float* kin) {
   const int4 bi = rec.bi;
   const int p = bi.x;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
@@ -442,6 +442,15 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
   ws[L.SN + b] = snapped ? 1.f : 0.f;
   st3(ws + L.V + kVel * b, w); st3(ws + L.V + kVel * b + 3, vin);
   st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
+  if (kin) {  // the step's record in the adjoint's tape (WsLayout::kin_offset)
+    float4* k4 = reinterpret_cast<float4*>(kin + WsLayout::kKin * b);
+    k4[0] = make_float4(R.c0.x, R.c0.y, R.c0.z, R.c1.x);
+    k4[1] = make_float4(R.c1.y, R.c1.z, R.c2.x, R.c2.y);
+    k4[2] = make_float4(R.c2.z, xb.x, xb.y, xb.z);
+    k4[3] = make_float4(w.x, w.y, w.z, vin.x);
+    k4[4] = make_float4(vin.y, vin.z, al.x, al.y);
+    k4[5] = make_float4(al.z, aa.x, aa.y, aa.z);
+  }
 }
 
 // Phase 1b for one body (all bodies at once, after 1a): spatial inertia, own Newton-Euler
@@ -1224,11 +1233,13 @@ struct PhaseClock {
 
 template <int TPW, bool ST = false>
 HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
-                   float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot, PhaseClock* pc = nullptr) {
-  // 1. root-to-leaf: kinematics, velocities, own forces, apple loads
+                   float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot, PhaseClock* pc = nullptr,
+                   float* kin = nullptr) {
+  // 1. root-to-leaf: kinematics, velocities, own forces, apple loads (and, on a taped step, the
+  // kinematics into the step's record at kin)
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec<ST>(m, v, b));
+    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec<ST>(m, v, b), kin);
     g.sync();
   }
   if (pc) pc->mark(0);
@@ -1407,6 +1418,18 @@ HD __noinline__ void tape_write(float* tape, const long long* tape_off, int n_st
   record_copy<TPW>(ws, L, s.qd, v, rec, true, g);  // ends on a group barrier
 }
 
+// Where a taped step's kinematics go in the adjoint's tape (the step's record, at
+// WsLayout::kin_offset), or null for a step the tape does not cover. Not inlined, as tape_write.
+HD __noinline__ float* tape_kin(float* tape, const long long* tape_off, int n_steps, int tape_steps, int w, int t,
+                                int nb, int nv, int nm, int na) {
+  const int k = t - (n_steps - tape_steps);
+  if (k < 0) return nullptr;
+  const int snap = WsLayout::snap_words(nb, nv, na);
+  float* base = tape + (long long)(tape_steps + 1) * tape_off[w];
+  return base + (long long)(tape_steps + 1) * snap + (long long)k * WsLayout::record_words(nb, nv, nm, na) +
+         WsLayout::kin_offset(nb, nv, nm, na);
+}
+
 // All steps of one world: its state is staged in the workspace for the whole rollout.
 template <int TPW, bool ST = false>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
@@ -1436,7 +1459,9 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
     // the step's first write to the staged state comes after several group barriers
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
     if (pcp) pcp->mark(8);
-    step_world<TPW, ST>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1, pcp);
+    float* kin = a.tape ? tape_kin(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, v.nb, v.nv, v.nm, v.na)
+                        : nullptr;
+    step_world<TPW, ST>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1, pcp, kin);
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
     if (pcp) pcp->mark(8);
     ++steps_run;
