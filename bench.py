@@ -583,18 +583,21 @@ def world_sweep(args, dev):
         return a.elapsed_time(b)
 
     out, headline, acc = [], None, None
-    sched = None
+    # one tree size: the schedules tuned on the headline batch (16384 worlds) serve every batch
+    # with the same size classes
+    tuner = B.Simulator(big.subset(range(16384)), fl, device=dev)
+    tuner.autotune(n_steps=10)
+    sched = tuner.schedules()
+    tuner.close()
+    del tuner
     for n in counts:
         f = big if n == big.n_worlds else big.subset(range(n))
         sim = B.Simulator(f, fl, device=dev)
-        # one tree size: the schedules tuned on the smallest batch serve every batch with the
-        # same size classes
-        if sched is not None and len(sched) == sim.counts.classes:
+        if len(sched) == sim.counts.classes:
             for k, sc in enumerate(sched):
                 B.set_schedule(sim.model, k, sc)
         else:
             sim.autotune(n_steps=10)
-            sched = sim.schedules()
         bodies = costs.body_count(f)
         steps = 100
         sim.reset()

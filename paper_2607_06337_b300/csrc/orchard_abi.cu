@@ -1427,8 +1427,9 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
   // Pass 2, the classes together as a rollout runs them (concurrently, one stream each): a
   // schedule that is fastest alone can lose once the other classes share the SMs. Largest class
   // first, each kept candidate is timed with the others at their current choice (best of two
-  // timings after a warm-up), and the one with the shortest whole-batch time stays.
-  for (int k = nk - 1; k >= 0 && result == OT_OK && nk > 1; --k) {
+  // timings after a warm-up), and the one with the shortest whole-batch time stays. With one
+  // class this re-times its kept candidates, best of two, against the noise of a single timing.
+  for (int k = nk - 1; k >= 0 && result == OT_OK; --k) {
     ClassInfo& ci = m->P.classes[k];
     if (kept[k].size() < 2) continue;
     float best = 1e30f;
