@@ -1314,7 +1314,17 @@ HD void copy4(float* dst, const float* src, int n, const Group<TPW>& g) {
   const int n4 = (n + 3) >> 2;
   float4* d4 = reinterpret_cast<float4*>(dst);
   const float4* s4 = reinterpret_cast<const float4*>(src);
-  for (int i = g.lane; i < n4; i += TPW) d4[i] = s4[i];
+  // four loads in flight per lane before their stores (the regions do not overlap, but through
+  // generic pointers the compiler cannot know it, and would wait out each load in turn)
+  int i = g.lane;
+  for (; i + 3 * TPW < n4; i += 4 * TPW) {
+    const float4 a = s4[i], b = s4[i + TPW], c = s4[i + 2 * TPW], d = s4[i + 3 * TPW];
+    d4[i] = a;
+    d4[i + TPW] = b;
+    d4[i + 2 * TPW] = c;
+    d4[i + 3 * TPW] = d;
+  }
+  for (; i < n4; i += TPW) d4[i] = s4[i];
 #else
   for (int i = g.lane; i < n; i += TPW) dst[i] = src[i];
 #endif
