@@ -334,9 +334,11 @@ ot_status ot_rollout_backward(ot_model* model, ot_state* state, int32_t n_steps,
  * Schedules and autotuning. Size classes are formed at upload from the world sizes.
  * ot_get_schedule / ot_set_schedule read or replace the schedule of class c.
  * ot_autotune times every candidate schedule of every class on `n_steps` steps with CUDA
- * events on `stream` and keeps the fastest. The state serves as scratch: every candidate runs
- * from whatever the previous one left, so its contents (and the world status words) are
- * meaningless afterwards; set it again with ot_state_set before simulating. */
+ * events on `stream`: each class alone, then its three fastest with all classes running
+ * together as a rollout runs them; it keeps the fastest. Every timed launch starts from the
+ * state as it was at the call (the call allocates one device copy of the state arrays, and
+ * frees it before returning), and the state is restored at the end. Synchronous: returns after
+ * the restore has completed on `stream`. */
 ot_status ot_get_schedule(const ot_model* model, int32_t size_class, ot_schedule* sched);
 ot_status ot_set_schedule(ot_model* model, int32_t size_class, const ot_schedule* sched);
 ot_status ot_autotune(ot_model* model, ot_state* state, int32_t n_steps, double dt, void* stream);

@@ -1374,6 +1374,14 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
     const ot_status r = ensure_class_streams(m);
     if (r != OT_OK) return r;
   }
+  // Every timed launch starts from the state as it was at the call (the state arrays, q to the
+  // status words, are contiguous from the buffer's base): a candidate timed on a state that
+  // earlier candidates have advanced would not be timed on the same work. Restored at the end.
+  const size_t state_bytes = state_layout(m).counters;
+  void* saved = nullptr;
+  OT_CUDA(cudaMalloc(&saved, std::max<size_t>(state_bytes, 16)));
+  OT_CUDA(cudaMemcpyAsync(saved, s->base, state_bytes, cudaMemcpyDeviceToDevice, st));
+  auto restore = [&]() { return cudaMemcpyAsync(s->base, saved, state_bytes, cudaMemcpyDeviceToDevice, st); };
   cudaEvent_t e0, e1;
   OT_CUDA(cudaEventCreate(&e0));
   OT_CUDA(cudaEventCreate(&e1));
@@ -1409,6 +1417,10 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
       float ms = 0;
       ot_status r = launch_class(m, s, k, a, st);  // warm-up and attribute set-up
       if (r != OT_OK) continue;
+      if (restore() != cudaSuccess) {
+        result = cuda_fail(cudaGetLastError());
+        break;
+      }
       cudaEventRecord(e0, st);
       r = launch_class(m, s, k, a, st);
       cudaEventRecord(e1, st);
@@ -1439,6 +1451,10 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
       float ms = 1e30f;
       for (int rep = 0; rep < 3 && result == OT_OK; ++rep) {
         float t = 0;
+        if (restore() != cudaSuccess) {
+          result = cuda_fail(cudaGetLastError());
+          break;
+        }
         const ot_status r = time_classes_together(m, s, a, st, e0, e1, &t);
         if (r == OT_ECUDA) result = r;
         if (r != OT_OK) break;
@@ -1451,6 +1467,9 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
     }
     ci.sched = best_s;
   }
+  if (restore() != cudaSuccess && result == OT_OK) result = cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(st) != cudaSuccess && result == OT_OK) result = cuda_fail(cudaGetLastError());
+  cudaFree(saved);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return result;

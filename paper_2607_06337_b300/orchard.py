@@ -544,8 +544,8 @@ class Simulator:
         return out
 
     def autotune(self, n_steps=20, dt=None, stream=None):
-        """Pick every class's fastest schedule; the state is scratch meanwhile, so it is reset
-        to the forest's initial state afterwards."""
+        """Pick every class's fastest schedule, every candidate timed from the current state
+        (ot_autotune restores it); then reset to the forest's initial state."""
         autotune(self.model, self.state, n_steps, self.flags.dt if dt is None else dt, stream)
         self.reset(stream=stream)
 
