@@ -266,6 +266,27 @@ def test_staged_model_records_give_the_same_states(workload, worlds, stage):
         assert out[0]["broken"].sum() + out[0]["detached"].sum() > 0
 
 
+def test_autotune_leaves_the_state_as_it_found_it():
+    """ot_autotune times every launch from a device copy of the state it was given and restores
+    the state at the end: uneven batch trees advanced 50 steps (pulls, a break or detach on the
+    way), then autotuned, hold bit-identical state arrays, status words included."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    f = I.make_forest(I.BATCH, worlds=[0, 700, 1400, 2100, 2800, 3500, 4095])
+    fl = I.Flags()
+    sim = B.Simulator(f, fl)
+    sim.reset()
+    sim.rollout(50)
+    torch.cuda.synchronize()
+    before = _gpu_state(sim)
+    B.autotune(sim.model, sim.state, 5, fl.dt)
+    torch.cuda.synchronize()
+    after = _gpu_state(sim)
+    sim.close()
+    for key in ("q", "qd", "ax", "broken", "break_step", "detached", "detach_step", "status"):
+        np.testing.assert_array_equal(after[key], before[key], err_msg=key)
+
+
 def test_tip_record_matches_oracle():
     f = I.make_forest(I.DIFF, worlds=[0, 1, 2])
     fl = I.Flags()
