@@ -254,9 +254,10 @@ ot_status ot_step(ot_model* model, ot_state* state, const float* ext_force, cons
  *   tape: the adjoint's full tape (ot_tape_bytes gives the size for n_steps; 16-byte aligned):
  *         every step's start state and what the reverse of the step reads from its forward
  *         pass (joint origins, DOF axes, the solution, apple data, the snapped flags, the
- *         factors, the end velocities), so that ot_rollout_backward runs no step again. It
- *         trades memory for the replay of checkpoint segments: about 40 KB per step of a
- *         200-body world (8 GB for 1024 such worlds over 200 steps). Its layout is internal:
+ *         factors, the end velocities, and the kinematics its kinematics sweep found), so
+ *         that ot_rollout_backward runs no step again and rebuilds no kinematics. It
+ *         trades memory for the replay of checkpoint segments: about 59 KB per step of a
+ *         200-body world (11.7 GB for 1024 such worlds over 200 steps). Its layout is internal:
  *         the caller owns the buffer, ot_rollout writes it, and ot_rollout_backward reads it
  *         for the same model and n_steps; keep it unmodified in between.
  *   tape_steps: how many of the rollout's final steps the tape covers (0: all n_steps). With
@@ -318,8 +319,8 @@ ot_status ot_backward_workspace_bytes(const ot_model* model, int32_t ckpt_every,
  * 0 restores the default by tree size: 64 up to 96 bodies, else 256). ot_autotune_backward
  * takes ot_rollout_backward's arguments (a recorded rollout), times each candidate of each
  * class on it with CUDA events on `stream`, one class at a time, and keeps the fastest. The
- * grads then hold meaningless values (they serve as scratch, as the state does for
- * ot_autotune); run ot_rollout_backward again for the gradients. The workspace size
+ * grads then hold meaningless values (they serve as scratch); run ot_rollout_backward again
+ * for the gradients. The workspace size
  * (ot_backward_workspace_bytes) fits every candidate, so it does not change with the choice. */
 ot_status ot_get_backward_schedule(const ot_model* model, int32_t size_class, int32_t* threads_per_world);
 ot_status ot_set_backward_schedule(ot_model* model, int32_t size_class, int32_t threads_per_world);
