@@ -41,6 +41,10 @@ METRIC = "body-steps/s fwd & fwd+adjoint, batched vs plain on B300; frac of FP32
 UNIT = "body-steps/s"
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 sub-partitions x 32)
 ORACLE_WORLDS_PER_CORE = 12      # the oracle's sample: this many worlds per host thread
+# steps each schedule candidate of a batch4096 class is timed on (20 let the picks vary from run
+# to run by 2%: per-world overheads weigh 50x more than in a 1000-step rollout; 50 and 100 gave
+# the same picks)
+TUNE_STEPS = 50
 REF_STEPS = 200                  # the reference arm: simulation steps per bench step
 
 
@@ -501,7 +505,7 @@ def damped_leg(args, dev, forest, S, flush):
     sim = B.Simulator(forest, fl, device=dev)
     stream = torch.cuda.current_stream()
     sim.reset()
-    sim.autotune(n_steps=20)
+    sim.autotune(n_steps=TUNE_STEPS)
     sim.reset()
     sim.rollout(S)
     flush.fill_(1)
@@ -658,7 +662,7 @@ def phase_clock_run(args):
     fl = I.Flags(fp64_twig_diam=0.005 if args.workload == I.STRESS else 0.0)
     sim = B.Simulator(forest, fl, device=dev)
     if not args.no_autotune:
-        sim.autotune(n_steps=20)
+        sim.autotune(n_steps=TUNE_STEPS)
     if args.stage != "auto":
         set_staging(sim, 0 if args.stage == "off" else -1)
     sim.reset()
@@ -761,7 +765,7 @@ def run_ours(args):
 
     if not args.no_autotune:
         reset()
-        sim.autotune(n_steps=20)
+        sim.autotune(n_steps=TUNE_STEPS)
     if args.stage != "auto":
         set_staging(sim, 0 if args.stage == "off" else -1)
     scheds = sim.class_infos()

@@ -132,7 +132,13 @@ typedef struct ot_schedule {
   int32_t threads_per_world;   /* 32, 64, 128, 256 or 512 */
   int32_t worlds_per_block;    /* groups of threads_per_world threads in one block */
   int32_t blocks;              /* persistent grid size (0: enough for one wave) */
-  int32_t global_workspace;    /* 1: per-step temporaries in the state's scratch area */
+  int32_t global_workspace;    /* 1: per-step temporaries in the state's scratch area (fixed
+                                  at upload for classes too large for shared memory);
+                                  0: all in shared memory; 2 (lean: classes of one world per
+                                  SM, 128-512 threads per world): the state, apple records and
+                                  snapped flags in global memory, the rest in shared memory
+                                  (a rollout that writes the adjoint's tape runs such a class
+                                  with 0, at the worlds per block that fit) */
   int32_t stage;               /* model records copied into shared memory per world, for all its
                                   steps (classes in shared memory only): -1 automatic, each of
                                   the parts (1 sweep topology and frames, 8 ancestor rows,

@@ -56,6 +56,9 @@ struct ClassInfo {
   int q_begin, q_end;
   int max_nb, max_nv, max_nm, max_na;
   long long ws_floats;
+  // the lean placement (WsLayout::make_lean), for classes that fit one world per SM at most:
+  // the class's largest shared part and global slot, floats (0: not offered)
+  long long lean_ws_floats = 0, lean_slot_floats = 0;
   ot_schedule sched;
   size_t scratch_off;  // byte offset of this class's scratch in the state buffer (global workspace)
   int scratch_slots;
@@ -466,10 +469,16 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
   // size classes by workspace bytes, queue sorted by (class, cost descending)
   const long long bounds[] = {6 * 1024, 14 * 1024, 28 * 1024, 55 * 1024, (long long)kSmemLimit / 4};
   const int n_bounds = 5;
+  // Worlds of one world per SM (above the fourth bound) are split once more: those whose lean
+  // placement (WsLayout::make_lean) fits two worlds per SM (228 KB per SM, 1 KB of it reserved
+  // per block) form a class of their own, ahead of the rest.
+  constexpr long long kLeanPairFloats = (228 * 1024 - 2 * 1024) / 2 / 4;
   std::vector<int> cls(W);
   for (int w = 0; w < W; ++w) {
     int c = 0;
     while (c < n_bounds && ws[w] > bounds[c]) ++c;
+    if (c > 3) ++c;
+    if (c == 3 && WsLayout::make_lean(wnb[w], wnv[w], (int)wnm[w], wna[w]).total > kLeanPairFloats) c = 4;
     cls[w] = c;
   }
   std::vector<int> order(W);
@@ -491,11 +500,16 @@ ot_status pack(const ot_tree_desc* d, Packed& P, double fp64_twig_diam = 0.0) {
       ci.max_nm = std::max(ci.max_nm, wnm[w]);
       ci.max_na = std::max(ci.max_na, wna[w]);
       ci.ws_floats = std::max(ci.ws_floats, ws[w]);
+      ci.lean_ws_floats =
+          std::max<long long>(ci.lean_ws_floats, WsLayout::make_lean(wnb[w], wnv[w], (int)wnm[w], wna[w]).total);
+      ci.lean_slot_floats = std::max<long long>(ci.lean_slot_floats, WsLayout::lean_slot_floats(wnb[w], wna[w]));
       ++j;
     }
     ci.q_end = j;
     ci.ws_floats = (ci.ws_floats + 3) / 4 * 4;
     ci.sched = default_schedule(ci.ws_floats, ci.max_nb);
+    // offered where the whole workspace in shared memory leaves room for one world per SM
+    if (ci.sched.global_workspace || (size_t)ci.ws_floats * 4 * 2 <= kSmemLimit) ci.lean_ws_floats = ci.lean_slot_floats = 0;
     P.classes.push_back(ci);
     i = j;
   }
@@ -659,8 +673,21 @@ struct StateLayout {
 // (for the plain form); global-workspace classes get four per SM, or one per SM for worlds
 // whose temporaries exceed 2 MB.
 size_t scratch_slots(const ot_model* m, const ClassInfo& ci) {
-  if (!ci.sched.global_workspace) return 1;
+  if (ci.sched.global_workspace != 1) return 1;
   return (size_t)m->n_sm * ((size_t)ci.ws_floats * 4 > (2u << 20) ? 1 : 4);
+}
+
+// Global slots of a class offered the lean placement: its groups resident at once, at most
+// kLeanSlotsPerSm per SM (class_shape caps the launch to them).
+constexpr int kLeanSlotsPerSm = 4;
+size_t lean_slots(const ot_model* m, const ClassInfo& ci) {
+  return ci.lean_slot_floats ? (size_t)kLeanSlotsPerSm * m->n_sm : 0;
+}
+
+// A class's scratch (floats): its global-workspace slots, or the lean placement's slots, which
+// never run together. Fixed when the model is uploaded, whatever the schedules become.
+size_t class_scratch_floats(const ot_model* m, const ClassInfo& ci) {
+  return std::max(scratch_slots(m, ci) * (size_t)ci.ws_floats, lean_slots(m, ci) * (size_t)ci.lean_slot_floats);
 }
 
 StateLayout state_layout(const ot_model* m) {
@@ -677,7 +704,7 @@ StateLayout state_layout(const ot_model* m) {
   // scratch: every class may run with global workspace; size for the slots its schedule can
   // have (global classes: 4 blocks of one world per SM; the plain form uses slot 0)
   size_t total_scratch_floats = 0;
-  for (const ClassInfo& ci : P.classes) total_scratch_floats += scratch_slots(m, ci) * (size_t)ci.ws_floats;
+  for (const ClassInfo& ci : P.classes) total_scratch_floats += class_scratch_floats(m, ci);
   L.scratch.push_back(c.take<float>(total_scratch_floats));
   L.total = c.off;
   return L;
@@ -687,12 +714,11 @@ size_t class_scratch_offset(const ot_model* m, int k, int* slots) {
   size_t off = 0;
   for (int i = 0; i < (int)m->P.classes.size(); ++i) {
     const ClassInfo& ci = m->P.classes[i];
-    size_t s = scratch_slots(m, ci);
     if (i == k) {
-      *slots = (int)s;
+      *slots = (int)scratch_slots(m, ci);
       return off;
     }
-    off += s * (size_t)ci.ws_floats;
+    off += class_scratch_floats(m, ci);
   }
   *slots = 0;
   return off;
@@ -734,6 +760,8 @@ StepArgs base_args(const ot_model* m, double dt) {
 struct Shape {
   size_t smem;
   int blocks;
+  int lean;  // the lean placement (schedule global_workspace 2, allowed for this launch)
+  int wpb;   // worlds per block of this launch
   size_t scratch_off;
   int stage_mask;
   long long stage_floats;
@@ -754,47 +782,59 @@ long long class_stage_floats(const ot_model* m, const ClassInfo& ci, int mask) {
   return mx;
 }
 
-ot_status class_shape(ot_model* m, int k, Shape* out) {
+// allow_lean false (a rollout that writes the adjoint's tape): a lean schedule runs with its
+// whole workspace in shared memory instead.
+ot_status class_shape(ot_model* m, int k, Shape* out, bool allow_lean = true) {
   ClassInfo& ci = m->P.classes[k];
   const ot_schedule& sc = ci.sched;
-  const size_t ws_block = sc.global_workspace ? 0 : (size_t)ci.ws_floats * 4 * sc.worlds_per_block;
+  const bool lean = sc.global_workspace == 2 && allow_lean && ci.lean_slot_floats > 0;
+  int wpb = sc.worlds_per_block;
+  if (sc.global_workspace == 2 && !lean)  // as many worlds per block as the whole workspace allows
+    wpb = (int)std::max<size_t>(1, std::min<size_t>(wpb, kSmemLimit / ((size_t)ci.ws_floats * 4)));
+  const size_t ws_block = sc.global_workspace == 1
+                              ? 0
+                              : (size_t)(lean ? ci.lean_ws_floats : ci.ws_floats) * 4 * wpb;
+  if (ws_block > kSmemLimit) return OT_ECAPACITY;
   int bps = 0;
-  OT_CUDA(kernel_attributes(sc.threads_per_world, false, sc.worlds_per_block, std::max<size_t>(ws_block, 1), &bps));
+  OT_CUDA(kernel_attributes(sc.threads_per_world, false, lean, wpb, std::max<size_t>(ws_block, 1), &bps));
   if (bps < 1) return OT_ECAPACITY;
   // staged model parts: each part, in kStageOrder, that keeps the blocks per SM of the bare
   // workspace
   int mask = 0;
   long long st = 0;
-  if (!sc.global_workspace && sc.stage != 0) {
+  if (sc.global_workspace != 1 && sc.stage != 0) {
     if (sc.stage > 0) {
       mask = sc.stage;
       st = class_stage_floats(m, ci, mask);
-      if (ws_block + (size_t)st * 4 * sc.worlds_per_block > kSmemLimit) return OT_ECAPACITY;
+      if (ws_block + (size_t)st * 4 * wpb > kSmemLimit) return OT_ECAPACITY;
     } else {
       for (int part : kStageOrder) {  // each part that still fits at the same blocks per SM
         const long long st2 = class_stage_floats(m, ci, mask | part);
-        const size_t smem2 = ws_block + (size_t)st2 * 4 * sc.worlds_per_block;
+        const size_t smem2 = ws_block + (size_t)st2 * 4 * wpb;
         if (smem2 > kSmemLimit) continue;
         int bps2 = 0;
-        OT_CUDA(kernel_attributes(sc.threads_per_world, true, sc.worlds_per_block, smem2, &bps2));
+        OT_CUDA(kernel_attributes(sc.threads_per_world, true, lean, wpb, smem2, &bps2));
         if (bps2 < bps) continue;
         mask |= part;
         st = st2;
       }
     }
   }
-  const size_t smem = ws_block + (size_t)st * 4 * sc.worlds_per_block;
-  if (mask) OT_CUDA(kernel_attributes(sc.threads_per_world, true, sc.worlds_per_block, smem, &bps));
+  const size_t smem = ws_block + (size_t)st * 4 * wpb;
+  if (mask) OT_CUDA(kernel_attributes(sc.threads_per_world, true, lean, wpb, smem, &bps));
   if (bps < 1) return OT_ECAPACITY;
   out->stage_mask = mask;
   out->stage_floats = st;
   out->bps = bps;
+  out->lean = lean ? 1 : 0;
+  out->wpb = wpb;
   int slots = 0;
   out->scratch_off = class_scratch_offset(m, k, &slots);
   int blocks = sc.blocks > 0 ? sc.blocks : bps * m->n_sm;
   const int worlds = ci.q_end - ci.q_begin;
-  blocks = std::min(blocks, (worlds + sc.worlds_per_block - 1) / sc.worlds_per_block);
-  if (sc.global_workspace) blocks = std::min(blocks, slots / std::max(1, sc.worlds_per_block));
+  blocks = std::min(blocks, (worlds + wpb - 1) / wpb);
+  if (sc.global_workspace == 1) blocks = std::min(blocks, slots / std::max(1, wpb));
+  if (lean) blocks = std::min(blocks, (int)(lean_slots(m, ci) / std::max(1, wpb)));
   out->smem = smem;
   out->blocks = blocks;
   return OT_OK;
@@ -809,14 +849,16 @@ ot_status launch_class_shaped(ot_model* m, ot_state* s, int k, StepArgs a, const
   a.q_end = ci.q_end;
   a.q_counter = s->q_counters + k;
   a.phase_clk = m->phase_clk && k < kBackPhaseRow ? m->phase_clk + (size_t)k * kPhaseSlots : nullptr;
-  a.ws_floats = ci.ws_floats;
-  a.global_ws = sc.global_workspace;
+  a.ws_floats = sh.lean ? ci.lean_ws_floats : ci.ws_floats;
+  a.global_ws = sc.global_workspace == 1;
+  a.lean = sh.lean;
+  a.lean_floats = ci.lean_slot_floats;
   a.stage_mask = sh.stage_mask;
   a.stage_floats = sh.stage_floats;
   DevState ds = s->dev;
   ds.scratch = s->dev.scratch + sh.scratch_off;
   OT_CUDA(cudaMemsetAsync(a.q_counter, 0, sizeof(int), st));
-  launch_rollout(sc.threads_per_world, sc.worlds_per_block, sh.blocks, sh.smem, st, m->dev, ds, a);
+  launch_rollout(sc.threads_per_world, sh.wpb, sh.blocks, sh.smem, st, m->dev, ds, a);
   OT_CUDA(cudaGetLastError());
   g_launches += 1;
   return OT_OK;
@@ -910,7 +952,7 @@ ot_status ot_class_info(ot_model* m, int32_t k, int64_t out[8]) {
   if (r != OT_OK) return r;
   out[0] = ci.q_end - ci.q_begin;
   out[1] = ci.max_nb;
-  out[2] = ci.ws_floats * 4;
+  out[2] = (sh.lean ? ci.lean_ws_floats : ci.ws_floats) * 4;
   out[3] = sh.stage_mask;
   out[4] = sh.stage_floats * 4;
   out[5] = (int64_t)sh.smem;
@@ -1253,7 +1295,7 @@ ot_status ot_rollout(ot_model* m, ot_state* s, int32_t n_steps, int32_t step0, d
   cudaStream_t cs = m->capture_stream;
   std::vector<Shape> shapes(m->P.classes.size());
   for (int k = 0; k < (int)m->P.classes.size(); ++k) {
-    ot_status r = class_shape(m, k, &shapes[k]);
+    ot_status r = class_shape(m, k, &shapes[k], a.tape == nullptr);  // no lean placement with a tape
     if (r != OT_OK) return r;
   }
   const int nk = (int)m->P.classes.size();
@@ -1320,7 +1362,7 @@ ot_status ot_rollout_plain(ot_model* m, ot_state* s, int32_t n_steps, int32_t st
   for (const ClassInfo& ci : P.classes)
     if ((size_t)ci.ws_floats * 4 <= kSmemLimit) smem_max = std::max(smem_max, (size_t)ci.ws_floats * 4);
   int bps = 0;
-  OT_CUDA(kernel_attributes(64, false, 1, smem_max, &bps));
+  OT_CUDA(kernel_attributes(64, false, false, 1, smem_max, &bps));
   for (int t = 0; t < n_steps; ++t) {
     a.step0 = step0 + t;
     for (int w = 0; w < P.W; ++w) {
@@ -1357,10 +1399,17 @@ ot_status ot_set_schedule(ot_model* m, int32_t k, const ot_schedule* sc) {
   if (t > 32 && sc->worlds_per_block > 15) return OT_EINVAL;
   if (t == 32 && sc->worlds_per_block > 16) return OT_EINVAL;
   if (sc->blocks < 0) return OT_EINVAL;
-  // a class's global-workspace setting is fixed at upload (it sizes the state's scratch)
-  if (sc->global_workspace != ci.sched.global_workspace) return OT_EINVAL;
-  if (!sc->global_workspace && (size_t)ci.ws_floats * 4 * sc->worlds_per_block > kSmemLimit) return OT_EINVAL;
-  if (sc->global_workspace && (size_t)sc->worlds_per_block * std::max(sc->blocks, 1) > scratch_slots(m, ci))
+  // a class's global-workspace setting (1) is fixed at upload (it sizes the state's scratch);
+  // a class in shared memory may take the lean placement (2) where it is offered
+  const int gw = sc->global_workspace;
+  if (gw < 0 || gw > 2) return OT_EINVAL;
+  if ((gw == 1) != (ci.sched.global_workspace == 1)) return OT_EINVAL;
+  if (gw == 2 && (!ci.lean_slot_floats || t < 128)) return OT_EINVAL;  // instantiated for 128-512 threads
+  if (gw == 0 && (size_t)ci.ws_floats * 4 * sc->worlds_per_block > kSmemLimit) return OT_EINVAL;
+  if (gw == 2 && ((size_t)ci.lean_ws_floats * 4 * sc->worlds_per_block > kSmemLimit ||
+                  (size_t)sc->worlds_per_block * std::max(sc->blocks, 1) > lean_slots(m, ci)))
+    return OT_EINVAL;
+  if (gw == 1 && (size_t)sc->worlds_per_block * std::max(sc->blocks, 1) > scratch_slots(m, ci))
     return OT_EINVAL;
   if (sc->stage < -1 || sc->stage > 127) return OT_EINVAL;
   m->P.classes[k].sched = *sc;
@@ -1396,16 +1445,24 @@ ot_status ot_autotune(ot_model* m, ot_state* s, int32_t n_steps, double dt, void
     ClassInfo& ci = m->P.classes[k];
     const ot_schedule keep = ci.sched;
     std::vector<ot_schedule> cands;
-    for (int t : {32, 64, 128, 256, 512})
-      for (int g : {1, 2, 3, 4, 6, 8, 12, 16})
-        for (int stage : {0, -1}) {  // model records read from global memory, or staged
-          ot_schedule c{t, g, 0, keep.global_workspace, stage};
-          if (t * g > 512) continue;
-          if (t > 32 && g > 15) continue;
-          if (!c.global_workspace && (size_t)ci.ws_floats * 4 * g > kSmemLimit) continue;
-          if (c.global_workspace && (g > 1 || stage != 0)) continue;
-          cands.push_back(c);
-        }
+    // placements: the class's own (all in global memory, or all in shared memory), and the lean
+    // one where it is offered
+    const int base_gw = keep.global_workspace == 1 ? 1 : 0;
+    for (int gw : {base_gw, 2}) {
+      if (gw == 2 && (base_gw == 1 || !ci.lean_slot_floats)) continue;
+      const long long wsf = gw == 2 ? ci.lean_ws_floats : ci.ws_floats;
+      for (int t : {32, 64, 128, 256, 512})
+        for (int g : {1, 2, 3, 4, 6, 8, 12, 16})
+          for (int stage : {0, -1}) {  // model records read from global memory, or staged
+            ot_schedule c{t, g, 0, gw, stage};
+            if (t * g > 512) continue;
+            if (t > 32 && g > 15) continue;
+            if (gw != 1 && (size_t)wsf * 4 * g > kSmemLimit) continue;
+            if (gw == 1 && (g > 1 || stage != 0)) continue;
+            if (gw == 2 && ((size_t)g > lean_slots(m, ci) || t < 128)) continue;
+            cands.push_back(c);
+          }
+    }
     std::vector<std::pair<float, int>> timed;
     for (int i = 0; i < (int)cands.size(); ++i) {
       const ot_schedule& c = cands[i];
@@ -1762,7 +1819,7 @@ ot_status static_step_plan(ot_model* m, const ot_state* s, const ot_force_schedu
     const long long slots = (long long)(scratch_floats / (size_t)ci.ws_floats);
     const int wpb = (int)std::min<long long>(sc.worlds_per_block, slots);
     int bps = 0;
-    OT_CUDA(kernel_attributes(sc.threads_per_world, false, wpb, 1, &bps));
+    OT_CUDA(kernel_attributes(sc.threads_per_world, false, false, wpb, 1, &bps));
     if (bps < 1) return OT_ECAPACITY;
     const int worlds = ci.q_end - ci.q_begin;
     long long blocks = std::min<long long>((long long)bps * m->n_sm, (worlds + wpb - 1) / wpb);

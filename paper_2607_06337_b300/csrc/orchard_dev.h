@@ -121,6 +121,8 @@ struct StepArgs {
                                   // launch's kPhaseSlots accumulators, or null
   int stage_mask;           // StageLayout parts copied into shared memory per world (0: none)
   long long stage_floats;   // shared-memory floats per group for them (the class's largest world)
+  int lean;                 // 1: the lean placement (WsLayout::make_lean; never with a tape)
+  long long lean_floats;    // floats per group of its global slots in DevState::scratch
 };
 
 // Parts of a world's model that a rollout can stage in shared memory (after the workspace),
@@ -245,6 +247,30 @@ struct WsLayout {
     L.IC = L.V = L.R = L.A = L.F = -1;
     return L;
   }
+  // The lean placement of the step's temporaries: the regions the sweeps, the mass matrix and
+  // the factorisation use (X, E, IC with V, r, and the shared region) in shared memory; the
+  // state stays in the world's state arrays in global memory, and the apple records (AT) and
+  // the snapped flags (SN) go to the group's slot of global memory (lean_slot_floats floats:
+  // AT at 0, SN at lean_sn). Offsets AT, SN and S are -1. No tape is written in this placement.
+  __host__ __device__ static WsLayout make_lean(int nb, int nv, int nm, int na) {
+    WsLayout L;
+    L.X = 0;
+    L.E = L.X + r4(3 * nb);
+    L.IC = L.E + r4(3 * nv);
+    L.r = L.IC + r4(10 * nb);
+    L.V = L.IC;
+    L.AT = L.SN = L.S = -1;
+    const int u = L.r + r4(nv);
+    L.R = u;
+    L.A = L.R + r4(9 * nb);
+    L.F = L.A + r4(6 * nb);
+    L.M = u;
+    const int end_sweeps = L.F + r4(6 * nb), end_m = L.M + r4(nm);
+    L.total = end_sweeps > end_m ? end_sweeps : end_m;
+    return L;
+  }
+  __host__ __device__ static int lean_sn(int na) { return r4(10 * na); }
+  __host__ __device__ static int lean_slot_floats(int nb, int na) { return r4(10 * na) + r4(nb); }
   __host__ __device__ static WsLayout make(int nb, int nv, int nm, int na) {
     WsLayout L;
     L.X = 0;                         // joint origins
@@ -331,7 +357,9 @@ long long backward_seg_floats(int nb, int nv, int nm, int na, int ckpt_every);
 
 void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes, cudaStream_t s,
                     const DevModel& m, const DevState& st, const StepArgs& a);
-// Occupancy of the rollout kernel for tpw threads per world, the staged instantiation or not.
-cudaError_t kernel_attributes(int tpw, bool staged, int groups_per_block, size_t smem_bytes, int* blocks_per_sm);
+// Occupancy of the rollout kernel for tpw threads per world, the staged instantiation or not,
+// the lean one (128-512 threads) or not.
+cudaError_t kernel_attributes(int tpw, bool staged, bool lean, int groups_per_block, size_t smem_bytes,
+                              int* blocks_per_sm);
 
 }  // namespace orchard

@@ -395,7 +395,8 @@ HD UpdRec upd_rec(const DevModel& m, const WorldView& v, int b) {
 }
 // Phase 1a for one body (root to leaf, level by level): kinematics, velocities, bias
 // acceleration, snapped flag.
-HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, const KinRec& rec, float* kin) {
+HD void forward_kin(const WState& s, const WsLayout& L, float* ws, float* sn, int b, f3 g, const KinRec& rec,
+                    float* kin) {
   const int4 bi = rec.bi;
   const int p = bi.x;
   const int dof0 = bi.y & 0x0fffffff, nd = (unsigned)bi.y >> 28;
@@ -438,8 +439,8 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
   stm(ws + L.R + 9 * b, R);
   st3(ws + L.X + 3 * b, xb);
   // on a snapped sub-tree (this joint or one above broken): applied forces disabled (App. B)
-  const bool snapped = s.broken[b] || (p >= 0 && ws[L.SN + p] != 0.f);
-  ws[L.SN + b] = snapped ? 1.f : 0.f;
+  const bool snapped = s.broken[b] || (p >= 0 && sn[p] != 0.f);
+  sn[b] = snapped ? 1.f : 0.f;
   st3(ws + L.V + kVel * b, w); st3(ws + L.V + kVel * b + 3, vin);
   st3(ws + L.A + 6 * b, al); st3(ws + L.A + 6 * b + 3, aa);
   if (kin) {  // the step's record in the adjoint's tape (WsLayout::kin_offset)
@@ -457,14 +458,14 @@ HD void forward_kin(const WState& s, const WsLayout& L, float* ws, int b, f3 g, 
 // force less the body damping, apple loads.
 template <bool ST = false>
 HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
-                      float* ws, int b, int t_abs, f3 g) {
+                      float* ws, const float* sn, float* atb, int b, int t_abs, f3 g) {
   const int4 bi = rec_bi<ST>(m, v, b);
   const float4 P0 = rec_p0<ST>(m, v, b), P2 = rec_p2<ST>(m, v, b), P3 = rec_p3<ST>(m, v, b);
   const m3 R = ldm(ws + L.R + 9 * b);
   const f3 xb = ld3(ws + L.X + 3 * b);
   const f3 w = ld3(ws + L.V + kVel * b), vin = ld3(ws + L.V + kVel * b + 3);
   const f3 al = ld3(ws + L.A + 6 * b), aa = ld3(ws + L.A + 6 * b + 3);
-  const bool snapped = ws[L.SN + b] != 0.f;
+  const bool snapped = sn[b] != 0.f;
 
   // spatial inertia of the body about x_b
   const float mb = P0.w;
@@ -546,7 +547,7 @@ HD void forward_force(const DevModel& m, const WState& s, const StepArgs& a, con
     n = n - cross(rh, fapp);
     f = f - fapp;
     if (kappa > 0.f) add_point(I, dt * dt * kappa, rh);
-    float* at = ws + L.AT + 10 * ai;
+    float* at = atb + 10 * ai;
     st3(at, avec);
     at[3] = beta; at[4] = T; at[5] = P;
     st3(at + 6, rh);
@@ -748,11 +749,11 @@ HD void update_body(const DevModel& m, const WState& s, const StepArgs& a, const
 // with its body's end-of-step velocity, and the detach tests.
 template <bool ST = false>
 HD void update_apple(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
-                     float* ws, int ai, int t_abs, int* frozen) {
+                     float* ws, const float* atb, int ai, int t_abs, int* frozen) {
   const int b = rec_abody<ST>(m, v, ai);
   const f3 w = ld3(ws + L.V + kVel * b), vl = ld3(ws + L.V + kVel * b + 3);
   const float dt = a.dt;
-  const float* at = ws + L.AT + 10 * ai;
+  const float* at = atb + 10 * ai;
   const bool det = s.detached[ai] != 0;
   const f3 rh = ld3(at + 6);
   const f3 vh = det ? mk(0, 0, 0) : vl + cross(w, rh);
@@ -1234,16 +1235,20 @@ struct PhaseClock {
 template <int TPW, bool ST = false>
 HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const WorldView& v, const WsLayout& L,
                    float* ws, const Group<TPW>& g, int t_abs, f3 gv, int tip_slot, PhaseClock* pc = nullptr,
-                   float* kin = nullptr) {
+                   float* kin = nullptr, float* lslot = nullptr) {
+  // the snapped flags and the apple records: in the workspace, or (lean placement, lslot) in
+  // the group's slot of global memory
+  float* sn = lslot ? lslot + WsLayout::lean_sn(v.na) : ws + L.SN;
   // 1. root-to-leaf: kinematics, velocities, own forces, apple loads (and, on a taped step, the
   // kinematics into the step's record at kin)
   for (int l = 0; l < v.nL; ++l) {
     const int lo = v.lv[l], hi = v.lv[l + 1];
-    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, b, gv, kin_rec<ST>(m, v, b), kin);
+    for (int b = lo + g.lane; b < hi; b += TPW) forward_kin(s, L, ws, sn, b, gv, kin_rec<ST>(m, v, b), kin);
     g.sync();
   }
   if (pc) pc->mark(0);
-  for (int b = g.lane; b < v.nb; b += TPW) forward_force<ST>(m, s, a, v, L, ws, b, t_abs, gv);
+  for (int b = g.lane; b < v.nb; b += TPW)
+    forward_force<ST>(m, s, a, v, L, ws, sn, lslot ? lslot : ws + L.AT, b, t_abs, gv);
   g.sync();
   if (pc) pc->mark(1);
   if (tip_slot >= 0) record_tips(m, a, v, L, ws, tip_slot, g);
@@ -1270,7 +1275,8 @@ HD void step_world(const DevModel& m, const WState& s, const StepArgs& a, const 
   }
   if (pc) pc->mark(6);
   if (v.na > 0) {
-    for (int ai = g.lane; ai < v.na; ai += TPW) update_apple<ST>(m, s, a, v, L, ws, ai, t_abs, g.flag);
+    for (int ai = g.lane; ai < v.na; ai += TPW)
+      update_apple<ST>(m, s, a, v, L, ws, lslot ? lslot : ws + L.AT, ai, t_abs, g.flag);
     g.sync();
   }
   if (pc) pc->mark(7);
@@ -1441,16 +1447,20 @@ HD __noinline__ float* tape_kin(float* tape, const long long* tape_off, int n_st
 }
 
 // All steps of one world: its state is staged in the workspace for the whole rollout.
+// lslot: the group's global slot in the lean placement (a.lean), else null.
 template <int TPW, bool ST = false>
-HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws,
+HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws, float* lslot,
                   const Group<TPW>& g) {
   WorldView v = world_view(m, w);
-  const WsLayout L = WsLayout::make(v.nb, v.nv, v.nm, v.na);
+  const WsLayout L = lslot ? WsLayout::make_lean(v.nb, v.nv, v.nm, v.na) : WsLayout::make(v.nb, v.nv, v.nm, v.na);
   const WState sg = world_state(S, v, w);
-  const WState s = staged_view(ws + L.S, v.nb, v.nv, v.na);
+  // the state staged in the workspace for the whole rollout, or (lean) read and written where
+  // it lives
+  const WState s = lslot ? sg : staged_view(ws + L.S, v.nb, v.nv, v.na);
   // the model records this class stages sit after the workspace, for all the world's steps
   if (ST) stage_world<TPW>(m, v, a.stage_mask, ws + a.ws_floats, g);  // launched with a shared workspace
-  copy_state<TPW>(s, sg, v, g);  // ends on a group barrier
+  if (!lslot) copy_state<TPW>(s, sg, v, g);  // ends on a group barrier
+  else g.sync();
   const float4 g4 = m.gravity[w];
   const f3 gv = mk(g4.x, g4.y, g4.z);
   if (g.lane == 0) *g.flag = (int)(*s.status & 1u);
@@ -1467,11 +1477,12 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
     if (a.ckpt && a.ckpt_every > 0 && t % a.ckpt_every == 0) write_ckpt(s, a, v, t / a.ckpt_every, g);
     if (*g.flag) break;  // frozen after a non-finite state (uniform across the group)
     // the step's first write to the staged state comes after several group barriers
+    // (the host never pairs a tape with the lean placement, whose workspace holds no state)
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, false, v.nb, v.nv, v.nm, v.na, ws, g);
     if (pcp) pcp->mark(8);
     float* kin = a.tape ? tape_kin(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, v.nb, v.nv, v.nm, v.na)
                         : nullptr;
-    step_world<TPW, ST>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1, pcp, kin);
+    step_world<TPW, ST>(m, s, a, v, L, ws, g, a.step0 + t, gv, (a.tips && t > 0) ? t - 1 : -1, pcp, kin, lslot);
     if (a.tape) tape_write<TPW>(a.tape, m.tape_off, a.n_steps, a.tape_steps, w, t, true, v.nb, v.nv, v.nm, v.na, ws, g);
     if (pcp) pcp->mark(8);
     ++steps_run;
@@ -1493,7 +1504,8 @@ HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w
     record_tips(m, a, v, L, ws, a.n_steps - 1, g);
     g.sync();
   }
-  copy_state<TPW>(sg, s, v, g);
+  if (!lslot) copy_state<TPW>(sg, s, v, g);
+  else g.sync();
 }
 
 }  // namespace

@@ -8,7 +8,8 @@ namespace {
 
 // ST: the instantiation that reads the model records a class stages in shared memory (the
 // other one reads them from the model in global memory and holds no pointers for them).
-template <int TPW, bool ST>
+// LN: the lean placement (WsLayout::make_lean), instantiated for 128-512 threads per world.
+template <int TPW, bool ST, bool LN>
 __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, StepArgs a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int frozen[16];
@@ -19,8 +20,10 @@ __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, St
   const int groups = blockDim.x / TPW;
   float* ws = a.global_ws ? s.scratch + (long long)(blockIdx.x * groups + g.id) * a.ws_floats
                           : smem + (long long)g.id * (a.ws_floats + a.stage_floats);
+  // the lean placement's global slot of this group (apple records, snapped flags)
+  float* lslot = LN ? s.scratch + (long long)(blockIdx.x * groups + g.id) * a.lean_floats : nullptr;
   if (a.single_world >= 0) {
-    run_world<TPW, ST>(m, s, a, a.single_world, ws, g);
+    run_world<TPW, ST>(m, s, a, a.single_world, ws, lslot, g);
     return;
   }
   __shared__ int next[16];
@@ -35,7 +38,7 @@ __global__ void __launch_bounds__(512) rollout_kernel(DevModel m, DevState s, St
       qi = blockIdx.x * groups + g.id;
     }
     if (qi >= a.q_end - a.q_begin) break;
-    run_world<TPW, ST>(m, s, a, m.queue[a.q_begin + qi], ws, g);
+    run_world<TPW, ST>(m, s, a, m.queue[a.q_begin + qi], ws, lslot, g);
     if (!a.q_counter) break;
   }
 }
@@ -56,27 +59,27 @@ unsigned long long* phase_clock_buffer() {
 #endif
 }
 
-template <bool ST>
+template <bool ST, bool LN>
 const void* rollout_fn(int tpw) {
   switch (tpw) {
-    case 32: return (const void*)rollout_kernel<32, ST>;
-    case 64: return (const void*)rollout_kernel<64, ST>;
-    case 128: return (const void*)rollout_kernel<128, ST>;
-    case 256: return (const void*)rollout_kernel<256, ST>;
-    case 512: return (const void*)rollout_kernel<512, ST>;
+    case 32: return LN ? nullptr : (const void*)rollout_kernel<32, ST, false>;
+    case 64: return LN ? nullptr : (const void*)rollout_kernel<64, ST, false>;
+    case 128: return (const void*)rollout_kernel<128, ST, LN>;
+    case 256: return (const void*)rollout_kernel<256, ST, LN>;
+    case 512: return (const void*)rollout_kernel<512, ST, LN>;
     default: return nullptr;
   }
 }
 
-template <bool ST>
+template <bool ST, bool LN>
 void launch_rollout_t(int tpw, int threads, int blocks, size_t smem_bytes, cudaStream_t st, const DevModel& m,
                       const DevState& s, const StepArgs& a) {
   switch (tpw) {
-    case 32: rollout_kernel<32, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 64: rollout_kernel<64, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 128: rollout_kernel<128, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 256: rollout_kernel<256, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
-    case 512: rollout_kernel<512, ST><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 32: if (!LN) rollout_kernel<32, ST, false><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 64: if (!LN) rollout_kernel<64, ST, false><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 128: rollout_kernel<128, ST, LN><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 256: rollout_kernel<256, ST, LN><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
+    case 512: rollout_kernel<512, ST, LN><<<blocks, threads, smem_bytes, st>>>(m, s, a); break;
     default: break;
   }
 }
@@ -85,12 +88,20 @@ void launch_rollout(int tpw, int groups_per_block, int blocks, size_t smem_bytes
                     const DevModel& m, const DevState& s, const StepArgs& a) {
   const int threads = tpw * groups_per_block;
   // the staged instantiation keeps the world's records and their table after its workspace
-  if (a.stage_mask && !a.global_ws) launch_rollout_t<true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
-  else launch_rollout_t<false>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+  const bool staged = a.stage_mask && !a.global_ws;
+  if (a.lean) {
+    if (staged) launch_rollout_t<true, true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+    else launch_rollout_t<false, true>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+  } else {
+    if (staged) launch_rollout_t<true, false>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+    else launch_rollout_t<false, false>(tpw, threads, blocks, smem_bytes, st, m, s, a);
+  }
 }
 
-cudaError_t kernel_attributes(int tpw, bool staged, int groups_per_block, size_t smem_bytes, int* blocks_per_sm) {
-  const void* fn = staged ? rollout_fn<true>(tpw) : rollout_fn<false>(tpw);
+cudaError_t kernel_attributes(int tpw, bool staged, bool lean, int groups_per_block, size_t smem_bytes,
+                              int* blocks_per_sm) {
+  const void* fn = lean ? (staged ? rollout_fn<true, true>(tpw) : rollout_fn<false, true>(tpw))
+                        : (staged ? rollout_fn<true, false>(tpw) : rollout_fn<false, false>(tpw));
   if (!fn) return cudaErrorInvalidValue;
   if (smem_bytes > kSmemLimitBytes) return cudaErrorInvalidValue;
   // the attribute belongs to the instantiation, shared by every class using it: always the limit

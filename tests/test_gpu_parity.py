@@ -266,6 +266,50 @@ def test_staged_model_records_give_the_same_states(workload, worlds, stage):
         assert out[0]["broken"].sum() + out[0]["detached"].sum() > 0
 
 
+def test_lean_placement_gives_the_same_states():
+    """The lean placement (schedule global_workspace 2: the state, the apple records and the
+    snapped flags in global memory, the rest of the workspace in shared memory) computes what the
+    whole-workspace placement does: the six largest batch trees and two small ones, with pulls,
+    breaks and detaches, bit-identical states and tips after 300 steps with checkpoints written
+    on the way; and a rollout that writes the adjoint's tape under a lean schedule (run in the
+    whole-workspace placement) gives the same states again."""
+    torch = _torch()
+    from paper_2607_06337_b300 import orchard as B
+    full = I.make_forest(I.BATCH, processes=8)
+    order = np.argsort(np.diff(full.body_off), kind="stable")
+    f = full.subset(sorted(order[-6:].tolist() + order[:2].tolist()))
+    fl = I.Flags()
+    n = 300
+    out = []
+    for lean, ce in ((False, 50), (True, 50), (True, 0)):
+        sim = B.Simulator(f, fl)
+        taken = 0
+        for k, sc in enumerate(sim.schedules()):
+            if lean and not sc.global_workspace:
+                try:
+                    B.set_schedule(sim.model, k, B.Schedule(256, 1, 0, 2, 0))
+                    taken += 1
+                except B.OrchardError:
+                    pass  # a class that fits two worlds per SM is not offered the lean placement
+        if lean:
+            assert taken >= 1
+            assert any(ci["workspace_bytes"] < 140 * 1024 for ci in sim.class_infos() if ci["max_bodies"] > 550)
+        tips, buf, rec = sim.record_buffers(n, ce)
+        sim.reset()
+        sim.rollout(n, record=rec)
+        torch.cuda.synchronize()
+        st = _gpu_state(sim)
+        st["tips"] = tips.cpu().numpy()
+        st["ckpt"] = buf.cpu().numpy() if ce else None
+        out.append(st)
+        sim.close()
+    for o in out[1:]:
+        for key in ("q", "qd", "ax", "broken", "break_step", "detached", "detach_step", "status", "tips"):
+            np.testing.assert_array_equal(o[key], out[0][key], err_msg=key)
+    np.testing.assert_array_equal(out[1]["ckpt"], out[0]["ckpt"], err_msg="checkpoints")
+    assert out[0]["broken"].sum() + out[0]["detached"].sum() > 0
+
+
 def test_autotune_leaves_the_state_as_it_found_it():
     """ot_autotune times every launch from a device copy of the state it was given and restores
     the state at the end: uneven batch trees advanced 50 steps (pulls, a break or detach on the
