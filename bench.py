@@ -587,10 +587,12 @@ def world_sweep(args, dev):
         return a.elapsed_time(b)
 
     out, headline, acc = [], None, None
-    # one tree size: the schedules tuned on the headline batch (16384 worlds) serve every batch
-    # with the same size classes
-    tuner = B.Simulator(big.subset(range(16384)), fl, device=dev)
-    tuner.autotune(n_steps=10)
+    # one tree size: the schedules tuned on 4096 of the trees, TUNE_STEPS steps per candidate,
+    # serve every batch with the same size classes (tuned on 10 steps, the pick between three
+    # worlds per block and three blocks per SM of one world changed from run to run; the first
+    # is 5% slower over the 1000-step headline)
+    tuner = B.Simulator(big.subset(range(4096)), fl, device=dev)
+    tuner.autotune(n_steps=TUNE_STEPS)
     sched = tuner.schedules()
     tuner.close()
     del tuner
