@@ -1446,8 +1446,8 @@ HD __noinline__ float* tape_kin(float* tape, const long long* tape_off, int n_st
          WsLayout::kin_offset(nb, nv, nm, na);
 }
 
-// All steps of one world: its state is staged in the workspace for the whole rollout.
-// lslot: the group's global slot in the lean placement (a.lean), else null.
+// All steps of one world: its state is staged in the workspace for the whole rollout, or with
+// the lean placement (lslot: the group's global slot, else null) kept in the state arrays.
 template <int TPW, bool ST = false>
 HD void run_world(const DevModel& m, const DevState& S, const StepArgs& a, int w, float* ws, float* lslot,
                   const Group<TPW>& g) {
