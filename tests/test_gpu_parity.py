@@ -294,6 +294,13 @@ def test_lean_placement_gives_the_same_states():
         if lean:
             assert taken >= 1
             assert any(ci["workspace_bytes"] < 140 * 1024 for ci in sim.class_infos() if ci["max_bodies"] > 550)
+            for k, sc in enumerate(sim.schedules()):
+                if sc.global_workspace == 2:  # instantiated for 128-512 threads per world only
+                    with pytest.raises(B.OrchardError):
+                        B.set_schedule(sim.model, k, B.Schedule(64, 1, 0, 2, 0))
+                elif not sc.global_workspace:  # classes of several worlds per SM: not offered
+                    with pytest.raises(B.OrchardError):
+                        B.set_schedule(sim.model, k, B.Schedule(256, 1, 0, 2, 0))
         tips, buf, rec = sim.record_buffers(n, ce)
         sim.reset()
         sim.rollout(n, record=rec)
