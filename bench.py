@@ -72,6 +72,10 @@ def parse():
     p.add_argument("--stage", default="auto", choices=["auto", "off", "on"],
                    help="off: after the autotune, run every class with no model records staged in shared "
                         "memory; on: with every part that keeps its blocks per SM staged (A/B of the staging)")
+    p.add_argument("--lean", default="auto", choices=["auto", "off", "on"],
+                   help="off: after the autotune, run a lean class with its whole workspace in shared memory "
+                        "(512 threads per world, automatic staging); on: every class offered the lean placement "
+                        "in it, at 256 threads per world (A/B, and the profile of that instantiation)")
     p.add_argument("--phase-clocks", action="store_true",
                    help="profiling: run the workload once on the phase-clock build and print the cycles per "
                         "world-step of each phase of the step, per size class")
@@ -638,6 +642,24 @@ def world_sweep(args, dev):
             "host_generation_s": gen_s}, acc
 
 
+def set_lean(sim, on):
+    """Every class offered the lean placement takes it (on: 256 threads, one world per block,
+    nothing staged), or every class in it returns to its whole workspace in shared memory at one
+    512-thread world per block with automatic staging (the autotuner's pick for the 553-600-body
+    batch4096 trees before the lean placement existed)."""
+    from paper_2607_06337_b300 import orchard as B
+    for k, sc in enumerate(sim.schedules()):
+        if sc.global_workspace == 1:
+            continue
+        if on:
+            try:
+                B.set_schedule(sim.model, k, B.Schedule(256, 1, 0, 2, 0))
+            except B.OrchardError:
+                pass  # not offered to this class
+        elif sc.global_workspace == 2:
+            B.set_schedule(sim.model, k, B.Schedule(512, 1, 0, 0, -1))
+
+
 def set_staging(sim, stage):
     """Every class keeps its schedule but stages `stage` (0: no model records in shared memory;
     -1: each part that keeps the class's blocks per SM)."""
@@ -667,6 +689,8 @@ def phase_clock_run(args):
         sim.autotune(n_steps=TUNE_STEPS)
     if args.stage != "auto":
         set_staging(sim, 0 if args.stage == "off" else -1)
+    if args.lean != "auto":
+        set_lean(sim, args.lean == "on")
     sim.reset()
     sim.rollout(S)
     torch.cuda.synchronize()
@@ -770,6 +794,8 @@ def run_ours(args):
         sim.autotune(n_steps=TUNE_STEPS)
     if args.stage != "auto":
         set_staging(sim, 0 if args.stage == "off" else -1)
+    if args.lean != "auto":
+        set_lean(sim, args.lean == "on")
     scheds = sim.class_infos()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
