@@ -150,7 +150,8 @@ typedef struct ot_schedule {
 } ot_schedule;
 
 /* What a size class resolves to under its current schedule: out[0] worlds, [1] largest world's
- * bodies, [2] per-world step temporaries (bytes), [3] the staged parts (mask), [4] their bytes
+ * bodies, [2] per-world step temporaries in the placement used (bytes; with the lean placement
+ * its shared-memory part), [3] the staged parts (mask), [4] their bytes
  * per world, [5] dynamic shared memory per block (bytes), [6] resident blocks per SM, [7] the
  * persistent grid's blocks. Sets the kernel's attributes (not inside a stream capture). */
 ot_status ot_class_info(ot_model* model, int32_t size_class, int64_t out[8]);
